@@ -1,0 +1,234 @@
+"""FP64 CPU oracle for multi-volume TSDF integration and raycasting.
+
+TEST INFRASTRUCTURE ONLY: the parity reference the CUDA library is checked
+against.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` import this package; the library never does, and this package
+imports nothing from the library.  The arithmetic lives in
+``mvtsdf_oracle.c`` (plain C, double precision, one voxel / one ray at a time,
+following the paper's steps); this module only marshals numpy arrays.
+
+Paper: Salvato, Finman, Leonard, "Multi-Volume High Resolution RGB-D Mapping
+with Dynamic Volume Placement", arXiv 1511.07106 -- Sec. Volumetric
+Integration, Sec. Raycasting, Algorithm 1, Sec. Comparison to KinectFusion.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "mvtsdf_oracle.c"), os.path.join(_HERE, "mvtsdf_oracle_grad.c")]
+_LIB = os.path.join(_HERE, "liboracle_mvtsdf.so")
+
+# per-voxel integration flags (decision within a margin of its threshold)
+IF_Z, IF_PIX, IF_GATE, IF_BAND = 1, 2, 4, 8
+# per-pixel raycast flags
+RF_SIGN, RF_CELL, RF_RANGE, RF_FACE, RF_TIE, RF_GRAD = 1, 2, 4, 8, 16, 32
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP) into an in-tree shared object."""
+    srcs = [s for s in _SRC if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fopenmp",
+                               "-o", tmp, *srcs, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Volume(C.Structure):
+    _fields_ = [("h", C.c_int32 * 3), ("r", C.c_int32 * 3), ("s", C.c_double),
+                ("F", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+                ("rgba", C.POINTER(C.c_uint8))]
+
+
+class _Intr(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("trunc_vox", C.c_double), ("w_max", C.c_double), ("color_w_max", C.c_int32),
+                ("z_min", C.c_double), ("z_max", C.c_double), ("step_vox", C.c_double),
+                ("eps_px", C.c_double), ("eps_sdf", C.c_double), ("eps_z", C.c_double),
+                ("eps_f", C.c_double), ("eps_q", C.c_double), ("eps_tau", C.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp, u8p, i64p, i32p = (C.POINTER(C.c_double), C.POINTER(C.c_uint8),
+                               C.POINTER(C.c_int64), C.POINTER(C.c_int32))
+        fp = C.POINTER(C.c_float)
+        _lib.orc_integrate.argtypes = [C.POINTER(_Volume), fp, u8p, C.POINTER(_Intr), dp,
+                                       C.POINTER(_Cfg), u8p, i64p]
+        _lib.orc_integrate_voxels.argtypes = [C.POINTER(_Volume), i64p, C.c_int64, fp, u8p,
+                                              C.POINTER(_Intr), dp, C.POINTER(_Cfg), u8p, i64p]
+        _lib.orc_raycast.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr), dp,
+                                     C.POINTER(_Cfg), dp, dp, u8p, dp, i32p, u8p]
+        _lib.orc_sample.argtypes = [C.POINTER(_Volume), dp, i32p]
+        _lib.orc_sample.restype = C.c_double
+        if hasattr(_lib, "orc_raycast_grad"):
+            _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
+                                              dp, C.POINTER(_Cfg), dp, dp, dp, dp, dp, dp,
+                                              C.POINTER(C.POINTER(C.c_double)), u8p]
+    return _lib
+
+
+@dataclass
+class Config:
+    """Method parameters (the paper leaves all of them unstated)."""
+    trunc_vox: float = 4.0
+    w_max: float = 128.0
+    color_w_max: int = 255
+    z_min: float = 0.0
+    z_max: float = float("inf")
+    step_vox: float = 1.0
+    eps_px: float = 1e-3
+    eps_sdf: float = 1e-3
+    eps_z: float = 1e-5
+    eps_f: float = 1e-4
+    eps_q: float = 1e-3
+    eps_tau: float = 1e-3
+
+    def _c(self) -> _Cfg:
+        return _Cfg(self.trunc_vox, self.w_max, int(self.color_w_max), self.z_min, self.z_max,
+                    self.step_vox, self.eps_px, self.eps_sdf, self.eps_z, self.eps_f, self.eps_q,
+                    self.eps_tau)
+
+
+@dataclass
+class Volume:
+    """One TSDF (sub)volume: lattice offset h (voxels), dims r, pitch s.
+
+    Arrays are indexed [z, y, x].  F is the TSDF in units of the truncation
+    distance, W the weight, rgba the colour with the colour weight in A."""
+    h: tuple
+    r: tuple
+    s: float
+    F: np.ndarray = field(default=None)
+    W: np.ndarray = field(default=None)
+    rgba: np.ndarray = field(default=None)
+
+    def __post_init__(self):
+        rx, ry, rz = (int(v) for v in self.r)
+        if self.F is None:
+            self.F = np.zeros((rz, ry, rx), np.float64)
+        if self.W is None:
+            self.W = np.zeros((rz, ry, rx), np.float64)
+        if self.rgba is None:
+            self.rgba = np.zeros((rz, ry, rx, 4), np.uint8)
+        self.F = np.ascontiguousarray(self.F, np.float64)
+        self.W = np.ascontiguousarray(self.W, np.float64)
+        self.rgba = np.ascontiguousarray(self.rgba, np.uint8)
+        assert self.F.shape == (rz, ry, rx) and self.W.shape == (rz, ry, rx)
+        assert self.rgba.shape == (rz, ry, rx, 4)
+
+    def _c(self) -> _Volume:
+        v = _Volume()
+        v.h[:] = [int(a) for a in self.h]
+        v.r[:] = [int(a) for a in self.r]
+        v.s = float(self.s)
+        v.F = self.F.ctypes.data_as(C.POINTER(C.c_double))
+        v.W = self.W.ctypes.data_as(C.POINTER(C.c_double))
+        v.rgba = self.rgba.ctypes.data_as(C.POINTER(C.c_uint8))
+        return v
+
+    def copy(self) -> "Volume":
+        return Volume(tuple(self.h), tuple(self.r), self.s, self.F.copy(), self.W.copy(),
+                      self.rgba.copy())
+
+
+def _intr(cam) -> _Intr:
+    return _Intr(float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy), int(cam.width),
+                 int(cam.height))
+
+
+def _pose(T) -> np.ndarray:
+    T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(4, 4))
+    return T
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def integrate(vol: Volume, depth, rgb, cam, T, cfg: Config = Config(), want_flags: bool = False):
+    """Integrate one frame into ``vol`` in place.  Returns (counts, flags):
+    counts = [updated voxels, colour-band voxels]; flags = per-voxel IF_* bits
+    (or None)."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, np.float32)
+    assert depth.shape == (cam.height, cam.width)
+    rgb = None if rgb is None else np.ascontiguousarray(rgb, np.uint8)
+    T = _pose(T)
+    flags = np.zeros(vol.F.shape, np.uint8) if want_flags else None
+    counts = np.zeros(2, np.int64)
+    cv, ci, cc = vol._c(), _intr(cam), cfg._c()
+    lib.orc_integrate(C.byref(cv), _ptr(depth, C.c_float), _ptr(rgb, C.c_uint8), C.byref(ci),
+                      _ptr(T, C.c_double), C.byref(cc), _ptr(flags, C.c_uint8),
+                      _ptr(counts, C.c_int64))
+    return counts, flags
+
+
+def integrate_voxels(vol: Volume, idx, depth, rgb, cam, T, cfg: Config = Config()):
+    """Integrate one frame into the listed voxels only (linear x-fastest
+    indices).  Returns (counts, flags over the whole volume; only the listed
+    voxels are written)."""
+    lib = _load()
+    idx = np.ascontiguousarray(idx, np.int64)
+    depth = np.ascontiguousarray(depth, np.float32)
+    rgb = None if rgb is None else np.ascontiguousarray(rgb, np.uint8)
+    T = _pose(T)
+    flags = np.zeros(vol.F.shape, np.uint8)
+    counts = np.zeros(2, np.int64)
+    cv, ci, cc = vol._c(), _intr(cam), cfg._c()
+    lib.orc_integrate_voxels(C.byref(cv), _ptr(idx, C.c_int64), C.c_int64(idx.size),
+                             _ptr(depth, C.c_float), _ptr(rgb, C.c_uint8), C.byref(ci),
+                             _ptr(T, C.c_double), C.byref(cc), _ptr(flags, C.c_uint8),
+                             _ptr(counts, C.c_int64))
+    return counts, flags
+
+
+def raycast(vols, cam, T, cfg: Config = Config(), ids=None):
+    """Raycast all volumes into one map.  Returns a dict of numpy arrays:
+    depth (H,W) [0 = no hit], normal (H,W,3), rgba (H,W,4), vertex (H,W,3),
+    vol (H,W) [-1 = no hit], flags (H,W) RF_* bits."""
+    lib = _load()
+    vols = list(vols)
+    n = len(vols)
+    ids = np.arange(n, dtype=np.int32) if ids is None else np.ascontiguousarray(ids, np.int32)
+    arr = (_Volume * max(n, 1))()
+    for i, v in enumerate(vols):
+        arr[i] = v._c()
+    H, W = int(cam.height), int(cam.width)
+    out = dict(depth=np.zeros((H, W)), normal=np.zeros((H, W, 3)), rgba=np.zeros((H, W, 4), np.uint8),
+               vertex=np.zeros((H, W, 3)), vol=np.zeros((H, W), np.int32),
+               flags=np.zeros((H, W), np.uint8))
+    T = _pose(T)
+    ci, cc = _intr(cam), cfg._c()
+    lib.orc_raycast(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
+                    C.byref(cc), _ptr(out["depth"], C.c_double), _ptr(out["normal"], C.c_double),
+                    _ptr(out["rgba"], C.c_uint8), _ptr(out["vertex"], C.c_double),
+                    _ptr(out["vol"], C.c_int32), _ptr(out["flags"], C.c_uint8))
+    return out
+
+
+def sample(vol: Volume, q):
+    """Trilinear TSDF value and validity at voxel coordinates q (x, y, z)."""
+    lib = _load()
+    qa = np.ascontiguousarray(q, np.float64)
+    valid = C.c_int32(0)
+    cv = vol._c()
+    val = lib.orc_sample(C.byref(cv), _ptr(qa, C.c_double), C.byref(valid))
+    return float(val), bool(valid.value)

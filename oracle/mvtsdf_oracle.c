@@ -1,0 +1,488 @@
+/*
+ * mvtsdf_oracle.c -- plain FP64 CPU oracle for multi-volume projective TSDF
+ * integration and raycasting, written from Salvato, Finman and Leonard,
+ * "Multi-Volume High Resolution RGB-D Mapping with Dynamic Volume Placement"
+ * (arXiv 1511.07106).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity reference for the CUDA
+ * library; only the test-suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it.  It shares no code, header, table or constant
+ * with the CUDA path.  Everything is computed in double precision, voxel by
+ * voxel and ray by ray, in the order the paper states the steps; there is no
+ * blocking, no bricking and no empty-space skipping here.
+ *
+ * Readings of the paper that this file fixes (the paper is silent or
+ * garbled at these points):
+ *   - voxel i of a volume with lattice offset h_t sits at world position
+ *     (h_t + i) * s, s = voxel pitch (Sec. Volumetric Integration, t_s = t_l + h_t;
+ *     Sec. Dynamic Mapping for SLAM, h_t on an integer lattice);
+ *   - the pose T = [R|t] maps camera to world (Sec. Depth Map Conversion);
+ *   - the "measured distance" is the projective distance along the voxel's
+ *     ray seen from the current camera: sdf = (D - z) * |p_c| / z
+ *     (Sec. Volumetric Integration, dist = D - d_m, read with d_m measured
+ *     from the camera of the current frame);
+ *   - "constrained to truncation bounds": voxels with sdf < -mu are not
+ *     updated, otherwise f = min(1, sdf / mu) in units of mu;
+ *   - "linearly increasing weight up to some maximum": per-frame weight 1,
+ *     F' = (F W + f) / (W + 1), W' = min(W + 1, W_max);
+ *   - colour (the paper shows coloured models but gives no rule): a running
+ *     average inside the band |sdf| < mu, rounded half up, colour weight in
+ *     the alpha byte capped at color_w_max;
+ *   - raycast (Sec. Raycasting, Algorithm 1): the ray of pixel (x, y) is
+ *     o = t, d = R K^-1 [x y 1]^T, so the ray parameter tau is z-depth.
+ *     Samples sit on the global grid tau_k = k * Delta with
+ *     Delta = step * s / |d| (same grid in every volume of equal pitch).
+ *     A sample is valid when the 8 corners of its trilinear cell have W > 0.
+ *     The first pair of consecutive valid samples with F > 0 then F <= 0
+ *     brackets the surface; an invalid sample breaks the pair.  The root of
+ *     the trilinear interpolant inside the bracket is found by bisection.
+ *   - normal = normalised analytic gradient of the trilinear interpolant in
+ *     the hit cell (the "derivative of the TSDF at the zero crossing");
+ *     colour = trilinear RGB in the hit cell, rounded half up;
+ *   - all volumes write one map; the smallest ray distance wins, exact ties
+ *     go to the lower volume id (Sec. Raycasting, last paragraph).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+
+#define ORC_EXPORT __attribute__((visibility("default")))
+
+typedef struct {
+    int32_t h[3];   /* lattice offset h_t, voxels */
+    int32_t r[3];   /* voxels per axis h_r */
+    double s;       /* voxel pitch, metres */
+    double *F;      /* r0*r1*r2 normalised TSDF, x fastest */
+    double *W;      /* r0*r1*r2 weights */
+    uint8_t *rgba;  /* 4 per voxel (A = colour weight), may be NULL */
+} orc_volume;
+
+typedef struct {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+} orc_intrinsics;
+
+typedef struct {
+    double trunc_vox;      /* truncation mu, in voxels */
+    double w_max;          /* weight cap */
+    int32_t color_w_max;   /* colour weight cap, <= 255 */
+    double z_min, z_max;   /* valid depth / ray range, metres */
+    double step_vox;       /* raycast sample spacing, voxels (<= 1) */
+    /* decision margins: outputs whose FP64 decision lies closer than these
+     * to a threshold are flagged (an FP32 implementation may decide them
+     * the other way). */
+    double eps_px;         /* pixel rounding, pixels */
+    double eps_sdf;        /* sdf thresholds, fraction of mu */
+    double eps_z;          /* camera z near 0, metres */
+    double eps_f;          /* sign of a ray sample, TSDF units */
+    double eps_q;          /* cell boundary, voxels */
+    double eps_tau;        /* sample-range endpoints, fraction of Delta */
+} orc_config;
+
+/* per-voxel integration flags */
+enum { ORC_IF_Z = 1, ORC_IF_PIX = 2, ORC_IF_GATE = 4, ORC_IF_BAND = 8 };
+/* per-pixel raycast flags */
+enum { ORC_RF_SIGN = 1, ORC_RF_CELL = 2, ORC_RF_RANGE = 4, ORC_RF_FACE = 8,
+       ORC_RF_TIE = 16, ORC_RF_GRAD = 32 };
+
+static size_t vox_index(const orc_volume *v, int64_t x, int64_t y, int64_t z)
+{
+    return ((size_t)z * (size_t)v->r[1] + (size_t)y) * (size_t)v->r[0] + (size_t)x;
+}
+
+static int near_half_integer_boundary(double u, double eps)
+{
+    /* nearest-pixel rounding floor(u + 1/2) changes where u + 1/2 is an integer */
+    double w = u + 0.5;
+    double fl = floor(w);
+    return (w - fl) < eps || (fl + 1.0 - w) < eps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Volumetric integration (Sec. Volumetric Integration; Algorithm 1, first  */
+/* double loop).  One voxel.                                                */
+/* ------------------------------------------------------------------------ */
+static void integrate_voxel(orc_volume *v, int64_t x, int64_t y, int64_t z,
+                            const float *depth, const uint8_t *rgb,
+                            const orc_intrinsics *K, const double R[9], const double t[3],
+                            const orc_config *c, uint8_t *flag, int64_t cnt[2])
+{
+    uint8_t fl = 0;
+    /* t_s = t_l + h_t, in metres */
+    const double pw[3] = { (double)(v->h[0] + x) * v->s,
+                           (double)(v->h[1] + y) * v->s,
+                           (double)(v->h[2] + z) * v->s };
+    const double dw[3] = { pw[0] - t[0], pw[1] - t[1], pw[2] - t[2] };
+    /* camera coordinates p_c = R^T (p_w - t) */
+    const double X = R[0] * dw[0] + R[3] * dw[1] + R[6] * dw[2];
+    const double Y = R[1] * dw[0] + R[4] * dw[1] + R[7] * dw[2];
+    const double Z = R[2] * dw[0] + R[5] * dw[1] + R[8] * dw[2];
+    const size_t i = vox_index(v, x, y, z);
+
+    if (fabs(Z) < c->eps_z) fl |= ORC_IF_Z;
+    if (!(Z > 0.0)) goto done;
+
+    /* project to the image and take the nearest pixel */
+    const double u = K->fx * X / Z + K->cx;
+    const double w = K->fy * Y / Z + K->cy;
+    if (near_half_integer_boundary(u, c->eps_px) || near_half_integer_boundary(w, c->eps_px))
+        fl |= ORC_IF_PIX;
+    const double ui = floor(u + 0.5), vi = floor(w + 0.5);
+    if (ui < 0.0 || vi < 0.0 || ui >= (double)K->width || vi >= (double)K->height) goto done;
+    const size_t pix = (size_t)vi * (size_t)K->width + (size_t)ui;
+
+    const double D = (double)depth[pix];
+    if (!(D > 0.0) || D < c->z_min || D > c->z_max) goto done;
+
+    /* projective signed distance along the voxel's ray */
+    const double norm_pc = sqrt(X * X + Y * Y + Z * Z);
+    const double sdf = (D - Z) * (norm_pc / Z);
+    const double mu = c->trunc_vox * v->s;
+    if (fabs(sdf + mu) < c->eps_sdf * mu) fl |= ORC_IF_GATE;
+    if (fabs(fabs(sdf) - mu) < c->eps_sdf * mu) fl |= ORC_IF_BAND;
+    if (sdf < -mu) goto done;
+
+    double f = sdf / mu;
+    if (f > 1.0) f = 1.0;
+
+    /* weighted running average with per-frame weight 1 and capped weight */
+    const double Wold = v->W[i];
+    v->F[i] = (v->F[i] * Wold + f) / (Wold + 1.0);
+    v->W[i] = (Wold + 1.0 < c->w_max) ? Wold + 1.0 : c->w_max;
+    cnt[0] += 1;
+
+    if (rgb && v->rgba && fabs(sdf) < mu) {
+        uint8_t *cv = v->rgba + 4 * i;
+        const int64_t wc = cv[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            const int64_t num = (int64_t)cv[ch] * wc + (int64_t)rgb[3 * pix + ch];
+            /* round half up of num / (wc + 1), in integers */
+            cv[ch] = (uint8_t)((2 * num + wc + 1) / (2 * (wc + 1)));
+        }
+        cv[3] = (uint8_t)((wc + 1 < c->color_w_max) ? wc + 1 : c->color_w_max);
+        cnt[1] += 1;
+    }
+done:
+    if (flag) flag[i] = fl;
+}
+
+static void pose_split(const double T[16], double R[9], double t[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) R[3 * a + b] = T[4 * a + b];
+        t[a] = T[4 * a + 3];
+    }
+}
+
+/* Integrate one depth (+ optional RGB) frame into one volume.
+ * depth: height*width float32 z-depth in metres (<= 0 or NaN = invalid).
+ * rgb:   height*width*3 uint8 registered to depth, or NULL.
+ * T:     4x4 row-major camera-to-world pose.
+ * flags: per-voxel decision flags (ORC_IF_*), or NULL.
+ * counts[0] += updated voxels, counts[1] += colour (band) voxels. */
+ORC_EXPORT void orc_integrate(orc_volume *v, const float *depth, const uint8_t *rgb,
+                              const orc_intrinsics *K, const double T[16],
+                              const orc_config *c, uint8_t *flags, int64_t counts[2])
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+    int64_t tot0 = 0, tot1 = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : tot0, tot1)
+    for (int64_t z = 0; z < v->r[2]; ++z) {
+        int64_t cnt[2] = {0, 0};
+        for (int64_t y = 0; y < v->r[1]; ++y)
+            for (int64_t x = 0; x < v->r[0]; ++x)
+                integrate_voxel(v, x, y, z, depth, rgb, K, R, t, c, flags, cnt);
+        tot0 += cnt[0];
+        tot1 += cnt[1];
+    }
+    if (counts) { counts[0] += tot0; counts[1] += tot1; }
+}
+
+/* The same update restricted to a list of voxels (linear indices, x
+ * fastest); used to check large volumes on a sample. */
+ORC_EXPORT void orc_integrate_voxels(orc_volume *v, const int64_t *idx, int64_t n,
+                                     const float *depth, const uint8_t *rgb,
+                                     const orc_intrinsics *K, const double T[16],
+                                     const orc_config *c, uint8_t *flags, int64_t counts[2])
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+    int64_t cnt[2] = {0, 0};
+    const int64_t rx = v->r[0], ry = v->r[1];
+    for (int64_t j = 0; j < n; ++j) {
+        const int64_t li = idx[j];
+        const int64_t x = li % rx, y = (li / rx) % ry, z = li / (rx * ry);
+        integrate_voxel(v, x, y, z, depth, rgb, K, R, t, c, flags, cnt);
+    }
+    if (counts) { counts[0] += cnt[0]; counts[1] += cnt[1]; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Raycasting (Sec. Raycasting; Algorithm 1, pixel loop).                   */
+/* ------------------------------------------------------------------------ */
+
+/* trilinear cell of a point given in GLOBAL voxel coordinates g (the
+ * paper's t_r; volume coordinates are t_r' = t_r - h_t): the lattice cell
+ * floor(g), shifted into the volume and clamped so that the cell's upper
+ * corner stays inside it.  Taking floor() before subtracting h_t makes the
+ * choice of cell independent of which volume evaluates the point. */
+static void cell_of(const orc_volume *v, const double g[3], int64_t cell[3], double fr[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(g[a]) - (double)v->h[a];
+        if (fl < 0.0) fl = 0.0;
+        if (fl > (double)(v->r[a] - 2)) fl = (double)(v->r[a] - 2);
+        cell[a] = (int64_t)fl;
+        fr[a] = g[a] - (fl + (double)v->h[a]);
+    }
+}
+
+static int cell_valid(const orc_volume *v, const int64_t cell[3])
+{
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                if (!(v->W[vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz)] > 0.0))
+                    return 0;
+    return 1;
+}
+
+/* trilinear interpolation of F in a given cell; optional analytic gradient
+ * (per voxel) */
+static double trilinear_in_cell(const orc_volume *v, const int64_t cell[3], const double fr[3],
+                                double grad[3])
+{
+    double c[2][2][2];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                c[dz][dy][dx] = v->F[vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz)];
+    const double x = fr[0], y = fr[1], z = fr[2];
+    double val = 0.0;
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const double wx = dx ? x : 1.0 - x;
+                const double wy = dy ? y : 1.0 - y;
+                const double wz = dz ? z : 1.0 - z;
+                const double cv = c[dz][dy][dx];
+                val += wx * wy * wz * cv;
+                g[0] += (dx ? 1.0 : -1.0) * wy * wz * cv;
+                g[1] += wx * (dy ? 1.0 : -1.0) * wz * cv;
+                g[2] += wx * wy * (dz ? 1.0 : -1.0) * cv;
+            }
+    if (grad) { grad[0] = g[0]; grad[1] = g[1]; grad[2] = g[2]; }
+    return val;
+}
+
+static uint8_t sample_flags(const orc_volume *v, const double q[3], int valid, double F,
+                            const orc_config *c)
+{
+    uint8_t fl = 0;
+    if (valid && fabs(F) < c->eps_f) fl |= ORC_RF_SIGN;
+    /* near a cell boundary: would the cell on the other side give another
+     * validity?  (the interpolant itself is continuous across the face) */
+    for (int a = 0; a < 3; ++a) {
+        const double fq = floor(q[a]);
+        const double below = q[a] - fq, above = fq + 1.0 - q[a];
+        if (below >= c->eps_q && above >= c->eps_q) continue;
+        double q2[3] = {q[0], q[1], q[2]};
+        q2[a] = (below < c->eps_q) ? fq - 0.5 * c->eps_q : fq + 1.0 + 0.5 * c->eps_q;
+        int64_t cell2[3];
+        double fr2[3];
+        cell_of(v, q2, cell2, fr2);
+        if (cell_valid(v, cell2) != valid) fl |= ORC_RF_CELL;
+    }
+    return fl;
+}
+
+typedef struct {
+    int hit;
+    double tau;
+    double grad[3];
+    int cell_ok;
+    double rgb[3];
+    uint8_t flags;
+} orc_hit;
+
+/* march one ray through one volume */
+static orc_hit march_volume(const orc_volume *v, const double o[3], const double d[3],
+                            const orc_config *c)
+{
+    orc_hit out;
+    memset(&out, 0, sizeof(out));
+    const double s = v->s;
+    /* ray in global voxel coordinates: g(tau) = q0 + tau * dv */
+    double q0[3], dv[3];
+    for (int a = 0; a < 3; ++a) {
+        q0[a] = o[a] / s;
+        dv[a] = d[a] / s;
+    }
+    /* interpolation domain [h_t, h_t + r - 1] per axis */
+    double lo = c->z_min, hi = c->z_max;
+    for (int a = 0; a < 3; ++a) {
+        const double bmin = (double)v->h[a], bmax = (double)(v->h[a] + v->r[a] - 1);
+        if (dv[a] == 0.0) {
+            if (q0[a] < bmin || q0[a] > bmax) return out;
+            continue;
+        }
+        double t0 = (bmin - q0[a]) / dv[a], t1 = (bmax - q0[a]) / dv[a];
+        if (t0 > t1) { const double tmp = t0; t0 = t1; t1 = tmp; }
+        if (t0 > lo) lo = t0;
+        if (t1 < hi) hi = t1;
+    }
+    if (!(lo <= hi)) return out;
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double Delta = c->step_vox * s / dn;
+    const double k0f = ceil(lo / Delta), k1f = floor(hi / Delta);
+    {
+        const double a = lo / Delta, b = hi / Delta;
+        if (fabs(a - floor(a + 0.5)) < c->eps_tau || fabs(b - floor(b + 0.5)) < c->eps_tau)
+            out.flags |= ORC_RF_RANGE;
+    }
+    int state = 0; /* 0 none, 1 previous valid sample > 0, -1 previous valid sample <= 0 */
+    double tau_prev = 0.0;
+    for (double kf = k0f; kf <= k1f; kf += 1.0) {
+        const double tau = kf * Delta;
+        double q[3];
+        for (int a = 0; a < 3; ++a) q[a] = q0[a] + tau * dv[a];
+        int64_t cell[3];
+        double fr[3];
+        cell_of(v, q, cell, fr);
+        const int valid = cell_valid(v, cell);
+        const double F = valid ? trilinear_in_cell(v, cell, fr, NULL) : 0.0;
+        out.flags |= sample_flags(v, q, valid, F, c);
+        if (!valid) { state = 0; continue; }
+        if (state == 1 && F <= 0.0) {
+            /* bracket (tau_prev, tau]: bisection on the trilinear interpolant */
+            double a = tau_prev, b = tau;
+            for (int it = 0; it < 64; ++it) {
+                const double m = 0.5 * (a + b);
+                if (m <= a || m >= b) break;
+                double qm[3];
+                for (int e = 0; e < 3; ++e) qm[e] = q0[e] + m * dv[e];
+                int64_t cm[3];
+                double fm[3];
+                cell_of(v, qm, cm, fm);
+                const double g = trilinear_in_cell(v, cm, fm, NULL);
+                if (g > 0.0) a = m; else b = m;
+            }
+            const double ts = 0.5 * (a + b);
+            double qs[3];
+            for (int e = 0; e < 3; ++e) qs[e] = q0[e] + ts * dv[e];
+            int64_t cs[3];
+            double fs[3];
+            cell_of(v, qs, cs, fs);
+            for (int e = 0; e < 3; ++e) {
+                const double fq = fs[e];
+                if (fq < c->eps_q || fq > 1.0 - c->eps_q) out.flags |= ORC_RF_FACE;
+            }
+            out.hit = 1;
+            out.tau = ts;
+            out.cell_ok = cell_valid(v, cs);
+            trilinear_in_cell(v, cs, fs, out.grad);
+            if (v->rgba) {
+                for (int ch = 0; ch < 3; ++ch) {
+                    double acc = 0.0;
+                    for (int dz = 0; dz < 2; ++dz)
+                        for (int dy = 0; dy < 2; ++dy)
+                            for (int dx = 0; dx < 2; ++dx) {
+                                const double wx = dx ? fs[0] : 1.0 - fs[0];
+                                const double wy = dy ? fs[1] : 1.0 - fs[1];
+                                const double wz = dz ? fs[2] : 1.0 - fs[2];
+                                const size_t vi = vox_index(v, cs[0] + dx, cs[1] + dy, cs[2] + dz);
+                                acc += wx * wy * wz * (double)v->rgba[4 * vi + ch];
+                            }
+                    out.rgb[ch] = acc;
+                }
+            }
+            return out;
+        }
+        state = (F > 0.0) ? 1 : -1;
+        tau_prev = tau;
+    }
+    return out;
+}
+
+/* Raycast a view of all given volumes into one map (shortest distance wins).
+ * Outputs (each may be NULL): depth[h*w] (0 = no hit), normal[h*w*3],
+ * rgba[h*w*4], vertex[h*w*3], hit_vol[h*w] (-1 = no hit), flags[h*w].
+ * ids gives each volume's id for tie-breaking (lower id wins). */
+ORC_EXPORT void orc_raycast(const orc_volume *vols, const int32_t *ids, int32_t nvol,
+                            const orc_intrinsics *K, const double T[16], const orc_config *c,
+                            double *depth, double *normal, uint8_t *rgba, double *vertex,
+                            int32_t *hit_vol, uint8_t *flags)
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+    const int64_t W = K->width, H = K->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t y = 0; y < H; ++y) {
+        orc_hit hits[nvol > 0 ? nvol : 1];
+        for (int64_t x = 0; x < W; ++x) {
+            const double dc[3] = { ((double)x - K->cx) / K->fx, ((double)y - K->cy) / K->fy, 1.0 };
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
+            orc_hit best;
+            memset(&best, 0, sizeof(best));
+            int32_t best_v = -1;
+            uint8_t fl = 0;
+            for (int32_t vi = 0; vi < nvol; ++vi) {
+                orc_hit hv = march_volume(&vols[vi], t, d, c);
+                fl |= hv.flags;
+                hits[vi] = hv;
+                if (!hv.hit) continue;
+                if (best_v < 0 || hv.tau < best.tau || (hv.tau == best.tau && ids[vi] < ids[best_v])) {
+                    best = hv;
+                    best_v = vi;
+                }
+            }
+            /* near-ties between volumes matter only where they disagree */
+            if (best_v >= 0) {
+                for (int32_t vi = 0; vi < nvol; ++vi) {
+                    if (vi == best_v || !hits[vi].hit) continue;
+                    if (fabs(hits[vi].tau - best.tau) > 1e-3 * vols[vi].s) continue;
+                    int differ = hits[vi].cell_ok != best.cell_ok;
+                    for (int a = 0; a < 3; ++a) {
+                        if (fabs(hits[vi].grad[a] - best.grad[a]) > 1e-6) differ = 1;
+                        if (fabs(hits[vi].rgb[a] - best.rgb[a]) > 1e-6) differ = 1;
+                    }
+                    if (differ) fl |= ORC_RF_TIE;
+                }
+            }
+            const size_t p = (size_t)y * (size_t)W + (size_t)x;
+            if (hit_vol) hit_vol[p] = best_v >= 0 ? ids[best_v] : -1;
+            if (flags) flags[p] = fl;
+            if (depth) depth[p] = best_v >= 0 ? best.tau : 0.0;
+            double n[3] = {0.0, 0.0, 0.0};
+            if (best_v >= 0 && best.cell_ok) {
+                const double gn = sqrt(best.grad[0] * best.grad[0] + best.grad[1] * best.grad[1] +
+                                       best.grad[2] * best.grad[2]);
+                if (gn > 0.0) for (int a = 0; a < 3; ++a) n[a] = best.grad[a] / gn;
+                if (gn < 1e-3 && flags) flags[p] |= ORC_RF_GRAD;
+            }
+            if (normal) for (int a = 0; a < 3; ++a) normal[3 * p + a] = n[a];
+            if (vertex) for (int a = 0; a < 3; ++a) vertex[3 * p + a] = best_v >= 0 ? t[a] + best.tau * d[a] : 0.0;
+            if (rgba) {
+                for (int ch = 0; ch < 3; ++ch)
+                    rgba[4 * p + ch] = (best_v >= 0 && best.cell_ok) ? (uint8_t)floor(best.rgb[ch] + 0.5) : 0;
+                rgba[4 * p + 3] = best_v >= 0 ? 255 : 0;
+            }
+        }
+    }
+}
+
+/* Trilinear value and validity at one point q (this volume's voxel
+ * coordinates) -- exposed for tests. */
+ORC_EXPORT double orc_sample(const orc_volume *v, const double q[3], int32_t *valid)
+{
+    int64_t cell[3];
+    double fr[3];
+    const double g[3] = { q[0] + v->h[0], q[1] + v->h[1], q[2] + v->h[2] };
+    cell_of(v, g, cell, fr);
+    if (valid) *valid = cell_valid(v, cell);
+    return trilinear_in_cell(v, cell, fr, NULL);
+}
