@@ -1,0 +1,468 @@
+"""Benchmark: per-frame TSDF integration + raycast of the 512^3 room workload.
+
+One step = one frame of the workload: integrate a 640x480 depth+RGB frame
+into the 512^3 (3 m, 5.86 mm voxels) volume, then raycast the 640x480
+depth/normal/colour/vertex maps at that frame's pose.  Frames are synthetic
+(seeded analytic room of boxes and spheres, axial depth noise, handheld
+trajectory), generated on the host before timing and resident in HBM while
+the device-timed region runs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  `value` is updated voxel-updates per second of
+the whole job (voxels whose TSDF changed, summed over ranks, divided by the
+slowest rank's time for K integrate+raycast steps).  Under torchrun each rank
+maps its own copy of the workload (independent problems: weak scaling, no
+data-path collective).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same steps.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1511_07106_b300 import synth  # noqa: E402  (numpy only; no CUDA)
+
+METRIC = "TSDF voxel-updates/s (integrate + raycast per frame)"
+UNIT = "voxel-updates/s"
+WORKLOAD = "room 512^3 single volume, 640x480 depth+RGB, integrate + raycast per frame"
+N_FRAMES_MAX = 300
+
+
+def _render(i):
+    wl = synth.room_512(frames=N_FRAMES_MAX)
+    return wl.frame(i)
+
+
+def make_frames(n, procs):
+    idx = [i % N_FRAMES_MAX for i in range(n)]
+    uniq = sorted(set(idx))
+    with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        got = dict(zip(uniq, ex.map(_render, uniq)))
+    return [got[i] for i in idx]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since it was captured (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != rec["source_sha256_16"]:
+        return None
+    return rec
+
+
+def run_native_steps(m, frames, poses, cam, maps, first, steps, dev_depth, dev_rgb, torch):
+    for k in range(steps):
+        i = first + k
+        m.integrate(dev_depth[i], dev_rgb[i], cam, poses[i])
+        m.raycast(cam, poses[i], out=maps)
+
+
+def bench_storage(torch, Mapper, Config, wl, frames, poses, fmt, warmup, steps, dev_depth, dev_rgb,
+                  clocks=None):
+    """Device-timed integrate+raycast steps for one storage format."""
+    (vs,) = wl.volumes
+    cam = wl.cam
+    m = Mapper(Config())
+    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
+    maps = m.alloc_maps(cam)
+    run_native_steps(m, frames, poses, cam, maps, 0, warmup, dev_depth, dev_rgb, torch)
+    m.synchronize()
+    m.stats(reset=True)
+    m.timings(reset=True)
+    m.set_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+    barrier(torch)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run_native_steps(m, frames, poses, cam, maps, warmup, steps, dev_depth, dev_rgb, torch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(torch)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    m.set_timing(False)
+    st = m.stats()
+    tm = m.timings()
+    out = dict(ms=ms, stats=st, timings=tm, clocks=clk, mapper=m, vid=vid, maps=maps)
+    return out
+
+
+def barrier(torch):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def allreduce_max(torch, x):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return float(x)
+
+
+def allreduce_sum(torch, x):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+    return float(x)
+
+
+def integrate_bytes_per_voxel(fmt):
+    return {"f32": 16, "f16": 8, "i16": 8}[fmt]
+
+
+def kernel_summary(res, fmt, cam, steps):
+    """Per-kernel average launch time and algorithmic bytes per launch."""
+    tm = res["timings"]
+    st = res["stats"]
+    H, W = cam.height, cam.width
+    out = {}
+    n_int = max(tm["integrate"][2], 1)
+    upd = st["updated"] / n_int
+    band = st["band"] / n_int
+    bricks = st["bricks"] / n_int
+    # read+write of (F, W) per updated voxel, of RGBA per band voxel, the frame
+    # once (depth f32 + RGB8), the work list and the brick flags
+    b_int = integrate_bytes_per_voxel(fmt) * upd + 8 * band + 7 * H * W + 8 * bricks + 2 * bricks
+    for name, (launches, ms, timed) in tm.items():
+        if timed == 0:
+            continue
+        avg_ms = ms / timed
+        e = {"launches": launches, "avg_ms": avg_ms, "share": 0.0}
+        if name == "integrate":
+            e["algorithmic_bytes"] = b_int
+            e["achieved_gbs"] = b_int / (avg_ms * 1e-3) / 1e9
+        if name == "raycast":
+            b_ray = 36 * H * W  # outputs: depth 4 + normal 12 + rgba 4 + vertex 12 + id 4
+            e["algorithmic_bytes"] = b_ray
+            e["achieved_gbs"] = b_ray / (avg_ms * 1e-3) / 1e9
+        out[name] = e
+    tot = sum(v["avg_ms"] * v["launches"] for v in out.values())
+    for v in out.values():
+        v["share"] = v["avg_ms"] * v["launches"] / tot if tot else 0.0
+    return out
+
+
+def cpu_baseline_sample(wl, frames, m, vid, first):
+    """The FP64 oracle as it stands on a bounded sample of one step: frame
+    `first` integrated into 8 evenly spread z-slabs of 8 voxels (1/8 of the
+    volume, starting from the GPU's state) and the raycast of every 8th
+    pixel.  Returns (updated voxels/s, seconds, sample description, cores)."""
+    import oracle
+    (vs,) = wl.volumes
+    F, W, rgba = m.read_decoded(vid)
+    d, c = frames[first]
+    T = wl.poses[first % N_FRAMES_MAX]
+    cfg = oracle.Config()
+    upd = 0
+    t0 = time.perf_counter()
+    nz = vs.r[2]
+    for k in range(8):
+        z0 = k * (nz // 8)
+        sl = slice(z0, z0 + 8)
+        sub = oracle.Volume((vs.h[0], vs.h[1], vs.h[2] + z0), (vs.r[0], vs.r[1], 8), vs.s,
+                            F[sl].copy(), W[sl].copy(), rgba[sl].copy())
+        cnt, _ = oracle.integrate(sub, d, c, wl.cam, T, cfg)
+        upd += int(cnt[0])
+    t_int = time.perf_counter() - t0
+    full = oracle.Volume(vs.h, vs.r, vs.s, F, W, rgba)
+    pix = np.arange(0, wl.cam.width * wl.cam.height, 8)
+    t0 = time.perf_counter()
+    oracle.raycast([full], wl.cam, T, cfg, ids=[vid], pixels=pix)
+    t_ray = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("one step: frame integrated into 8 z-slabs x 8 voxels (1/8 of the 512^3 volume) + "
+              "raycast of every 8th pixel (1/8 of 640x480); FP64 C oracle, OpenMP")
+    return upd / (t_int + t_ray), t_int + t_ray, sample, cores
+
+
+def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
+    """Same metric through the public API with host buffers: per step, copy the
+    frame from pinned host memory, integrate, raycast, read depth/normal/colour
+    back to pinned host memory."""
+    (vs,) = wl.volumes
+    cam = wl.cam
+    m = Mapper(Config())
+    m.add_volume(vs.h, vs.r, vs.s, "f32")
+    H, W = cam.height, cam.width
+    hd = [torch.from_numpy(f[0]).pin_memory() for f in frames]
+    hc = [torch.from_numpy(f[1]).pin_memory() for f in frames]
+    dd = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    dc = torch.empty((H, W, 3), dtype=torch.uint8, device="cuda")
+    maps = m.alloc_maps(cam, vertex=False)
+    out_d = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    out_n = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    out_c = torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()
+
+    def step(i):
+        dd.copy_(hd[i], non_blocking=True)
+        dc.copy_(hc[i], non_blocking=True)
+        m.integrate(dd, dc, cam, wl.poses[i % N_FRAMES_MAX])
+        m.raycast(cam, wl.poses[i % N_FRAMES_MAX], out=maps)
+        out_d.copy_(maps["depth"], non_blocking=True)
+        out_n.copy_(maps["normal"], non_blocking=True)
+        out_c.copy_(maps["rgba"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for i in range(warmup):
+        step(i)
+    m.stats(reset=True)
+    barrier(torch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        step(warmup + k)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    barrier(torch)
+    st = m.stats()
+    m.close()
+    h2d = 4 * H * W + 3 * H * W
+    d2h = 4 * H * W + 12 * H * W + 4 * H * W
+    return st["updated"], dt, h2d, d2h
+
+
+def main_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
+    if rank != 0:
+        return
+    wl = synth.room_512(frames=N_FRAMES_MAX)
+    n = args.warmup + args.steps
+    frames = make_frames(n, min(16, os.cpu_count() or 1))
+    import oracle
+    oracle.build()
+    (vs,) = wl.volumes
+    vol = oracle.Volume(vs.h, vs.r, vs.s)
+    cfg = oracle.Config()
+    nz = vs.r[2]
+    # each step integrates its frame into one 8-voxel z-slab (1/64 of the
+    # volume, cycling through the volume) and raycasts every 64th pixel
+    upd_total, t_total = 0, 0.0
+    for k in range(n):
+        d, c = frames[k]
+        T = wl.poses[k % N_FRAMES_MAX]
+        z0 = ((k * 7) % 64) * (nz // 64)
+        sl = slice(z0, z0 + 8)
+        sub = oracle.Volume((vs.h[0], vs.h[1], vs.h[2] + z0), (vs.r[0], vs.r[1], 8), vs.s,
+                            vol.F[sl], vol.W[sl], vol.rgba[sl])
+        t0 = time.perf_counter()
+        cnt, _ = oracle.integrate(sub, d, c, wl.cam, T, cfg)
+        vol.F[sl], vol.W[sl], vol.rgba[sl] = sub.F, sub.W, sub.rgba
+        oracle.raycast([vol], wl.cam, T, cfg, pixels=np.arange(k % 64, wl.cam.width * wl.cam.height, 64))
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            upd_total += int(cnt[0])
+            t_total += dt
+    value = upd_total / t_total if t_total > 0 else 0.0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("per step: the frame integrated into one 8-voxel z-slab (1/64 of the 512^3 volume) and "
+              "every 64th pixel raycast; FP64 C oracle, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_total / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-variants", action="store_true", help="skip the f16/i16 storage runs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return main_reference(args, rank)
+
+    n = args.warmup + args.steps
+    procs = max(1, min(16, (os.cpu_count() or 2) // max(world, 1)))
+    frames = make_frames(n, procs)  # before any CUDA call
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1511_07106_b300 import Config, Mapper
+
+    wl = synth.room_512(frames=N_FRAMES_MAX)
+    cam = wl.cam
+    (vs,) = wl.volumes
+    poses = [wl.poses[i % N_FRAMES_MAX] for i in range(n)]
+    dev_depth = torch.from_numpy(np.stack([f[0] for f in frames])).cuda()
+    dev_rgb = torch.from_numpy(np.stack([f[1] for f in frames])).cuda()
+
+    try:
+        clocks = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid))
+    except Exception:
+        clocks = ClockSampler(local_rank)
+    res = bench_storage(torch, Mapper, Config, wl, frames, poses, "f32", args.warmup, args.steps,
+                        dev_depth, dev_rgb, clocks=clocks)
+    ms_max = allreduce_max(torch, res["ms"])
+    upd_sum = allreduce_sum(torch, res["stats"]["updated"])
+    value = upd_sum / (ms_max * 1e-3)
+    kern = kernel_summary(res, "f32", cam, args.steps)
+    peak, peak_kind = measured_peaks()
+    dom = max(kern, key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
+    dk = kern[dom]
+    tr = traffic_record(dom)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": dk.get("achieved_gbs"), "peak": peak,
+                "unit": "GB/s", "frac": (dk.get("achieved_gbs") or 0.0) / peak,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6.4 TB/s"}
+    ik = kern.get("integrate", {})
+    tri = traffic_record("integrate")
+    integrate_roofline = {"bound": "hbm", "achieved": ik.get("achieved_gbs"), "peak": peak,
+                          "unit": "GB/s", "frac": (ik.get("achieved_gbs") or 0.0) / peak,
+                          "traffic": tri["dram_bytes_per_launch"] if tri else None}
+    launches = sum(v[0] for v in res["timings"].values())
+    m = res["mapper"]
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "volume": "512^3 F32 TSDF + F32 weight + RGBA8, 5.86 mm",
+                       "image": "640x480", "frames": n, "trunc_voxels": 4, "w_max": 128,
+                       "l2": "inputs larger than L2 (1.61 GB volume per rank)",
+                       "parallelism": f"independent mapping job per GPU x{world}"},
+            "raycast_mrays_per_s": world * cam.width * cam.height * args.steps / (ms_max * 1e-3) / 1e6,
+            "swept_voxel_updates_per_s": world * int(np.prod(vs.r)) * args.steps / (ms_max * 1e-3),
+            "updated_voxels_per_frame": res["stats"]["updated"] / args.steps,
+            "kernels": kern, "roofline": roofline, "integrate_roofline": integrate_roofline,
+            "gpu_launches": launches, "clocks": res["clocks"]}
+
+    if not args.no_variants:
+        variants = {}
+        for fmt in ("f16", "i16"):
+            r = bench_storage(torch, Mapper, Config, wl, frames, poses, fmt, args.warmup, args.steps,
+                              dev_depth, dev_rgb)
+            k = kernel_summary(r, fmt, cam, args.steps)
+            msx = allreduce_max(torch, r["ms"])
+            variants[fmt] = {"value": allreduce_sum(torch, r["stats"]["updated"]) / (msx * 1e-3),
+                             "ms_per_step": msx / args.steps,
+                             "integrate_ms": k.get("integrate", {}).get("avg_ms"),
+                             "integrate_gbs": k.get("integrate", {}).get("achieved_gbs"),
+                             "raycast_ms": k.get("raycast", {}).get("avg_ms")}
+            r["mapper"].close()
+        line["variants"] = variants
+
+    upd, dt, h2d, d2h = e2e_run(torch, Mapper, Config, wl, frames, args.steps, args.warmup)
+    dt_max = allreduce_max(torch, dt)
+    line["e2e"] = {"value": allreduce_sum(torch, upd) / dt_max, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, sample, cores = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample, "seconds": secs}
+    m.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

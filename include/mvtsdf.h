@@ -1,0 +1,250 @@
+/*
+ * mvtsdf.h -- C ABI of the B300 multi-volume TSDF mapping library.
+ *
+ * The library implements the data-parallel hot path of the multi-volume
+ * RGB-D mapper of Salvato, Finman and Leonard, "Multi-Volume High Resolution
+ * RGB-D Mapping with Dynamic Volume Placement" (arXiv 1511.07106):
+ *   - a set H of TSDF subvolumes h = (h_l, h_r, h_t) that can be added and
+ *     removed at any frame (Sec. Dynamic Volume Allocation, Input and Output;
+ *     Sec. Insertion and Removal);
+ *   - projective TSDF + colour integration of a depth (+RGB) frame into every
+ *     active volume (Sec. Volumetric Integration; Algorithm 1, first loop);
+ *   - the per-pixel raycast of those volumes into depth / normal / colour /
+ *     vertex maps, all volumes writing one map where the shortest ray distance
+ *     wins (Sec. Raycasting; Algorithm 1, second loop);
+ *   - moving a volume between GPU memory and host memory
+ *     (Sec. Memory Passing; Algorithm 1, uploadToGPU / uploadToCPU).
+ *
+ * Conventions shared by every call:
+ *   - Poses are 4x4 row-major camera-to-world matrices T = [R | t] in double
+ *     precision (Sec. Depth Map Conversion, T^i = [R^i | t^i]).  Camera frame:
+ *     x right, y down, z forward.
+ *   - Voxel i of a volume with lattice offset h_t and pitch s sits at world
+ *     position (h_t + i) * s (Sec. Volumetric Integration, t_s = t_l + h_t).
+ *     Volumes whose offsets differ by integer multiples of (h_r - 2) tile space
+ *     with the paper's two-voxel overlap (Sec. Initialization).
+ *   - Depth is float32 z-depth in metres, row-major height x width; a value
+ *     <= 0, NaN, or outside [z_min, z_max] is "no measurement".  RGB is uint8
+ *     height x width x 3, registered to depth with the same intrinsics.
+ *   - TSDF values are stored in units of the truncation distance mu
+ *     (range [-1, 1]); weights count frames, capped at w_max.
+ *   - Device buffers passed in are owned by the caller and must stay valid
+ *     until the work queued on `stream` has finished.  Volume storage in GPU
+ *     memory and in pinned host memory is owned by the library.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous with respect to the
+ *     host unless stated otherwise.
+ *   - Every call returns an mv_status; no call aborts or throws.  The message
+ *     of the last failure on a context is available from mv_last_error().
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef MVTSDF_H
+#define MVTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mv_ctx mv_ctx;
+
+typedef enum {
+    MV_OK = 0,
+    MV_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad enum) */
+    MV_ERR_OOM = 2,            /* GPU or pinned host allocation failed */
+    MV_ERR_CUDA = 3,           /* a CUDA runtime call failed (message in mv_last_error) */
+    MV_ERR_NOT_FOUND = 4,      /* no volume with that id */
+    MV_ERR_NOT_RESIDENT = 5,   /* the volume is swapped out to host memory */
+    MV_ERR_BUSY = 6,           /* operation conflicts with the volume's state */
+    MV_ERR_DEVICE_TIMEOUT = 7, /* a bounded device-side loop gave up (status word set) */
+    MV_ERR_CAPACITY = 8        /* more volumes / pixels than the library's fixed limits */
+} mv_status;
+
+/* TSDF storage format of one volume.  F32: float32 TSDF + float32 weight
+ * (8 bytes per voxel).  F16: IEEE half TSDF (round to nearest even) + uint16
+ * weight (4 bytes).  I16: int16 TSDF = round(F * 32767) clamped to +-32767 +
+ * uint16 weight (4 bytes).  Every format adds 4 bytes of RGBA8 colour whose
+ * alpha byte is the colour weight.  The update itself is computed in float32
+ * for every format. */
+typedef enum { MV_TSDF_F32 = 0, MV_TSDF_F16 = 1, MV_TSDF_I16 = 2 } mv_tsdf_fmt;
+
+/* Pinhole intrinsics K (Sec. Input and Output): pixel (x, y) with integer
+ * coordinates is the pixel centre; a camera point (X, Y, Z) projects to
+ * u = fx X / Z + cx, v = fy Y / Z + cy. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} mv_intrinsics;
+
+/* Method parameters (the paper leaves all of them unstated). */
+typedef struct {
+    float trunc_voxels;  /* truncation distance mu, in voxels of each volume (default 4) */
+    float w_max;         /* weight cap; <= 65535 for F16/I16 volumes (default 128) */
+    int32_t color_w_max; /* colour weight cap, 1..255 (default 255) */
+    float z_min, z_max;  /* accepted depth range and raycast range, metres (default 0, +inf) */
+    float ray_step;      /* raycast sample spacing in voxels, [1/64, 1] (default 1) */
+    int32_t n_bisect;    /* bisection steps inside the bracket before the final secant (default 8) */
+} mv_config;
+
+/* One subvolume h = (h_l, h_r, h_t) (Sec. Initialization): h_l = voxel_size * h_r. */
+typedef struct {
+    int32_t h_t[3];      /* lattice offset in voxels */
+    int32_t h_r[3];      /* voxels per axis, each >= 2 */
+    float voxel_size;    /* pitch s in metres, > 0 */
+    int32_t fmt;         /* mv_tsdf_fmt */
+} mv_volume_desc;
+
+typedef struct {
+    mv_volume_desc desc;
+    int32_t resident;    /* 1: in GPU memory, 0: swapped out to pinned host memory */
+    int32_t reserved;
+    uint64_t device_bytes; /* GPU bytes held by the volume */
+    uint64_t host_bytes;   /* pinned host bytes held by the volume */
+} mv_volume_info;
+
+/* Integration counters accumulated on the device since the last reset. */
+typedef struct {
+    uint64_t swept;      /* voxels examined (voxels of bricks in the view frustum) */
+    uint64_t updated;    /* voxels whose TSDF and weight were updated */
+    uint64_t band;       /* voxels whose colour was updated (|sdf| < mu) */
+    uint64_t bricks;     /* 8x8x8 bricks processed */
+} mv_stats;
+
+/* Kernel kinds counted and timed by mv_get_timings. */
+enum {
+    MV_KERNEL_SETUP = 0,       /* per-call camera constants of every volume */
+    MV_KERNEL_BRICK_LIST = 1,  /* frustum work list of bricks */
+    MV_KERNEL_INTEGRATE = 2,   /* TSDF + colour update of the listed bricks */
+    MV_KERNEL_RAYCAST = 3,     /* per-pixel march, refinement, shading and merge */
+    MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
+    MV_KERNEL_KINDS = 8
+};
+
+typedef struct {
+    uint64_t launches[MV_KERNEL_KINDS]; /* kernels launched, by kind */
+    double ms[MV_KERNEL_KINDS];         /* summed device time, by kind, while timing is on */
+    uint64_t timed[MV_KERNEL_KINDS];    /* launches included in ms */
+} mv_timings;
+
+/* Library version string (static storage). */
+const char *mv_version(void);
+
+/* Fill *out with the default configuration.  MV_ERR_ARG if out is NULL. */
+mv_status mv_config_default(mv_config *out);
+
+/* Create a context on CUDA device `device` (made current on the calling
+ * thread).  cfg may be NULL for defaults.  Fails with MV_ERR_ARG on invalid
+ * parameters, MV_ERR_CUDA if the device cannot be used. */
+mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out);
+
+/* Wait for all of the context's work, free every volume (GPU and host) and
+ * the context.  NULL is accepted. */
+mv_status mv_destroy(mv_ctx *ctx);
+
+/* Message of the last failed call on ctx (static or context-owned storage,
+ * valid until the next call on ctx). */
+const char *mv_last_error(const mv_ctx *ctx);
+
+/* Add a volume (Sec. Dynamic Volume Allocation: "a volume can be added to the
+ * set at any point").  Allocates its storage in GPU memory and clears it to
+ * F = 0, W = 0 (unobserved), colour 0, ordered on the context's internal
+ * stream before any later call.  *out_id receives an id that is never
+ * reused.  MV_ERR_OOM if GPU memory is exhausted (nothing is allocated),
+ * MV_ERR_CAPACITY beyond 4096 volumes. */
+mv_status mv_add_volume(mv_ctx *ctx, const mv_volume_desc *desc, int32_t *out_id);
+
+/* Remove a volume from the set and free its GPU and host storage once work
+ * already queued on it has finished (Sec. Insertion and Removal). */
+mv_status mv_remove_volume(mv_ctx *ctx, int32_t id);
+
+/* Describe a volume.  MV_ERR_NOT_FOUND for an unknown id. */
+mv_status mv_query(mv_ctx *ctx, int32_t id, mv_volume_info *out);
+
+/* List volume ids in ascending order: writes min(count, cap) ids to ids
+ * (may be NULL when cap == 0) and the total into *count. */
+mv_status mv_list_volumes(mv_ctx *ctx, int32_t *ids, int32_t cap, int32_t *count);
+
+/* Integrate one frame into every resident volume in one batched pass: a
+ * work list of the 8x8x8 bricks that intersect the view frustum of every
+ * resident volume is built on the device, then one persistent kernel updates
+ * them (Sec. Volumetric Integration).  depth: device float32 [height*width];
+ * rgb: device uint8 [height*width*3] or NULL (no colour update).  Volumes
+ * that are swapped out are skipped, as the paper processes only active
+ * volumes.  Asynchronous on `stream`. */
+mv_status mv_integrate(mv_ctx *ctx, const float *depth, const uint8_t *rgb,
+                       const mv_intrinsics *K, const double T_c2w[16], void *stream);
+
+/* The same update for one volume only (the paper's per-volume step of
+ * Algorithm 1).  MV_ERR_NOT_RESIDENT if the volume is swapped out. */
+mv_status mv_integrate_volume(mv_ctx *ctx, int32_t id, const float *depth, const uint8_t *rgb,
+                              const mv_intrinsics *K, const double T_c2w[16], void *stream);
+
+/* Raycast every resident volume into one set of maps in one pass; for each
+ * pixel the hit with the smallest ray distance wins, exact ties going to the
+ * lower volume id (Sec. Raycasting).  Output device buffers (each may be
+ * NULL): depth float32 [h*w] (z-depth, 0 = no hit), normal float32 [h*w*3]
+ * (unit, world frame, facing the camera; 0 where the hit cell has an
+ * unobserved corner), rgba uint8 [h*w*4] (A = 255 on hits, 0 otherwise),
+ * vertex float32 [h*w*3] (world frame), vol_id int32 [h*w] (-1 = no hit).
+ * Asynchronous on `stream`. */
+mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16],
+                     float *depth, float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id,
+                     void *stream);
+
+/* Raycast one volume and merge its hits into the maps (the paper's
+ * per-volume raycast: "all raycasting steps modify the same map").  With
+ * first != 0 the maps are (re)initialised by this call; otherwise a pixel is
+ * overwritten only when this volume's hit is nearer, or equally near with a
+ * lower id.  depth and vol_id are required (they carry the merge state);
+ * the other outputs may be NULL. */
+mv_status mv_raycast_volume(mv_ctx *ctx, int32_t id, int32_t first, const mv_intrinsics *K,
+                            const double T_c2w[16], float *depth, float *normal, uint8_t *rgba,
+                            float *vertex, int32_t *vol_id, void *stream);
+
+/* Move a volume to pinned host memory (the paper's download, "uploadToCPU")
+ * on the library's swap stream, after the work already queued on `stream`;
+ * its GPU memory is released once the copy has finished.  From this call on
+ * the volume is skipped by mv_integrate / mv_raycast.  MV_ERR_OOM if pinned
+ * memory cannot be allocated (the volume then stays resident). */
+mv_status mv_swap_out(mv_ctx *ctx, int32_t id, void *stream);
+
+/* Bring a swapped-out volume back to GPU memory ("uploadToGPU") on the swap
+ * stream; later calls on any stream wait for the copy.  MV_ERR_OOM if GPU
+ * memory is exhausted (the volume stays on the host). */
+mv_status mv_swap_in(mv_ctx *ctx, int32_t id, void *stream);
+
+/* Synchronous copy of a volume's state to host memory in linear order
+ * (index ((z * h_r[1]) + y) * h_r[0] + x).  host_fw receives the raw storage
+ * per voxel: F32 -> 2 x float32 (F, W); F16 -> uint32 (bits 0-15 IEEE half F,
+ * bits 16-31 uint16 W); I16 -> uint32 (bits 0-15 int16 F, bits 16-31 uint16 W).
+ * host_rgba receives 4 bytes per voxel (may be NULL).  Works for resident
+ * and swapped-out volumes. */
+mv_status mv_read_volume(mv_ctx *ctx, int32_t id, void *host_fw, uint8_t *host_rgba);
+
+/* Synchronous overwrite of a volume's state from host memory in the layout of
+ * mv_read_volume (host_rgba NULL keeps the colour).  Used to prefill volumes
+ * and to restore checkpoints. */
+mv_status mv_write_volume(mv_ctx *ctx, int32_t id, const void *host_fw, const uint8_t *host_rgba);
+
+/* Read (and optionally reset) the integration counters; synchronises the
+ * context's work. */
+mv_status mv_get_stats(mv_ctx *ctx, mv_stats *out, int32_t reset);
+
+/* Turn per-kernel timing on or off.  While on, every kernel launch is
+ * bracketed by two CUDA events recorded on the launching stream. */
+mv_status mv_set_timing(mv_ctx *ctx, int32_t enable);
+
+/* Launch counts and (while timing was on) summed device time per kernel kind
+ * since the last reset; synchronises the context's work. */
+mv_status mv_get_timings(mv_ctx *ctx, mv_timings *out, int32_t reset);
+
+/* Wait until all work of the context (all streams it used) has finished. */
+mv_status mv_synchronize(mv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MVTSDF_H */

@@ -76,6 +76,9 @@ def _load():
                                               C.POINTER(_Intr), dp, C.POINTER(_Cfg), u8p, i64p]
         _lib.orc_raycast.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr), dp,
                                      C.POINTER(_Cfg), dp, dp, u8p, dp, i32p, u8p]
+        _lib.orc_raycast_pixels.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
+                                            dp, C.POINTER(_Cfg), i64p, C.c_int64, dp, dp, u8p, dp,
+                                            i32p, u8p]
         _lib.orc_sample.argtypes = [C.POINTER(_Volume), dp, i32p]
         _lib.orc_sample.restype = C.c_double
         if hasattr(_lib, "orc_raycast_grad"):
@@ -200,10 +203,11 @@ def integrate_voxels(vol: Volume, idx, depth, rgb, cam, T, cfg: Config = Config(
     return counts, flags
 
 
-def raycast(vols, cam, T, cfg: Config = Config(), ids=None):
+def raycast(vols, cam, T, cfg: Config = Config(), ids=None, pixels=None):
     """Raycast all volumes into one map.  Returns a dict of numpy arrays:
     depth (H,W) [0 = no hit], normal (H,W,3), rgba (H,W,4), vertex (H,W,3),
-    vol (H,W) [-1 = no hit], flags (H,W) RF_* bits."""
+    vol (H,W) [-1 = no hit], flags (H,W) RF_* bits.  With ``pixels`` (linear
+    indices y*W + x) only those pixels are computed; the rest stay 0."""
     lib = _load()
     vols = list(vols)
     n = len(vols)
@@ -217,10 +221,17 @@ def raycast(vols, cam, T, cfg: Config = Config(), ids=None):
                flags=np.zeros((H, W), np.uint8))
     T = _pose(T)
     ci, cc = _intr(cam), cfg._c()
-    lib.orc_raycast(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
-                    C.byref(cc), _ptr(out["depth"], C.c_double), _ptr(out["normal"], C.c_double),
-                    _ptr(out["rgba"], C.c_uint8), _ptr(out["vertex"], C.c_double),
-                    _ptr(out["vol"], C.c_int32), _ptr(out["flags"], C.c_uint8))
+    outs = (_ptr(out["depth"], C.c_double), _ptr(out["normal"], C.c_double),
+            _ptr(out["rgba"], C.c_uint8), _ptr(out["vertex"], C.c_double),
+            _ptr(out["vol"], C.c_int32), _ptr(out["flags"], C.c_uint8))
+    if pixels is None:
+        lib.orc_raycast(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
+                        C.byref(cc), *outs)
+    else:
+        pix = np.ascontiguousarray(pixels, np.int64)
+        lib.orc_raycast_pixels(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci),
+                               _ptr(T, C.c_double), C.byref(cc), _ptr(pix, C.c_int64),
+                               C.c_int64(pix.size), *outs)
     return out
 
 

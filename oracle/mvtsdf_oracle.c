@@ -407,6 +407,64 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
     return out;
 }
 
+/* One pixel: march every volume, keep the nearest hit (exact ties to the
+ * lower id), write that pixel's outputs. */
+static void raycast_pixel(const orc_volume *vols, const int32_t *ids, int32_t nvol,
+                          const orc_intrinsics *K, const double R[9], const double t[3],
+                          const orc_config *c, int64_t x, int64_t y, orc_hit *hits,
+                          double *depth, double *normal, uint8_t *rgba, double *vertex,
+                          int32_t *hit_vol, uint8_t *flags)
+{
+    const double dc[3] = { ((double)x - K->cx) / K->fx, ((double)y - K->cy) / K->fy, 1.0 };
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
+    orc_hit best;
+    memset(&best, 0, sizeof(best));
+    int32_t best_v = -1;
+    uint8_t fl = 0;
+    for (int32_t vi = 0; vi < nvol; ++vi) {
+        orc_hit hv = march_volume(&vols[vi], t, d, c);
+        fl |= hv.flags;
+        hits[vi] = hv;
+        if (!hv.hit) continue;
+        if (best_v < 0 || hv.tau < best.tau || (hv.tau == best.tau && ids[vi] < ids[best_v])) {
+            best = hv;
+            best_v = vi;
+        }
+    }
+    /* near-ties between volumes matter only where they disagree */
+    if (best_v >= 0) {
+        for (int32_t vi = 0; vi < nvol; ++vi) {
+            if (vi == best_v || !hits[vi].hit) continue;
+            if (fabs(hits[vi].tau - best.tau) > 1e-3 * vols[vi].s) continue;
+            int differ = hits[vi].cell_ok != best.cell_ok;
+            for (int a = 0; a < 3; ++a) {
+                if (fabs(hits[vi].grad[a] - best.grad[a]) > 1e-6) differ = 1;
+                if (fabs(hits[vi].rgb[a] - best.rgb[a]) > 1e-6) differ = 1;
+            }
+            if (differ) fl |= ORC_RF_TIE;
+        }
+    }
+    const size_t p = (size_t)y * (size_t)K->width + (size_t)x;
+    if (hit_vol) hit_vol[p] = best_v >= 0 ? ids[best_v] : -1;
+    if (depth) depth[p] = best_v >= 0 ? best.tau : 0.0;
+    double n[3] = {0.0, 0.0, 0.0};
+    if (best_v >= 0 && best.cell_ok) {
+        const double gn = sqrt(best.grad[0] * best.grad[0] + best.grad[1] * best.grad[1] +
+                               best.grad[2] * best.grad[2]);
+        if (gn > 0.0) for (int a = 0; a < 3; ++a) n[a] = best.grad[a] / gn;
+        if (gn < 1e-3) fl |= ORC_RF_GRAD;
+    }
+    if (flags) flags[p] = fl;
+    if (normal) for (int a = 0; a < 3; ++a) normal[3 * p + a] = n[a];
+    if (vertex) for (int a = 0; a < 3; ++a) vertex[3 * p + a] = best_v >= 0 ? t[a] + best.tau * d[a] : 0.0;
+    if (rgba) {
+        for (int ch = 0; ch < 3; ++ch)
+            rgba[4 * p + ch] = (best_v >= 0 && best.cell_ok) ? (uint8_t)floor(best.rgb[ch] + 0.5) : 0;
+        rgba[4 * p + 3] = best_v >= 0 ? 255 : 0;
+    }
+}
+
 /* Raycast a view of all given volumes into one map (shortest distance wins).
  * Outputs (each may be NULL): depth[h*w] (0 = no hit), normal[h*w*3],
  * rgba[h*w*4], vertex[h*w*3], hit_vol[h*w] (-1 = no hit), flags[h*w].
@@ -422,56 +480,26 @@ ORC_EXPORT void orc_raycast(const orc_volume *vols, const int32_t *ids, int32_t 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t y = 0; y < H; ++y) {
         orc_hit hits[nvol > 0 ? nvol : 1];
-        for (int64_t x = 0; x < W; ++x) {
-            const double dc[3] = { ((double)x - K->cx) / K->fx, ((double)y - K->cy) / K->fy, 1.0 };
-            double d[3];
-            for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
-            orc_hit best;
-            memset(&best, 0, sizeof(best));
-            int32_t best_v = -1;
-            uint8_t fl = 0;
-            for (int32_t vi = 0; vi < nvol; ++vi) {
-                orc_hit hv = march_volume(&vols[vi], t, d, c);
-                fl |= hv.flags;
-                hits[vi] = hv;
-                if (!hv.hit) continue;
-                if (best_v < 0 || hv.tau < best.tau || (hv.tau == best.tau && ids[vi] < ids[best_v])) {
-                    best = hv;
-                    best_v = vi;
-                }
-            }
-            /* near-ties between volumes matter only where they disagree */
-            if (best_v >= 0) {
-                for (int32_t vi = 0; vi < nvol; ++vi) {
-                    if (vi == best_v || !hits[vi].hit) continue;
-                    if (fabs(hits[vi].tau - best.tau) > 1e-3 * vols[vi].s) continue;
-                    int differ = hits[vi].cell_ok != best.cell_ok;
-                    for (int a = 0; a < 3; ++a) {
-                        if (fabs(hits[vi].grad[a] - best.grad[a]) > 1e-6) differ = 1;
-                        if (fabs(hits[vi].rgb[a] - best.rgb[a]) > 1e-6) differ = 1;
-                    }
-                    if (differ) fl |= ORC_RF_TIE;
-                }
-            }
-            const size_t p = (size_t)y * (size_t)W + (size_t)x;
-            if (hit_vol) hit_vol[p] = best_v >= 0 ? ids[best_v] : -1;
-            if (flags) flags[p] = fl;
-            if (depth) depth[p] = best_v >= 0 ? best.tau : 0.0;
-            double n[3] = {0.0, 0.0, 0.0};
-            if (best_v >= 0 && best.cell_ok) {
-                const double gn = sqrt(best.grad[0] * best.grad[0] + best.grad[1] * best.grad[1] +
-                                       best.grad[2] * best.grad[2]);
-                if (gn > 0.0) for (int a = 0; a < 3; ++a) n[a] = best.grad[a] / gn;
-                if (gn < 1e-3 && flags) flags[p] |= ORC_RF_GRAD;
-            }
-            if (normal) for (int a = 0; a < 3; ++a) normal[3 * p + a] = n[a];
-            if (vertex) for (int a = 0; a < 3; ++a) vertex[3 * p + a] = best_v >= 0 ? t[a] + best.tau * d[a] : 0.0;
-            if (rgba) {
-                for (int ch = 0; ch < 3; ++ch)
-                    rgba[4 * p + ch] = (best_v >= 0 && best.cell_ok) ? (uint8_t)floor(best.rgb[ch] + 0.5) : 0;
-                rgba[4 * p + 3] = best_v >= 0 ? 255 : 0;
-            }
-        }
+        for (int64_t x = 0; x < W; ++x)
+            raycast_pixel(vols, ids, nvol, K, R, t, c, x, y, hits, depth, normal, rgba, vertex,
+                          hit_vol, flags);
+    }
+}
+
+/* The same for a list of pixels (linear indices y * width + x); outputs are
+ * full-size maps of which only the listed pixels are written. */
+ORC_EXPORT void orc_raycast_pixels(const orc_volume *vols, const int32_t *ids, int32_t nvol,
+                                   const orc_intrinsics *K, const double T[16], const orc_config *c,
+                                   const int64_t *pix, int64_t npix, double *depth, double *normal,
+                                   uint8_t *rgba, double *vertex, int32_t *hit_vol, uint8_t *flags)
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < npix; ++j) {
+        orc_hit hits[nvol > 0 ? nvol : 1];
+        raycast_pixel(vols, ids, nvol, K, R, t, c, pix[j] % K->width, pix[j] / K->width, hits,
+                      depth, normal, rgba, vertex, hit_vol, flags);
     }
 }
 

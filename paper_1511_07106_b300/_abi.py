@@ -1,0 +1,119 @@
+"""ctypes binding of the C ABI in ``include/mvtsdf.h`` (argument marshalling only).
+
+Every ``mv_*`` function of the header is exposed here under the same name with
+the same arguments; all computation happens in ``libmvtsdf.so``.  There is no
+fallback: if the library is missing or cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmvtsdf.so")
+
+MV_OK, MV_ERR_ARG, MV_ERR_OOM, MV_ERR_CUDA, MV_ERR_NOT_FOUND = 0, 1, 2, 3, 4
+MV_ERR_NOT_RESIDENT, MV_ERR_BUSY, MV_ERR_DEVICE_TIMEOUT, MV_ERR_CAPACITY = 5, 6, 7, 8
+STATUS_NAMES = {0: "MV_OK", 1: "MV_ERR_ARG", 2: "MV_ERR_OOM", 3: "MV_ERR_CUDA", 4: "MV_ERR_NOT_FOUND",
+                5: "MV_ERR_NOT_RESIDENT", 6: "MV_ERR_BUSY", 7: "MV_ERR_DEVICE_TIMEOUT",
+                8: "MV_ERR_CAPACITY"}
+MV_TSDF_F32, MV_TSDF_F16, MV_TSDF_I16 = 0, 1, 2
+FORMATS = {"f32": MV_TSDF_F32, "f16": MV_TSDF_F16, "i16": MV_TSDF_I16}
+
+
+class mv_intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class mv_config(C.Structure):
+    _fields_ = [("trunc_voxels", C.c_float), ("w_max", C.c_float), ("color_w_max", C.c_int32),
+                ("z_min", C.c_float), ("z_max", C.c_float), ("ray_step", C.c_float),
+                ("n_bisect", C.c_int32)]
+
+
+class mv_volume_desc(C.Structure):
+    _fields_ = [("h_t", C.c_int32 * 3), ("h_r", C.c_int32 * 3), ("voxel_size", C.c_float),
+                ("fmt", C.c_int32)]
+
+
+class mv_volume_info(C.Structure):
+    _fields_ = [("desc", mv_volume_desc), ("resident", C.c_int32), ("reserved", C.c_int32),
+                ("device_bytes", C.c_uint64), ("host_bytes", C.c_uint64)]
+
+
+class mv_stats(C.Structure):
+    _fields_ = [("swept", C.c_uint64), ("updated", C.c_uint64), ("band", C.c_uint64),
+                ("bricks", C.c_uint64)]
+
+
+MV_KERNEL_KINDS = 8
+KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags"}
+
+
+class mv_timings(C.Structure):
+    _fields_ = [("launches", C.c_uint64 * MV_KERNEL_KINDS), ("ms", C.c_double * MV_KERNEL_KINDS),
+                ("timed", C.c_uint64 * MV_KERNEL_KINDS)]
+
+
+_P = C.c_void_p
+_D16 = C.POINTER(C.c_double)
+_SIGNATURES = {
+    "mv_version": ([], C.c_char_p),
+    "mv_config_default": ([C.POINTER(mv_config)], C.c_int),
+    "mv_create": ([C.POINTER(mv_config), C.c_int32, C.POINTER(_P)], C.c_int),
+    "mv_destroy": ([_P], C.c_int),
+    "mv_last_error": ([_P], C.c_char_p),
+    "mv_add_volume": ([_P, C.POINTER(mv_volume_desc), C.POINTER(C.c_int32)], C.c_int),
+    "mv_remove_volume": ([_P, C.c_int32], C.c_int),
+    "mv_query": ([_P, C.c_int32, C.POINTER(mv_volume_info)], C.c_int),
+    "mv_list_volumes": ([_P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "mv_integrate": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
+    "mv_integrate_volume": ([_P, C.c_int32, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
+    "mv_raycast": ([_P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
+    "mv_raycast_volume": ([_P, C.c_int32, C.c_int32, C.POINTER(mv_intrinsics), _D16, _P, _P, _P,
+                           _P, _P, _P], C.c_int),
+    "mv_swap_out": ([_P, C.c_int32, _P], C.c_int),
+    "mv_swap_in": ([_P, C.c_int32, _P], C.c_int),
+    "mv_read_volume": ([_P, C.c_int32, _P, _P], C.c_int),
+    "mv_write_volume": ([_P, C.c_int32, _P, _P], C.c_int),
+    "mv_get_stats": ([_P, C.POINTER(mv_stats), C.c_int32], C.c_int),
+    "mv_set_timing": ([_P, C.c_int32], C.c_int),
+    "mv_get_timings": ([_P, C.POINTER(mv_timings), C.c_int32], C.c_int),
+    "mv_synchronize": ([_P], C.c_int),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libmvtsdf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1511_07106_b300.build` (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_functions():
+    return list(_SIGNATURES)
+
+
+class MVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def __getattr__(name):
+    # mv_* names resolve to the C functions themselves
+    if name in _SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)

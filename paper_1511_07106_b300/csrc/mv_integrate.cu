@@ -1,0 +1,396 @@
+// mv_integrate.cu -- projective TSDF + colour integration (sm_103a).
+//
+// Sec. Volumetric Integration / Algorithm 1 (first loop) of Salvato, Finman,
+// Leonard, arXiv 1511.07106.  The paper sweeps one thread per (x, y) column
+// over z for every voxel of every volume.  Here the sweep is restricted to
+// the 8x8x8 bricks of all resident volumes that intersect the camera
+// frustum: a work list is compacted on the device (brick_list_kernel) and a
+// persistent kernel (integrate_kernel) streams each listed brick through
+// registers: 4 voxels per thread, 128 threads per brick, 16- or 32-byte
+// vector loads/stores of contiguous brick storage.  The per-voxel arithmetic
+// is the paper's: position t_s = (h_t + t_l) s, projection to the nearest
+// pixel, projective distance, truncation, weighted running average.
+#include "mv_internal.cuh"
+
+namespace mv {
+
+// ---------------------------------------------------------------------------
+// per-call setup: camera position in every volume's voxel units
+// ---------------------------------------------------------------------------
+__global__ void frame_setup_kernel(const VolDev *__restrict__ vols, int nvol, FrameParams P,
+                                   VolFrame *__restrict__ vf, unsigned *__restrict__ counter)
+{
+    for (int v = threadIdx.x; v < nvol; v += blockDim.x) {
+        const double s = (double)vols[v].s;
+        VolFrame f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double q = P.t[a] / s;
+            const double fl = floor(q);
+            f.cam_int[a] = (int)fl;
+            f.cam_frac[a] = (float)(q - fl);
+        }
+        vf[v] = f;
+    }
+    if (threadIdx.x == 0 && counter) *counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// frustum test of one brick (conservative: never drops a brick that holds a
+// voxel the per-voxel test would update)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
+                                              const FrameParams &P, long long b)
+{
+    const int bx = (int)(b % v.nb[0]);
+    const int by = (int)((b / v.nb[0]) % v.nb[1]);
+    const int bz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
+    float lo[3], hi[3];
+    const int bi[3] = {bx, by, bz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int l = bi[a] * kBrick;
+        const int u = min(l + kBrick - 1, v.r[a] - 1);
+        lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
+        hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
+    }
+    // plane coefficients (camera frame, voxel units); inside when >= 0
+    const float kl = (P.cx + 0.5f) / P.fx, kr = ((float)P.width - 0.5f - P.cx) / P.fx;
+    const float kt = (P.cy + 0.5f) / P.fy, kb = ((float)P.height - 0.5f - P.cy) / P.fy;
+    const float zfar = P.z_max * v.inv_s + P.trunc_vox;
+    bool in_near = false, in_l = false, in_r = false, in_t = false, in_b = false, in_far = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float x = (c & 1) ? hi[0] : lo[0];
+        const float y = (c & 2) ? hi[1] : lo[1];
+        const float z = (c & 4) ? hi[2] : lo[2];
+        const float X = P.Rf[0] * x + P.Rf[3] * y + P.Rf[6] * z;
+        const float Y = P.Rf[1] * x + P.Rf[4] * y + P.Rf[7] * z;
+        const float Z = P.Rf[2] * x + P.Rf[5] * y + P.Rf[8] * z;
+        const float m = 1e-4f * (fabsf(X) + fabsf(Y) + fabsf(Z)) + 1e-3f;
+        in_near |= Z > -m;
+        in_l |= X + kl * Z > -m;
+        in_r |= kr * Z - X > -m;
+        in_t |= Y + kt * Z > -m;
+        in_b |= kb * Z - Y > -m;
+        in_far |= !(Z > zfar + m);
+    }
+    return in_near && in_l && in_r && in_t && in_b && in_far;
+}
+
+// One thread per brick; warp-aggregated append of visible bricks.
+// Bricks are indexed globally over [gb_begin, gb_begin + total) by the
+// prefix sums brick_base of the table.
+__global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restrict__ vols, int nvol,
+                                                         const VolFrame *__restrict__ vfs,
+                                                         FrameParams P, long long gb_begin,
+                                                         long long total, uint2 *__restrict__ list,
+                                                         unsigned *__restrict__ counter)
+{
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += stride) {
+        const long long g = base + lane;
+        bool vis = false;
+        int v = 0;
+        long long b = 0;
+        if (g < total) {
+            const long long gb = gb_begin + g;
+            int lo = 0, hi = nvol - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (vols[mid].brick_base <= gb) lo = mid; else hi = mid - 1;
+            }
+            v = lo;
+            b = gb - vols[v].brick_base;
+            vis = brick_visible(vols[v], vfs[v], P, b);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, vis);
+        unsigned pos = 0;
+        if (lane == 0 && mask) pos = atomicAdd(counter, (unsigned)__popc(mask));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, (unsigned)b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// integration of one brick by a 128-thread CTA
+// ---------------------------------------------------------------------------
+struct VoxelUpdate {
+    float f[4];      // truncated distance of this frame (units of mu)
+    int pix[4];      // pixel index (colour lookup)
+    unsigned upd;    // bit j: voxel j updated
+    unsigned band;   // bit j: voxel j within the colour band
+    unsigned inside; // bit j: voxel j inside the volume (not padding)
+};
+
+__device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &fr,
+                                               const FrameParams &P, long long b,
+                                               const float *__restrict__ depth, VoxelUpdate &u)
+{
+    const int t = threadIdx.x;
+    const int lx0 = (t & 1) * 4, ly = (t >> 1) & 7, lz = t >> 4;
+    const int bx = (int)(b % v.nb[0]);
+    const int by = (int)((b / v.nb[0]) % v.nb[1]);
+    const int bz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
+    const int gx = bx * kBrick + lx0, gy = by * kBrick + ly, gz = bz * kBrick + lz;
+    // voxel position relative to the camera, in voxel units: exact lattice
+    // difference minus the camera's sub-voxel fraction
+    const float rx = (float)(v.h[0] + gx - fr.cam_int[0]) - fr.cam_frac[0];
+    const float ry = (float)(v.h[1] + gy - fr.cam_int[1]) - fr.cam_frac[1];
+    const float rz = (float)(v.h[2] + gz - fr.cam_int[2]) - fr.cam_frac[2];
+    // camera coordinates p_c = R^T (p_w - t)
+    const float X0 = P.Rf[0] * rx + P.Rf[3] * ry + P.Rf[6] * rz;
+    const float Y0 = P.Rf[1] * rx + P.Rf[4] * ry + P.Rf[7] * rz;
+    const float Z0 = P.Rf[2] * rx + P.Rf[5] * ry + P.Rf[8] * rz;
+    const float mu = P.trunc_vox, inv_mu = 1.0f / P.trunc_vox;
+    const bool row_in = gy < v.r[1] && gz < v.r[2];
+    u.upd = u.band = u.inside = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        u.f[j] = 0.f;
+        u.pix[j] = 0;
+        if (!(row_in && gx + j < v.r[0])) continue;
+        u.inside |= 1u << j;
+        const float X = X0 + (float)j * P.Rf[0];
+        const float Y = Y0 + (float)j * P.Rf[1];
+        const float Z = Z0 + (float)j * P.Rf[2];
+        if (!(Z > 0.f)) continue;
+        const float iz = 1.0f / Z;
+        const float uf = fmaf(P.fx * X, iz, P.cx);
+        const float vf = fmaf(P.fy * Y, iz, P.cy);
+        const int ui = __float2int_rd(uf + 0.5f), vi = __float2int_rd(vf + 0.5f);
+        if (ui < 0 || vi < 0 || ui >= P.width || vi >= P.height) continue;
+        const int p = vi * P.width + ui;
+        const float D = __ldg(depth + p);
+        if (!(D > 0.f) || D < P.z_min || D > P.z_max) continue;
+        // projective distance along the voxel's ray, in voxels
+        const float lam = sqrtf(X * X + Y * Y + Z * Z) * iz;
+        const float sdf = (D * v.inv_s - Z) * lam;
+        if (sdf < -mu) continue;
+        u.f[j] = fminf(1.0f, sdf * inv_mu);
+        u.pix[j] = p;
+        u.upd |= 1u << j;
+        if (fabsf(sdf) < mu) u.band |= 1u << j;
+    }
+}
+
+__device__ __forceinline__ uint32_t blend_rgba(uint32_t old, const uint8_t *__restrict__ rgb, int p,
+                                               int cw_max)
+{
+    const int wc = (int)(old >> 24);
+    uint32_t out = 0u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const int c = (int)((old >> (8 * ch)) & 0xFFu);
+        const int x = (int)__ldg(rgb + 3 * p + ch);
+        const int num = c * wc + x;
+        // round half up of num / (wc + 1), in integers
+        const int nc = (2 * num + wc + 1) / (2 * (wc + 1));
+        out |= (uint32_t)nc << (8 * ch);
+    }
+    out |= (uint32_t)min(wc + 1, cw_max) << 24;
+    return out;
+}
+
+template <int FMT>
+__device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame &fr,
+                                                const FrameParams &P, long long b,
+                                                const float *__restrict__ depth,
+                                                const uint8_t *__restrict__ rgb,
+                                                unsigned long long &n_swept,
+                                                unsigned long long &n_upd,
+                                                unsigned long long &n_band)
+{
+    VoxelUpdate u;
+    project_voxels(v, fr, P, b, depth, u);
+    const int t = threadIdx.x;
+    const long long vox0 = b * kBrickVox + 4 * t;  // first of this thread's 4 voxels
+    bool all_pos = true;  // every voxel this thread updated is stored > 0
+
+    if (u.upd) {
+        const float wmax = P.w_max;
+        if (FMT == MV_TSDF_F32) {
+            float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(v.fw) + vox0);
+            float4 a = p[0], c = p[1];
+            float F[4] = {a.x, a.z, c.x, c.z}, W[4] = {a.y, a.w, c.y, c.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!((u.upd >> j) & 1u)) continue;
+                const float Fn = __fdiv_rn(fmaf(F[j], W[j], u.f[j]), W[j] + 1.0f);
+                W[j] = fminf(W[j] + 1.0f, wmax);
+                F[j] = Fn;
+                all_pos &= Fn > 0.f;
+            }
+            p[0] = make_float4(F[0], W[0], F[1], W[1]);
+            p[1] = make_float4(F[2], W[2], F[3], W[3]);
+        } else {
+            uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(v.fw) + vox0);
+            uint4 a = *p;
+            uint32_t q[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!((u.upd >> j) & 1u)) continue;
+                float F, W;
+                if (FMT == MV_TSDF_F16) decode_f16(q[j], F, W); else decode_i16(q[j], F, W);
+                const float Fn = __fdiv_rn(fmaf(F, W, u.f[j]), W + 1.0f);
+                const float Wn = fminf(W + 1.0f, wmax);
+                if (FMT == MV_TSDF_F16) {
+                    q[j] = encode_f16(Fn, Wn);
+                    all_pos &= stored_f16(Fn) > 0.f;
+                } else {
+                    q[j] = encode_i16(Fn, Wn);
+                    all_pos &= stored_i16(Fn) > 0.f;
+                }
+            }
+            *p = make_uint4(q[0], q[1], q[2], q[3]);
+        }
+        if (rgb && u.band) {
+            uint4 *pc = reinterpret_cast<uint4 *>(v.rgba + vox0);
+            uint4 c = *pc;
+            uint32_t cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((u.band >> j) & 1u) cc[j] = blend_rgba(cc[j], rgb, u.pix[j], P.color_w_max);
+            *pc = make_uint4(cc[0], cc[1], cc[2], cc[3]);
+        }
+    }
+    const int nu = __popc(u.upd);
+    n_swept += __popc(u.inside);
+    n_upd += nu;
+    if (rgb) n_band += __popc(u.band);
+
+    // brick flag maintenance (exact summaries, see mv_internal.cuh)
+    const int brick_upd = __syncthreads_count(nu);
+    const int brick_pos = __syncthreads_and(all_pos ? 1 : 0);
+    if (t == 0) {
+        const uint8_t old = v.bflag[b];
+        uint8_t nf = 0;
+        if (brick_pos && (brick_upd == kBrickVox || (old & kFlagFree))) nf |= kFlagFree;
+        if ((old & kFlagEmpty) && brick_upd == 0) nf |= kFlagEmpty;
+        if (nf != old) v.bflag[b] = nf;
+    }
+}
+
+__global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict__ vols,
+                                                        const VolFrame *__restrict__ vfs,
+                                                        const uint2 *__restrict__ list,
+                                                        const unsigned *__restrict__ counter,
+                                                        FrameParams P, const float *__restrict__ depth,
+                                                        const uint8_t *__restrict__ rgb,
+                                                        Stats *__restrict__ stats)
+{
+    const unsigned n = *counter;
+    unsigned long long n_swept = 0, n_upd = 0, n_band = 0, n_bricks = 0;
+    for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint2 it = list[i];
+        const VolDev &v = vols[it.x];
+        const VolFrame fr = vfs[it.x];
+        switch (v.fmt) {
+        case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
+        case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
+        default: integrate_brick<MV_TSDF_I16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
+        }
+        ++n_bricks;
+    }
+    // one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_swept += __shfl_down_sync(0xffffffffu, n_swept, o);
+        n_upd += __shfl_down_sync(0xffffffffu, n_upd, o);
+        n_band += __shfl_down_sync(0xffffffffu, n_band, o);
+    }
+    if ((threadIdx.x & 31) == 0 && stats) {
+        if (n_swept) atomicAdd(&stats->swept, n_swept);
+        if (n_upd) atomicAdd(&stats->updated, n_upd);
+        if (n_band) atomicAdd(&stats->band, n_band);
+        if (threadIdx.x == 0 && n_bricks) atomicAdd(&stats->bricks, n_bricks);
+    }
+}
+
+// Exact brick flags from the stored voxels (after a host write).
+template <int FMT>
+__device__ __forceinline__ void voxel_state(const VolDev &v, long long off, bool &valid, bool &pos)
+{
+    float F, W;
+    if (FMT == MV_TSDF_F32) {
+        const float2 q = reinterpret_cast<const float2 *>(v.fw)[off];
+        F = q.x; W = q.y;
+    } else {
+        const uint32_t q = reinterpret_cast<const uint32_t *>(v.fw)[off];
+        if (FMT == MV_TSDF_F16) decode_f16(q, F, W); else decode_i16(q, F, W);
+    }
+    valid = W > 0.f;
+    pos = F > 0.f;
+}
+
+__global__ void __launch_bounds__(128) brick_flags_kernel(VolDev v)
+{
+    for (long long b = blockIdx.x; b < v.nbricks; b += gridDim.x) {
+        bool all_free = true, all_empty = true;
+        for (int k = threadIdx.x; k < kBrickVox; k += blockDim.x) {
+            bool valid, pos;
+            const long long off = b * kBrickVox + k;
+            if (v.fmt == MV_TSDF_F32) voxel_state<MV_TSDF_F32>(v, off, valid, pos);
+            else if (v.fmt == MV_TSDF_F16) voxel_state<MV_TSDF_F16>(v, off, valid, pos);
+            else voxel_state<MV_TSDF_I16>(v, off, valid, pos);
+            all_free &= valid && pos;
+            all_empty &= !valid;
+        }
+        const int f = __syncthreads_and(all_free ? 1 : 0);
+        const int e = __syncthreads_and(all_empty ? 1 : 0);
+        if (threadIdx.x == 0) v.bflag[b] = (uint8_t)((f ? kFlagFree : 0) | (e ? kFlagEmpty : 0));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_frame_setup(const VolDev *vols, int nvol, const FrameParams &P, VolFrame *vf,
+                               unsigned *counter, cudaStream_t s)
+{
+    frame_setup_kernel<<<1, 256, 0, s>>>(vols, nvol, P, vf, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_list(const VolDev *vols, int nvol, const VolFrame *vfs,
+                              const FrameParams &P, long long gb_begin, long long total,
+                              uint2 *list, unsigned *counter, int num_sms, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    brick_list_kernel<<<(unsigned)blocks, 256, 0, s>>>(vols, nvol, vfs, P, gb_begin, total, list, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const VolDev *vols, const VolFrame *vfs, const uint2 *list,
+                             const unsigned *counter, const FrameParams &P, const float *depth,
+                             const uint8_t *rgb, Stats *stats, int grid, cudaStream_t s)
+{
+    integrate_kernel<<<grid, 128, 0, s>>>(vols, vfs, list, counter, P, depth, rgb, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_flags(const VolDev &v, int num_sms, cudaStream_t s)
+{
+    long long blocks = v.nbricks;
+    const long long cap = (long long)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    brick_flags_kernel<<<(unsigned)blocks, 128, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+int integrate_occupancy_grid(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel, 128, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 8;
+    return num_sms * per_sm;
+}
+
+}  // namespace mv

@@ -1,0 +1,112 @@
+// mv_internal.cuh -- device-side data structures shared by the kernels and the
+// runtime of the multi-volume TSDF library (sm_103a).
+//
+// Volume storage is brick-major: a volume of h_r voxels per axis is padded to
+// whole 8x8x8 bricks; brick (bx, by, bz) is stored contiguously at brick index
+// (bz * nby + by) * nbx + bx, and inside a brick voxel (lx, ly, lz) sits at
+// (lz * 8 + ly) * 8 + lx.  Padding voxels (index >= h_r) are never integrated
+// and keep W = 0.  Every brick also has one flag byte summarising its voxels
+// (all observed and positive / all unobserved), maintained by the integration
+// kernel and used by the raycast to step over whole bricks exactly.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mvtsdf.h"
+
+namespace mv {
+
+constexpr int kBrick = 8;
+constexpr int kBrickVox = 512;
+constexpr uint8_t kFlagFree = 1;   // every voxel of the brick has W > 0 and F > 0
+constexpr uint8_t kFlagEmpty = 2;  // every voxel of the brick has W == 0
+constexpr int kMaxVolumes = 4096;
+
+// One volume as the kernels see it.
+struct VolDev {
+    void *fw;          // brick-major TSDF+weight storage (8 B/voxel F32, 4 B/voxel F16/I16)
+    uint32_t *rgba;    // brick-major RGBA8, A = colour weight
+    uint8_t *bflag;    // one flag byte per brick
+    int h[3];          // lattice offset h_t
+    int r[3];          // voxels per axis h_r
+    int nb[3];         // bricks per axis
+    float s, inv_s;    // pitch and its reciprocal
+    int fmt;           // mv_tsdf_fmt
+    int id;            // public id (merge tie-break)
+    long long brick_base;  // prefix sum of nbricks over the table (work-list indexing)
+    long long nbricks;
+};
+
+// Camera position in one volume's global voxel units, split into an exact
+// integer lattice part and a fraction in [0, 1): positions relative to the
+// camera are then formed as (integer difference) - fraction in float32
+// without losing the lattice alignment shared by volumes of equal pitch.
+struct VolFrame {
+    int cam_int[3];
+    float cam_frac[3];
+};
+
+// Per-call parameters, passed by value.
+struct FrameParams {
+    double R[9];       // camera-to-world rotation, row-major
+    double t[3];       // camera centre, metres
+    float Rf[9];
+    float fx, fy, cx, cy;
+    int width, height;
+    float z_min, z_max;
+    float trunc_vox;
+    float w_max;
+    int color_w_max;
+    float ray_step;
+    int n_bisect;
+};
+
+struct Stats {
+    unsigned long long swept, updated, band, bricks;
+};
+
+// ---------------------------------------------------------------------------
+// storage codecs: decode to / encode from float32 (F in units of mu, W count)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void decode_f16(uint32_t v, float &F, float &W)
+{
+    F = __half2float(__ushort_as_half((unsigned short)(v & 0xFFFFu)));
+    W = (float)(v >> 16);
+}
+__device__ __forceinline__ uint32_t encode_f16(float F, float W)
+{
+    return (uint32_t)__half_as_ushort(__float2half_rn(F)) | ((uint32_t)W << 16);
+}
+__device__ __forceinline__ void decode_i16(uint32_t v, float &F, float &W)
+{
+    F = (float)(short)(v & 0xFFFFu) * (1.0f / 32767.0f);
+    W = (float)(v >> 16);
+}
+__device__ __forceinline__ uint32_t encode_i16(float F, float W)
+{
+    int q = __float2int_rn(F * 32767.0f);
+    q = max(-32767, min(32767, q));
+    return (uint32_t)(unsigned short)(short)q | ((uint32_t)W << 16);
+}
+
+// decoded value of a just-encoded F (the sign that is actually stored)
+__device__ __forceinline__ float stored_f16(float F)
+{
+    return __half2float(__float2half_rn(F));
+}
+__device__ __forceinline__ float stored_i16(float F)
+{
+    int q = __float2int_rn(F * 32767.0f);
+    return (float)max(-32767, min(32767, q));
+}
+
+// element offset of voxel (x, y, z) in brick-major order
+__device__ __forceinline__ long long vox_offset(const VolDev &v, int x, int y, int z)
+{
+    const long long b = ((long long)(z >> 3) * v.nb[1] + (y >> 3)) * v.nb[0] + (x >> 3);
+    return b * kBrickVox + (((z & 7) << 6) | ((y & 7) << 3) | (x & 7));
+}
+
+}  // namespace mv

@@ -1,0 +1,383 @@
+// mv_raycast.cu -- per-pixel raycast of all resident volumes (sm_103a).
+//
+// Sec. Raycasting / Algorithm 1 (second loop) of Salvato, Finman, Leonard,
+// arXiv 1511.07106: each pixel's ray is marched through each volume, the
+// zero crossing of the trilinearly interpolated TSDF gives the vertex, the
+// TSDF derivative there gives the normal, and all volumes write one map where
+// the shortest ray distance wins.
+//
+// March semantics (identical to the FP64 oracle): samples lie on the global
+// grid tau_k = k * Delta, Delta = step * s / |d|, positions are taken in
+// global voxel coordinates (the paper's t_r; volume coordinates t_r - h_t),
+// a sample is valid when the 8 corners of its cell are observed (W > 0), and
+// the first pair of consecutive valid samples going from F > 0 to F <= 0
+// brackets the surface, refined by bisection and a final secant step.
+//
+// B300 design: one thread per pixel, 8x4-pixel warp tiles for gather
+// locality, every volume of the view in one launch with the nearest hit kept
+// in registers.  Free space is crossed brick by brick: when the sample's
+// 8x8x8 cell brick is known to hold only observed positive voxels (or only
+// unobserved ones) every grid sample inside it would be valid-positive (or
+// invalid), so the march jumps to the brick's last sample without reading
+// voxels -- an exact shortcut, not an approximation.
+#include <float.h>
+#include <limits.h>
+
+#include "mv_internal.cuh"
+
+namespace mv {
+
+struct RayOut {
+    float *depth;
+    float *normal;
+    uint32_t *rgba;
+    float *vertex;
+    int *vol_id;
+};
+
+template <int FMT>
+__device__ __forceinline__ void load_fw(const VolDev &v, long long off, float &F, float &W)
+{
+    if (FMT == MV_TSDF_F32) {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(v.fw) + off);
+        F = q.x;
+        W = q.y;
+    } else {
+        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(v.fw) + off);
+        if (FMT == MV_TSDF_F16) decode_f16(q, F, W); else decode_i16(q, F, W);
+    }
+}
+
+// Offsets of the 8 corners of the cell with lower corner (x, y, z).
+struct Corners {
+    long long base;
+    long long ox, oy, oz;
+};
+
+__device__ __forceinline__ Corners cell_corners(const VolDev &v, int x, int y, int z)
+{
+    Corners c;
+    c.base = vox_offset(v, x, y, z);
+    c.ox = ((x & 7) == 7) ? (long long)(kBrickVox - 7) : 1;
+    c.oy = ((y & 7) == 7) ? (long long)v.nb[0] * kBrickVox - 56 : 8;
+    c.oz = ((z & 7) == 7) ? (long long)v.nb[0] * v.nb[1] * kBrickVox - 448 : 64;
+    return c;
+}
+
+// Trilinear F in a cell; valid = all 8 corners observed.
+template <int FMT>
+__device__ __forceinline__ float trilinear(const VolDev &v, const Corners &c, float fx, float fy,
+                                           float fz, bool &valid)
+{
+    float F[8], W[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long off = c.base + ((k & 1) ? c.ox : 0) + ((k & 2) ? c.oy : 0) + ((k & 4) ? c.oz : 0);
+        load_fw<FMT>(v, off, F[k], W[k]);
+    }
+    valid = (W[0] > 0.f) & (W[1] > 0.f) & (W[2] > 0.f) & (W[3] > 0.f) & (W[4] > 0.f) &
+            (W[5] > 0.f) & (W[6] > 0.f) & (W[7] > 0.f);
+    const float x00 = fmaf(fx, F[1] - F[0], F[0]);
+    const float x10 = fmaf(fx, F[3] - F[2], F[2]);
+    const float x01 = fmaf(fx, F[5] - F[4], F[4]);
+    const float x11 = fmaf(fx, F[7] - F[6], F[6]);
+    const float y0 = fmaf(fy, x10 - x00, x00);
+    const float y1 = fmaf(fy, x11 - x01, x01);
+    return fmaf(fz, y1 - y0, y0);
+}
+
+// Per-volume ray state in this volume's global voxel units, relative to the
+// camera's lattice point cam_int: sample k sits at rr(k) = cam_frac + k * dq.
+struct VolRay {
+    float fr[3];   // cam_frac
+    float dq[3];   // grid step in voxels
+    int oi[3];     // cam_int - h_t (local index of the camera's lattice point)
+};
+
+// Cell (local, clamped) and fractions of the point rr (camera-relative).
+__device__ __forceinline__ void locate(const VolDev &v, const VolRay &vr, const float rr[3],
+                                       int cell[3], float f[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float fl = floorf(rr[a]);
+        int c = (int)fl + vr.oi[a];
+        c = max(0, min(v.r[a] - 2, c));
+        cell[a] = c;
+        f[a] = rr[a] - (float)(c - vr.oi[a]);
+    }
+}
+
+template <int FMT>
+__device__ __forceinline__ float eval_at(const VolDev &v, const VolRay &vr, float k, bool &valid)
+{
+    float rr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+    int cell[3];
+    float f[3];
+    locate(v, vr, rr, cell, f);
+    const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+    return trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
+}
+
+__device__ __forceinline__ uint8_t brick_flag_or_free(const VolDev &v, int bx, int by, int bz)
+{
+    if (bx >= v.nb[0] || by >= v.nb[1] || bz >= v.nb[2]) return kFlagFree;
+    return __ldg(v.bflag + ((long long)bz * v.nb[1] + by) * v.nb[0] + bx);
+}
+
+struct Hit {
+    float tau;
+    int id;
+    int slot;
+    float n[3];
+    uint32_t rgba;
+};
+
+// Gradient (normal) and colour in the hit cell.
+template <int FMT>
+__device__ __forceinline__ void shade(const VolDev &v, const VolRay &vr, float ks, Hit &h)
+{
+    float rr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rr[a] = fmaf(ks, vr.dq[a], vr.fr[a]);
+    int cell[3];
+    float f[3];
+    locate(v, vr, rr, cell, f);
+    const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+    float F[8], W[8];
+    uint32_t col[8];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long off = c.base + ((k & 1) ? c.ox : 0) + ((k & 2) ? c.oy : 0) + ((k & 4) ? c.oz : 0);
+        load_fw<FMT>(v, off, F[k], W[k]);
+        col[k] = __ldg(v.rgba + off);
+        ok &= W[k] > 0.f;
+    }
+    h.n[0] = h.n[1] = h.n[2] = 0.f;
+    h.rgba = 0xFF000000u;
+    if (!ok) return;
+    const float x = f[0], y = f[1], z = f[2];
+    float g[3] = {0.f, 0.f, 0.f};
+    float rgb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float wx = (k & 1) ? x : 1.f - x;
+        const float wy = (k & 2) ? y : 1.f - y;
+        const float wz = (k & 4) ? z : 1.f - z;
+        g[0] += ((k & 1) ? 1.f : -1.f) * wy * wz * F[k];
+        g[1] += wx * ((k & 2) ? 1.f : -1.f) * wz * F[k];
+        g[2] += wx * wy * ((k & 4) ? 1.f : -1.f) * F[k];
+        const float w = wx * wy * wz;
+        rgb[0] += w * (float)(col[k] & 0xFFu);
+        rgb[1] += w * (float)((col[k] >> 8) & 0xFFu);
+        rgb[2] += w * (float)((col[k] >> 16) & 0xFFu);
+    }
+    const float gn2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (gn2 > 0.f) {
+        const float inv = rsqrtf(gn2);
+        h.n[0] = g[0] * inv;
+        h.n[1] = g[1] * inv;
+        h.n[2] = g[2] * inv;
+    }
+    uint32_t out = 0xFF000000u;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const int cv = min(255, max(0, (int)floorf(rgb[ch] + 0.5f)));
+        out |= (uint32_t)cv << (8 * ch);
+    }
+    h.rgba = out;
+}
+
+// March one ray through one volume; updates `best` when this volume's hit is
+// nearer (or equally near with a lower id).
+template <int FMT>
+__device__ void march_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
+                             const float d[3], float dn, int slot, Hit &best)
+{
+    VolRay vr;
+    float dirv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vr.fr[a] = vf.cam_frac[a];
+        vr.oi[a] = vf.cam_int[a] - v.h[a];
+        dirv[a] = d[a] * v.inv_s;
+    }
+    // domain [h_t, h_t + r - 1] in camera-relative coordinates
+    float lo = P.z_min, hi = P.z_max;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float bmin = (float)(-vr.oi[a]) - vr.fr[a];
+        const float bmax = (float)(v.r[a] - 1 - vr.oi[a]) - vr.fr[a];
+        if (dirv[a] == 0.f) {
+            if (bmin > 0.f || bmax < 0.f) return;
+            continue;
+        }
+        const float inv = 1.0f / dirv[a];
+        float t0 = bmin * inv, t1 = bmax * inv;
+        if (t0 > t1) { const float tt = t0; t0 = t1; t1 = tt; }
+        lo = fmaxf(lo, t0);
+        hi = fminf(hi, t1);
+    }
+    if (!(lo <= hi)) return;
+    if (lo > best.tau) return;  // cannot beat the current nearest hit
+    const float Delta = P.ray_step * v.s / dn;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vr.dq[a] = dirv[a] * Delta;
+    const float k0 = ceilf(lo / Delta), k1 = floorf(hi / Delta);
+    if (!(k1 >= k0)) return;
+    // integer trip count: bounded even where float k would stop advancing
+    // (the domain spans at most sqrt(3) * 8192 / (1/64) grid steps)
+    const int nk = (int)fminf(k1 - k0, 1.0e6f);
+    const float m = 1e-3f;  // safety margin (voxels) of the brick shortcut
+
+    int state = 0;  // 0: no valid previous sample, 1: previous valid > 0, -1: previous valid <= 0
+    float Fprev = 0.f;
+    bool prev_read = false;  // Fprev was read (not implied by a brick shortcut)
+    for (int kk = 0; kk <= nk; ++kk) {
+        const float k = k0 + (float)kk;
+        float rr[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+        // exact free-space / unobserved-space shortcut
+        {
+            float L[3];
+            int bi[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                L[a] = (float)vr.oi[a] + rr[a];
+                bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
+            }
+            const uint8_t f0 = brick_flag_or_free(v, bi[0], bi[1], bi[2]);
+            bool free_cell = false;
+            if (f0 & kFlagFree) {
+                free_cell = true;
+#pragma unroll
+                for (int c = 1; c < 8; ++c)
+                    free_cell &= (brick_flag_or_free(v, bi[0] + (c & 1), bi[1] + ((c >> 1) & 1),
+                                                     bi[2] + ((c >> 2) & 1)) & kFlagFree) != 0;
+            }
+            if (free_cell || (f0 & kFlagEmpty)) {
+                float steps = FLT_MAX;
+                bool inside = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float blo = (float)(bi[a] * kBrick) + m;
+                    const float bhi = (float)min(bi[a] * kBrick + kBrick, v.r[a] - 1) - m;
+                    inside &= (L[a] >= blo) & (L[a] <= bhi);
+                    if (vr.dq[a] > 0.f) steps = fminf(steps, (bhi - L[a]) / vr.dq[a]);
+                    else if (vr.dq[a] < 0.f) steps = fminf(steps, (blo - L[a]) / vr.dq[a]);
+                }
+                if (inside && steps >= 0.f) {
+                    // samples k .. k + skip are all valid-positive (or all invalid)
+                    const int skip = (int)fminf(floorf(steps), (float)(nk - kk));
+                    state = free_cell ? 1 : 0;
+                    prev_read = false;
+                    kk += skip;
+                    continue;
+                }
+            }
+        }
+        int cell[3];
+        float f[3];
+        locate(v, vr, rr, cell, f);
+        const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+        bool valid;
+        const float F = trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
+        if (!valid) { state = 0; continue; }
+        if (state == 1 && F <= 0.f) {
+            // bracket (k-1, k]: bisection on the interpolant, then a secant step
+            float a = k - 1.0f, b = k, ga = Fprev, gb = F;
+            if (!prev_read) {
+                bool vv;
+                ga = eval_at<FMT>(v, vr, a, vv);
+            }
+            for (int it = 0; it < P.n_bisect; ++it) {
+                const float mid = 0.5f * (a + b);
+                bool vv;
+                const float g = eval_at<FMT>(v, vr, mid, vv);
+                if (g > 0.f) { a = mid; ga = g; } else { b = mid; gb = g; }
+            }
+            const float den = ga - gb;
+            const float ks = den > 0.f ? fmaf(b - a, ga / den, a) : 0.5f * (a + b);
+            const float tau = ks * Delta;
+            if (tau < best.tau || (tau == best.tau && v.id < best.id)) {
+                best.tau = tau;
+                best.id = v.id;
+                best.slot = slot;
+                shade<FMT>(v, vr, ks, best);
+            }
+            return;
+        }
+        state = (F > 0.f) ? 1 : -1;
+        Fprev = F;
+        prev_read = true;
+    }
+}
+
+__global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__ vols,
+                                                      const VolFrame *__restrict__ vfs, int nvol,
+                                                      FrameParams P, RayOut out, int merge)
+{
+    // 16x8-pixel CTA; each warp covers an 8x4 tile
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * 16 + (w & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (w >> 1) * 4 + (lane >> 3);
+    if (px >= P.width || py >= P.height) return;
+    const float dc0 = ((float)px - P.cx) / P.fx, dc1 = ((float)py - P.cy) / P.fy;
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = P.Rf[3 * a] * dc0 + P.Rf[3 * a + 1] * dc1 + P.Rf[3 * a + 2];
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+
+    Hit best;
+    best.tau = FLT_MAX;
+    best.id = INT_MAX;
+    best.slot = -1;
+    best.n[0] = best.n[1] = best.n[2] = 0.f;
+    best.rgba = 0u;
+    const size_t p = (size_t)py * P.width + px;
+    if (merge && out.depth[p] > 0.f) {
+        best.tau = out.depth[p];
+        best.id = out.vol_id[p];
+        best.slot = -2;  // existing entry
+    }
+    for (int i = 0; i < nvol; ++i) {
+        const VolDev &v = vols[i];
+        const VolFrame vf = vfs[i];
+        switch (v.fmt) {
+        case MV_TSDF_F32: march_volume<MV_TSDF_F32>(v, vf, P, d, dn, i, best); break;
+        case MV_TSDF_F16: march_volume<MV_TSDF_F16>(v, vf, P, d, dn, i, best); break;
+        default: march_volume<MV_TSDF_I16>(v, vf, P, d, dn, i, best); break;
+        }
+    }
+    if (best.slot == -2) return;  // merge: the existing entry stays
+    const bool hit = best.slot >= 0;
+    if (out.depth) out.depth[p] = hit ? best.tau : 0.f;
+    if (out.vol_id) out.vol_id[p] = hit ? best.id : -1;
+    if (out.normal) {
+        out.normal[3 * p + 0] = hit ? best.n[0] : 0.f;
+        out.normal[3 * p + 1] = hit ? best.n[1] : 0.f;
+        out.normal[3 * p + 2] = hit ? best.n[2] : 0.f;
+    }
+    if (out.rgba) out.rgba[p] = hit ? best.rgba : 0u;
+    if (out.vertex) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            out.vertex[3 * p + a] = hit ? (float)P.t[a] + best.tau * d[a] : 0.f;
+    }
+}
+
+cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,
+                           float *depth, float *normal, uint8_t *rgba, float *vertex, int *vol_id,
+                           int merge, cudaStream_t s)
+{
+    RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
+    dim3 grid((P.width + 15) / 16, (P.height + 7) / 8);
+    raycast_kernel<<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge);
+    return cudaGetLastError();
+}
+
+}  // namespace mv

@@ -1,0 +1,837 @@
+// mv_runtime.cu -- host runtime behind the C ABI of include/mvtsdf.h.
+//
+// Owns the volume registry (the paper's set H of subvolumes, Sec. Dynamic
+// Volume Allocation), the device table of resident volumes that the batched
+// kernels index, the per-call scratch (brick work list, per-volume camera
+// constants, counters), and the swap engine that moves volumes between GPU
+// memory and pinned host memory on a side stream (Sec. Memory Passing).
+//
+// Ordering: every call that queues GPU work waits (cudaStreamWaitEvent) for
+// the previous call's work, so calls on one context execute in call order
+// whatever streams they are given.  Volume storage is allocated and freed
+// stream-ordered (cudaMallocAsync / cudaFreeAsync) on the swap stream, so
+// swapping a volume out never blocks the host or the compute stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mv_internal.cuh"
+
+namespace mv {
+cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t);
+cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
+                              long long, uint2 *, unsigned *, int, cudaStream_t);
+cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
+                             const FrameParams &, const float *, const uint8_t *, Stats *, int,
+                             cudaStream_t);
+cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
+cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
+                           float *, uint8_t *, float *, int *, int, cudaStream_t);
+int integrate_occupancy_grid(int num_sms);
+}  // namespace mv
+
+using namespace mv;
+
+namespace {
+
+struct Volume {
+    int id = -1;
+    mv_volume_desc desc{};
+    int nb[3] = {0, 0, 0};
+    long long nbricks = 0;
+    size_t fw_bytes = 0, rgba_bytes = 0, flag_bytes = 0;
+    void *d_fw = nullptr;
+    uint32_t *d_rgba = nullptr;
+    uint8_t *d_flag = nullptr;
+    void *h_fw = nullptr;
+    uint32_t *h_rgba = nullptr;
+    uint8_t *h_flag = nullptr;
+    bool resident = false;
+    cudaEvent_t ready = nullptr;  // allocation / swap-in copy finished
+    bool ready_pending = false;
+};
+
+size_t fw_elem_bytes(int fmt) { return fmt == MV_TSDF_F32 ? 8 : 4; }
+
+}  // namespace
+
+struct mv_ctx {
+    mv_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    int grid_integrate = 0;
+    std::map<int, Volume *> vols;
+    int next_id = 0;
+    cudaStream_t swap_stream = nullptr;
+    cudaEvent_t last_event = nullptr;
+    bool last_recorded = false;
+    // device table of resident volumes (sorted by id)
+    std::vector<VolDev> table;
+    std::vector<int> table_ids;
+    bool table_dirty = true;
+    VolDev *d_table = nullptr;
+    VolFrame *d_vf = nullptr;
+    uint2 *d_list = nullptr;
+    size_t list_cap = 0;  // entries
+    unsigned *d_counter = nullptr;
+    Stats *d_stats = nullptr;
+    // per-kernel launch counts and optional event timing
+    bool timing = false;
+    struct Timed { int kind; cudaEvent_t a, b; };
+    std::vector<Timed> timed_pending;
+    std::vector<cudaEvent_t> event_pool;
+    uint64_t launches[MV_KERNEL_KINDS] = {};
+    double ms[MV_KERNEL_KINDS] = {};
+    uint64_t timed[MV_KERNEL_KINDS] = {};
+    std::string err;
+};
+
+namespace {
+
+mv_status fail(mv_ctx *c, mv_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+mv_status cuda_fail(mv_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? MV_ERR_OOM : MV_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MV_CUDA(c, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+bool valid_config(const mv_config &c)
+{
+    return c.trunc_voxels > 0.f && std::isfinite(c.trunc_voxels) && c.w_max >= 1.f &&
+           c.w_max <= 1e30f && c.color_w_max >= 1 && c.color_w_max <= 255 && c.z_min >= 0.f &&
+           c.z_max > c.z_min && c.ray_step >= 1.0f / 64.0f && c.ray_step <= 1.f && c.n_bisect >= 0 &&
+           c.n_bisect <= 64;
+}
+
+FrameParams make_params(const mv_ctx *c, const mv_intrinsics *K, const double T[16])
+{
+    FrameParams P;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            P.R[3 * a + b] = T[4 * a + b];
+            P.Rf[3 * a + b] = (float)T[4 * a + b];
+        }
+        P.t[a] = T[4 * a + 3];
+    }
+    P.fx = K->fx; P.fy = K->fy; P.cx = K->cx; P.cy = K->cy;
+    P.width = K->width; P.height = K->height;
+    P.z_min = c->cfg.z_min; P.z_max = c->cfg.z_max;
+    P.trunc_vox = c->cfg.trunc_voxels;
+    P.w_max = c->cfg.w_max;
+    P.color_w_max = c->cfg.color_w_max;
+    P.ray_step = c->cfg.ray_step;
+    P.n_bisect = c->cfg.n_bisect;
+    return P;
+}
+
+bool valid_frame(const mv_intrinsics *K, const double *T)
+{
+    if (!K || !T) return false;
+    if (K->width <= 0 || K->height <= 0 || K->width > 16384 || K->height > 16384) return false;
+    if (!(K->fx > 0.f) || !(K->fy > 0.f) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
+        !std::isfinite(K->cx) || !std::isfinite(K->cy))
+        return false;
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T[i])) return false;
+    return true;
+}
+
+VolDev make_voldev(const Volume &v)
+{
+    VolDev d{};
+    d.fw = v.d_fw;
+    d.rgba = v.d_rgba;
+    d.bflag = v.d_flag;
+    for (int a = 0; a < 3; ++a) {
+        d.h[a] = v.desc.h_t[a];
+        d.r[a] = v.desc.h_r[a];
+        d.nb[a] = v.nb[a];
+    }
+    d.s = v.desc.voxel_size;
+    d.inv_s = 1.0f / v.desc.voxel_size;
+    d.fmt = v.desc.fmt;
+    d.id = v.id;
+    d.nbricks = v.nbricks;
+    return d;
+}
+
+// Order this call after the previous call and after pending volume copies;
+// refresh the device table when the resident set changed.
+mv_status begin_call(mv_ctx *c, cudaStream_t s)
+{
+    if (c->last_recorded) MV_CUDA(c, cudaStreamWaitEvent(s, c->last_event, 0));
+    for (auto &kv : c->vols) {
+        Volume *v = kv.second;
+        if (!v->ready_pending) continue;
+        if (cudaEventQuery(v->ready) == cudaSuccess) {
+            v->ready_pending = false;
+            continue;
+        }
+        MV_CUDA(c, cudaStreamWaitEvent(s, v->ready, 0));
+    }
+    if (c->table_dirty) {
+        c->table.clear();
+        c->table_ids.clear();
+        long long base = 0;
+        for (auto &kv : c->vols) {
+            Volume *v = kv.second;
+            if (!v->resident) continue;
+            VolDev d = make_voldev(*v);
+            d.brick_base = base;
+            base += v->nbricks;
+            c->table.push_back(d);
+            c->table_ids.push_back(v->id);
+        }
+        if (!c->table.empty())
+            MV_CUDA(c, cudaMemcpyAsync(c->d_table, c->table.data(), c->table.size() * sizeof(VolDev),
+                                       cudaMemcpyHostToDevice, s));
+        // the work list holds at most one entry per resident brick
+        if ((size_t)base > c->list_cap) {
+            if (c->d_list) MV_CUDA(c, cudaFreeAsync(c->d_list, s));
+            c->d_list = nullptr;
+            c->list_cap = 0;
+            MV_CUDA(c, cudaMallocAsync((void **)&c->d_list, (size_t)base * sizeof(uint2), s));
+            c->list_cap = (size_t)base;
+        }
+        c->table_dirty = false;
+    }
+    return MV_OK;
+}
+
+mv_status end_call(mv_ctx *c, cudaStream_t s)
+{
+    MV_CUDA(c, cudaEventRecord(c->last_event, s));
+    c->last_recorded = true;
+    return MV_OK;
+}
+
+cudaEvent_t pool_event(mv_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch one kernel (a callable returning cudaError_t), counting it and, when
+// timing is on, bracketing it with events on its stream.
+template <typename F>
+cudaError_t counted_launch(mv_ctx *c, int kind, cudaStream_t s, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->timing) {
+        a = pool_event(c);
+        b = pool_event(c);
+        if (a && b) cudaEventRecord(a, s);
+    }
+    cudaError_t e = launch();
+    c->launches[kind] += 1;
+    if (a && b) {
+        cudaEventRecord(b, s);
+        c->timed_pending.push_back({kind, a, b});
+    } else {
+        if (a) c->event_pool.push_back(a);
+        if (b) c->event_pool.push_back(b);
+    }
+    return e;
+}
+
+mv_status collect_timings(mv_ctx *c)
+{
+    for (auto &t : c->timed_pending) {
+        MV_CUDA(c, cudaEventSynchronize(t.b));
+        float ms = 0.f;
+        MV_CUDA(c, cudaEventElapsedTime(&ms, t.a, t.b));
+        c->ms[t.kind] += ms;
+        c->timed[t.kind] += 1;
+        c->event_pool.push_back(t.a);
+        c->event_pool.push_back(t.b);
+    }
+    c->timed_pending.clear();
+    return MV_OK;
+}
+
+int table_slot(const mv_ctx *c, int id)
+{
+    auto it = std::lower_bound(c->table_ids.begin(), c->table_ids.end(), id);
+    if (it == c->table_ids.end() || *it != id) return -1;
+    return (int)(it - c->table_ids.begin());
+}
+
+mv_status find_volume(mv_ctx *c, int32_t id, Volume **out)
+{
+    auto it = c->vols.find(id);
+    if (it == c->vols.end()) return fail(c, MV_ERR_NOT_FOUND, "no volume with id " + std::to_string(id));
+    *out = it->second;
+    return MV_OK;
+}
+
+mv_status wait_all(mv_ctx *c)
+{
+    if (c->last_recorded) MV_CUDA(c, cudaEventSynchronize(c->last_event));
+    MV_CUDA(c, cudaStreamSynchronize(c->swap_stream));
+    return MV_OK;
+}
+
+// brick-major <-> linear conversion on the host
+template <typename T>
+void bricks_to_linear(const Volume &v, const T *src, T *dst)
+{
+    const int rx = v.desc.h_r[0], ry = v.desc.h_r[1], rz = v.desc.h_r[2];
+    for (int z = 0; z < rz; ++z)
+        for (int y = 0; y < ry; ++y) {
+            const long long rowb = ((long long)(z >> 3) * v.nb[1] + (y >> 3)) * v.nb[0];
+            const int inner = ((z & 7) << 6) | ((y & 7) << 3);
+            T *d = dst + ((size_t)z * ry + y) * rx;
+            for (int x = 0; x < rx; ++x)
+                d[x] = src[(rowb + (x >> 3)) * kBrickVox + inner + (x & 7)];
+        }
+}
+
+template <typename T>
+void linear_to_bricks(const Volume &v, const T *src, T *dst)
+{
+    const int rx = v.desc.h_r[0], ry = v.desc.h_r[1], rz = v.desc.h_r[2];
+    for (int z = 0; z < rz; ++z)
+        for (int y = 0; y < ry; ++y) {
+            const long long rowb = ((long long)(z >> 3) * v.nb[1] + (y >> 3)) * v.nb[0];
+            const int inner = ((z & 7) << 6) | ((y & 7) << 3);
+            const T *s = src + ((size_t)z * ry + y) * rx;
+            for (int x = 0; x < rx; ++x)
+                dst[(rowb + (x >> 3)) * kBrickVox + inner + (x & 7)] = s[x];
+        }
+}
+
+void free_host(Volume *v)
+{
+    if (v->h_fw) cudaFreeHost(v->h_fw);
+    if (v->h_rgba) cudaFreeHost(v->h_rgba);
+    if (v->h_flag) cudaFreeHost(v->h_flag);
+    v->h_fw = nullptr;
+    v->h_rgba = nullptr;
+    v->h_flag = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mv_version(void) { return "mvtsdf 0.1.0 (sm_103a)"; }
+
+mv_status mv_config_default(mv_config *out)
+{
+    if (!out) return MV_ERR_ARG;
+    out->trunc_voxels = 4.0f;
+    out->w_max = 128.0f;
+    out->color_w_max = 255;
+    out->z_min = 0.0f;
+    out->z_max = INFINITY;
+    out->ray_step = 1.0f;
+    out->n_bisect = 8;
+    return MV_OK;
+}
+
+mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out)
+{
+    if (!out) return MV_ERR_ARG;
+    *out = nullptr;
+    mv_config c;
+    if (cfg) c = *cfg; else mv_config_default(&c);
+    if (!valid_config(c)) return MV_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MV_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return MV_ERR_CUDA;
+    mv_ctx *x = new mv_ctx();
+    x->cfg = c;
+    x->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x->swap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->last_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_table, sizeof(VolDev) * kMaxVolumes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_vf, sizeof(VolFrame) * kMaxVolumes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_counter, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_stats, sizeof(Stats));
+    if (e == cudaSuccess) e = cudaMemset(x->d_stats, 0, sizeof(Stats));
+    if (e != cudaSuccess) {
+        mv_destroy(x);
+        return e == cudaErrorMemoryAllocation ? MV_ERR_OOM : MV_ERR_CUDA;
+    }
+    x->grid_integrate = integrate_occupancy_grid(x->num_sms);
+    *out = x;
+    return MV_OK;
+}
+
+mv_status mv_destroy(mv_ctx *c)
+{
+    if (!c) return MV_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    // stream-ordered allocations go back through the stream-ordered allocator
+    cudaStream_t s = c->swap_stream;
+    for (auto &kv : c->vols) {
+        Volume *v = kv.second;
+        if (v->d_fw) cudaFreeAsync(v->d_fw, s);
+        if (v->d_rgba) cudaFreeAsync(v->d_rgba, s);
+        if (v->d_flag) cudaFreeAsync(v->d_flag, s);
+    }
+    if (c->d_list) cudaFreeAsync(c->d_list, s);
+    if (s) cudaStreamSynchronize(s);
+    for (auto &kv : c->vols) {
+        Volume *v = kv.second;
+        free_host(v);
+        if (v->ready) cudaEventDestroy(v->ready);
+        delete v;
+    }
+    if (c->d_table) cudaFree(c->d_table);
+    if (c->d_vf) cudaFree(c->d_vf);
+    if (c->d_counter) cudaFree(c->d_counter);
+    if (c->d_stats) cudaFree(c->d_stats);
+    for (auto &t : c->timed_pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->last_event) cudaEventDestroy(c->last_event);
+    if (c->swap_stream) cudaStreamDestroy(c->swap_stream);
+    delete c;
+    return MV_OK;
+}
+
+const char *mv_last_error(const mv_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
+{
+    if (!c || !d || !out_id) return fail(c, MV_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (d->h_r[a] < 2 || d->h_r[a] > 8192) return fail(c, MV_ERR_ARG, "h_r must be in [2, 8192]");
+    if (!(d->voxel_size > 0.f) || !std::isfinite(d->voxel_size)) return fail(c, MV_ERR_ARG, "voxel_size must be > 0");
+    if (d->fmt < MV_TSDF_F32 || d->fmt > MV_TSDF_I16) return fail(c, MV_ERR_ARG, "bad storage format");
+    if (d->fmt != MV_TSDF_F32 && c->cfg.w_max > 65535.f)
+        return fail(c, MV_ERR_ARG, "w_max > 65535 does not fit a uint16 weight");
+    if ((int)c->vols.size() >= kMaxVolumes) return fail(c, MV_ERR_CAPACITY, "too many volumes");
+    cudaSetDevice(c->device);
+    Volume *v = new Volume();
+    v->desc = *d;
+    v->nbricks = 1;
+    for (int a = 0; a < 3; ++a) {
+        v->nb[a] = (d->h_r[a] + kBrick - 1) / kBrick;
+        v->nbricks *= v->nb[a];
+    }
+    v->fw_bytes = (size_t)v->nbricks * kBrickVox * fw_elem_bytes(d->fmt);
+    v->rgba_bytes = (size_t)v->nbricks * kBrickVox * 4;
+    v->flag_bytes = (size_t)v->nbricks;
+    cudaStream_t s = c->swap_stream;
+    cudaError_t e = cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocAsync(&v->d_fw, v->fw_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_rgba, v->rgba_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_flag, v->flag_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_fw, 0, v->fw_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_rgba, 0, v->rgba_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, kFlagEmpty, v->flag_bytes, s);
+    if (e == cudaSuccess) e = cudaEventRecord(v->ready, s);
+    if (e != cudaSuccess) {
+        if (v->d_fw) cudaFreeAsync(v->d_fw, s);
+        if (v->d_rgba) cudaFreeAsync(v->d_rgba, s);
+        if (v->d_flag) cudaFreeAsync(v->d_flag, s);
+        cudaStreamSynchronize(s);
+        if (v->ready) cudaEventDestroy(v->ready);
+        delete v;
+        cudaGetLastError();
+        return cuda_fail(c, e, "allocating volume storage");
+    }
+    v->ready_pending = true;
+    v->resident = true;
+    v->id = c->next_id++;
+    c->vols[v->id] = v;
+    c->table_dirty = true;
+    *out_id = v->id;
+    return MV_OK;
+}
+
+mv_status mv_remove_volume(mv_ctx *c, int32_t id)
+{
+    if (!c) return MV_ERR_ARG;
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->swap_stream;
+    if (c->last_recorded) MV_CUDA(c, cudaStreamWaitEvent(s, c->last_event, 0));
+    if (v->d_fw) MV_CUDA(c, cudaFreeAsync(v->d_fw, s));
+    if (v->d_rgba) MV_CUDA(c, cudaFreeAsync(v->d_rgba, s));
+    if (v->d_flag) MV_CUDA(c, cudaFreeAsync(v->d_flag, s));
+    if (v->h_fw || v->h_rgba || v->h_flag) {
+        MV_CUDA(c, cudaStreamSynchronize(s));  // in-flight copies may still read the host copy
+        free_host(v);
+    }
+    if (v->ready) {
+        cudaEventSynchronize(v->ready);
+        cudaEventDestroy(v->ready);
+    }
+    c->vols.erase(id);
+    delete v;
+    c->table_dirty = true;
+    return MV_OK;
+}
+
+mv_status mv_query(mv_ctx *c, int32_t id, mv_volume_info *out)
+{
+    if (!c || !out) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    out->desc = v->desc;
+    out->resident = v->resident ? 1 : 0;
+    out->reserved = 0;
+    const size_t tot = v->fw_bytes + v->rgba_bytes + v->flag_bytes;
+    out->device_bytes = v->resident ? tot : 0;
+    out->host_bytes = v->h_fw ? tot : 0;
+    return MV_OK;
+}
+
+mv_status mv_list_volumes(mv_ctx *c, int32_t *ids, int32_t cap, int32_t *count)
+{
+    if (!c || !count || (cap > 0 && !ids)) return fail(c, MV_ERR_ARG, "null argument");
+    int n = 0;
+    for (auto &kv : c->vols) {
+        if (n < cap) ids[n] = kv.first;
+        ++n;
+    }
+    *count = n;
+    return MV_OK;
+}
+
+static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, const uint8_t *rgb,
+                                const mv_intrinsics *K, const double T[16], void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (only_id >= 0) {
+        Volume *v;
+        mv_status st = find_volume(c, only_id, &v);
+        if (st) return st;
+        if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "volume is swapped out");
+    }
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    if (c->table.empty()) return end_call(c, s);
+    const FrameParams P = make_params(c, K, T);
+    int slot0 = 0, nvol = (int)c->table.size();
+    if (only_id >= 0) {
+        slot0 = table_slot(c, only_id);
+        nvol = 1;
+    }
+    const VolDev *tab = c->d_table + slot0;
+    VolFrame *vf = c->d_vf + slot0;
+    const long long gb0 = c->table[slot0].brick_base;
+    const long long total = only_id >= 0 ? c->table[slot0].nbricks
+                                         : c->table.back().brick_base + c->table.back().nbricks;
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
+        return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
+        return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
+        return launch_integrate(tab, vf, c->d_list, c->d_counter, P, depth, rgb, c->d_stats,
+                                c->grid_integrate, s); }));
+    return end_call(c, s);
+}
+
+mv_status mv_integrate(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                       const double T[16], void *stream)
+{
+    return integrate_impl(c, -1, depth, rgb, K, T, stream);
+}
+
+mv_status mv_integrate_volume(mv_ctx *c, int32_t id, const float *depth, const uint8_t *rgb,
+                              const mv_intrinsics *K, const double T[16], void *stream)
+{
+    if (id < 0) return fail(c, MV_ERR_NOT_FOUND, "negative id");
+    return integrate_impl(c, id, depth, rgb, K, T, stream);
+}
+
+static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_intrinsics *K,
+                              const double T[16], float *depth, float *normal, uint8_t *rgba,
+                              float *vertex, int32_t *vol_id, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad view arguments");
+    const bool merge = only_id >= 0 && !first;
+    if (only_id >= 0 && (!depth || !vol_id))
+        return fail(c, MV_ERR_ARG, "per-volume raycast needs depth and vol_id (merge state)");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (only_id >= 0) {
+        Volume *v;
+        mv_status st = find_volume(c, only_id, &v);
+        if (st) return st;
+        if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "volume is swapped out");
+    }
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    const FrameParams P = make_params(c, K, T);
+    int slot0 = 0, nvol = (int)c->table.size();
+    if (only_id >= 0) {
+        slot0 = table_slot(c, only_id);
+        nvol = 1;
+    }
+    const VolDev *tab = c->d_table + slot0;
+    VolFrame *vf = c->d_vf + slot0;
+    if (nvol > 0)
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
+            return launch_frame_setup(tab, nvol, P, vf, nullptr, s); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
+        return launch_raycast(tab, vf, nvol, P, depth, normal, rgba, vertex, vol_id, merge ? 1 : 0, s); }));
+    return end_call(c, s);
+}
+
+mv_status mv_raycast(mv_ctx *c, const mv_intrinsics *K, const double T[16], float *depth,
+                     float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id, void *stream)
+{
+    return raycast_impl(c, -1, 1, K, T, depth, normal, rgba, vertex, vol_id, stream);
+}
+
+mv_status mv_raycast_volume(mv_ctx *c, int32_t id, int32_t first, const mv_intrinsics *K,
+                            const double T[16], float *depth, float *normal, uint8_t *rgba,
+                            float *vertex, int32_t *vol_id, void *stream)
+{
+    if (id < 0) return fail(c, MV_ERR_NOT_FOUND, "negative id");
+    return raycast_impl(c, id, first, K, T, depth, normal, rgba, vertex, vol_id, stream);
+}
+
+mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    if (!v->resident) return MV_OK;
+    cudaSetDevice(c->device);
+    if (!v->h_fw) {
+        cudaError_t e = cudaHostAlloc(&v->h_fw, v->fw_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_rgba, v->rgba_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_flag, v->flag_bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            free_host(v);
+            cudaGetLastError();
+            return fail(c, MV_ERR_OOM, "pinned host allocation failed");
+        }
+    }
+    cudaStream_t s = c->swap_stream;
+    // after all earlier work of the context and of the caller's stream
+    if (c->last_recorded) MV_CUDA(c, cudaStreamWaitEvent(s, c->last_event, 0));
+    MV_CUDA(c, cudaEventRecord(c->last_event, (cudaStream_t)stream));
+    MV_CUDA(c, cudaStreamWaitEvent(s, c->last_event, 0));
+    if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(s, v->ready, 0));
+    MV_CUDA(c, cudaMemcpyAsync(v->h_fw, v->d_fw, v->fw_bytes, cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaMemcpyAsync(v->h_rgba, v->d_rgba, v->rgba_bytes, cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaMemcpyAsync(v->h_flag, v->d_flag, v->flag_bytes, cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaFreeAsync(v->d_fw, s));
+    MV_CUDA(c, cudaFreeAsync(v->d_rgba, s));
+    MV_CUDA(c, cudaFreeAsync(v->d_flag, s));
+    MV_CUDA(c, cudaEventRecord(v->ready, s));
+    v->ready_pending = true;
+    v->d_fw = nullptr;
+    v->d_rgba = nullptr;
+    v->d_flag = nullptr;
+    v->resident = false;
+    c->table_dirty = true;
+    return MV_OK;
+}
+
+mv_status mv_swap_in(mv_ctx *c, int32_t id, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    if (v->resident) return MV_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->swap_stream;
+    (void)stream;
+    void *fw = nullptr, *rgba = nullptr, *flag = nullptr;
+    cudaError_t e = cudaMallocAsync(&fw, v->fw_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&rgba, v->rgba_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&flag, v->flag_bytes, s);
+    if (e != cudaSuccess) {
+        if (fw) cudaFreeAsync(fw, s);
+        if (rgba) cudaFreeAsync(rgba, s);
+        if (flag) cudaFreeAsync(flag, s);
+        cudaGetLastError();
+        return cuda_fail(c, e, "allocating GPU memory for swap-in");
+    }
+    MV_CUDA(c, cudaMemcpyAsync(fw, v->h_fw, v->fw_bytes, cudaMemcpyHostToDevice, s));
+    MV_CUDA(c, cudaMemcpyAsync(rgba, v->h_rgba, v->rgba_bytes, cudaMemcpyHostToDevice, s));
+    MV_CUDA(c, cudaMemcpyAsync(flag, v->h_flag, v->flag_bytes, cudaMemcpyHostToDevice, s));
+    MV_CUDA(c, cudaEventRecord(v->ready, s));
+    v->ready_pending = true;
+    v->d_fw = fw;
+    v->d_rgba = (uint32_t *)rgba;
+    v->d_flag = (uint8_t *)flag;
+    v->resident = true;
+    c->table_dirty = true;
+    return MV_OK;
+}
+
+mv_status mv_read_volume(mv_ctx *c, int32_t id, void *host_fw, uint8_t *host_rgba)
+{
+    if (!c || !host_fw) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    cudaSetDevice(c->device);
+    st = wait_all(c);
+    if (st) return st;
+    if (v->ready_pending) MV_CUDA(c, cudaEventSynchronize(v->ready));
+    std::vector<uint8_t> fw, col;
+    const void *src_fw = v->h_fw;
+    const void *src_col = v->h_rgba;
+    if (v->resident) {
+        fw.resize(v->fw_bytes);
+        MV_CUDA(c, cudaMemcpy(fw.data(), v->d_fw, v->fw_bytes, cudaMemcpyDeviceToHost));
+        src_fw = fw.data();
+        if (host_rgba) {
+            col.resize(v->rgba_bytes);
+            MV_CUDA(c, cudaMemcpy(col.data(), v->d_rgba, v->rgba_bytes, cudaMemcpyDeviceToHost));
+            src_col = col.data();
+        }
+    }
+    if (v->desc.fmt == MV_TSDF_F32)
+        bricks_to_linear(*v, (const uint64_t *)src_fw, (uint64_t *)host_fw);
+    else
+        bricks_to_linear(*v, (const uint32_t *)src_fw, (uint32_t *)host_fw);
+    if (host_rgba) bricks_to_linear(*v, (const uint32_t *)src_col, (uint32_t *)host_rgba);
+    return MV_OK;
+}
+
+mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint8_t *host_rgba)
+{
+    if (!c || !host_fw) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    cudaSetDevice(c->device);
+    st = wait_all(c);
+    if (st) return st;
+    if (v->ready_pending) MV_CUDA(c, cudaEventSynchronize(v->ready));
+    std::vector<uint8_t> fw(v->fw_bytes, 0), col;
+    if (v->desc.fmt == MV_TSDF_F32)
+        linear_to_bricks(*v, (const uint64_t *)host_fw, (uint64_t *)fw.data());
+    else
+        linear_to_bricks(*v, (const uint32_t *)host_fw, (uint32_t *)fw.data());
+    if (host_rgba) {
+        col.assign(v->rgba_bytes, 0);
+        linear_to_bricks(*v, (const uint32_t *)host_rgba, (uint32_t *)col.data());
+    }
+    if (v->resident) {
+        MV_CUDA(c, cudaMemcpy(v->d_fw, fw.data(), v->fw_bytes, cudaMemcpyHostToDevice));
+        if (host_rgba) MV_CUDA(c, cudaMemcpy(v->d_rgba, col.data(), v->rgba_bytes, cudaMemcpyHostToDevice));
+        const VolDev d = make_voldev(*v);
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_FLAGS, c->swap_stream, [&] {
+            return launch_brick_flags(d, c->num_sms, c->swap_stream); }));
+        MV_CUDA(c, cudaStreamSynchronize(c->swap_stream));
+    } else {
+        std::memcpy(v->h_fw, fw.data(), v->fw_bytes);
+        if (host_rgba) std::memcpy(v->h_rgba, col.data(), v->rgba_bytes);
+        // exact flags on the host
+        for (long long b = 0; b < v->nbricks; ++b) {
+            bool all_free = true, all_empty = true;
+            for (int k = 0; k < kBrickVox; ++k) {
+                float F, W;
+                const size_t off = (size_t)b * kBrickVox + k;
+                if (v->desc.fmt == MV_TSDF_F32) {
+                    const float *q = (const float *)fw.data() + 2 * off;
+                    F = q[0];
+                    W = q[1];
+                } else {
+                    const uint32_t q = ((const uint32_t *)fw.data())[off];
+                    W = (float)(q >> 16);
+                    const uint16_t lo = (uint16_t)(q & 0xFFFFu);
+                    if (v->desc.fmt == MV_TSDF_I16) F = (float)(int16_t)lo;
+                    else F = (lo & 0x7FFFu) && !(lo & 0x8000u) ? 1.f : ((lo & 0x8000u) ? -1.f : 0.f);
+                }
+                all_free &= (W > 0.f) && (F > 0.f);
+                all_empty &= !(W > 0.f);
+            }
+            v->h_flag[b] = (uint8_t)((all_free ? kFlagFree : 0) | (all_empty ? kFlagEmpty : 0));
+        }
+    }
+    return MV_OK;
+}
+
+mv_status mv_get_stats(mv_ctx *c, mv_stats *out, int32_t reset)
+{
+    if (!c || !out) return fail(c, MV_ERR_ARG, "null argument");
+    cudaSetDevice(c->device);
+    mv_status st = wait_all(c);
+    if (st) return st;
+    Stats h;
+    MV_CUDA(c, cudaMemcpy(&h, c->d_stats, sizeof(Stats), cudaMemcpyDeviceToHost));
+    out->swept = h.swept;
+    out->updated = h.updated;
+    out->band = h.band;
+    out->bricks = h.bricks;
+    if (reset) MV_CUDA(c, cudaMemset(c->d_stats, 0, sizeof(Stats)));
+    return MV_OK;
+}
+
+mv_status mv_set_timing(mv_ctx *c, int32_t enable)
+{
+    if (!c) return MV_ERR_ARG;
+    c->timing = enable != 0;
+    return MV_OK;
+}
+
+mv_status mv_get_timings(mv_ctx *c, mv_timings *out, int32_t reset)
+{
+    if (!c || !out) return fail(c, MV_ERR_ARG, "null argument");
+    cudaSetDevice(c->device);
+    mv_status st = wait_all(c);
+    if (st) return st;
+    st = collect_timings(c);
+    if (st) return st;
+    for (int k = 0; k < MV_KERNEL_KINDS; ++k) {
+        out->launches[k] = c->launches[k];
+        out->ms[k] = c->ms[k];
+        out->timed[k] = c->timed[k];
+    }
+    if (reset) {
+        std::fill(c->launches, c->launches + MV_KERNEL_KINDS, 0);
+        std::fill(c->ms, c->ms + MV_KERNEL_KINDS, 0.0);
+        std::fill(c->timed, c->timed + MV_KERNEL_KINDS, 0);
+    }
+    return MV_OK;
+}
+
+mv_status mv_synchronize(mv_ctx *c)
+{
+    if (!c) return MV_ERR_ARG;
+    cudaSetDevice(c->device);
+    return wait_all(c);
+}
+
+}  // extern "C"

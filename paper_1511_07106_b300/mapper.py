@@ -1,0 +1,272 @@
+"""Python front end of the multi-volume TSDF library: torch tensors in, C ABI calls out.
+
+``Mapper`` owns one ``mv_ctx``.  It only marshals arguments (device pointers
+of torch tensors, the current CUDA stream, poses as float64) to the functions
+of ``include/mvtsdf.h``; every step of integration and raycasting runs in
+``libmvtsdf.so``.  Paper: Salvato, Finman, Leonard, arXiv 1511.07106.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import MVError
+
+
+@dataclass
+class Config:
+    """Method parameters; see mv_config in include/mvtsdf.h."""
+    trunc_voxels: float = 4.0
+    w_max: float = 128.0
+    color_w_max: int = 255
+    z_min: float = 0.0
+    z_max: float = float("inf")
+    ray_step: float = 1.0
+    n_bisect: int = 8
+
+    def _c(self):
+        return _abi.mv_config(self.trunc_voxels, self.w_max, int(self.color_w_max), self.z_min,
+                              self.z_max, self.ray_step, int(self.n_bisect))
+
+
+def intrinsics(cam) -> "_abi.mv_intrinsics":
+    return _abi.mv_intrinsics(float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                              int(cam.width), int(cam.height))
+
+
+def _pose(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _dptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def decode(raw: np.ndarray, fmt: int):
+    """Raw per-voxel storage (as returned by read_volume) -> (F, W) float64."""
+    if fmt == _abi.MV_TSDF_F32:
+        return raw[..., 0].astype(np.float64), raw[..., 1].astype(np.float64)
+    lo = (raw & 0xFFFF).astype(np.uint16)
+    W = (raw >> 16).astype(np.float64)
+    if fmt == _abi.MV_TSDF_F16:
+        F = lo.view(np.float16).astype(np.float64)
+    else:
+        F = lo.view(np.int16).astype(np.float64) / 32767.0
+    return F, W
+
+
+def encode(F: np.ndarray, W: np.ndarray, fmt: int) -> np.ndarray:
+    """(F, W) -> raw per-voxel storage (inverse of decode up to the format's rounding)."""
+    if fmt == _abi.MV_TSDF_F32:
+        return np.stack([F, W], -1).astype(np.float32)
+    Wq = np.clip(np.rint(W), 0, 65535).astype(np.uint32)
+    if fmt == _abi.MV_TSDF_F16:
+        lo = np.asarray(F, np.float16).view(np.uint16).astype(np.uint32)
+    else:
+        lo = np.clip(np.rint(np.asarray(F, np.float64) * 32767.0), -32767, 32767).astype(np.int16)
+        lo = lo.view(np.uint16).astype(np.uint32)
+    return (lo | (Wq << 16)).astype(np.uint32)
+
+
+class Mapper:
+    """A set of TSDF subvolumes on one GPU (the paper's set H)."""
+
+    def __init__(self, config: Optional[Config] = None, device: int = 0):
+        self._lib = _abi.lib()
+        self.config = config or Config()
+        cfg = self.config._c()
+        h = C.c_void_p()
+        st = self._lib.mv_create(C.byref(cfg), int(device), C.byref(h))
+        if st != _abi.MV_OK:
+            raise MVError(st, "mv_create failed")
+        self._h = h
+        self.device = device
+        self._fmt = {}
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st != _abi.MV_OK:
+            msg = self._lib.mv_last_error(self._h)
+            raise MVError(st, msg.decode() if msg else "")
+
+    # -- volumes ----------------------------------------------------------
+    def add_volume(self, h_t, h_r, voxel_size: float, fmt="f32") -> int:
+        f = _abi.FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        d = _abi.mv_volume_desc((C.c_int32 * 3)(*[int(a) for a in h_t]),
+                                (C.c_int32 * 3)(*[int(a) for a in h_r]), float(voxel_size), f)
+        out = C.c_int32()
+        self._check(self._lib.mv_add_volume(self._h, C.byref(d), C.byref(out)))
+        self._fmt[out.value] = f
+        return out.value
+
+    def remove_volume(self, vid: int):
+        self._check(self._lib.mv_remove_volume(self._h, int(vid)))
+        self._fmt.pop(vid, None)
+
+    def query(self, vid: int) -> dict:
+        info = _abi.mv_volume_info()
+        self._check(self._lib.mv_query(self._h, int(vid), C.byref(info)))
+        d = info.desc
+        return dict(h_t=tuple(d.h_t), h_r=tuple(d.h_r), voxel_size=d.voxel_size, fmt=d.fmt,
+                    resident=bool(info.resident), device_bytes=info.device_bytes,
+                    host_bytes=info.host_bytes)
+
+    def volumes(self) -> list:
+        n = C.c_int32()
+        self._check(self._lib.mv_list_volumes(self._h, None, 0, C.byref(n)))
+        ids = (C.c_int32 * max(n.value, 1))()
+        self._check(self._lib.mv_list_volumes(self._h, ids, n.value, C.byref(n)))
+        return list(ids[: n.value])
+
+    # -- per frame --------------------------------------------------------
+    def integrate(self, depth, rgb, cam, T, stream=None):
+        """Integrate one frame into every resident volume (one batched pass)."""
+        import torch
+        K = intrinsics(cam)
+        n = cam.width * cam.height
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_integrate(
+            self._h, _dptr(depth, torch.float32, n, "depth"), _dptr(rgb, torch.uint8, 3 * n, "rgb"),
+            C.byref(K), Tp, _stream(stream)))
+        del keep
+
+    def integrate_volume(self, vid, depth, rgb, cam, T, stream=None):
+        import torch
+        K = intrinsics(cam)
+        n = cam.width * cam.height
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_integrate_volume(
+            self._h, int(vid), _dptr(depth, torch.float32, n, "depth"),
+            _dptr(rgb, torch.uint8, 3 * n, "rgb"), C.byref(K), Tp, _stream(stream)))
+        del keep
+
+    def alloc_maps(self, cam, vertex=True):
+        import torch
+        dev = torch.device("cuda", self.device)
+        H, W = cam.height, cam.width
+        out = dict(depth=torch.empty((H, W), dtype=torch.float32, device=dev),
+                   normal=torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+                   rgba=torch.empty((H, W, 4), dtype=torch.uint8, device=dev),
+                   vol_id=torch.empty((H, W), dtype=torch.int32, device=dev))
+        if vertex:
+            out["vertex"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        return out
+
+    def _map_ptrs(self, out, cam):
+        import torch
+        n = cam.width * cam.height
+        return (_dptr(out.get("depth"), torch.float32, n, "depth"),
+                _dptr(out.get("normal"), torch.float32, 3 * n, "normal"),
+                _dptr(out.get("rgba"), torch.uint8, 4 * n, "rgba"),
+                _dptr(out.get("vertex"), torch.float32, 3 * n, "vertex"),
+                _dptr(out.get("vol_id"), torch.int32, n, "vol_id"))
+
+    def raycast(self, cam, T, out=None, stream=None) -> dict:
+        """Raycast all resident volumes into depth/normal/rgba/vertex/vol_id maps."""
+        out = out if out is not None else self.alloc_maps(cam)
+        K = intrinsics(cam)
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_raycast(self._h, C.byref(K), Tp, *self._map_ptrs(out, cam),
+                                         _stream(stream)))
+        del keep
+        return out
+
+    def raycast_volume(self, vid, first, cam, T, out, stream=None) -> dict:
+        K = intrinsics(cam)
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_raycast_volume(self._h, int(vid), int(bool(first)), C.byref(K), Tp,
+                                                *self._map_ptrs(out, cam), _stream(stream)))
+        del keep
+        return out
+
+    # -- memory passing ---------------------------------------------------
+    def swap_out(self, vid, stream=None):
+        self._check(self._lib.mv_swap_out(self._h, int(vid), _stream(stream)))
+
+    def swap_in(self, vid, stream=None):
+        self._check(self._lib.mv_swap_in(self._h, int(vid), _stream(stream)))
+
+    def read_volume(self, vid, rgba=True):
+        """Synchronous read -> (raw storage [z,y,x,...], rgba [z,y,x,4] or None)."""
+        q = self.query(vid)
+        rx, ry, rz = q["h_r"]
+        if q["fmt"] == _abi.MV_TSDF_F32:
+            raw = np.empty((rz, ry, rx, 2), np.float32)
+        else:
+            raw = np.empty((rz, ry, rx), np.uint32)
+        col = np.empty((rz, ry, rx, 4), np.uint8) if rgba else None
+        self._check(self._lib.mv_read_volume(self._h, int(vid), raw.ctypes.data_as(C.c_void_p),
+                                             None if col is None else col.ctypes.data_as(C.c_void_p)))
+        return raw, col
+
+    def read_decoded(self, vid):
+        """Synchronous read -> (F, W, rgba) with F, W as float64 [z, y, x]."""
+        raw, col = self.read_volume(vid)
+        F, W = decode(raw, self.query(vid)["fmt"])
+        return F, W, col
+
+    def write_volume(self, vid, raw, rgba=None):
+        raw = np.ascontiguousarray(raw)
+        col = None if rgba is None else np.ascontiguousarray(rgba, np.uint8)
+        self._check(self._lib.mv_write_volume(self._h, int(vid), raw.ctypes.data_as(C.c_void_p),
+                                              None if col is None else col.ctypes.data_as(C.c_void_p)))
+
+    def write_decoded(self, vid, F, W, rgba=None):
+        self.write_volume(vid, encode(np.asarray(F), np.asarray(W), self.query(vid)["fmt"]), rgba)
+
+    # -- misc ---------------------------------------------------------------
+    def stats(self, reset=False) -> dict:
+        s = _abi.mv_stats()
+        self._check(self._lib.mv_get_stats(self._h, C.byref(s), int(bool(reset))))
+        return dict(swept=s.swept, updated=s.updated, band=s.band, bricks=s.bricks)
+
+    def set_timing(self, enable: bool):
+        self._check(self._lib.mv_set_timing(self._h, int(bool(enable))))
+
+    def timings(self, reset=False) -> dict:
+        """{kernel: (launches, summed ms, timed launches)} since the last reset."""
+        t = _abi.mv_timings()
+        self._check(self._lib.mv_get_timings(self._h, C.byref(t), int(bool(reset))))
+        return {name: (t.launches[k], t.ms[k], t.timed[k]) for k, name in _abi.KERNEL_NAMES.items()}
+
+    def synchronize(self):
+        self._check(self._lib.mv_synchronize(self._h))

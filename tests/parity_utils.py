@@ -1,0 +1,101 @@
+"""Shared helpers of the GPU parity tests: move inputs to the device, rebuild
+oracle volumes from the CUDA path's state, and compare raycast maps under the
+tolerances stated below.
+
+Tolerances (derived from the arithmetic):
+  * TSDF, float32 storage: |dF| <= 1e-4 (units of mu) per lockstep frame on
+    voxels whose FP64 decisions are not within the oracle's margins;
+  * TSDF, half / int16 storage: 1e-4 + half a storage quantum at the value;
+  * weights: exact; colour: exact (integer arithmetic), off-band only;
+  * raycast: hit/miss identical on unflagged pixels (<= 0.1 % allowed),
+    depth within 0.1 voxel along the ray, normals within 1 degree, colour
+    within 1 LSB.
+"""
+import numpy as np
+
+import oracle
+
+F32_TOL = 1e-4
+DEPTH_TOL_VOX = 0.1
+NORMAL_TOL_DEG = 1.0
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_volume_from_gpu(m, vid, spec):
+    F, W, rgba = m.read_decoded(vid)
+    return oracle.Volume(tuple(spec.h), tuple(spec.r), float(spec.s), F, W, rgba)
+
+
+def storage_quantum(F, fmt):
+    """Half a quantum of the storage format at value F (0 for float32)."""
+    if fmt == "f16":
+        return np.spacing(np.abs(F).astype(np.float16)).astype(np.float64) / 2
+    if fmt == "i16":
+        return np.full(np.shape(F), 0.5 / 32767.0)
+    return np.zeros(np.shape(F))
+
+
+def check_lockstep(before, F, W, rgba, flags, fmt="f32", tol=F32_TOL, with_colour=True):
+    """Compare the GPU state after one frame with the oracle's update of the
+    same prior state; returns (max |dF| on checked voxels, flagged fraction)."""
+    dec = (flags & (oracle.IF_Z | oracle.IF_PIX | oracle.IF_GATE)) != 0
+    ok = ~dec
+    dF = np.abs(F - before.F)
+    lim = tol + storage_quantum(before.F, fmt)
+    bad = ok & (dF > lim)
+    assert not bad.any(), (f"{bad.sum()} voxels exceed the TSDF tolerance; worst "
+                           f"{dF[bad].max():.3g} at {np.argwhere(bad)[:5].tolist()}")
+    badw = ok & (W != before.W)
+    assert not badw.any(), f"{badw.sum()} weights differ, e.g. {np.argwhere(badw)[:5].tolist()}"
+    if with_colour:
+        okc = ok & ((flags & oracle.IF_BAND) == 0)
+        badc = okc[..., None] & (rgba != before.rgba)
+        assert not badc.any(), f"{badc.any(-1).sum()} colours differ"
+    return float(dF[ok].max()) if ok.any() else 0.0, float(dec.mean())
+
+
+def compare_raycast(g, o, cam, T, pitch, mask=None, require_hits=0.05):
+    """g: GPU maps (numpy), o: oracle maps.  mask: pixels to compare (the
+    oracle's sampled pixels), default all.  Returns a summary dict."""
+    H, W = cam.height, cam.width
+    if mask is None:
+        mask = np.ones((H, W), bool)
+    hard = (o["flags"] & (oracle.RF_SIGN | oracle.RF_CELL | oracle.RF_RANGE | oracle.RF_TIE)) != 0
+    ok = mask & ~hard
+    gh, oh = g["depth"] > 0, o["depth"] > 0
+    mism = ok & (gh != oh)
+    assert mism.sum() <= max(1, 1e-3 * ok.sum()), f"hit/miss differs on {mism.sum()} of {ok.sum()} pixels"
+    both = ok & gh & oh
+    assert both.sum() >= require_hits * mask.sum(), f"too few hits to compare ({both.sum()})"
+    # metric length of the ray direction per unit tau
+    xs = (np.arange(W) - cam.cx) / cam.fx
+    ys = (np.arange(H) - cam.cy) / cam.fy
+    dn = np.sqrt(xs[None, :] ** 2 + ys[:, None] ** 2 + 1.0)
+    derr = np.abs(g["depth"].astype(np.float64) - o["depth"]) * dn / pitch
+    assert derr[both].max() <= DEPTH_TOL_VOX, f"depth error {derr[both].max():.3g} voxel"
+    assert np.all(g["vol_id"][both] == o["vol"][both])
+    shade_ok = both & ((o["flags"] & (oracle.RF_FACE | oracle.RF_GRAD)) == 0)
+    on = np.linalg.norm(o["normal"], axis=-1) > 0.5
+    cmp_n = shade_ok & on
+    cosang = np.sum(g["normal"].astype(np.float64) * o["normal"], -1)
+    assert cosang[cmp_n].min() >= np.cos(np.radians(NORMAL_TOL_DEG)), \
+        f"normal error {np.degrees(np.arccos(np.clip(cosang[cmp_n].min(), -1, 1))):.3g} deg"
+    assert np.all(np.linalg.norm(g["normal"][shade_ok & ~on], axis=-1) == 0)
+    dc = np.abs(g["rgba"].astype(np.int32) - o["rgba"].astype(np.int32))
+    assert dc[shade_ok].max(initial=0) <= 1, "colour differs by more than 1 LSB"
+    verr = np.linalg.norm(g["vertex"].astype(np.float64) - o["vertex"], axis=-1) / pitch
+    assert verr[both].max() <= DEPTH_TOL_VOX + 1e-3 * np.abs(o["vertex"][both]).max() / pitch
+    return dict(compared=int(ok.sum()), flagged=int((mask & hard).sum()), hits=int(both.sum()),
+                max_depth_err_vox=float(derr[both].max()), mismatches=int(mism.sum()))
+
+
+def gpu_maps(out):
+    return {k: host(v) for k, v in out.items()}

@@ -1,0 +1,325 @@
+"""CUDA path vs FP64 oracle, through the C ABI (libmvtsdf.so), on a B300.
+
+Integration is checked in lockstep: before each frame the GPU state is read
+back and the oracle applies the same frame to it in FP64; the GPU's state
+after the frame must match within the tolerances of parity_utils.  The
+raycast is checked by raycasting the GPU's own final state in the oracle.
+Sizes span several bricks and ragged tails; one test runs the full 512^3 /
+640x480 workload on sampled voxels and pixels."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_07106_b300 import Config, Mapper, MVError, synth
+from parity_utils import (check_lockstep, compare_raycast, dev, gpu_maps, host,
+                          oracle_volume_from_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+def ocfg(cfg: Config):
+    return oracle.Config(trunc_vox=cfg.trunc_voxels, w_max=cfg.w_max, color_w_max=cfg.color_w_max,
+                         z_min=cfg.z_min, z_max=cfg.z_max, step_vox=cfg.ray_step)
+
+
+def run_lockstep(wl, fmt="f32", frames=None, cfg=Config(), with_colour=True):
+    m = Mapper(cfg)
+    (vs,) = wl.volumes
+    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
+    oc = ocfg(cfg)
+    worst, flagged = 0.0, 0.0
+    n = wl.n_frames if frames is None else frames
+    for i in range(n):
+        d, c = wl.frame(i)
+        before = oracle_volume_from_gpu(m, vid, vs)
+        counts, flags = oracle.integrate(before, d, c if with_colour else None, wl.cam, wl.poses[i],
+                                         oc, want_flags=True)
+        m.stats(reset=True)
+        m.integrate(dev(d), dev(c) if with_colour else None, wl.cam, wl.poses[i])
+        F, W, rgba = m.read_decoded(vid)
+        w, fl = check_lockstep(before, F, W, rgba, flags, fmt=fmt, with_colour=with_colour)
+        worst, flagged = max(worst, w), max(flagged, fl)
+        st = m.stats()
+        nflag = int((flags != 0).sum())
+        assert abs(st["updated"] - counts[0]) <= nflag
+        if with_colour:
+            assert abs(st["band"] - counts[1]) <= nflag
+    return m, vid, worst, flagged
+
+
+@pytest.fixture(scope="module")
+def c1_run():
+    wl = synth.single_volume_128()
+    m, vid, worst, flagged = run_lockstep(wl)
+    yield wl, m, vid, worst, flagged
+    m.close()
+
+
+def test_integrate_lockstep_128(c1_run):
+    wl, m, vid, worst, flagged = c1_run
+    assert worst <= 1e-4
+    assert flagged < 0.01
+    F, W, _ = m.read_decoded(vid)
+    assert (W > 0).mean() > 0.1
+
+
+@pytest.mark.parametrize("pose_index", [0, 11, 29])
+def test_raycast_parity_128(c1_run, pose_index):
+    wl, m, vid, _, _ = c1_run
+    (vs,) = wl.volumes
+    T = wl.poses[pose_index]
+    g = gpu_maps(m.raycast(wl.cam, T))
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    o = oracle.raycast([ov], wl.cam, T, ocfg(m.config), ids=[vid])
+    summary = compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.3)
+    assert summary["max_depth_err_vox"] < 0.02
+
+
+@pytest.mark.parametrize("fmt", ["f16", "i16"])
+def test_reduced_storage_lockstep_and_raycast(fmt):
+    wl = synth.single_volume_128(frames=10, res=64)
+    m, vid, worst, flagged = run_lockstep(wl, fmt=fmt)
+    (vs,) = wl.volumes
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    T = wl.poses[3]
+    g = gpu_maps(m.raycast(wl.cam, T))
+    o = oracle.raycast([ov], wl.cam, T, ocfg(m.config), ids=[vid])
+    compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.3)
+    m.close()
+
+
+def test_ragged_volume_and_image():
+    """Volume dims not multiples of the 8-voxel brick, image not a multiple of
+    the 16x8 raycast tile, non-cubic volume."""
+    base = synth.single_volume_128(frames=6, res=40)
+    cam = synth.Camera(115.0, 115.0, 70.3, 52.1, 141, 103)
+    vs = synth.VolumeSpec((-21, -13, -5), (45, 29, 37), 0.06)
+    wl = synth.Workload("ragged", cam, base.scene, base.poses, [vs], base.seed)
+    m, vid, worst, _ = run_lockstep(wl)
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    for T in (wl.poses[0], wl.poses[4]):
+        g = gpu_maps(m.raycast(cam, T))
+        o = oracle.raycast([ov], cam, T, ocfg(m.config), ids=[vid])
+        compare_raycast(g, o, cam, T, vs.s, require_hits=0.1)
+    m.close()
+
+
+def test_smallest_volume_and_invalid_depth():
+    cam = synth.Camera(20.0, 20.0, 7.5, 5.5, 16, 12)
+    m = Mapper()
+    vid = m.add_volume((0, 0, 10), (2, 2, 2), 0.05)
+    T = np.eye(4)
+    for bad in (0.0, np.nan, -1.0):
+        d = np.full((12, 16), bad, np.float32)
+        m.integrate(dev(d), None, cam, T)
+    assert m.stats()["updated"] == 0
+    F, W, _ = m.read_decoded(vid)
+    assert np.all(W == 0) and np.all(F == 0)
+    d = np.full((12, 16), 0.53, np.float32)
+    m.integrate(dev(d), None, cam, T)
+    F, W, _ = m.read_decoded(vid)
+    ov = oracle.Volume((0, 0, 10), (2, 2, 2), 0.05)
+    oracle.integrate(ov, d, None, cam, T, oracle.Config())
+    np.testing.assert_allclose(F, ov.F, atol=1e-6)
+    np.testing.assert_array_equal(W, ov.W)
+    m.close()
+
+
+def test_empty_context_raycast_is_all_miss():
+    cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
+    m = Mapper()
+    out = gpu_maps(m.raycast(cam, np.eye(4)))
+    assert np.all(out["depth"] == 0) and np.all(out["vol_id"] == -1) and np.all(out["rgba"] == 0)
+    m.integrate(dev(np.ones((15, 20), np.float32)), None, cam, np.eye(4))
+    m.close()
+
+
+def test_tiling_invariance_on_gpu():
+    """2x2x2 subvolumes with the two-voxel overlap equal one volume covering
+    them, bit for bit, after integration and in the merged raycast
+    (Sec. Comparison to KinectFusion)."""
+    wl = synth.single_volume_128(frames=8, res=34)
+    tl = synth.tiled(wl, 2)
+    (vs,) = wl.volumes
+    single, tiles = Mapper(), Mapper()
+    sid = single.add_volume(vs.h, vs.r, vs.s)
+    tids = [tiles.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        single.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+        tiles.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+    Fs, Ws, Cs = single.read_decoded(sid)
+    for t, tid in zip(tl.volumes, tids):
+        F, W, C = tiles.read_decoded(tid)
+        o = [t.h[a] - vs.h[a] for a in range(3)]
+        sl = (slice(o[2], o[2] + t.r[2]), slice(o[1], o[1] + t.r[1]), slice(o[0], o[0] + t.r[0]))
+        np.testing.assert_array_equal(F, Fs[sl])
+        np.testing.assert_array_equal(W, Ws[sl])
+        np.testing.assert_array_equal(C, Cs[sl])
+    for T in (wl.poses[1], wl.poses[5]):
+        a = gpu_maps(single.raycast(wl.cam, T))
+        b = gpu_maps(tiles.raycast(wl.cam, T))
+        assert (a["depth"] > 0).mean() > 0.3
+        np.testing.assert_array_equal(a["depth"], b["depth"])
+        np.testing.assert_array_equal(a["normal"], b["normal"])
+        np.testing.assert_array_equal(a["rgba"], b["rgba"])
+    # and the tiles against the oracle's multi-volume raycast
+    ovs = [oracle_volume_from_gpu(tiles, tid, t) for t, tid in zip(tl.volumes, tids)]
+    T = wl.poses[3]
+    g = gpu_maps(tiles.raycast(wl.cam, T))
+    o = oracle.raycast(ovs, wl.cam, T, ocfg(tiles.config), ids=tids)
+    compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.3)
+    single.close()
+    tiles.close()
+
+
+def test_per_volume_path_equals_batched_path():
+    wl = synth.single_volume_128(frames=5, res=34)
+    tl = synth.tiled(wl, 2)
+    a, b = Mapper(), Mapper()
+    ida = [a.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    idb = [b.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        a.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+        for vid in idb:
+            b.integrate_volume(vid, dev(d), dev(c), wl.cam, wl.poses[i])
+    for x, y in zip(ida, idb):
+        Fa, Wa, Ca = a.read_decoded(x)
+        Fb, Wb, Cb = b.read_decoded(y)
+        np.testing.assert_array_equal(Fa, Fb)
+        np.testing.assert_array_equal(Wa, Wb)
+        np.testing.assert_array_equal(Ca, Cb)
+    T = wl.poses[2]
+    ga = gpu_maps(a.raycast(wl.cam, T))
+    out = b.alloc_maps(wl.cam)
+    for k, vid in enumerate(idb):
+        b.raycast_volume(vid, k == 0, wl.cam, T, out)
+    gb = gpu_maps(out)
+    for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+        np.testing.assert_array_equal(ga[key], gb[key])
+    a.close()
+    b.close()
+
+
+def test_plane_filled_volume_raycast_is_exact():
+    """A linear signed distance written into the volume: the GPU hit equals the
+    analytic ray--plane intersection within FP32 rounding."""
+    m = Mapper()
+    h, r, s = (-30, -30, -30), (60, 60, 60), 0.02
+    vid = m.add_volume(h, r, s)
+    rng = np.random.default_rng(7)
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    dd = 0.03
+    z, y, x = np.meshgrid(*[np.arange(k) for k in r[::-1]], indexing="ij")
+    p = np.stack([(h[0] + x) * s, (h[1] + y) * s, (h[2] + z) * s], -1)
+    F = np.clip((dd - p @ n) / (4 * s), -1, 1)
+    m.write_decoded(vid, F, np.ones_like(F))
+    eye = -0.9 * n
+    T = synth.look_at(eye, eye + n + np.array([0.05, -0.03, 0.02]))
+    cam = synth.Camera(50.0, 50.0, 31.5, 23.5, 64, 48)
+    g = gpu_maps(m.raycast(cam, T))
+    o, d = synth.pixel_rays(cam, T)
+    tau = (dd - o @ n) / (d @ n)
+    pt = o + tau[..., None] * d
+    inside = np.all((pt > (np.array(h) + 1) * s) & (pt < (np.array(h) + np.array(r) - 2) * s), -1)
+    assert inside.mean() > 0.5
+    err = np.abs(g["depth"] - tau) * np.linalg.norm(d, axis=-1) / s
+    assert err[inside].max() < 2e-3
+    cosang = g["normal"][inside] @ (-n)
+    assert cosang.min() > math.cos(math.radians(0.1))
+    m.close()
+
+
+def test_swap_out_in_roundtrip():
+    wl = synth.single_volume_128(frames=6, res=34)
+    tl = synth.tiled(wl, 2)
+    m = Mapper()
+    ids = [m.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    for i in range(3):
+        d, c = wl.frame(i)
+        m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+    keep = ids[0]
+    F0, W0, C0 = m.read_decoded(keep)
+    m.swap_out(keep)
+    q = m.query(keep)
+    assert not q["resident"] and q["host_bytes"] > 0 and q["device_bytes"] == 0
+    with pytest.raises(MVError):
+        m.integrate_volume(keep, dev(wl.frame(3)[0]), None, wl.cam, wl.poses[3])
+    for i in range(3, 6):
+        d, c = wl.frame(i)
+        m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])  # skips the swapped-out volume
+    F1, W1, C1 = m.read_decoded(keep)  # read from host memory
+    np.testing.assert_array_equal(F0, F1)
+    np.testing.assert_array_equal(W0, W1)
+    np.testing.assert_array_equal(C0, C1)
+    out = gpu_maps(m.raycast(wl.cam, wl.poses[0]))
+    assert not np.any(out["vol_id"] == keep)
+    m.swap_in(keep)
+    assert m.query(keep)["resident"]
+    F2, W2, C2 = m.read_decoded(keep)
+    np.testing.assert_array_equal(F0, F2)
+    np.testing.assert_array_equal(W0, W2)
+    # the volume takes part again
+    d, c = wl.frame(0)
+    m.integrate(dev(d), dev(c), wl.cam, wl.poses[0])
+    F3, W3, _ = m.read_decoded(keep)
+    assert np.any(W3 != W2)
+    m.remove_volume(ids[1])
+    assert ids[1] not in m.volumes()
+    m.close()
+
+
+def test_errors_leave_context_usable():
+    m = Mapper()
+    with pytest.raises(MVError) as e:
+        m.add_volume((0, 0, 0), (8192, 8192, 8192), 0.001)  # ~4.4 TB
+    assert "OOM" in str(e.value)
+    with pytest.raises(MVError):
+        m.remove_volume(12345)
+    with pytest.raises(MVError):
+        m.integrate_volume(77, dev(np.zeros((4, 4), np.float32)), None,
+                           synth.Camera(4.0, 4.0, 1.5, 1.5, 4, 4), np.eye(4))
+    vid = m.add_volume((0, 0, 0), (16, 16, 16), 0.01)
+    m.integrate(dev(np.ones((4, 4), np.float32)), None, synth.Camera(4.0, 4.0, 1.5, 1.5, 4, 4), np.eye(4))
+    m.synchronize()
+    assert vid in m.volumes()
+    m.close()
+
+
+def test_full_size_512_sampled_parity():
+    """The 512^3 / 640x480 room workload in the benchmark's launch
+    configuration: lockstep parity of frame 4 on 2 M sampled voxels and the
+    raycast on every 11th pixel."""
+    wl = synth.room_512(frames=5)
+    (vs,) = wl.volumes
+    m = Mapper()
+    vid = m.add_volume(vs.h, vs.r, vs.s)
+    for i in range(4):
+        d, c = wl.frame(i)
+        m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+    before = oracle_volume_from_gpu(m, vid, vs)
+    rng = np.random.default_rng(0)
+    # sample half from updated-looking voxels (W > 0) and half uniformly
+    seen = np.flatnonzero(before.W.reshape(-1) > 0)
+    idx = np.unique(np.concatenate([rng.choice(seen, 1_000_000), rng.integers(0, before.F.size, 1_000_000)]))
+    d, c = wl.frame(4)
+    _, flags = oracle.integrate_voxels(before, idx, d, c, wl.cam, wl.poses[4], ocfg(m.config))
+    m.integrate(dev(d), dev(c), wl.cam, wl.poses[4])
+    F, W, rgba = m.read_decoded(vid)
+    sel = np.zeros(before.F.shape, bool)
+    sel.reshape(-1)[idx] = True
+    fl = np.where(sel, flags, 255)  # unsampled voxels are excluded via the flag
+    check_lockstep(before, F, W, rgba, fl)
+    after = oracle_volume_from_gpu(m, vid, vs)
+    T = wl.poses[4]
+    pix = np.arange(0, wl.cam.width * wl.cam.height, 11)
+    o = oracle.raycast([after], wl.cam, T, ocfg(m.config), ids=[vid], pixels=pix)
+    g = gpu_maps(m.raycast(wl.cam, T))
+    mask = np.zeros((wl.cam.height, wl.cam.width), bool)
+    mask.reshape(-1)[pix] = True
+    compare_raycast(g, o, wl.cam, T, vs.s, mask=mask, require_hits=0.5)
+    m.close()
