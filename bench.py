@@ -363,6 +363,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-variants", action="store_true", help="skip the f16/i16 storage runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -428,6 +429,9 @@ def main():
             "raycast_mrays_per_s": world * cam.width * cam.height * args.steps / (ms_max * 1e-3) / 1e6,
             "swept_voxel_updates_per_s": world * int(np.prod(vs.r)) * args.steps / (ms_max * 1e-3),
             "updated_voxels_per_frame": res["stats"]["updated"] / args.steps,
+            "swept_voxels_per_frame": res["stats"]["swept"] / args.steps,
+            "bricks_per_frame": res["stats"]["bricks"] / args.steps,
+            "band_voxels_per_frame": res["stats"]["band"] / args.steps,
             "kernels": kern, "roofline": roofline, "integrate_roofline": integrate_roofline,
             "gpu_launches": launches, "clocks": res["clocks"]}
 
@@ -446,10 +450,11 @@ def main():
             r["mapper"].close()
         line["variants"] = variants
 
-    upd, dt, h2d, d2h = e2e_run(torch, Mapper, Config, wl, frames, args.steps, args.warmup)
-    dt_max = allreduce_max(torch, dt)
-    line["e2e"] = {"value": allreduce_sum(torch, upd) / dt_max, "unit": UNIT,
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    if not args.no_e2e:
+        upd, dt, h2d, d2h = e2e_run(torch, Mapper, Config, wl, frames, args.steps, args.warmup)
+        dt_max = allreduce_max(torch, dt)
+        line["e2e"] = {"value": allreduce_sum(torch, upd) / dt_max, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, sample, cores = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)

@@ -228,6 +228,14 @@ mv_status mv_read_volume(mv_ctx *ctx, int32_t id, void *host_fw, uint8_t *host_r
  * and to restore checkpoints. */
 mv_status mv_write_volume(mv_ctx *ctx, int32_t id, const void *host_fw, const uint8_t *host_rgba);
 
+/* Synchronous copy of a volume's per-brick summary flags (one byte per
+ * 8x8x8 brick, brick index (bz * nby + by) * nbx + bx with nb = ceil(h_r / 8);
+ * bit 0: every voxel of the brick observed with F > 0, bit 1: no voxel of the
+ * brick observed).  The raycast relies on these summaries to step over whole
+ * bricks; they are exposed so that their soundness can be checked.
+ * MV_ERR_ARG if cap is smaller than the brick count. */
+mv_status mv_read_brick_flags(mv_ctx *ctx, int32_t id, uint8_t *host_flags, uint64_t cap);
+
 /* Read (and optionally reset) the integration counters; synchronises the
  * context's work. */
 mv_status mv_get_stats(mv_ctx *ctx, mv_stats *out, int32_t reset);

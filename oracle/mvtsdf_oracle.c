@@ -339,8 +339,12 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
     const double Delta = c->step_vox * s / dn;
     const double k0f = ceil(lo / Delta), k1f = floor(hi / Delta);
     {
+        /* an endpoint within eps of a grid sample may include or exclude that
+         * sample in another precision; an endpoint at tau = 0 (the camera) is
+         * exact in every precision */
         const double a = lo / Delta, b = hi / Delta;
-        if (fabs(a - floor(a + 0.5)) < c->eps_tau || fabs(b - floor(b + 0.5)) < c->eps_tau)
+        if ((a != 0.0 && fabs(a - floor(a + 0.5)) < c->eps_tau) ||
+            (b != 0.0 && fabs(b - floor(b + 0.5)) < c->eps_tau))
             out.flags |= ORC_RF_RANGE;
     }
     int state = 0; /* 0 none, 1 previous valid sample > 0, -1 previous valid sample <= 0 */

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "mv_swap_in": ([_P, C.c_int32, _P], C.c_int),
     "mv_read_volume": ([_P, C.c_int32, _P, _P], C.c_int),
     "mv_write_volume": ([_P, C.c_int32, _P, _P], C.c_int),
+    "mv_read_brick_flags": ([_P, C.c_int32, _P, C.c_uint64], C.c_int),
     "mv_get_stats": ([_P, C.POINTER(mv_stats), C.c_int32], C.c_int),
     "mv_set_timing": ([_P, C.c_int32], C.c_int),
     "mv_get_timings": ([_P, C.POINTER(mv_timings), C.c_int32], C.c_int),

@@ -40,11 +40,8 @@ __global__ void frame_setup_kernel(const VolDev *__restrict__ vols, int nvol, Fr
 // voxel the per-voxel test would update)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
-                                              const FrameParams &P, long long b)
+                                              const FrameParams &P, int bx, int by, int bz)
 {
-    const int bx = (int)(b % v.nb[0]);
-    const int by = (int)((b / v.nb[0]) % v.nb[1]);
-    const int bz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
     float lo[3], hi[3];
     const int bi[3] = {bx, by, bz};
 #pragma unroll
@@ -94,7 +91,7 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
         const long long g = base + lane;
         bool vis = false;
         int v = 0;
-        long long b = 0;
+        unsigned packed = 0;
         if (g < total) {
             const long long gb = gb_begin + g;
             int lo = 0, hi = nvol - 1;
@@ -103,14 +100,20 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
                 if (vols[mid].brick_base <= gb) lo = mid; else hi = mid - 1;
             }
             v = lo;
-            b = gb - vols[v].brick_base;
-            vis = brick_visible(vols[v], vfs[v], P, b);
+            const VolDev &vd = vols[v];
+            const unsigned b = (unsigned)(gb - vd.brick_base);  // < 2^30 bricks per volume
+            const unsigned bx = b % (unsigned)vd.nb[0];
+            const unsigned byz = b / (unsigned)vd.nb[0];
+            const unsigned by = byz % (unsigned)vd.nb[1];
+            const unsigned bz = byz / (unsigned)vd.nb[1];
+            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz);
+            packed = bx | (by << 10) | (bz << 20);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
         unsigned pos = 0;
         if (lane == 0 && mask) pos = atomicAdd(counter, (unsigned)__popc(mask));
         pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, (unsigned)b);
+        if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, packed);
     }
 }
 
@@ -126,14 +129,11 @@ struct VoxelUpdate {
 };
 
 __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &fr,
-                                               const FrameParams &P, long long b,
+                                               const FrameParams &P, int bx, int by, int bz,
                                                const float *__restrict__ depth, VoxelUpdate &u)
 {
     const int t = threadIdx.x;
     const int lx0 = (t & 1) * 4, ly = (t >> 1) & 7, lz = t >> 4;
-    const int bx = (int)(b % v.nb[0]);
-    const int by = (int)((b / v.nb[0]) % v.nb[1]);
-    const int bz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
     const int gx = bx * kBrick + lx0, gy = by * kBrick + ly, gz = bz * kBrick + lz;
     // voxel position relative to the camera, in voxel units: exact lattice
     // difference minus the camera's sub-voxel fraction
@@ -157,7 +157,7 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         const float Y = Y0 + (float)j * P.Rf[1];
         const float Z = Z0 + (float)j * P.Rf[2];
         if (!(Z > 0.f)) continue;
-        const float iz = 1.0f / Z;
+        const float iz = __fdividef(1.0f, Z);  // ~2 ulp; decisions near pixel edges are margins
         const float uf = fmaf(P.fx * X, iz, P.cx);
         const float vf = fmaf(P.fy * Y, iz, P.cy);
         const int ui = __float2int_rd(uf + 0.5f), vi = __float2int_rd(vf + 0.5f);
@@ -166,7 +166,8 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         const float D = __ldg(depth + p);
         if (!(D > 0.f) || D < P.z_min || D > P.z_max) continue;
         // projective distance along the voxel's ray, in voxels
-        const float lam = sqrtf(X * X + Y * Y + Z * Z) * iz;
+        const float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+        const float lam = n2 * rsqrtf(n2) * iz;  // |p_c| / z
         const float sdf = (D * v.inv_s - Z) * lam;
         if (sdf < -mu) continue;
         u.f[j] = fminf(1.0f, sdf * inv_mu);
@@ -196,29 +197,42 @@ __device__ __forceinline__ uint32_t blend_rgba(uint32_t old, const uint8_t *__re
 
 template <int FMT>
 __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame &fr,
-                                                const FrameParams &P, long long b,
+                                                const FrameParams &P, unsigned packed,
                                                 const float *__restrict__ depth,
                                                 const uint8_t *__restrict__ rgb,
                                                 unsigned long long &n_swept,
                                                 unsigned long long &n_upd,
                                                 unsigned long long &n_band)
 {
-    VoxelUpdate u;
-    project_voxels(v, fr, P, b, depth, u);
+    const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = (int)(packed >> 20);
+    const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
     const int t = threadIdx.x;
     const long long vox0 = b * kBrickVox + 4 * t;  // first of this thread's 4 voxels
+    // issue this thread's 32 (16) bytes of brick storage before the projection
+    // so that the HBM latency overlaps the depth-image gather
+    float4 a32, c32;
+    uint4 a16;
+    if (FMT == MV_TSDF_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(v.fw) + vox0);
+        a32 = p[0];
+        c32 = p[1];
+    } else {
+        a16 = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint32_t *>(v.fw) + vox0);
+    }
+    VoxelUpdate u;
+    project_voxels(v, fr, P, bx, by, bz, depth, u);
     bool all_pos = true;  // every voxel this thread updated is stored > 0
 
     if (u.upd) {
         const float wmax = P.w_max;
         if (FMT == MV_TSDF_F32) {
             float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(v.fw) + vox0);
-            float4 a = p[0], c = p[1];
-            float F[4] = {a.x, a.z, c.x, c.z}, W[4] = {a.y, a.w, c.y, c.w};
+            float F[4] = {a32.x, a32.z, c32.x, c32.z}, W[4] = {a32.y, a32.w, c32.y, c32.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!((u.upd >> j) & 1u)) continue;
-                const float Fn = __fdiv_rn(fmaf(F[j], W[j], u.f[j]), W[j] + 1.0f);
+                // (F W + f) / (W + 1) in increment form
+                const float Fn = F[j] + __fdividef(u.f[j] - F[j], W[j] + 1.0f);
                 W[j] = fminf(W[j] + 1.0f, wmax);
                 F[j] = Fn;
                 all_pos &= Fn > 0.f;
@@ -227,14 +241,13 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
             p[1] = make_float4(F[2], W[2], F[3], W[3]);
         } else {
             uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(v.fw) + vox0);
-            uint4 a = *p;
-            uint32_t q[4] = {a.x, a.y, a.z, a.w};
+            uint32_t q[4] = {a16.x, a16.y, a16.z, a16.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!((u.upd >> j) & 1u)) continue;
                 float F, W;
                 if (FMT == MV_TSDF_F16) decode_f16(q[j], F, W); else decode_i16(q[j], F, W);
-                const float Fn = __fdiv_rn(fmaf(F, W, u.f[j]), W + 1.0f);
+                const float Fn = F + __fdividef(u.f[j] - F, W + 1.0f);
                 const float Wn = fminf(W + 1.0f, wmax);
                 if (FMT == MV_TSDF_F16) {
                     q[j] = encode_f16(Fn, Wn);
@@ -261,14 +274,17 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
     n_upd += nu;
     if (rgb) n_band += __popc(u.band);
 
-    // brick flag maintenance (exact summaries, see mv_internal.cuh)
-    const int brick_upd = __syncthreads_count(nu);
+    // brick flag maintenance (exact summaries, see mv_internal.cuh): FREE when
+    // every voxel was updated to a positive value, or the brick was FREE and
+    // every updated voxel stayed positive; EMPTY while no voxel was ever updated
+    const int brick_all = __syncthreads_and(u.upd == 0xFu ? 1 : 0);
+    const int brick_any = __syncthreads_or(u.upd != 0u ? 1 : 0);
     const int brick_pos = __syncthreads_and(all_pos ? 1 : 0);
     if (t == 0) {
         const uint8_t old = v.bflag[b];
         uint8_t nf = 0;
-        if (brick_pos && (brick_upd == kBrickVox || (old & kFlagFree))) nf |= kFlagFree;
-        if ((old & kFlagEmpty) && brick_upd == 0) nf |= kFlagEmpty;
+        if (brick_pos && (brick_all || (old & kFlagFree))) nf |= kFlagFree;
+        if ((old & kFlagEmpty) && !brick_any) nf |= kFlagEmpty;
         if (nf != old) v.bflag[b] = nf;
     }
 }

@@ -783,6 +783,24 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
     return MV_OK;
 }
 
+mv_status mv_read_brick_flags(mv_ctx *c, int32_t id, uint8_t *host_flags, uint64_t cap)
+{
+    if (!c || !host_flags) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    if (cap < (uint64_t)v->nbricks) return fail(c, MV_ERR_ARG, "flag buffer too small");
+    cudaSetDevice(c->device);
+    st = wait_all(c);
+    if (st) return st;
+    if (v->ready_pending) MV_CUDA(c, cudaEventSynchronize(v->ready));
+    if (v->resident)
+        MV_CUDA(c, cudaMemcpy(host_flags, v->d_flag, v->flag_bytes, cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(host_flags, v->h_flag, v->flag_bytes);
+    return MV_OK;
+}
+
 mv_status mv_get_stats(mv_ctx *c, mv_stats *out, int32_t reset)
 {
     if (!c || !out) return fail(c, MV_ERR_ARG, "null argument");

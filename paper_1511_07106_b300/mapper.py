@@ -244,6 +244,15 @@ class Mapper:
         F, W = decode(raw, self.query(vid)["fmt"])
         return F, W, col
 
+    def read_brick_flags(self, vid):
+        """Per-brick summary flags [nbz, nby, nbx] (bit 0 observed-positive, bit 1 unobserved)."""
+        q = self.query(vid)
+        nb = [(r + 7) // 8 for r in q["h_r"]]
+        out = np.empty((nb[2], nb[1], nb[0]), np.uint8)
+        self._check(self._lib.mv_read_brick_flags(self._h, int(vid), out.ctypes.data_as(C.c_void_p),
+                                                  C.c_uint64(out.size)))
+        return out
+
     def write_volume(self, vid, raw, rgba=None):
         raw = np.ascontiguousarray(raw)
         col = None if rgba is None else np.ascontiguousarray(rgba, np.uint8)

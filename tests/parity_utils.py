@@ -99,3 +99,27 @@ def compare_raycast(g, o, cam, T, pitch, mask=None, require_hits=0.05):
 
 def gpu_maps(out):
     return {k: host(v) for k, v in out.items()}
+
+
+def check_brick_flags(m, vid, spec, min_free_recall=0.0):
+    """Soundness of the per-brick summaries the raycast skips over: FREE implies
+    every voxel of the brick (padding included) observed with F > 0, EMPTY
+    implies none observed.  Returns the fraction of all-observed-positive
+    bricks that carry the FREE flag."""
+    flags = m.read_brick_flags(vid)
+    F, W, _ = m.read_decoded(vid)
+    nbz, nby, nbx = flags.shape
+    pad = np.zeros((nbz * 8, nby * 8, nbx * 8), bool)
+    pos = np.zeros_like(pad)
+    rz, ry, rx = F.shape
+    pad[:rz, :ry, :rx] = W > 0
+    pos[:rz, :ry, :rx] = (W > 0) & (F > 0)
+    b_all_pos = pos.reshape(nbz, 8, nby, 8, nbx, 8).all(axis=(1, 3, 5))
+    b_none = ~pad.reshape(nbz, 8, nby, 8, nbx, 8).any(axis=(1, 3, 5))
+    free = (flags & 1) != 0
+    empty = (flags & 2) != 0
+    assert not np.any(free & ~b_all_pos), "FREE flag on a brick with an unobserved or non-positive voxel"
+    assert not np.any(empty & ~b_none), "EMPTY flag on a brick with an observed voxel"
+    recall = free[b_all_pos].mean() if b_all_pos.any() else 1.0
+    assert recall >= min_free_recall, f"only {recall:.2%} of free bricks flagged"
+    return float(recall)

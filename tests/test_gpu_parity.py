@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 from paper_1511_07106_b300 import Config, Mapper, MVError, synth
-from parity_utils import (check_lockstep, compare_raycast, dev, gpu_maps, host,
-                          oracle_volume_from_gpu)
+from parity_utils import (check_brick_flags, check_lockstep, compare_raycast, dev, gpu_maps,
+                          host, oracle_volume_from_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,13 @@ def test_integrate_lockstep_128(c1_run):
     assert flagged < 0.01
     F, W, _ = m.read_decoded(vid)
     assert (W > 0).mean() > 0.1
+
+
+def test_brick_flags_sound_and_effective(c1_run):
+    wl, m, vid, _, _ = c1_run
+    (vs,) = wl.volumes
+    recall = check_brick_flags(m, vid, vs, min_free_recall=0.5)
+    assert recall > 0.5
 
 
 @pytest.mark.parametrize("pose_index", [0, 11, 29])

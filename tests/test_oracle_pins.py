@@ -511,3 +511,20 @@ def test_nearest_pixel_lookup(oracle_lib):
     # the lookup is not plain truncation of the projection
     floor_pix = np.floor(vp).astype(int) * CAM_S.width + np.floor(up).astype(int)
     assert np.any(floor_pix != nearest)
+
+
+def test_decision_flags_are_rare_on_a_typical_view(oracle_lib):
+    """The margins flag only decisions an FP32 implementation could take the
+    other way; on an ordinary view they must leave almost every pixel and
+    voxel comparable."""
+    wl = synth.single_volume_128(frames=3, res=48)
+    (vs,) = wl.volumes
+    vol = oracle.Volume(vs.h, vs.r, vs.s)
+    for i in range(3):
+        d, c = wl.frame(i)
+        _, fl = oracle.integrate(vol, d, c, wl.cam, wl.poses[i], oracle.Config(), want_flags=True)
+        assert (fl != 0).mean() < 0.01
+    out = oracle.raycast([vol], wl.cam, wl.poses[1], oracle.Config())
+    hard = out["flags"] & (oracle.RF_SIGN | oracle.RF_CELL | oracle.RF_RANGE | oracle.RF_TIE)
+    assert (hard != 0).mean() < 0.03
+    assert (out["depth"] > 0).mean() > 0.3
