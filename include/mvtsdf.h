@@ -248,6 +248,54 @@ mv_status mv_set_timing(mv_ctx *ctx, int32_t enable);
  * since the last reset; synchronises the context's work. */
 mv_status mv_get_timings(mv_ctx *ctx, mv_timings *out, int32_t reset);
 
+/* ---------------------------------------------------------------------------
+ * Integration without allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate GPU memory themselves or through the library -- code that
+ * runs inside a host framework's memory budget, inside a pre-sized memory
+ * pool, or where a cudaMalloc would synchronise the device at a bad time.
+ * It integrates one frame into one volume whose storage the caller owns and
+ * passes in, and it allocates nothing: no context, no cudaMalloc, no
+ * cudaFree.  Its working memory (the frustum brick list and per-call
+ * constants) is one fixed array of about 2 MiB compiled into the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *
+ * The caller's storage uses the library's brick layout: the volume is padded
+ * to nb = ceil(h_r / 8) bricks per axis; brick (bx, by, bz) is stored at
+ * brick index (bz * nby + by) * nbx + bx, 512 voxels each, voxel (lx, ly, lz)
+ * at (lz * 8 + ly) * 8 + lx inside its brick.  fw holds 8 bytes per voxel for
+ * MV_TSDF_F32 (float32 F, float32 W) and 4 bytes for MV_TSDF_F16 / I16 (the
+ * codes of mv_read_volume); rgba 4 bytes per voxel; brick_flags 1 byte per
+ * brick.  A new volume starts with fw and rgba all zero and every brick flag
+ * equal to 2 (nothing observed).  fw must be 16-byte aligned.
+ * ------------------------------------------------------------------------- */
+
+/* Largest volume mv_integrate_noalloc accepts, in 8x8x8 bricks (64^3 bricks:
+ * a 512^3 volume). */
+#define MV_NOALLOC_MAX_BRICKS 262144
+
+typedef struct {
+    mv_volume_desc desc;  /* h_t, h_r, voxel_size, fmt */
+    void *fw;             /* device, brick-major TSDF + weight */
+    uint8_t *rgba;        /* device, brick-major RGBA8 */
+    uint8_t *brick_flags; /* device, one byte per brick */
+} mv_volume_view;
+
+/* Integrate one frame into a caller-owned volume, allocating nothing.  cfg
+ * may be NULL for defaults.  Works on the current CUDA device.  The first
+ * call on a device looks up the address of the library's fixed working array
+ * on that device, so make that first call before any stream capture.  All
+ * calls share that one array: calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.  Returns MV_ERR_CAPACITY, without launching anything, for a
+ * volume of more than MV_NOALLOC_MAX_BRICKS bricks; MV_ERR_ARG for a null or
+ * misaligned pointer or an invalid size, format or frame.  Asynchronous on
+ * `stream` otherwise. */
+mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_config *cfg, const float *depth,
+                               const uint8_t *rgb, const mv_intrinsics *K, const double T_c2w[16],
+                               void *stream);
+
 /* Wait until all work of the context (all streams it used) has finished. */
 mv_status mv_synchronize(mv_ctx *ctx);
 

@@ -56,6 +56,14 @@ class mv_timings(C.Structure):
                 ("timed", C.c_uint64 * MV_KERNEL_KINDS)]
 
 
+MV_NOALLOC_MAX_BRICKS = 262144
+
+
+class mv_volume_view(C.Structure):
+    _fields_ = [("desc", mv_volume_desc), ("fw", C.c_void_p), ("rgba", C.c_void_p),
+                ("brick_flags", C.c_void_p)]
+
+
 _P = C.c_void_p
 _D16 = C.POINTER(C.c_double)
 _SIGNATURES = {
@@ -82,6 +90,8 @@ _SIGNATURES = {
     "mv_set_timing": ([_P, C.c_int32], C.c_int),
     "mv_get_timings": ([_P, C.POINTER(mv_timings), C.c_int32], C.c_int),
     "mv_synchronize": ([_P], C.c_int),
+    "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
+                              C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
 }
 
 _lib = None
