@@ -432,6 +432,9 @@ def main():
             "swept_voxels_per_frame": res["stats"]["swept"] / args.steps,
             "bricks_per_frame": res["stats"]["bricks"] / args.steps,
             "band_voxels_per_frame": res["stats"]["band"] / args.steps,
+            "raycast_samples_per_ray": res["stats"]["ray_samples"] / max(res["stats"]["rays"], 1),
+            "raycast_skips_per_ray": res["stats"]["ray_skips"] / max(res["stats"]["rays"], 1),
+            "raycast_hit_fraction": res["stats"]["ray_hits"] / max(res["stats"]["rays"], 1),
             "kernels": kern, "roofline": roofline, "integrate_roofline": integrate_roofline,
             "gpu_launches": launches, "clocks": res["clocks"]}
 

@@ -104,12 +104,16 @@ typedef struct {
     uint64_t host_bytes;   /* pinned host bytes held by the volume */
 } mv_volume_info;
 
-/* Integration counters accumulated on the device since the last reset. */
+/* Work counters accumulated on the device since the last reset. */
 typedef struct {
-    uint64_t swept;      /* voxels examined (voxels of bricks in the view frustum) */
-    uint64_t updated;    /* voxels whose TSDF and weight were updated */
-    uint64_t band;       /* voxels whose colour was updated (|sdf| < mu) */
-    uint64_t bricks;     /* 8x8x8 bricks processed */
+    uint64_t swept;       /* integration: voxels examined (voxels of bricks in the view frustum) */
+    uint64_t updated;     /* integration: voxels whose TSDF and weight were updated */
+    uint64_t band;        /* integration: voxels whose colour was updated (|sdf| < mu) */
+    uint64_t bricks;      /* integration: 8x8x8 bricks processed */
+    uint64_t rays;        /* raycast: pixels marched */
+    uint64_t ray_samples; /* raycast: grid samples evaluated by trilinear interpolation */
+    uint64_t ray_skips;   /* raycast: whole-brick shortcuts taken */
+    uint64_t ray_hits;    /* raycast: pixels with a surface hit */
 } mv_stats;
 
 /* Kernel kinds counted and timed by mv_get_timings. */
@@ -119,6 +123,7 @@ enum {
     MV_KERNEL_INTEGRATE = 2,   /* TSDF + colour update of the listed bricks */
     MV_KERNEL_RAYCAST = 3,     /* per-pixel march, refinement, shading and merge */
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
+    MV_KERNEL_CELL_FLAGS = 5,  /* raycast step-over flags refreshed after an integration */
     MV_KERNEL_KINDS = 8
 };
 
@@ -231,7 +236,7 @@ mv_status mv_write_volume(mv_ctx *ctx, int32_t id, const void *host_fw, const ui
 /* Synchronous copy of a volume's per-brick summary flags (one byte per
  * 8x8x8 brick, brick index (bz * nby + by) * nbx + bx with nb = ceil(h_r / 8);
  * bit 0: every voxel of the brick observed with F > 0, bit 1: no voxel of the
- * brick observed).  The raycast relies on these summaries to step over whole
+ * brick observed, bit 2: no voxel of the brick observed with F <= 0).  The raycast relies on these summaries to step over whole
  * bricks; they are exposed so that their soundness can be checked.
  * MV_ERR_ARG if cap is smaller than the brick count. */
 mv_status mv_read_brick_flags(mv_ctx *ctx, int32_t id, uint8_t *host_flags, uint64_t cap);
@@ -267,8 +272,9 @@ mv_status mv_get_timings(mv_ctx *ctx, mv_timings *out, int32_t reset);
  * at (lz * 8 + ly) * 8 + lx inside its brick.  fw holds 8 bytes per voxel for
  * MV_TSDF_F32 (float32 F, float32 W) and 4 bytes for MV_TSDF_F16 / I16 (the
  * codes of mv_read_volume); rgba 4 bytes per voxel; brick_flags 1 byte per
- * brick.  A new volume starts with fw and rgba all zero and every brick flag
- * equal to 2 (nothing observed).  fw must be 16-byte aligned.
+ * brick (the summaries of mv_read_brick_flags).  A new volume starts with fw
+ * and rgba all zero and every brick flag equal to 6 (nothing observed, hence
+ * nothing observed at or behind a surface).  fw must be 16-byte aligned.
  * ------------------------------------------------------------------------- */
 
 /* Largest volume mv_integrate_noalloc accepts, in 8x8x8 bricks (64^3 bricks:

@@ -44,11 +44,13 @@ class mv_volume_info(C.Structure):
 
 class mv_stats(C.Structure):
     _fields_ = [("swept", C.c_uint64), ("updated", C.c_uint64), ("band", C.c_uint64),
-                ("bricks", C.c_uint64)]
+                ("bricks", C.c_uint64), ("rays", C.c_uint64), ("ray_samples", C.c_uint64),
+                ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64)]
 
 
 MV_KERNEL_KINDS = 8
-KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags"}
+KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
+                5: "cell_flags"}
 
 
 class mv_timings(C.Structure):

@@ -276,7 +276,8 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
 
     // brick flag maintenance (exact summaries, see mv_internal.cuh): FREE when
     // every voxel was updated to a positive value, or the brick was FREE and
-    // every updated voxel stayed positive; EMPTY while no voxel was ever updated
+    // every updated voxel stayed positive; EMPTY while no voxel was ever
+    // updated; NONEG like FREE but without requiring every voxel observed
     const int brick_all = __syncthreads_and(u.upd == 0xFu ? 1 : 0);
     const int brick_any = __syncthreads_or(u.upd != 0u ? 1 : 0);
     const int brick_pos = __syncthreads_and(all_pos ? 1 : 0);
@@ -285,6 +286,7 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
         uint8_t nf = 0;
         if (brick_pos && (brick_all || (old & kFlagFree))) nf |= kFlagFree;
         if ((old & kFlagEmpty) && !brick_any) nf |= kFlagEmpty;
+        if (brick_pos && (brick_all || (old & kFlagNoNeg))) nf |= kFlagNoNeg;
         if (nf != old) v.bflag[b] = nf;
     }
 }
@@ -344,7 +346,7 @@ __device__ __forceinline__ void voxel_state(const VolDev &v, long long off, bool
 __global__ void __launch_bounds__(128) brick_flags_kernel(VolDev v)
 {
     for (long long b = blockIdx.x; b < v.nbricks; b += gridDim.x) {
-        bool all_free = true, all_empty = true;
+        bool all_free = true, all_empty = true, no_neg = true;
         for (int k = threadIdx.x; k < kBrickVox; k += blockDim.x) {
             bool valid, pos;
             const long long off = b * kBrickVox + k;
@@ -353,10 +355,63 @@ __global__ void __launch_bounds__(128) brick_flags_kernel(VolDev v)
             else voxel_state<MV_TSDF_I16>(v, off, valid, pos);
             all_free &= valid && pos;
             all_empty &= !valid;
+            no_neg &= !valid || pos;
         }
         const int f = __syncthreads_and(all_free ? 1 : 0);
         const int e = __syncthreads_and(all_empty ? 1 : 0);
-        if (threadIdx.x == 0) v.bflag[b] = (uint8_t)((f ? kFlagFree : 0) | (e ? kFlagEmpty : 0));
+        const int nn = __syncthreads_and(no_neg ? 1 : 0);
+        if (threadIdx.x == 0)
+            v.bflag[b] = (uint8_t)((f ? kFlagFree : 0) | (e ? kFlagEmpty : 0) | (nn ? kFlagNoNeg : 0));
+    }
+}
+
+// Cell-brick flag of cell brick (cx, cy, cz): the trilinear cells whose lower
+// corner lies in that brick read voxels of the 8 bricks (cx, cy, cz) + {0,1}^3;
+// bricks beyond the volume only hold cells outside the interpolation domain.
+__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz)
+{
+    bool skip = true;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), z = cz + ((e >> 2) & 1);
+        if (x < v.nb[0] && y < v.nb[1] && z < v.nb[2])
+            skip &= (v.bflag[((long long)z * v.nb[1] + y) * v.nb[0] + x] & kFlagNoNeg) != 0;
+    }
+    v.cflag[((long long)cz * v.nb[1] + cy) * v.nb[0] + cx] = skip ? kCellSkip : 0;
+}
+
+// After an integration: refresh the cell-brick flags that the listed bricks
+// feed (each listed brick b is read by the cell bricks b - {0,1}^3).  Cells
+// written by two threads get the same value from the same final voxel flags.
+__global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restrict__ vols,
+                                                         const uint2 *__restrict__ list,
+                                                         const unsigned *__restrict__ counter)
+{
+    const unsigned long long n = 8ull * (*counter);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const uint2 it = list[i >> 3];
+        const int d = (int)(i & 7);
+        const VolDev &v = vols[it.x];
+        if (!v.cflag) continue;
+        const int cx = (int)(it.y & 1023u) - (d & 1);
+        const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
+        const int cz = (int)(it.y >> 20) - ((d >> 2) & 1);
+        if (cx < 0 || cy < 0 || cz < 0) continue;
+        update_cell_flag(v, cx, cy, cz);
+    }
+}
+
+// Every cell-brick flag of one volume (after a host write).
+__global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < v.nbricks; b += stride) {
+        const int cx = (int)(b % v.nb[0]);
+        const int cy = (int)((b / v.nb[0]) % v.nb[1]);
+        const int cz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
+        update_cell_flag(v, cx, cy, cz);
     }
 }
 
@@ -397,6 +452,19 @@ cudaError_t launch_brick_flags(const VolDev &v, int num_sms, cudaStream_t s)
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     brick_flags_kernel<<<(unsigned)blocks, 128, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long cblocks = (v.nbricks + 255) / 256;
+    if (cblocks > cap) cblocks = cap;
+    if (cblocks < 1) cblocks = 1;
+    cell_flags_all_kernel<<<(unsigned)cblocks, 256, 0, s>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsigned *counter,
+                              int num_sms, cudaStream_t s)
+{
+    cell_flags_kernel<<<num_sms * 4, 256, 0, s>>>(vols, list, counter);
     return cudaGetLastError();
 }
 

@@ -6,8 +6,11 @@
 // (bz * nby + by) * nbx + bx, and inside a brick voxel (lx, ly, lz) sits at
 // (lz * 8 + ly) * 8 + lx.  Padding voxels (index >= h_r) are never integrated
 // and keep W = 0.  Every brick also has one flag byte summarising its voxels
-// (all observed and positive / all unobserved), maintained by the integration
-// kernel and used by the raycast to step over whole bricks exactly.
+// (all observed and positive / all unobserved / no observed voxel with F <= 0),
+// maintained by the integration kernel, and every brick has one "cell brick"
+// byte saying whether the trilinear cells whose lower corner lies in the brick
+// can be stepped over by the raycast (see mv_raycast.cu).  Both byte arrays
+// live in one allocation: voxel-brick flags first, then cell-brick flags.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -22,6 +25,9 @@ constexpr int kBrick = 8;
 constexpr int kBrickVox = 512;
 constexpr uint8_t kFlagFree = 1;   // every voxel of the brick has W > 0 and F > 0
 constexpr uint8_t kFlagEmpty = 2;  // every voxel of the brick has W == 0
+constexpr uint8_t kFlagNoNeg = 4;  // no voxel of the brick has W > 0 and F <= 0
+constexpr uint8_t kFlagsNew = kFlagEmpty | kFlagNoNeg;  // a freshly cleared brick
+constexpr uint8_t kCellSkip = 1;   // the 8 bricks b + {0,1}^3 all carry kFlagNoNeg
 constexpr int kMaxVolumes = 4096;
 
 // One volume as the kernels see it.
@@ -29,6 +35,7 @@ struct VolDev {
     void *fw;          // brick-major TSDF+weight storage (8 B/voxel F32, 4 B/voxel F16/I16)
     uint32_t *rgba;    // brick-major RGBA8, A = colour weight
     uint8_t *bflag;    // one flag byte per brick
+    uint8_t *cflag;    // one cell-brick byte per brick (may be null where no raycast reads it)
     int h[3];          // lattice offset h_t
     int r[3];          // voxels per axis h_r
     int nb[3];         // bricks per axis
@@ -65,6 +72,7 @@ struct FrameParams {
 
 struct Stats {
     unsigned long long swept, updated, band, bricks;
+    unsigned long long rays, ray_samples, ray_skips, ray_hits;
 };
 
 // ---------------------------------------------------------------------------

@@ -15,11 +15,9 @@
 //
 // B300 design: one thread per pixel, 8x4-pixel warp tiles for gather
 // locality, every volume of the view in one launch with the nearest hit kept
-// in registers.  Free space is crossed brick by brick: when the sample's
-// 8x8x8 cell brick is known to hold only observed positive voxels (or only
-// unobserved ones) every grid sample inside it would be valid-positive (or
-// invalid), so the march jumps to the brick's last sample without reading
-// voxels -- an exact shortcut, not an approximation.
+// in registers.  Space that cannot hold a surface crossing is crossed brick by
+// brick with a 3D DDA over per-brick flags (see march_volume): an exact
+// shortcut, not an approximation.
 #include <float.h>
 #include <limits.h>
 
@@ -121,11 +119,9 @@ __device__ __forceinline__ float eval_at(const VolDev &v, const VolRay &vr, floa
     return trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
 }
 
-__device__ __forceinline__ uint8_t brick_flag_or_free(const VolDev &v, int bx, int by, int bz)
-{
-    if (bx >= v.nb[0] || by >= v.nb[1] || bz >= v.nb[2]) return kFlagFree;
-    return __ldg(v.bflag + ((long long)bz * v.nb[1] + by) * v.nb[0] + bx);
-}
+struct RayCount {
+    unsigned samples, skips;
+};
 
 struct Hit {
     float tau;
@@ -191,11 +187,70 @@ __device__ __forceinline__ void shade(const VolDev &v, const VolRay &vr, float k
     h.rgba = out;
 }
 
+// Length (in grid samples from the current one, at local position L inside
+// cell brick b0) of the run of consecutive step-over cell bricks along the
+// ray, minus a safety margin of m voxels before the run's exit face and
+// before the volume's last voxel plane (where cells are clamped).  3D DDA
+// over bricks, at most nb0 + nb1 + nb2 + 3 steps.
+__device__ __forceinline__ void dda_axis(float L, float dq, int b0, int r, float m, float &tmax,
+                                         float &tdel, int &step, float &tdom)
+{
+    if (dq > 0.f) {
+        tmax = ((float)((b0 + 1) * kBrick) - L) / dq;
+        tdel = (float)kBrick / dq;
+        step = 1;
+        tdom = fminf(tdom, ((float)(r - 1) - m - L) / dq);
+    } else if (dq < 0.f) {
+        tmax = ((float)(b0 * kBrick) - L) / dq;
+        tdel = -(float)kBrick / dq;
+        step = -1;
+    } else {
+        tmax = 3.0e38f;
+        tdel = 3.0e38f;
+        step = 0;
+    }
+}
+
+__device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], const float dq[3],
+                                          const int b0[3], float m)
+{
+    float tx, ty, tz, dx, dy, dz, tdom = 3.0e38f;
+    int sx, sy, sz;
+    dda_axis(L[0], dq[0], b0[0], v.r[0], m, tx, dx, sx, tdom);
+    dda_axis(L[1], dq[1], b0[1], v.r[1], m, ty, dy, sy, tdom);
+    dda_axis(L[2], dq[2], b0[2], v.r[2], m, tz, dz, sz, tdom);
+    int bx = b0[0], by = b0[1], bz = b0[2];
+    const int nbx = v.nb[0], nby = v.nb[1], nbz = v.nb[2];
+    const int max_steps = nbx + nby + nbz + 3;
+    float texit = 0.f, dexit = 1.f;
+    for (int it = 0; it < max_steps; ++it) {
+        bool out;
+        if (tx <= ty && tx <= tz) {
+            texit = tx; dexit = fabsf(dq[0]); bx += sx; tx += dx; out = bx < 0 || bx >= nbx;
+        } else if (ty <= tz) {
+            texit = ty; dexit = fabsf(dq[1]); by += sy; ty += dy; out = by < 0 || by >= nby;
+        } else {
+            texit = tz; dexit = fabsf(dq[2]); bz += sz; tz += dz; out = bz < 0 || bz >= nbz;
+        }
+        if (out) break;
+        if (!(__ldg(v.cflag + ((long long)bz * nby + by) * nbx + bx) & kCellSkip)) break;
+    }
+    return fminf(texit - m / dexit, tdom);
+}
+
 // March one ray through one volume; updates `best` when this volume's hit is
 // nearer (or equally near with a lower id).
+//
+// Step-over rule: a sample can end a bracket only if it is valid with F <= 0,
+// which needs an observed voxel with F <= 0 among its cell's corners.  Inside
+// a run of cell bricks flagged kCellSkip no such voxel exists, so no sample in
+// the run can end a bracket, and the march state after the run is fixed by
+// the run's last sample alone.  The march therefore jumps to that last sample
+// (at least m voxels inside the run) and evaluates it normally: the result is
+// that of the dense march, not an approximation.
 template <int FMT>
 __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
-                             const float d[3], float dn, int slot, Hit &best)
+                             const float d[3], float dn, int slot, Hit &best, RayCount &rc)
 {
     VolRay vr;
     float dirv[3];
@@ -231,52 +286,47 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
     // integer trip count: bounded even where float k would stop advancing
     // (the domain spans at most sqrt(3) * 8192 / (1/64) grid steps)
     const int nk = (int)fminf(k1 - k0, 1.0e6f);
-    const float m = 1e-3f;  // safety margin (voxels) of the brick shortcut
+    const float m = 1e-3f;  // safety margin (voxels) of the step-over rule
 
     int state = 0;  // 0: no valid previous sample, 1: previous valid > 0, -1: previous valid <= 0
     float Fprev = 0.f;
-    bool prev_read = false;  // Fprev was read (not implied by a brick shortcut)
+    long long cur_b = -1;
     for (int kk = 0; kk <= nk; ++kk) {
-        const float k = k0 + (float)kk;
-        float rr[3];
+        float k = k0 + (float)kk;
+        float rr[3], L[3];
+        int bi[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
-        // exact free-space / unobserved-space shortcut
-        {
-            float L[3];
-            int bi[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                L[a] = (float)vr.oi[a] + rr[a];
-                bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
-            }
-            const uint8_t f0 = brick_flag_or_free(v, bi[0], bi[1], bi[2]);
-            bool free_cell = false;
-            if (f0 & kFlagFree) {
-                free_cell = true;
-#pragma unroll
-                for (int c = 1; c < 8; ++c)
-                    free_cell &= (brick_flag_or_free(v, bi[0] + (c & 1), bi[1] + ((c >> 1) & 1),
-                                                     bi[2] + ((c >> 2) & 1)) & kFlagFree) != 0;
-            }
-            if (free_cell || (f0 & kFlagEmpty)) {
-                float steps = FLT_MAX;
+        for (int a = 0; a < 3; ++a) {
+            rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+            L[a] = (float)vr.oi[a] + rr[a];
+            bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
+        }
+        long long bidx = ((long long)bi[2] * v.nb[1] + bi[1]) * v.nb[0] + bi[0];
+        if (bidx != cur_b) {
+            cur_b = bidx;
+            if (__ldg(v.cflag + bidx) & kCellSkip) {
                 bool inside = true;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float blo = (float)(bi[a] * kBrick) + m;
-                    const float bhi = (float)min(bi[a] * kBrick + kBrick, v.r[a] - 1) - m;
-                    inside &= (L[a] >= blo) & (L[a] <= bhi);
-                    if (vr.dq[a] > 0.f) steps = fminf(steps, (bhi - L[a]) / vr.dq[a]);
-                    else if (vr.dq[a] < 0.f) steps = fminf(steps, (blo - L[a]) / vr.dq[a]);
-                }
-                if (inside && steps >= 0.f) {
-                    // samples k .. k + skip are all valid-positive (or all invalid)
-                    const int skip = (int)fminf(floorf(steps), (float)(nk - kk));
-                    state = free_cell ? 1 : 0;
-                    prev_read = false;
-                    kk += skip;
-                    continue;
+                for (int a = 0; a < 3; ++a)
+                    inside &= (L[a] >= (float)(bi[a] * kBrick) + m) &
+                              (L[a] <= (float)min(bi[a] * kBrick + kBrick, v.r[a] - 1) - m);
+                if (inside) {
+                    const float run = skip_run(v, L, vr.dq, bi, m);
+                    const int jump = (int)fminf(floorf(run), (float)(nk - kk));
+                    if (jump > 0) {
+                        // land on the run's last sample and evaluate it below
+                        kk += jump;
+                        k = k0 + (float)kk;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+                            L[a] = (float)vr.oi[a] + rr[a];
+                            bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
+                        }
+                        cur_b = ((long long)bi[2] * v.nb[1] + bi[1]) * v.nb[0] + bi[0];
+                        state = 0;
+                        ++rc.skips;
+                    }
                 }
             }
         }
@@ -286,14 +336,11 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
         const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
         bool valid;
         const float F = trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
+        ++rc.samples;
         if (!valid) { state = 0; continue; }
         if (state == 1 && F <= 0.f) {
             // bracket (k-1, k]: bisection on the interpolant, then a secant step
             float a = k - 1.0f, b = k, ga = Fprev, gb = F;
-            if (!prev_read) {
-                bool vv;
-                ga = eval_at<FMT>(v, vr, a, vv);
-            }
             for (int it = 0; it < P.n_bisect; ++it) {
                 const float mid = 0.5f * (a + b);
                 bool vv;
@@ -313,19 +360,34 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
         }
         state = (F > 0.f) ? 1 : -1;
         Fprev = F;
-        prev_read = true;
     }
 }
 
-__global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__ vols,
-                                                      const VolFrame *__restrict__ vfs, int nvol,
-                                                      FrameParams P, RayOut out, int merge)
+__device__ __forceinline__ void add_counts(Stats *stats, unsigned rays, unsigned samples,
+                                           unsigned skips, unsigned hits)
 {
-    // 16x8-pixel CTA; each warp covers an 8x4 tile
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * 16 + (w & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 8 + (w >> 1) * 4 + (lane >> 3);
-    if (px >= P.width || py >= P.height) return;
+    // one atomic per counter per warp (all lanes call this)
+    unsigned long long a = rays, b = samples, c = skips, e = hits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        e += __shfl_down_sync(0xffffffffu, e, o);
+    }
+    if ((threadIdx.x & 31) == 0 && stats) {
+        if (a) atomicAdd(&stats->rays, a);
+        if (b) atomicAdd(&stats->ray_samples, b);
+        if (c) atomicAdd(&stats->ray_skips, c);
+        if (e) atomicAdd(&stats->ray_hits, e);
+    }
+}
+
+__device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
+                                            const VolFrame *__restrict__ vfs, int nvol,
+                                            const FrameParams &P, const RayOut &out, int merge,
+                                            int px, int py, RayCount &rc)
+{
     const float dc0 = ((float)px - P.cx) / P.fx, dc1 = ((float)py - P.cy) / P.fy;
     float d[3];
 #pragma unroll
@@ -348,9 +410,9 @@ __global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__
         const VolDev &v = vols[i];
         const VolFrame vf = vfs[i];
         switch (v.fmt) {
-        case MV_TSDF_F32: march_volume<MV_TSDF_F32>(v, vf, P, d, dn, i, best); break;
-        case MV_TSDF_F16: march_volume<MV_TSDF_F16>(v, vf, P, d, dn, i, best); break;
-        default: march_volume<MV_TSDF_I16>(v, vf, P, d, dn, i, best); break;
+        case MV_TSDF_F32: march_volume<MV_TSDF_F32>(v, vf, P, d, dn, i, best, rc); break;
+        case MV_TSDF_F16: march_volume<MV_TSDF_F16>(v, vf, P, d, dn, i, best, rc); break;
+        default: march_volume<MV_TSDF_I16>(v, vf, P, d, dn, i, best, rc); break;
         }
     }
     if (best.slot == -2) return;  // merge: the existing entry stays
@@ -370,13 +432,29 @@ __global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__
     }
 }
 
+__global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__ vols,
+                                                      const VolFrame *__restrict__ vfs, int nvol,
+                                                      FrameParams P, RayOut out, int merge,
+                                                      Stats *__restrict__ stats)
+{
+    // 16x8-pixel CTA; each warp covers an 8x4 tile
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * 16 + (w & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (w >> 1) * 4 + (lane >> 3);
+    const bool active = px < P.width && py < P.height;
+    RayCount rc{0u, 0u};
+    if (active) trace_pixel(vols, vfs, nvol, P, out, merge, px, py, rc);
+    add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips,
+               (active && out.depth && out.depth[(size_t)py * P.width + px] > 0.f) ? 1u : 0u);
+}
+
 cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,
                            float *depth, float *normal, uint8_t *rgba, float *vertex, int *vol_id,
-                           int merge, cudaStream_t s)
+                           int merge, Stats *stats, cudaStream_t s)
 {
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
     dim3 grid((P.width + 15) / 16, (P.height + 7) / 8);
-    raycast_kernel<<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge);
+    raycast_kernel<<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,9 @@ cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, co
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t);
 cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
+cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
-                           float *, uint8_t *, float *, int *, int, cudaStream_t);
+                           float *, uint8_t *, float *, int *, int, Stats *, cudaStream_t);
 int integrate_occupancy_grid(int num_sms);
 }  // namespace mv
 
@@ -157,6 +158,7 @@ VolDev make_voldev(const Volume &v)
     d.fw = v.d_fw;
     d.rgba = v.d_rgba;
     d.bflag = v.d_flag;
+    d.cflag = v.d_flag ? v.d_flag + v.nbricks : nullptr;
     for (int a = 0; a < 3; ++a) {
         d.h[a] = v.desc.h_t[a];
         d.r[a] = v.desc.h_r[a];
@@ -442,7 +444,7 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     }
     v->fw_bytes = (size_t)v->nbricks * kBrickVox * fw_elem_bytes(d->fmt);
     v->rgba_bytes = (size_t)v->nbricks * kBrickVox * 4;
-    v->flag_bytes = (size_t)v->nbricks;
+    v->flag_bytes = 2 * (size_t)v->nbricks;  // voxel-brick flags, then cell-brick flags
     cudaStream_t s = c->swap_stream;
     cudaError_t e = cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocAsync(&v->d_fw, v->fw_bytes, s);
@@ -450,7 +452,8 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_flag, v->flag_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_fw, 0, v->fw_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_rgba, 0, v->rgba_bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, kFlagEmpty, v->flag_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, kFlagsNew, (size_t)v->nbricks, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag + v->nbricks, kCellSkip, (size_t)v->nbricks, s);
     if (e == cudaSuccess) e = cudaEventRecord(v->ready, s);
     if (e != cudaSuccess) {
         if (v->d_fw) cudaFreeAsync(v->d_fw, s);
@@ -558,6 +561,8 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
         return launch_integrate(tab, vf, c->d_list, c->d_counter, P, depth, rgb, c->d_stats,
                                 c->grid_integrate, s); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
+        return launch_cell_flags(tab, c->d_list, c->d_counter, c->num_sms, s); }));
     return end_call(c, s);
 }
 
@@ -605,7 +610,8 @@ static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_in
         MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
             return launch_frame_setup(tab, nvol, P, vf, nullptr, s); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
-        return launch_raycast(tab, vf, nvol, P, depth, normal, rgba, vertex, vol_id, merge ? 1 : 0, s); }));
+        return launch_raycast(tab, vf, nvol, P, depth, normal, rgba, vertex, vol_id, merge ? 1 : 0,
+                              c->d_stats, s); }));
     return end_call(c, s);
 }
 
@@ -757,9 +763,10 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
     } else {
         std::memcpy(v->h_fw, fw.data(), v->fw_bytes);
         if (host_rgba) std::memcpy(v->h_rgba, col.data(), v->rgba_bytes);
-        // exact flags on the host
-        for (long long b = 0; b < v->nbricks; ++b) {
-            bool all_free = true, all_empty = true;
+        // exact flags on the host: voxel-brick summaries, then cell-brick flags
+        const long long nb = v->nbricks;
+        for (long long b = 0; b < nb; ++b) {
+            bool all_free = true, all_empty = true, no_neg = true;
             for (int k = 0; k < kBrickVox; ++k) {
                 float F, W;
                 const size_t off = (size_t)b * kBrickVox + k;
@@ -774,10 +781,24 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
                     if (v->desc.fmt == MV_TSDF_I16) F = (float)(int16_t)lo;
                     else F = (lo & 0x7FFFu) && !(lo & 0x8000u) ? 1.f : ((lo & 0x8000u) ? -1.f : 0.f);
                 }
-                all_free &= (W > 0.f) && (F > 0.f);
-                all_empty &= !(W > 0.f);
+                const bool valid = W > 0.f;
+                all_free &= valid && (F > 0.f);
+                all_empty &= !valid;
+                no_neg &= !valid || (F > 0.f);
             }
-            v->h_flag[b] = (uint8_t)((all_free ? kFlagFree : 0) | (all_empty ? kFlagEmpty : 0));
+            v->h_flag[b] = (uint8_t)((all_free ? kFlagFree : 0) | (all_empty ? kFlagEmpty : 0) |
+                                     (no_neg ? kFlagNoNeg : 0));
+        }
+        for (long long b = 0; b < nb; ++b) {
+            const int cx = (int)(b % v->nb[0]), cy = (int)((b / v->nb[0]) % v->nb[1]);
+            const int cz = (int)(b / ((long long)v->nb[0] * v->nb[1]));
+            bool skip = true;
+            for (int e = 0; e < 8; ++e) {
+                const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), z = cz + ((e >> 2) & 1);
+                if (x < v->nb[0] && y < v->nb[1] && z < v->nb[2])
+                    skip &= (v->h_flag[((long long)z * v->nb[1] + y) * v->nb[0] + x] & kFlagNoNeg) != 0;
+            }
+            v->h_flag[nb + b] = skip ? kCellSkip : 0;
         }
     }
     return MV_OK;
@@ -795,9 +816,9 @@ mv_status mv_read_brick_flags(mv_ctx *c, int32_t id, uint8_t *host_flags, uint64
     if (st) return st;
     if (v->ready_pending) MV_CUDA(c, cudaEventSynchronize(v->ready));
     if (v->resident)
-        MV_CUDA(c, cudaMemcpy(host_flags, v->d_flag, v->flag_bytes, cudaMemcpyDeviceToHost));
+        MV_CUDA(c, cudaMemcpy(host_flags, v->d_flag, (size_t)v->nbricks, cudaMemcpyDeviceToHost));
     else
-        std::memcpy(host_flags, v->h_flag, v->flag_bytes);
+        std::memcpy(host_flags, v->h_flag, (size_t)v->nbricks);
     return MV_OK;
 }
 
@@ -813,6 +834,10 @@ mv_status mv_get_stats(mv_ctx *c, mv_stats *out, int32_t reset)
     out->updated = h.updated;
     out->band = h.band;
     out->bricks = h.bricks;
+    out->rays = h.rays;
+    out->ray_samples = h.ray_samples;
+    out->ray_skips = h.ray_skips;
+    out->ray_hits = h.ray_hits;
     if (reset) MV_CUDA(c, cudaMemset(c->d_stats, 0, sizeof(Stats)));
     return MV_OK;
 }

@@ -266,7 +266,7 @@ class Mapper:
     def stats(self, reset=False) -> dict:
         s = _abi.mv_stats()
         self._check(self._lib.mv_get_stats(self._h, C.byref(s), int(bool(reset))))
-        return dict(swept=s.swept, updated=s.updated, band=s.band, bricks=s.bricks)
+        return {k: getattr(s, k) for k, _ in _abi.mv_stats._fields_}
 
     def set_timing(self, enable: bool):
         self._check(self._lib.mv_set_timing(self._h, int(bool(enable))))

@@ -118,8 +118,13 @@ def check_brick_flags(m, vid, spec, min_free_recall=0.0):
     b_none = ~pad.reshape(nbz, 8, nby, 8, nbx, 8).any(axis=(1, 3, 5))
     free = (flags & 1) != 0
     empty = (flags & 2) != 0
+    noneg = (flags & 4) != 0
+    neg = np.zeros_like(pad)
+    neg[:rz, :ry, :rx] = (W > 0) & ~(F > 0)
+    b_no_neg = ~neg.reshape(nbz, 8, nby, 8, nbx, 8).any(axis=(1, 3, 5))
     assert not np.any(free & ~b_all_pos), "FREE flag on a brick with an unobserved or non-positive voxel"
     assert not np.any(empty & ~b_none), "EMPTY flag on a brick with an observed voxel"
+    assert not np.any(noneg & ~b_no_neg), "NONEG flag on a brick with an observed voxel F <= 0"
     recall = free[b_all_pos].mean() if b_all_pos.any() else 1.0
     assert recall >= min_free_recall, f"only {recall:.2%} of free bricks flagged"
     return float(recall)

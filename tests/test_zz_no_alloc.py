@@ -41,7 +41,7 @@ def test_noalloc_integrate_matches_context_call_twice():
     # caller-owned storage of a new volume: zero TSDF/weight/colour, every brick unobserved
     fw = torch.zeros(nbricks * 512 * 2, dtype=torch.float32, device="cuda")
     rgba = torch.zeros(nbricks * 512 * 4, dtype=torch.uint8, device="cuda")
-    flags = torch.full((nbricks,), 2, dtype=torch.uint8, device="cuda")
+    flags = torch.full((nbricks,), 6, dtype=torch.uint8, device="cuda")
     desc = _abi.mv_volume_desc((C.c_int32 * 3)(*vs.h), (C.c_int32 * 3)(*vs.r), vs.s, _abi.MV_TSDF_F32)
     view = _abi.mv_volume_view(desc, fw.data_ptr(), rgba.data_ptr(), flags.data_ptr())
     K = intrinsics(wl.cam)
