@@ -21,13 +21,15 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "mvtsdf_oracle.c"), os.path.join(_HERE, "mvtsdf_oracle_grad.c")]
+_SRC = [os.path.join(_HERE, "mvtsdf_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle_mvtsdf.so")
 
 # per-voxel integration flags (decision within a margin of its threshold)
 IF_Z, IF_PIX, IF_GATE, IF_BAND = 1, 2, 4, 8
 # per-pixel raycast flags
 RF_SIGN, RF_CELL, RF_RANGE, RF_FACE, RF_TIE, RF_GRAD = 1, 2, 4, 8, 16, 32
+# pixels excluded from raycast gradients
+GX_NOHIT, GX_CELL, GX_FACE, GX_GRAZE = 1, 2, 4, 8
 
 
 def build(force: bool = False) -> str:
@@ -81,10 +83,9 @@ def _load():
                                             i32p, u8p]
         _lib.orc_sample.argtypes = [C.POINTER(_Volume), dp, i32p]
         _lib.orc_sample.restype = C.c_double
-        if hasattr(_lib, "orc_raycast_grad"):
-            _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
-                                              dp, C.POINTER(_Cfg), dp, dp, dp, dp, dp, dp,
-                                              C.POINTER(C.POINTER(C.c_double)), u8p]
+        _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
+                                          dp, C.POINTER(_Cfg), dp, dp, dp, dp, dp, dp,
+                                          C.POINTER(C.POINTER(C.c_double)), u8p]
     return _lib
 
 
@@ -243,3 +244,57 @@ def sample(vol: Volume, q):
     cv = vol._c()
     val = lib.orc_sample(C.byref(cv), _ptr(qa, C.c_double), C.byref(valid))
     return float(val), bool(valid.value)
+
+
+def raycast_grad(vols, cam, T, grad_depth=None, grad_rgb=None, cfg: Config = Config(), ids=None,
+                 want_tsdf=True):
+    """Gradients of the raycast (left se(3) pose perturbation xi = (rho, phi)
+    in the world frame, and the TSDF voxel values).  grad_depth (H, W) and
+    grad_rgb (H, W, 3; colour in [0, 1]) are the upstream gradients (None =
+    0).  Returns dict: depth, grad_pose (6,), jac_tau (H, W, 6), jac_rgb
+    (H, W, 3, 6), grad_F (list of arrays like each volume's F, or None),
+    excluded (H, W) GX_* bits."""
+    lib = _load()
+    vols = list(vols)
+    n = len(vols)
+    ids = np.arange(n, dtype=np.int32) if ids is None else np.ascontiguousarray(ids, np.int32)
+    arr = (_Volume * max(n, 1))()
+    for i, v in enumerate(vols):
+        arr[i] = v._c()
+    H, W = int(cam.height), int(cam.width)
+    gd = None if grad_depth is None else np.ascontiguousarray(grad_depth, np.float64)
+    gc = None if grad_rgb is None else np.ascontiguousarray(grad_rgb, np.float64)
+    out = dict(depth=np.zeros((H, W)), grad_pose=np.zeros(6), jac_tau=np.zeros((H, W, 6)),
+               jac_rgb=np.zeros((H, W, 3, 6)), excluded=np.zeros((H, W), np.uint8))
+    gF = [np.zeros_like(v.F) for v in vols] if want_tsdf else None
+    ptrs = (C.POINTER(C.c_double) * max(n, 1))()
+    if gF is not None:
+        for i, g in enumerate(gF):
+            ptrs[i] = g.ctypes.data_as(C.POINTER(C.c_double))
+    T = _pose(T)
+    ci, cc = _intr(cam), cfg._c()
+    lib.orc_raycast_grad(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
+                         C.byref(cc), _ptr(out["depth"], C.c_double), _ptr(gd, C.c_double),
+                         _ptr(gc, C.c_double), _ptr(out["grad_pose"], C.c_double),
+                         _ptr(out["jac_tau"], C.c_double), _ptr(out["jac_rgb"], C.c_double),
+                         ptrs if gF is not None else None, _ptr(out["excluded"], C.c_uint8))
+    out["grad_F"] = gF
+    return out
+
+
+def se3_exp(xi):
+    """exp of a twist xi = (rho, phi) as a 4x4 matrix (Rodrigues + V rho)."""
+    rho, phi = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    th = np.linalg.norm(phi)
+    Px = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-12:
+        Rm = np.eye(3) + Px
+        V = np.eye(3) + 0.5 * Px
+    else:
+        a, b = np.sin(th) / th, (1 - np.cos(th)) / th ** 2
+        cc = (th - np.sin(th)) / th ** 3
+        Rm = np.eye(3) + a * Px + b * Px @ Px
+        V = np.eye(3) + b * Px + cc * Px @ Px
+    E = np.eye(4)
+    E[:3, :3], E[:3, 3] = Rm, V @ rho
+    return E
