@@ -124,6 +124,8 @@ enum {
     MV_KERNEL_RAYCAST = 3,     /* per-pixel march, refinement, shading and merge */
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
     MV_KERNEL_CELL_FLAGS = 5,  /* raycast step-over flags refreshed after an integration */
+    MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
+    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 kernels are also counted by kind) */
     MV_KERNEL_KINDS = 8
 };
 
@@ -198,6 +200,18 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
                      float *depth, float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id,
                      void *stream);
 
+/* One frame of the paper's per-frame loop: integrate the frame into every
+ * resident volume, then raycast every resident volume at the same pose, as
+ * one CUDA graph launch (6 kernels).  Same semantics and outputs as
+ * mv_integrate followed by mv_raycast.  The graph is built on the first call
+ * and rebuilt when the set of resident volumes or the image size changes;
+ * otherwise each call only updates the graph's kernel parameters (pose and
+ * buffers).  While timing is on, the graph is timed as a whole
+ * (MV_KERNEL_FRAME_GRAPH). */
+mv_status mv_frame(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                   const double T_c2w[16], float *depth_out, float *normal, uint8_t *rgba,
+                   float *vertex, int32_t *vol_id, void *stream);
+
 /* Raycast one volume and merge its hits into the maps (the paper's
  * per-volume raycast: "all raycasting steps modify the same map").  With
  * first != 0 the maps are (re)initialised by this call; otherwise a pixel is
@@ -207,6 +221,37 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
 mv_status mv_raycast_volume(mv_ctx *ctx, int32_t id, int32_t first, const mv_intrinsics *K,
                             const double T_c2w[16], float *depth, float *normal, uint8_t *rgba,
                             float *vertex, int32_t *vol_id, void *stream);
+
+/* Gradient target of mv_raycast_backward: the TSDF gradient of volume `id`
+ * is accumulated (+=) into grad_tsdf, a device float32 array in the linear
+ * order of mv_read_volume (h_r[0] * h_r[1] * h_r[2] values). */
+typedef struct {
+    int32_t id;
+    float *grad_tsdf;
+} mv_grad_target;
+
+/* Gradients of raycast depth and colour (not in the paper; the
+ * differentiable raycast used for pose refinement).  For n_poses views that
+ * were raycast with mv_raycast (depth and vol_id of each view, device,
+ * n_poses x height x width, unchanged since), and upstream gradients
+ * grad_depth (dL/d depth, n x h x w) and grad_rgb (dL/d colour with colour in
+ * [0, 1], n x h x w x 3), either may be NULL:
+ *   grad_pose (device, n x 6, overwritten) receives dL/dxi for the left
+ *   perturbation T(xi) = exp(xi^) T of each pose, xi = (rho, phi) in the
+ *   world frame (rho translation in metres, phi rotation in radians);
+ *   each target's grad_tsdf receives += dL/dF for that volume's TSDF values
+ *   (F in units of the truncation distance).
+ * The hit cell is re-derived from depth and vol_id (no per-step storage).
+ * Colour is differentiated as the unrounded trilinear colour of the hit cell
+ * (the forward's 8-bit rounding is passed straight through).  Pixels with no
+ * hit, an unobserved corner, grazing incidence or a hit within 1e-3 voxel of
+ * a cell face contribute nothing.  T_c2w: host, n_poses x 16 doubles.
+ * Asynchronous on `stream`; float atomics make the summation order, and so
+ * the last bits of the result, vary between runs. */
+mv_status mv_raycast_backward(mv_ctx *ctx, const mv_intrinsics *K, const double *T_c2w,
+                              int32_t n_poses, const float *depth, const int32_t *vol_id,
+                              const float *grad_depth, const float *grad_rgb, float *grad_pose,
+                              const mv_grad_target *targets, int32_t n_targets, void *stream);
 
 /* Move a volume to pinned host memory (the paper's download, "uploadToCPU")
  * on the library's swap stream, after the work already queued on `stream`;

@@ -50,12 +50,16 @@ class mv_stats(C.Structure):
 
 MV_KERNEL_KINDS = 8
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
-                5: "cell_flags"}
+                5: "cell_flags", 6: "backward", 7: "frame_graph"}
 
 
 class mv_timings(C.Structure):
     _fields_ = [("launches", C.c_uint64 * MV_KERNEL_KINDS), ("ms", C.c_double * MV_KERNEL_KINDS),
                 ("timed", C.c_uint64 * MV_KERNEL_KINDS)]
+
+
+class mv_grad_target(C.Structure):
+    _fields_ = [("id", C.c_int32), ("grad_tsdf", C.c_void_p)]
 
 
 MV_NOALLOC_MAX_BRICKS = 262144
@@ -81,8 +85,11 @@ _SIGNATURES = {
     "mv_integrate": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_integrate_volume": ([_P, C.c_int32, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_raycast": ([_P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
+    "mv_frame": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_raycast_volume": ([_P, C.c_int32, C.c_int32, C.POINTER(mv_intrinsics), _D16, _P, _P, _P,
                            _P, _P, _P], C.c_int),
+    "mv_raycast_backward": ([_P, C.POINTER(mv_intrinsics), _D16, C.c_int32, _P, _P, _P, _P, _P,
+                             C.POINTER(mv_grad_target), C.c_int32, _P], C.c_int),
     "mv_swap_out": ([_P, C.c_int32, _P], C.c_int),
     "mv_swap_in": ([_P, C.c_int32, _P], C.c_int),
     "mv_read_volume": ([_P, C.c_int32, _P, _P], C.c_int),

@@ -1,0 +1,205 @@
+// mv_backward.cu -- gradients of the raycast (sm_103a).
+//
+// Not in the paper: the differentiable form of the raycast of Sec. Raycasting,
+// used to refine camera poses against rendered depth and colour.  The pose is
+// perturbed on the left, T(xi) = exp(xi^) T with xi = (rho, phi) in the world
+// frame.  At the hit x* = t + tau* d with the analytic trilinear gradient g of
+// the hit cell and its corner weights w_j:
+//   dtau/dxi = -(g, x* x g) / (g.d),     dtau/dF_j = -w_j / (g.d),
+//   dx*/dxi  = [I | -[x*]_x] + d dtau/dxi,
+//   C(x) = sum_j w_j(x) c_j / 255,  dC/dxi = J_C dx*/dxi,  dC/dF_j = J_C d dtau/dF_j.
+// The backward pass does not store march samples: it re-derives the hit cell
+// from the forward's depth and volume id (one thread per pixel and pose).
+// Pixels without a hit, with an unobserved corner, at grazing incidence
+// (|g.d| <= 1e-3 |g||d|) or within 1e-3 voxel of a cell face are skipped.
+#include "mv_internal.cuh"
+
+namespace mv {
+
+struct BackwardArgs {
+    const VolDev *vols;
+    int nvol;
+    float *const *grad_tsdf;  // per table slot: dense float32 [z][y][x], or null
+    const double *poses;      // n x 16 row-major camera-to-world
+    int n_poses;
+    float fx, fy, cx, cy;
+    int width, height;
+    const float *depth;       // n x h x w (forward tau*)
+    const int *vol_id;        // n x h x w
+    const float *grad_depth;  // n x h x w or null
+    const float *grad_rgb;    // n x h x w x 3 or null
+    float *grad_pose;         // n x 6 (accumulated)
+};
+
+__device__ __forceinline__ int slot_of(const VolDev *vols, int nvol, int id)
+{
+    int lo = 0, hi = nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (vols[mid].id < id) lo = mid + 1; else hi = mid;
+    }
+    return (nvol > 0 && vols[lo].id == id) ? lo : -1;
+}
+
+template <int FMT>
+__device__ __forceinline__ void corner_fw(const VolDev &v, long long off, float &F, float &W)
+{
+    if (FMT == MV_TSDF_F32) {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(v.fw) + off);
+        F = q.x;
+        W = q.y;
+    } else {
+        const uint32_t q = __ldg(reinterpret_cast<const uint32_t *>(v.fw) + off);
+        if (FMT == MV_TSDF_F16) decode_f16(q, F, W); else decode_i16(q, F, W);
+    }
+}
+
+// Per-pixel gradient terms; returns false for skipped pixels.
+template <int FMT>
+__device__ bool pixel_grad(const VolDev &v, const double *T, float tau, const float d[3],
+                           float gdep, const float gc[3], float jpose[6], long long corner_off[8],
+                           long long lin[8], float &coef, float w[8])
+{
+    // hit point in this volume's voxel coordinates, from the camera position in FP64
+    float q[3], xs[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double cam = T[4 * a + 3] / (double)v.s - (double)v.h[a];
+        q[a] = (float)cam + tau * d[a] * v.inv_s;
+        xs[a] = (float)T[4 * a + 3] + tau * d[a];
+    }
+    int cell[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float fl = floorf(q[a]);
+        const int c = max(0, min(v.r[a] - 2, (int)fl));
+        cell[a] = c;
+        fr[a] = q[a] - (float)c;
+        if (fr[a] < 1e-3f || fr[a] > 1.0f - 1e-3f) return false;
+    }
+    const long long base = vox_offset(v, cell[0], cell[1], cell[2]);
+    const long long ox = ((cell[0] & 7) == 7) ? (long long)(kBrickVox - 7) : 1;
+    const long long oy = ((cell[1] & 7) == 7) ? (long long)v.nb[0] * kBrickVox - 56 : 8;
+    const long long oz = ((cell[2] & 7) == 7) ? (long long)v.nb[0] * v.nb[1] * kBrickVox - 448 : 64;
+    float g[3] = {0.f, 0.f, 0.f};
+    float JC[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const long long off = base + (dx ? ox : 0) + (dy ? oy : 0) + (dz ? oz : 0);
+        corner_off[k] = off;
+        lin[k] = ((long long)(cell[2] + dz) * v.r[1] + (cell[1] + dy)) * v.r[0] + (cell[0] + dx);
+        float F, W;
+        corner_fw<FMT>(v, off, F, W);
+        if (!(W > 0.f)) return false;
+        const uint32_t col = __ldg(v.rgba + off);
+        const float wx = dx ? fr[0] : 1.f - fr[0];
+        const float wy = dy ? fr[1] : 1.f - fr[1];
+        const float wz = dz ? fr[2] : 1.f - fr[2];
+        w[k] = wx * wy * wz;
+        const float gw0 = (dx ? 1.f : -1.f) * wy * wz * v.inv_s;
+        const float gw1 = wx * (dy ? 1.f : -1.f) * wz * v.inv_s;
+        const float gw2 = wx * wy * (dz ? 1.f : -1.f) * v.inv_s;
+        g[0] += F * gw0;
+        g[1] += F * gw1;
+        g[2] += F * gw2;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float c = (float)((col >> (8 * ch)) & 0xFFu) * (1.0f / 255.0f);
+            JC[ch][0] += c * gw0;
+            JC[ch][1] += c * gw1;
+            JC[ch][2] += c * gw2;
+        }
+    }
+    const float gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
+    const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(fabsf(gd) > 1e-3f * gn * dn)) return false;
+    const float inv_gd = 1.0f / gd;
+    float jt[6];
+    jt[0] = -g[0] * inv_gd;
+    jt[1] = -g[1] * inv_gd;
+    jt[2] = -g[2] * inv_gd;
+    jt[3] = -(xs[1] * g[2] - xs[2] * g[1]) * inv_gd;
+    jt[4] = -(xs[2] * g[0] - xs[0] * g[2]) * inv_gd;
+    jt[5] = -(xs[0] * g[1] - xs[1] * g[0]) * inv_gd;
+    // u = J_C^T gc (colour upstream pulled back to the hit point)
+    float u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = JC[0][a] * gc[0] + JC[1][a] * gc[1] + JC[2][a] * gc[2];
+    // dC/dxi^T gc = u^T ([I | -[x*]_x] + d jt^T) = (u, x* x u) + (u.d) jt
+    const float ud = u[0] * d[0] + u[1] * d[1] + u[2] * d[2];
+    jpose[0] = gdep * jt[0] + u[0] + ud * jt[0];
+    jpose[1] = gdep * jt[1] + u[1] + ud * jt[1];
+    jpose[2] = gdep * jt[2] + u[2] + ud * jt[2];
+    jpose[3] = gdep * jt[3] + (xs[1] * u[2] - xs[2] * u[1]) + ud * jt[3];
+    jpose[4] = gdep * jt[4] + (xs[2] * u[0] - xs[0] * u[2]) + ud * jt[4];
+    jpose[5] = gdep * jt[5] + (xs[0] * u[1] - xs[1] * u[0]) + ud * jt[5];
+    // dL/dF_j = (gdep + u.d) dtau/dF_j = -(gdep + u.d) w_j / gd
+    coef = -(gdep + ud) * inv_gd;
+    return true;
+}
+
+__global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
+{
+    const int p = blockIdx.z;
+    const int px = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int py = blockIdx.y * 8 + (threadIdx.x >> 4);
+    const double *T = A.poses + 16 * p;
+    float jp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (px < A.width && py < A.height) {
+        const size_t pix = ((size_t)p * A.height + py) * A.width + px;
+        const float tau = A.depth[pix];
+        const int id = A.vol_id[pix];
+        const int slot = (tau > 0.f && id >= 0) ? slot_of(A.vols, A.nvol, id) : -1;
+        if (slot >= 0) {
+            const VolDev &v = A.vols[slot];
+            const float dc0 = ((float)px - A.cx) / A.fx, dc1 = ((float)py - A.cy) / A.fy;
+            float d[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                d[a] = (float)T[4 * a] * dc0 + (float)T[4 * a + 1] * dc1 + (float)T[4 * a + 2];
+            const float gdep = A.grad_depth ? A.grad_depth[pix] : 0.f;
+            float gc[3] = {0.f, 0.f, 0.f};
+            if (A.grad_rgb) {
+                gc[0] = A.grad_rgb[3 * pix];
+                gc[1] = A.grad_rgb[3 * pix + 1];
+                gc[2] = A.grad_rgb[3 * pix + 2];
+            }
+            long long off[8], lin[8];
+            float w[8], coef = 0.f;
+            bool ok;
+            switch (v.fmt) {
+            case MV_TSDF_F32: ok = pixel_grad<MV_TSDF_F32>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            case MV_TSDF_F16: ok = pixel_grad<MV_TSDF_F16>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            default: ok = pixel_grad<MV_TSDF_I16>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            }
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) jp[k] = 0.f;
+            } else if (A.grad_tsdf && A.grad_tsdf[slot]) {
+                float *gt = A.grad_tsdf[slot];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) atomicAdd(gt + lin[k], coef * w[k]);
+            }
+        }
+    }
+    // pose gradient: warp sums, then one atomic per warp and component
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float s = jp[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(A.grad_pose + 6 * p + k, s);
+    }
+}
+
+cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s)
+{
+    dim3 grid((A.width + 15) / 16, (A.height + 7) / 8, A.n_poses);
+    raycast_backward_kernel<<<grid, 128, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace mv

@@ -299,12 +299,26 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
                                                         const uint8_t *__restrict__ rgb,
                                                         Stats *__restrict__ stats)
 {
+    __shared__ VolDev s_v;
+    __shared__ VolFrame s_f;
+    int cached = -1;
     const unsigned n = *counter;
     unsigned long long n_swept = 0, n_upd = 0, n_band = 0, n_bricks = 0;
     for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
         const uint2 it = list[i];
-        const VolDev &v = vols[it.x];
-        const VolFrame fr = vfs[it.x];
+        // the volume descriptor and camera constants are staged in shared
+        // memory once per change of volume (uniform across the CTA)
+        if ((int)it.x != cached) {
+            __syncthreads();
+            if (threadIdx.x < sizeof(VolDev) / 4)
+                reinterpret_cast<int *>(&s_v)[threadIdx.x] = reinterpret_cast<const int *>(vols + it.x)[threadIdx.x];
+            if (threadIdx.x < sizeof(VolFrame) / 4)
+                reinterpret_cast<int *>(&s_f)[threadIdx.x] = reinterpret_cast<const int *>(vfs + it.x)[threadIdx.x];
+            __syncthreads();
+            cached = (int)it.x;
+        }
+        const VolDev &v = s_v;
+        const VolFrame fr = s_f;
         switch (v.fmt) {
         case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
         case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
@@ -466,6 +480,41 @@ cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsig
 {
     cell_flags_kernel<<<num_sms * 4, 256, 0, s>>>(vols, list, counter);
     return cudaGetLastError();
+}
+
+cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
+                             cudaGraphNode_t dep, const VolDev *vols, int nvol, const FrameParams &P,
+                             VolFrame *vf)
+{
+    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *> a(vols, nvol, P, vf, nullptr);
+    return graph_node(g, exec, node, dep, a.params((const void *)frame_setup_kernel, 1, 256));
+}
+
+// Graph nodes of one integration: setup -> brick list -> integrate -> cell flags.
+cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[4],
+                            cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
+                            const FrameParams &P, long long total, uint2 *list, unsigned *counter,
+                            const float *depth, const uint8_t *rgb, Stats *stats, int grid_int,
+                            int num_sms)
+{
+    long long lb = (total + 255) / 256;
+    const long long cap = (long long)num_sms * 8;
+    if (lb > cap) lb = cap;
+    if (lb < 1) lb = 1;
+    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *> a0(vols, nvol, P, vf, counter);
+    cudaError_t e = graph_node(g, exec, &nodes[0], dep, a0.params((const void *)frame_setup_kernel, 1, 256));
+    if (e != cudaSuccess) return e;
+    NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *>
+        a1(vols, nvol, vf, P, 0LL, total, list, counter);
+    e = graph_node(g, exec, &nodes[1], nodes[0], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
+    if (e != cudaSuccess) return e;
+    NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,
+             const uint8_t *, Stats *>
+        a2(vols, vf, list, counter, P, depth, rgb, stats);
+    e = graph_node(g, exec, &nodes[2], nodes[1], a2.params((const void *)integrate_kernel, grid_int, 128));
+    if (e != cudaSuccess) return e;
+    NodeArgs<const VolDev *, const uint2 *, const unsigned *> a3(vols, list, counter);
+    return graph_node(g, exec, &nodes[3], nodes[2], a3.params((const void *)cell_flags_kernel, num_sms * 4, 256));
 }
 
 int integrate_occupancy_grid(int num_sms)

@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <tuple>
+#include <utility>
+
 #include "mvtsdf.h"
 
 namespace mv {
@@ -108,6 +111,39 @@ __device__ __forceinline__ float stored_i16(float F)
 {
     int q = __float2int_rn(F * 32767.0f);
     return (float)max(-32767, min(32767, q));
+}
+
+// ---------------------------------------------------------------------------
+// host helper: kernel-node parameters for explicitly built CUDA graphs.  The
+// argument values are held here until cudaGraphAddKernelNode or
+// cudaGraphExecKernelNodeSetParams has copied them.
+// ---------------------------------------------------------------------------
+template <typename... Args>
+struct NodeArgs {
+    std::tuple<Args...> vals;
+    void *ptrs[sizeof...(Args)];
+    explicit NodeArgs(Args... a) : vals(a...) { fill(std::index_sequence_for<Args...>{}); }
+    template <size_t... I>
+    void fill(std::index_sequence<I...>) { ((ptrs[I] = (void *)&std::get<I>(vals)), ...); }
+    cudaKernelNodeParams params(const void *func, dim3 grid, dim3 block)
+    {
+        cudaKernelNodeParams p{};
+        p.func = const_cast<void *>(func);
+        p.gridDim = grid;
+        p.blockDim = block;
+        p.sharedMemBytes = 0;
+        p.kernelParams = ptrs;
+        p.extra = nullptr;
+        return p;
+    }
+};
+
+// Add (exec == null) or update (exec != null) one kernel node.
+inline cudaError_t graph_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
+                              cudaGraphNode_t dep, const cudaKernelNodeParams &p)
+{
+    if (exec) return cudaGraphExecKernelNodeSetParams(exec, *node, &p);
+    return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &p);
 }
 
 // element offset of voxel (x, y, z) in brick-major order

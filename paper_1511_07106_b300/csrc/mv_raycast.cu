@@ -432,7 +432,7 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     }
 }
 
-__global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__ vols,
+__global__ void __launch_bounds__(128, 8) raycast_kernel(const VolDev *__restrict__ vols,
                                                       const VolFrame *__restrict__ vfs, int nvol,
                                                       FrameParams P, RayOut out, int merge,
                                                       Stats *__restrict__ stats)
@@ -446,6 +446,25 @@ __global__ void __launch_bounds__(128) raycast_kernel(const VolDev *__restrict__
     if (active) trace_pixel(vols, vfs, nvol, P, out, merge, px, py, rc);
     add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips,
                (active && out.depth && out.depth[(size_t)py * P.width + px] > 0.f) ? 1u : 0u);
+}
+
+cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
+                             cudaGraphNode_t dep, const VolDev *vols, int nvol, const FrameParams &P,
+                             VolFrame *vf);
+
+// Graph nodes of one raycast of all volumes: setup -> raycast.
+cudaError_t graph_raycast(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[2],
+                          cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
+                          const FrameParams &P, float *depth, float *normal, uint8_t *rgba,
+                          float *vertex, int *vol_id, Stats *stats)
+{
+    cudaError_t e = frame_setup_node(g, exec, &nodes[0], dep, vols, nvol, P, vf);
+    if (e != cudaSuccess) return e;
+    RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
+    NodeArgs<const VolDev *, const VolFrame *, int, FrameParams, RayOut, int, Stats *> a(
+        vols, vf, nvol, P, o, 0, stats);
+    dim3 grid((P.width + 15) / 16, (P.height + 7) / 8);
+    return graph_node(g, exec, &nodes[1], nodes[0], a.params((const void *)raycast_kernel, grid, 128));
 }
 
 cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,

@@ -33,6 +33,27 @@ cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, i
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
                            float *, uint8_t *, float *, int *, int, Stats *, cudaStream_t);
 int integrate_occupancy_grid(int num_sms);
+struct BackwardArgs {
+    const VolDev *vols;
+    int nvol;
+    float *const *grad_tsdf;
+    const double *poses;
+    int n_poses;
+    float fx, fy, cx, cy;
+    int width, height;
+    const float *depth;
+    const int *vol_id;
+    const float *grad_depth;
+    const float *grad_rgb;
+    float *grad_pose;
+};
+cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
+cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[4], cudaGraphNode_t,
+                            const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
+                            unsigned *, const float *, const uint8_t *, Stats *, int, int);
+cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[2], cudaGraphNode_t,
+                          const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
+                          uint8_t *, float *, int *, Stats *);
 }  // namespace mv
 
 using namespace mv;
@@ -74,12 +95,26 @@ struct mv_ctx {
     std::vector<VolDev> table;
     std::vector<int> table_ids;
     bool table_dirty = true;
+    unsigned long long table_version = 0;
+    // per-frame CUDA graph (mv_frame): rebuilt when its shape changes,
+    // otherwise only its kernel-node parameters are updated
+    struct FrameGraph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t nodes[6] = {};
+        unsigned long long table_version = ~0ull;
+        int width = 0, height = 0, grid_int = 0;
+    } fg;
     VolDev *d_table = nullptr;
     VolFrame *d_vf = nullptr;
     uint2 *d_list = nullptr;
     size_t list_cap = 0;  // entries
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
+    // raycast backward: per-slot gradient pointers and the poses of one call
+    float **d_grad_ptrs = nullptr;
+    double *d_poses = nullptr;
+    int poses_cap = 0;
     // per-kernel launch counts and optional event timing
     bool timing = false;
     struct Timed { int kind; cudaEvent_t a, b; };
@@ -211,6 +246,7 @@ mv_status begin_call(mv_ctx *c, cudaStream_t s)
             c->list_cap = (size_t)base;
         }
         c->table_dirty = false;
+        c->table_version += 1;
     }
     return MV_OK;
 }
@@ -372,6 +408,7 @@ mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out)
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_vf, sizeof(VolFrame) * kMaxVolumes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_counter, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_stats, sizeof(Stats));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_grad_ptrs, sizeof(float *) * kMaxVolumes);
     if (e == cudaSuccess) e = cudaMemset(x->d_stats, 0, sizeof(Stats));
     if (e != cudaSuccess) {
         mv_destroy(x);
@@ -407,6 +444,10 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_vf) cudaFree(c->d_vf);
     if (c->d_counter) cudaFree(c->d_counter);
     if (c->d_stats) cudaFree(c->d_stats);
+    if (c->d_grad_ptrs) cudaFree(c->d_grad_ptrs);
+    if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
+    if (c->fg.g) cudaGraphDestroy(c->fg.g);
+    if (c->d_poses) cudaFree(c->d_poses);
     for (auto &t : c->timed_pending) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -627,6 +668,112 @@ mv_status mv_raycast_volume(mv_ctx *c, int32_t id, int32_t first, const mv_intri
 {
     if (id < 0) return fail(c, MV_ERR_NOT_FOUND, "negative id");
     return raycast_impl(c, id, first, K, T, depth, normal, rgba, vertex, vol_id, stream);
+}
+
+mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                   const double T[16], float *depth_out, float *normal, uint8_t *rgba, float *vertex,
+                   int32_t *vol_id, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    const FrameParams P = make_params(c, K, T);
+    const int nvol = (int)c->table.size();
+    if (nvol == 0) {  // nothing to integrate: the maps are all misses
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
+            return launch_raycast(c->d_table, c->d_vf, 0, P, depth_out, normal, rgba, vertex, vol_id, 0,
+                                  c->d_stats, s); }));
+        return end_call(c, s);
+    }
+    const long long total = c->table.back().brick_base + c->table.back().nbricks;
+    auto &fg = c->fg;
+    const bool rebuild = !fg.exec || fg.table_version != c->table_version || fg.width != K->width ||
+                         fg.height != K->height || fg.grid_int != c->grid_integrate;
+    if (rebuild) {
+        if (fg.exec) cudaGraphExecDestroy(fg.exec);
+        if (fg.g) cudaGraphDestroy(fg.g);
+        fg.exec = nullptr;
+        fg.g = nullptr;
+        MV_CUDA(c, cudaGraphCreate(&fg.g, 0));
+    }
+    cudaGraphExec_t upd = rebuild ? nullptr : fg.exec;
+    MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
+                               c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
+                               c->num_sms));
+    MV_CUDA(c, graph_raycast(fg.g, upd, fg.nodes + 4, fg.nodes[3], c->d_table, nvol, c->d_vf, P,
+                             depth_out, normal, rgba, vertex, vol_id, c->d_stats));
+    if (rebuild) {
+        MV_CUDA(c, cudaGraphInstantiate(&fg.exec, fg.g, 0));
+        fg.table_version = c->table_version;
+        fg.width = K->width;
+        fg.height = K->height;
+        fg.grid_int = c->grid_integrate;
+    }
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_FRAME_GRAPH, s, [&] { return cudaGraphLaunch(fg.exec, s); }));
+    const int kinds[6] = {MV_KERNEL_SETUP, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE, MV_KERNEL_CELL_FLAGS,
+                          MV_KERNEL_SETUP, MV_KERNEL_RAYCAST};
+    for (int k : kinds) c->launches[k] += 1;
+    return end_call(c, s);
+}
+
+mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,
+                              const float *depth, const int32_t *vol_id, const float *grad_depth,
+                              const float *grad_rgb, float *grad_pose, const mv_grad_target *targets,
+                              int32_t n_targets, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (n_poses < 1 || n_poses > 65535 || !depth || !vol_id || !grad_pose || (n_targets > 0 && !targets) ||
+        n_targets < 0)
+        return fail(c, MV_ERR_ARG, "bad backward arguments");
+    for (int i = 0; i < n_poses; ++i)
+        if (!valid_frame(K, T + 16 * i)) return fail(c, MV_ERR_ARG, "bad view arguments");
+    for (int i = 0; i < n_targets; ++i) {
+        Volume *v;
+        mv_status st = find_volume(c, targets[i].id, &v);
+        if (st) return st;
+        if (!targets[i].grad_tsdf) return fail(c, MV_ERR_ARG, "null gradient buffer");
+        if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "gradient target is swapped out");
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    if (n_poses > c->poses_cap) {
+        if (c->d_poses) MV_CUDA(c, cudaFreeAsync(c->d_poses, s));
+        c->d_poses = nullptr;
+        c->poses_cap = 0;
+        MV_CUDA(c, cudaMallocAsync((void **)&c->d_poses, sizeof(double) * 16 * n_poses, s));
+        c->poses_cap = n_poses;
+    }
+    MV_CUDA(c, cudaMemcpyAsync(c->d_poses, T, sizeof(double) * 16 * n_poses, cudaMemcpyHostToDevice, s));
+    std::vector<float *> ptrs(c->table.size() > 0 ? c->table.size() : 1, nullptr);
+    for (int i = 0; i < n_targets; ++i) {
+        const int slot = table_slot(c, targets[i].id);
+        if (slot >= 0) ptrs[slot] = targets[i].grad_tsdf;
+    }
+    if (!c->table.empty())
+        MV_CUDA(c, cudaMemcpyAsync(c->d_grad_ptrs, ptrs.data(), sizeof(float *) * c->table.size(),
+                                   cudaMemcpyHostToDevice, s));
+    MV_CUDA(c, cudaMemsetAsync(grad_pose, 0, sizeof(float) * 6 * n_poses, s));
+    BackwardArgs A;
+    A.vols = c->d_table;
+    A.nvol = (int)c->table.size();
+    A.grad_tsdf = c->d_grad_ptrs;
+    A.poses = c->d_poses;
+    A.n_poses = n_poses;
+    A.fx = K->fx; A.fy = K->fy; A.cx = K->cx; A.cy = K->cy;
+    A.width = K->width; A.height = K->height;
+    A.depth = depth;
+    A.vol_id = vol_id;
+    A.grad_depth = grad_depth;
+    A.grad_rgb = grad_rgb;
+    A.grad_pose = grad_pose;
+    if (A.nvol > 0)
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_BACKWARD, s, [&] { return launch_raycast_backward(A, s); }));
+    return end_call(c, s);
 }
 
 mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)

@@ -1,0 +1,143 @@
+"""Differentiable raycast: torch.autograd.Function over the library's raycast.
+
+Not in the paper: rendered depth/colour of the TSDF volumes as a function of
+the camera poses (and of the TSDF values), for gradient-based pose refinement.
+The forward pass is ``mv_raycast`` per view; the backward pass is
+``mv_raycast_backward`` (one CUDA launch for all views), which re-derives each
+hit from the saved depth and volume id.  Colour is differentiated as the
+unrounded trilinear colour (the 8-bit rounding of the forward is passed
+straight through).
+
+The library returns dL/dxi for the left perturbation T(xi) = exp(xi^) T.  The
+Function's input is the 4x4 pose itself; it returns dL/dT as the tangent-space
+vector field with exactly those directional derivatives, so any smooth
+parametrisation of T built in torch (e.g. ``pose_from_twist``) gets the exact
+gradient by autograd.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from .mapper import Mapper, intrinsics
+
+
+def _generators(dtype=torch.float64, device="cpu"):
+    """se(3) generators G_k with xi^ = sum_k xi_k G_k, xi = (rho, phi)."""
+    G = torch.zeros(6, 4, 4, dtype=dtype, device=device)
+    for k in range(3):
+        G[k, k, 3] = 1.0
+    # [e_x]_x, [e_y]_x, [e_z]_x
+    G[3, 1, 2], G[3, 2, 1] = -1.0, 1.0
+    G[4, 0, 2], G[4, 2, 0] = 1.0, -1.0
+    G[5, 0, 1], G[5, 1, 0] = -1.0, 1.0
+    return G
+
+
+def hat(xi: torch.Tensor) -> torch.Tensor:
+    """(..., 6) twists -> (..., 4, 4) matrices xi^."""
+    G = _generators(xi.dtype, xi.device)
+    return torch.einsum("...k,kij->...ij", xi, G)
+
+
+def pose_from_twist(xi: torch.Tensor, T0: torch.Tensor) -> torch.Tensor:
+    """T = exp(xi^) T0 (differentiable in xi)."""
+    return torch.matrix_exp(hat(xi)) @ T0
+
+
+def tangent_cotangent(T: torch.Tensor, g_xi: torch.Tensor) -> torch.Tensor:
+    """dL/dT whose Frobenius pairing with the tangent directions G_k T gives
+    g_xi[k] exactly (the dual basis of {G_k T} in their span)."""
+    G = _generators(T.dtype, T.device)
+    B = torch.einsum("kij,njl->nkil", G, T).reshape(T.shape[0], 6, 16)  # rows: vec(G_k T)
+    gram = B @ B.transpose(1, 2)                                        # (n, 6, 6)
+    coeff = torch.linalg.solve(gram, g_xi.unsqueeze(-1)).squeeze(-1)    # (n, 6)
+    return (coeff.unsqueeze(-1) * B).sum(1).reshape(-1, 4, 4)
+
+
+class RaycastFn(torch.autograd.Function):
+    """depth (n, H, W), colour (n, H, W, 3) in [0, 1] = f(T (n, 4, 4), *tsdf).
+
+    ``tsdf`` are placeholder leaves, one per entry of ``tsdf_ids``, shaped like
+    each volume (h_r[2], h_r[1], h_r[0]); their .grad receives dL/dF."""
+
+    @staticmethod
+    def forward(ctx, T, mapper: Mapper, cam, tsdf_ids, *tsdf):
+        n = T.shape[0]
+        H, W = cam.height, cam.width
+        dev = torch.device("cuda", mapper.device)
+        depth = torch.empty((n, H, W), dtype=torch.float32, device=dev)
+        vid = torch.empty((n, H, W), dtype=torch.int32, device=dev)
+        rgba = torch.empty((n, H, W, 4), dtype=torch.uint8, device=dev)
+        Tn = T.detach().to("cpu", torch.float64).contiguous().numpy()
+        for i in range(n):
+            mapper.raycast(cam, Tn[i], out={"depth": depth[i], "vol_id": vid[i], "rgba": rgba[i]})
+        colour = rgba[..., :3].float() / 255.0
+        ctx.mapper, ctx.cam, ctx.tsdf_ids = mapper, cam, list(tsdf_ids)
+        ctx.poses = Tn
+        ctx.tsdf_shapes = [t.shape for t in tsdf]
+        ctx.save_for_backward(T, depth, vid)
+        ctx.mark_non_differentiable(vid)
+        return depth, colour
+
+    @staticmethod
+    def backward(ctx, g_depth, g_colour):
+        T, depth, vid = ctx.saved_tensors
+        mapper, cam = ctx.mapper, ctx.cam
+        n = T.shape[0]
+        dev = depth.device
+        gd = None if g_depth is None else g_depth.contiguous().float()
+        gc = None if g_colour is None else g_colour.contiguous().float()
+        grad_xi = torch.zeros((n, 6), dtype=torch.float32, device=dev)
+        gts = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ctx.tsdf_shapes]
+        mapper.raycast_backward(cam, ctx.poses, depth, vid, gd, gc, grad_xi,
+                                dict(zip(ctx.tsdf_ids, gts)))
+        gT = tangent_cotangent(T.detach().to(torch.float64), grad_xi.to(torch.float64).cpu())
+        return (gT.to(T.dtype).to(T.device), None, None, None, *gts)
+
+
+def render(mapper: Mapper, cam, T: torch.Tensor, tsdf=None):
+    """Differentiable render of the mapper's volumes at poses T (n, 4, 4).
+    tsdf: optional {volume id: placeholder leaf} for TSDF gradients."""
+    tsdf = tsdf or {}
+    return RaycastFn.apply(T, mapper, cam, list(tsdf.keys()), *tsdf.values())
+
+
+def tsdf_leaf(mapper: Mapper, vid: int) -> torch.Tensor:
+    """A zero tensor shaped like volume vid whose .grad receives dL/dF."""
+    rx, ry, rz = mapper.query(vid)["h_r"]
+    return torch.zeros((rz, ry, rx), dtype=torch.float32, device=torch.device("cuda", mapper.device),
+                       requires_grad=True)
+
+
+def l1_loss(depth, colour, ref_depth, ref_colour, colour_weight=0.1):
+    """Mean L1 over pixels valid in both renders: depth + colour_weight * colour."""
+    valid = (depth > 0) & (ref_depth > 0)
+    nv = valid.sum().clamp(min=1)
+    ld = (torch.abs(depth - ref_depth) * valid).sum() / nv
+    lc = (torch.abs(colour - ref_colour).sum(-1) * valid).sum() / nv
+    return ld + colour_weight * lc
+
+
+def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, lr=2e-3,
+                 colour_weight=0.1, callback=None):
+    """Adam on twists xi (T = exp(xi^) T_init) minimising l1_loss against
+    reference renders.  Returns (T_final (n,4,4) float64 numpy, losses)."""
+    T0 = torch.as_tensor(np.asarray(T_init), dtype=torch.float64)
+    xi = torch.zeros((T0.shape[0], 6), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([xi], lr=lr)
+    losses = []
+    for it in range(steps):
+        opt.zero_grad()
+        T = pose_from_twist(xi, T0)
+        depth, colour = render(mapper, cam, T)
+        loss = l1_loss(depth, colour, ref_depth, ref_colour, colour_weight)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+        if callback:
+            callback(it, pose_from_twist(xi.detach(), T0).numpy(), float(loss))
+    return pose_from_twist(xi.detach(), T0).numpy(), losses

@@ -210,6 +210,19 @@ class Mapper:
         del keep
         return out
 
+    def frame(self, depth, rgb, cam, T, out=None, stream=None) -> dict:
+        """Integrate the frame and raycast the same view, as one CUDA graph."""
+        import torch
+        out = out if out is not None else self.alloc_maps(cam)
+        K = intrinsics(cam)
+        n = cam.width * cam.height
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_frame(self._h, _dptr(depth, torch.float32, n, "depth"),
+                                       _dptr(rgb, torch.uint8, 3 * n, "rgb"), C.byref(K), Tp,
+                                       *self._map_ptrs(out, cam), _stream(stream)))
+        del keep
+        return out
+
     def raycast_volume(self, vid, first, cam, T, out, stream=None) -> dict:
         K = intrinsics(cam)
         _, Tp = keep = _pose(T)
@@ -217,6 +230,28 @@ class Mapper:
                                                 *self._map_ptrs(out, cam), _stream(stream)))
         del keep
         return out
+
+    def raycast_backward(self, cam, poses, depth, vol_id, grad_depth, grad_rgb, grad_pose,
+                         targets=None, stream=None):
+        """Raycast gradients (see mv_raycast_backward).  poses: (n, 4, 4) host
+        float64; depth/vol_id: (n, H, W) device maps of the forward; grad_pose
+        (n, 6) float32 device output; targets: {volume id: float32 device
+        tensor shaped like the volume} receiving += dL/dF."""
+        import torch
+        P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+        n = P.shape[0]
+        npx = n * cam.width * cam.height
+        K = intrinsics(cam)
+        targets = targets or {}
+        arr = (_abi.mv_grad_target * max(len(targets), 1))()
+        for i, (vid, t) in enumerate(targets.items()):
+            arr[i] = _abi.mv_grad_target(int(vid), _dptr(t, torch.float32, None, "grad_tsdf").value)
+        self._check(self._lib.mv_raycast_backward(
+            self._h, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)), n,
+            _dptr(depth, torch.float32, npx, "depth"), _dptr(vol_id, torch.int32, npx, "vol_id"),
+            _dptr(grad_depth, torch.float32, npx, "grad_depth"),
+            _dptr(grad_rgb, torch.float32, 3 * npx, "grad_rgb"),
+            _dptr(grad_pose, torch.float32, 6 * n, "grad_pose"), arr, len(targets), _stream(stream)))
 
     # -- memory passing ---------------------------------------------------
     def swap_out(self, vid, stream=None):

@@ -353,3 +353,72 @@ def tiled(wl: Workload, split: int = 2) -> Workload:
                 vols.append(VolumeSpec(hh, (r, r, r), v.s))
     return Workload(wl.name + f" as {split}^3 tiles of {r}^3", wl.cam, wl.scene, wl.poses, vols,
                     wl.seed, wl.trunc_vox, wl.w_max, wl.z_range)
+
+
+def room_tiles(res: int = 256, pitch: float = 0.002, split: int = 2, frames: int = 300, seed: int = 5,
+               width: int = 640, height: int = 480) -> Workload:
+    """Differentiable-raycast workload: split^3 subvolumes of res^3 voxels at
+    `pitch` on the lattice h_t = k (res - 2) (two-voxel overlap) covering a
+    cube of side (split (res - 2) + 2) pitch, holding a scaled room with 6
+    boxes and 4 spheres; a handheld path scaled to the room (frames at
+    640x480, fx = fy = 525)."""
+    rng = np.random.Generator(np.random.Philox(key=(seed << 32) | 0xABC))
+    side = (split * (res - 2) + 2) * pitch
+    half = side / 2.0
+    s = _f32(pitch)
+    h0 = -int(round(half / s))
+    margin = 0.04 * side
+    lo = (-half + margin, -half + margin, margin)
+    hi = (half - margin, half - margin, side - margin)
+    scene = Scene()
+    scene.rooms = np.array([list(lo) + list(hi)])
+    boxes, sph = [], []
+    L = side / 3.0
+    while len(boxes) < 6:
+        sx, sy, sz = rng.uniform(0.05, 0.2, size=3) * L
+        x = rng.uniform(lo[0] + sx, hi[0] - sx)
+        y = rng.uniform(lo[1] + sy, hi[1] - sy)
+        if math.hypot(x, y) < 0.25 * side:
+            continue
+        boxes.append([x - sx / 2, y - sy / 2, lo[2], x + sx / 2, y + sy / 2, lo[2] + sz])
+    while len(sph) < 4:
+        r = rng.uniform(0.04, 0.1) * L
+        x = rng.uniform(lo[0] + r, hi[0] - r)
+        y = rng.uniform(lo[1] + r, hi[1] - r)
+        if math.hypot(x, y) < 0.25 * side + r:
+            continue
+        sph.append([x, y, rng.uniform(lo[2] + r, lo[2] + 0.5 * side), r])
+    scene.boxes = np.array(boxes)
+    scene.spheres = np.array(sph)
+    f = 525.0 * width / 640.0
+    cam = Camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
+    poses = handheld_trajectory(frames, seed, (0.0, 0.0, 0.45 * side), (0.08 * side, 0.08 * side, 0.05 * side),
+                                0.4 * side, 0.35 * side, v_max=0.5 * side / 3.0)
+    vols = []
+    for kz in range(split):
+        for ky in range(split):
+            for kx in range(split):
+                vols.append(VolumeSpec((h0 + kx * (res - 2), h0 + ky * (res - 2), kz * (res - 2) - 2),
+                                       (res, res, res), s))
+    return Workload(f"{split ** 3} x {res}^3 tiles at {pitch * 1e3:g} mm, {width}x{height}", cam, scene,
+                    poses, vols, seed, z_range=(0.1, 5.0))
+
+
+def perturb_poses(poses, seed: int = 6, sigma_t: float = 0.02, sigma_r_deg: float = 1.0):
+    """Each pose moved on the left by a random twist: translation N(0, sigma_t)
+    per axis, rotation by N(0, sigma_r) degrees about a random axis."""
+    rng = np.random.Generator(np.random.Philox(key=(int(seed) << 32) | 0x5E3))
+    out = []
+    for T in poses:
+        axis = rng.normal(size=3)
+        ang = math.radians(rng.normal() * sigma_r_deg)
+        D = np.eye(4)
+        D[:3, :3] = rotation(axis, ang)
+        D[:3, 3] = rng.normal(size=3) * sigma_t
+        # rotate about the camera centre, then translate
+        c = np.asarray(T)[:3, 3]
+        P = np.eye(4)
+        P[:3, :3] = D[:3, :3]
+        P[:3, 3] = c - D[:3, :3] @ c + D[:3, 3]
+        out.append(P @ np.asarray(T))
+    return out

@@ -330,3 +330,39 @@ def test_full_size_512_sampled_parity():
     mask.reshape(-1)[pix] = True
     compare_raycast(g, o, wl.cam, T, vs.s, mask=mask, require_hits=0.5)
     m.close()
+
+
+def test_frame_graph_equals_separate_calls():
+    """mv_frame (one CUDA graph per frame, parameters updated in place) gives
+    the same volumes and maps as mv_integrate + mv_raycast, also across a
+    change of the resident set (graph rebuilt)."""
+    wl = synth.single_volume_128(frames=6, res=34)
+    tl = synth.tiled(wl, 2)
+    a, b = Mapper(), Mapper()
+    ida = [a.add_volume(t.h, t.r, t.s) for t in tl.volumes[:4]]
+    idb = [b.add_volume(t.h, t.r, t.s) for t in tl.volumes[:4]]
+    for i in range(wl.n_frames):
+        if i == 3:  # change the resident set mid-sequence
+            ida.append(a.add_volume(*_spec(tl.volumes[4])))
+            idb.append(b.add_volume(*_spec(tl.volumes[4])))
+            b.swap_out(idb[0])
+            a.swap_out(ida[0])
+        d, c = wl.frame(i)
+        a.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+        ga = gpu_maps(a.raycast(wl.cam, wl.poses[i]))
+        gb = gpu_maps(b.frame(dev(d), dev(c), wl.cam, wl.poses[i]))
+        for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+            np.testing.assert_array_equal(ga[key], gb[key])
+    for x, y in zip(ida, idb):
+        Fa, Wa, Ca = a.read_decoded(x)
+        Fb, Wb, Cb = b.read_decoded(y)
+        np.testing.assert_array_equal(Fa, Fb)
+        np.testing.assert_array_equal(Wa, Wb)
+        np.testing.assert_array_equal(Ca, Cb)
+    assert b.timings()["frame_graph"][0] == wl.n_frames
+    a.close()
+    b.close()
+
+
+def _spec(t):
+    return t.h, t.r, t.s
