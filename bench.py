@@ -130,26 +130,22 @@ def traffic_record(kernel):
     return rec
 
 
-def run_native_steps(m, frames, poses, cam, maps, first, steps, dev_depth, dev_rgb, torch):
+def run_graph_steps(m, poses, cam, maps, first, steps, dev_depth, dev_rgb):
+    """One frame per step: integrate + raycast as one CUDA graph (mv_frame)."""
+    for k in range(steps):
+        i = first + k
+        m.frame(dev_depth[i], dev_rgb[i], cam, poses[i], out=maps)
+
+
+def run_eager_steps(m, poses, cam, maps, first, steps, dev_depth, dev_rgb):
+    """The same step as separate calls (per-kernel event timing possible)."""
     for k in range(steps):
         i = first + k
         m.integrate(dev_depth[i], dev_rgb[i], cam, poses[i])
         m.raycast(cam, poses[i], out=maps)
 
 
-def bench_storage(torch, Mapper, Config, wl, frames, poses, fmt, warmup, steps, dev_depth, dev_rgb,
-                  clocks=None):
-    """Device-timed integrate+raycast steps for one storage format."""
-    (vs,) = wl.volumes
-    cam = wl.cam
-    m = Mapper(Config())
-    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
-    maps = m.alloc_maps(cam)
-    run_native_steps(m, frames, poses, cam, maps, 0, warmup, dev_depth, dev_rgb, torch)
-    m.synchronize()
-    m.stats(reset=True)
-    m.timings(reset=True)
-    m.set_timing(True)
+def timed(torch, fn, clocks=None):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if clocks:
@@ -157,16 +153,40 @@ def bench_storage(torch, Mapper, Config, wl, frames, poses, fmt, warmup, steps, 
     barrier(torch)
     torch.cuda.synchronize()
     e0.record(stream)
-    run_native_steps(m, frames, poses, cam, maps, warmup, steps, dev_depth, dev_rgb, torch)
+    fn()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(torch)
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks else None
-    m.set_timing(False)
+    return e0.elapsed_time(e1), clk
+
+
+def bench_storage(torch, Mapper, Config, wl, poses, fmt, warmup, steps, dev_depth, dev_rgb,
+                  clocks=None, instrument=True):
+    """Device-timed steps for one storage format: `steps` graph steps (the
+    measured throughput), then `steps` eager steps on the following frames
+    with per-kernel CUDA events (the per-kernel roofline)."""
+    (vs,) = wl.volumes
+    cam = wl.cam
+    m = Mapper(Config())
+    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
+    maps = m.alloc_maps(cam)
+    run_graph_steps(m, poses, cam, maps, 0, warmup, dev_depth, dev_rgb)
+    m.synchronize()
+    m.stats(reset=True)
+    m.timings(reset=True)
+    ms, clk = timed(torch, lambda: run_graph_steps(m, poses, cam, maps, warmup, steps, dev_depth, dev_rgb),
+                    clocks)
     st = m.stats()
-    tm = m.timings()
-    out = dict(ms=ms, stats=st, timings=tm, clocks=clk, mapper=m, vid=vid, maps=maps)
+    tm_graph = m.timings(reset=True)
+    out = dict(ms=ms, stats=st, graph_timings=tm_graph, clocks=clk, mapper=m, vid=vid, maps=maps)
+    if instrument:
+        m.stats(reset=True)
+        m.set_timing(True)
+        ms_e, _ = timed(torch, lambda: run_eager_steps(m, poses, cam, maps, warmup + steps, steps,
+                                                      dev_depth, dev_rgb))
+        m.set_timing(False)
+        out.update(eager_ms=ms_e, eager_stats=m.stats(), timings=m.timings())
     return out
 
 
@@ -201,9 +221,9 @@ def integrate_bytes_per_voxel(fmt):
 def kernel_summary(res, fmt, cam, steps):
     """Per-kernel average launch time and algorithmic bytes per launch."""
     tm = res["timings"]
-    st = res["stats"]
     H, W = cam.height, cam.width
     out = {}
+    st = res["eager_stats"]
     n_int = max(tm["integrate"][2], 1)
     upd = st["updated"] / n_int
     band = st["band"] / n_int
@@ -284,8 +304,7 @@ def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
     def step(i):
         dd.copy_(hd[i], non_blocking=True)
         dc.copy_(hc[i], non_blocking=True)
-        m.integrate(dd, dc, cam, wl.poses[i % N_FRAMES_MAX])
-        m.raycast(cam, wl.poses[i % N_FRAMES_MAX], out=maps)
+        m.frame(dd, dc, cam, wl.poses[i % N_FRAMES_MAX], out=maps)
         out_d.copy_(maps["depth"], non_blocking=True)
         out_n.copy_(maps["normal"], non_blocking=True)
         out_c.copy_(maps["rgba"], non_blocking=True)
@@ -374,7 +393,7 @@ def main():
     if args.impl == "reference":
         return main_reference(args, rank)
 
-    n = args.warmup + args.steps
+    n = args.warmup + 2 * args.steps
     procs = max(1, min(16, (os.cpu_count() or 2) // max(world, 1)))
     frames = make_frames(n, procs)  # before any CUDA call
 
@@ -396,7 +415,7 @@ def main():
         clocks = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid))
     except Exception:
         clocks = ClockSampler(local_rank)
-    res = bench_storage(torch, Mapper, Config, wl, frames, poses, "f32", args.warmup, args.steps,
+    res = bench_storage(torch, Mapper, Config, wl, poses, "f32", args.warmup, args.steps,
                         dev_depth, dev_rgb, clocks=clocks)
     ms_max = allreduce_max(torch, res["ms"])
     upd_sum = allreduce_sum(torch, res["stats"]["updated"])
@@ -416,7 +435,8 @@ def main():
     integrate_roofline = {"bound": "hbm", "achieved": ik.get("achieved_gbs"), "peak": peak,
                           "unit": "GB/s", "frac": (ik.get("achieved_gbs") or 0.0) / peak,
                           "traffic": tri["dram_bytes_per_launch"] if tri else None}
-    launches = sum(v[0] for v in res["timings"].values())
+    # kernels of the graph timed region (frame_graph counts graph launches, not kernels)
+    launches = sum(v[0] for k, v in res["graph_timings"].items() if k != "frame_graph")
     m = res["mapper"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -432,6 +452,7 @@ def main():
             "swept_voxels_per_frame": res["stats"]["swept"] / args.steps,
             "bricks_per_frame": res["stats"]["bricks"] / args.steps,
             "band_voxels_per_frame": res["stats"]["band"] / args.steps,
+            "eager_ms_per_step": res["eager_ms"] / args.steps,
             "raycast_samples_per_ray": res["stats"]["ray_samples"] / max(res["stats"]["rays"], 1),
             "raycast_skips_per_ray": res["stats"]["ray_skips"] / max(res["stats"]["rays"], 1),
             "raycast_hit_fraction": res["stats"]["ray_hits"] / max(res["stats"]["rays"], 1),
@@ -441,7 +462,7 @@ def main():
     if not args.no_variants:
         variants = {}
         for fmt in ("f16", "i16"):
-            r = bench_storage(torch, Mapper, Config, wl, frames, poses, fmt, args.warmup, args.steps,
+            r = bench_storage(torch, Mapper, Config, wl, poses, fmt, args.warmup, args.steps,
                               dev_depth, dev_rgb)
             k = kernel_summary(r, fmt, cam, args.steps)
             msx = allreduce_max(torch, r["ms"])

@@ -222,6 +222,28 @@ mv_status mv_raycast_volume(mv_ctx *ctx, int32_t id, int32_t first, const mv_int
                             const double T_c2w[16], float *depth, float *normal, uint8_t *rgba,
                             float *vertex, int32_t *vol_id, void *stream);
 
+/* Launch shapes chosen by mv_autotune (or set by mv_set_tuning). */
+typedef struct {
+    int32_t raycast_tile;          /* 0: 16x8 CTA of 8x4 warps, 1: 32x4 of 8x4, 2: 8x16 of 8x4,
+                                      3: 32x4 CTA of 32x1 warps */
+    int32_t integrate_ctas_per_sm; /* persistent integration grid = SMs x this */
+    float raycast_ms[4];           /* measured per tile shape (mv_autotune only) */
+    float integrate_ms[5];         /* measured for 2, 4, 6, 8, 10 CTAs per SM (mv_autotune only) */
+} mv_tuning;
+
+/* Choose the raycast pixel tile and the integration grid size by timing the
+ * candidates on this frame and view: the raycast runs on the resident volumes
+ * (it changes no state), the integration on temporary scratch storage shaped
+ * like the largest resident volume (the map is not modified).  Synchronous;
+ * the choice applies to every later call of the context (results do not
+ * depend on it, only speed). */
+mv_status mv_autotune(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                      const double T_c2w[16], mv_tuning *out, void *stream);
+
+/* Set / read the launch shapes (raycast_tile, integrate_ctas_per_sm). */
+mv_status mv_set_tuning(mv_ctx *ctx, const mv_tuning *t);
+mv_status mv_get_tuning(mv_ctx *ctx, mv_tuning *t);
+
 /* Gradient target of mv_raycast_backward: the TSDF gradient of volume `id`
  * is accumulated (+=) into grad_tsdf, a device float32 array in the linear
  * order of mv_read_volume (h_r[0] * h_r[1] * h_r[2] values). */

@@ -58,6 +58,11 @@ class mv_timings(C.Structure):
                 ("timed", C.c_uint64 * MV_KERNEL_KINDS)]
 
 
+class mv_tuning(C.Structure):
+    _fields_ = [("raycast_tile", C.c_int32), ("integrate_ctas_per_sm", C.c_int32),
+                ("raycast_ms", C.c_float * 4), ("integrate_ms", C.c_float * 5)]
+
+
 class mv_grad_target(C.Structure):
     _fields_ = [("id", C.c_int32), ("grad_tsdf", C.c_void_p)]
 
@@ -88,6 +93,9 @@ _SIGNATURES = {
     "mv_frame": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_raycast_volume": ([_P, C.c_int32, C.c_int32, C.POINTER(mv_intrinsics), _D16, _P, _P, _P,
                            _P, _P, _P], C.c_int),
+    "mv_autotune": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, C.POINTER(mv_tuning), _P], C.c_int),
+    "mv_set_tuning": ([_P, C.POINTER(mv_tuning)], C.c_int),
+    "mv_get_tuning": ([_P, C.POINTER(mv_tuning)], C.c_int),
     "mv_raycast_backward": ([_P, C.POINTER(mv_intrinsics), _D16, C.c_int32, _P, _P, _P, _P, _P,
                              C.POINTER(mv_grad_target), C.c_int32, _P], C.c_int),
     "mv_swap_out": ([_P, C.c_int32, _P], C.c_int),

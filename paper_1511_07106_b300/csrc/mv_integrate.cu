@@ -517,13 +517,15 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
     return graph_node(g, exec, &nodes[3], nodes[2], a3.params((const void *)cell_flags_kernel, num_sms * 4, 256));
 }
 
-int integrate_occupancy_grid(int num_sms)
+int integrate_max_ctas_per_sm()
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integrate_kernel, 128, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 8;
-    return num_sms * per_sm;
+    return per_sm;
 }
+
+int integrate_occupancy_grid(int num_sms) { return num_sms * integrate_max_ctas_per_sm(); }
 
 }  // namespace mv

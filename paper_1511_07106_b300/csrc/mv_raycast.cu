@@ -33,8 +33,8 @@ struct RayOut {
     int *vol_id;
 };
 
-template <int FMT>
-__device__ __forceinline__ void load_fw(const VolDev &v, long long off, float &F, float &W)
+template <int FMT, typename Off>
+__device__ __forceinline__ void load_fw(const VolDev &v, Off off, float &F, float &W)
 {
     if (FMT == MV_TSDF_F32) {
         const float2 q = __ldg(reinterpret_cast<const float2 *>(v.fw) + off);
@@ -46,31 +46,55 @@ __device__ __forceinline__ void load_fw(const VolDev &v, long long off, float &F
     }
 }
 
-// Offsets of the 8 corners of the cell with lower corner (x, y, z).
-struct Corners {
-    long long base;
-    long long ox, oy, oz;
+// Brick-layout strides of one volume, hoisted out of the march.  Off is
+// uint32_t for volumes of fewer than 2^32 voxels (cheaper address math), else
+// long long.
+template <typename Off>
+struct Geo {
+    Off nb0, nb01;  // bricks per row, per slice
+    Off oy, oz;     // element step to the +y / +z neighbour across a brick face
+    int nby;
 };
 
-__device__ __forceinline__ Corners cell_corners(const VolDev &v, int x, int y, int z)
+template <typename Off>
+__device__ __forceinline__ Geo<Off> make_geo(const VolDev &v)
 {
-    Corners c;
-    c.base = vox_offset(v, x, y, z);
-    c.ox = ((x & 7) == 7) ? (long long)(kBrickVox - 7) : 1;
-    c.oy = ((y & 7) == 7) ? (long long)v.nb[0] * kBrickVox - 56 : 8;
-    c.oz = ((z & 7) == 7) ? (long long)v.nb[0] * v.nb[1] * kBrickVox - 448 : 64;
+    Geo<Off> g;
+    g.nb0 = (Off)v.nb[0];
+    g.nb01 = (Off)v.nb[0] * (Off)v.nb[1];
+    g.oy = g.nb0 * (Off)kBrickVox - (Off)56;
+    g.oz = g.nb01 * (Off)kBrickVox - (Off)448;
+    g.nby = v.nb[1];
+    return g;
+}
+
+// Offsets of the 8 corners of the cell with lower corner (x, y, z).
+template <typename Off>
+struct Corners {
+    Off base, ox, oy, oz;
+};
+
+template <typename Off>
+__device__ __forceinline__ Corners<Off> cell_corners(const Geo<Off> &g, int x, int y, int z)
+{
+    Corners<Off> c;
+    const Off b = (Off)(z >> 3) * g.nb01 + (Off)(y >> 3) * g.nb0 + (Off)(x >> 3);
+    c.base = b * (Off)kBrickVox + (Off)(((z & 7) << 6) | ((y & 7) << 3) | (x & 7));
+    c.ox = ((x & 7) == 7) ? (Off)(kBrickVox - 7) : (Off)1;
+    c.oy = ((y & 7) == 7) ? g.oy : (Off)8;
+    c.oz = ((z & 7) == 7) ? g.oz : (Off)64;
     return c;
 }
 
 // Trilinear F in a cell; valid = all 8 corners observed.
-template <int FMT>
-__device__ __forceinline__ float trilinear(const VolDev &v, const Corners &c, float fx, float fy,
+template <int FMT, typename Off>
+__device__ __forceinline__ float trilinear(const VolDev &v, const Corners<Off> &c, float fx, float fy,
                                            float fz, bool &valid)
 {
     float F[8], W[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const long long off = c.base + ((k & 1) ? c.ox : 0) + ((k & 2) ? c.oy : 0) + ((k & 4) ? c.oz : 0);
+        const Off off = c.base + ((k & 1) ? c.ox : (Off)0) + ((k & 2) ? c.oy : (Off)0) + ((k & 4) ? c.oz : (Off)0);
         load_fw<FMT>(v, off, F[k], W[k]);
     }
     valid = (W[0] > 0.f) & (W[1] > 0.f) & (W[2] > 0.f) & (W[3] > 0.f) & (W[4] > 0.f) &
@@ -106,8 +130,9 @@ __device__ __forceinline__ void locate(const VolDev &v, const VolRay &vr, const 
     }
 }
 
-template <int FMT>
-__device__ __forceinline__ float eval_at(const VolDev &v, const VolRay &vr, float k, bool &valid)
+template <int FMT, typename Off>
+__device__ __forceinline__ float eval_at(const VolDev &v, const Geo<Off> &g, const VolRay &vr, float k,
+                                         bool &valid)
 {
     float rr[3];
 #pragma unroll
@@ -115,7 +140,7 @@ __device__ __forceinline__ float eval_at(const VolDev &v, const VolRay &vr, floa
     int cell[3];
     float f[3];
     locate(v, vr, rr, cell, f);
-    const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+    const Corners<Off> c = cell_corners(g, cell[0], cell[1], cell[2]);
     return trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
 }
 
@@ -132,8 +157,9 @@ struct Hit {
 };
 
 // Gradient (normal) and colour in the hit cell.
-template <int FMT>
-__device__ __forceinline__ void shade(const VolDev &v, const VolRay &vr, float ks, Hit &h)
+template <int FMT, typename Off>
+__device__ __forceinline__ void shade(const VolDev &v, const Geo<Off> &geo, const VolRay &vr, float ks,
+                                      Hit &h)
 {
     float rr[3];
 #pragma unroll
@@ -141,13 +167,13 @@ __device__ __forceinline__ void shade(const VolDev &v, const VolRay &vr, float k
     int cell[3];
     float f[3];
     locate(v, vr, rr, cell, f);
-    const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+    const Corners<Off> c = cell_corners(geo, cell[0], cell[1], cell[2]);
     float F[8], W[8];
     uint32_t col[8];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const long long off = c.base + ((k & 1) ? c.ox : 0) + ((k & 2) ? c.oy : 0) + ((k & 4) ? c.oz : 0);
+        const Off off = c.base + ((k & 1) ? c.ox : (Off)0) + ((k & 2) ? c.oy : (Off)0) + ((k & 4) ? c.oz : (Off)0);
         load_fw<FMT>(v, off, F[k], W[k]);
         col[k] = __ldg(v.rgba + off);
         ok &= W[k] > 0.f;
@@ -248,10 +274,11 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
 // the run's last sample alone.  The march therefore jumps to that last sample
 // (at least m voxels inside the run) and evaluates it normally: the result is
 // that of the dense march, not an approximation.
-template <int FMT>
+template <int FMT, typename Off>
 __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
                              const float d[3], float dn, int slot, Hit &best, RayCount &rc)
 {
+    const Geo<Off> g = make_geo<Off>(v);
     VolRay vr;
     float dirv[3];
 #pragma unroll
@@ -290,26 +317,29 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
 
     int state = 0;  // 0: no valid previous sample, 1: previous valid > 0, -1: previous valid <= 0
     float Fprev = 0.f;
-    long long cur_b = -1;
+    int cur_b = -1;
     for (int kk = 0; kk <= nk; ++kk) {
         float k = k0 + (float)kk;
-        float rr[3], L[3];
-        int bi[3];
+        float rr[3], f[3];
+        int cell[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
-            L[a] = (float)vr.oi[a] + rr[a];
-            bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
-        }
-        long long bidx = ((long long)bi[2] * v.nb[1] + bi[1]) * v.nb[0] + bi[0];
+        for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+        locate(v, vr, rr, cell, f);
+        // brick of the sample's cell (its lower corner)
+        int bidx = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
         if (bidx != cur_b) {
             cur_b = bidx;
             if (__ldg(v.cflag + bidx) & kCellSkip) {
+                float L[3];
+                int bi[3];
                 bool inside = true;
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+                for (int a = 0; a < 3; ++a) {
+                    L[a] = (float)vr.oi[a] + rr[a];
+                    bi[a] = cell[a] >> 3;
                     inside &= (L[a] >= (float)(bi[a] * kBrick) + m) &
                               (L[a] <= (float)min(bi[a] * kBrick + kBrick, v.r[a] - 1) - m);
+                }
                 if (inside) {
                     const float run = skip_run(v, L, vr.dq, bi, m);
                     const int jump = (int)fminf(floorf(run), (float)(nk - kk));
@@ -318,22 +348,16 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                         kk += jump;
                         k = k0 + (float)kk;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
-                            L[a] = (float)vr.oi[a] + rr[a];
-                            bi[a] = max(0, min(v.nb[a] - 1, (int)floorf(L[a] * 0.125f)));
-                        }
-                        cur_b = ((long long)bi[2] * v.nb[1] + bi[1]) * v.nb[0] + bi[0];
+                        for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
+                        locate(v, vr, rr, cell, f);
+                        cur_b = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
                         state = 0;
                         ++rc.skips;
                     }
                 }
             }
         }
-        int cell[3];
-        float f[3];
-        locate(v, vr, rr, cell, f);
-        const Corners c = cell_corners(v, cell[0], cell[1], cell[2]);
+        const Corners<Off> c = cell_corners(g, cell[0], cell[1], cell[2]);
         bool valid;
         const float F = trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
         ++rc.samples;
@@ -343,9 +367,10 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
             float a = k - 1.0f, b = k, ga = Fprev, gb = F;
             for (int it = 0; it < P.n_bisect; ++it) {
                 const float mid = 0.5f * (a + b);
+                if (mid <= a || mid >= b) break;  // interval at float resolution
                 bool vv;
-                const float g = eval_at<FMT>(v, vr, mid, vv);
-                if (g > 0.f) { a = mid; ga = g; } else { b = mid; gb = g; }
+                const float gm = eval_at<FMT>(v, g, vr, mid, vv);
+                if (gm > 0.f) { a = mid; ga = gm; } else { b = mid; gb = gm; }
             }
             const float den = ga - gb;
             const float ks = den > 0.f ? fmaf(b - a, ga / den, a) : 0.5f * (a + b);
@@ -354,7 +379,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                 best.tau = tau;
                 best.id = v.id;
                 best.slot = slot;
-                shade<FMT>(v, vr, ks, best);
+                shade<FMT>(v, g, vr, ks, best);
             }
             return;
         }
@@ -409,10 +434,19 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     for (int i = 0; i < nvol; ++i) {
         const VolDev &v = vols[i];
         const VolFrame vf = vfs[i];
-        switch (v.fmt) {
-        case MV_TSDF_F32: march_volume<MV_TSDF_F32>(v, vf, P, d, dn, i, best, rc); break;
-        case MV_TSDF_F16: march_volume<MV_TSDF_F16>(v, vf, P, d, dn, i, best, rc); break;
-        default: march_volume<MV_TSDF_I16>(v, vf, P, d, dn, i, best, rc); break;
+        const bool narrow = v.nbricks * kBrickVox <= 0xFFFFFFFFll;
+        if (narrow) {
+            switch (v.fmt) {
+            case MV_TSDF_F32: march_volume<MV_TSDF_F32, uint32_t>(v, vf, P, d, dn, i, best, rc); break;
+            case MV_TSDF_F16: march_volume<MV_TSDF_F16, uint32_t>(v, vf, P, d, dn, i, best, rc); break;
+            default: march_volume<MV_TSDF_I16, uint32_t>(v, vf, P, d, dn, i, best, rc); break;
+            }
+        } else {
+            switch (v.fmt) {
+            case MV_TSDF_F32: march_volume<MV_TSDF_F32, long long>(v, vf, P, d, dn, i, best, rc); break;
+            case MV_TSDF_F16: march_volume<MV_TSDF_F16, long long>(v, vf, P, d, dn, i, best, rc); break;
+            default: march_volume<MV_TSDF_I16, long long>(v, vf, P, d, dn, i, best, rc); break;
+            }
         }
     }
     if (best.slot == -2) return;  // merge: the existing entry stays
@@ -432,20 +466,57 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     }
 }
 
-__global__ void __launch_bounds__(128, 8) raycast_kernel(const VolDev *__restrict__ vols,
-                                                      const VolFrame *__restrict__ vfs, int nvol,
-                                                      FrameParams P, RayOut out, int merge,
-                                                      Stats *__restrict__ stats)
+// Pixel tiles (128 threads per CTA, selected by the autotuner):
+//   0: 16x8 CTA of 2x2 warps, each warp an 8x4 tile
+//   1: 32x4 CTA of 4x1 warps, each warp an 8x4 tile
+//   2: 8x16 CTA of 1x4 warps, each warp an 8x4 tile
+//   3: 32x4 CTA of 1x4 warps, each warp a 32x1 row
+template <int TILE>
+struct Tile {
+    static constexpr int W = (TILE == 0) ? 16 : (TILE == 2) ? 8 : 32;
+    static constexpr int H = 128 / W;
+    __device__ static void pixel(int w, int lane, int &x, int &y)
+    {
+        if (TILE == 0) { x = (w & 1) * 8 + (lane & 7); y = (w >> 1) * 4 + (lane >> 3); }
+        else if (TILE == 1) { x = w * 8 + (lane & 7); y = lane >> 3; }
+        else if (TILE == 2) { x = lane & 7; y = w * 4 + (lane >> 3); }
+        else { x = lane; y = w; }
+    }
+};
+
+template <int TILE>
+__global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restrict__ vols,
+                                                         const VolFrame *__restrict__ vfs, int nvol,
+                                                         FrameParams P, RayOut out, int merge,
+                                                         Stats *__restrict__ stats)
 {
-    // 16x8-pixel CTA; each warp covers an 8x4 tile
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * 16 + (w & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 8 + (w >> 1) * 4 + (lane >> 3);
+    int tx, ty;
+    Tile<TILE>::pixel(w, lane, tx, ty);
+    const int px = blockIdx.x * Tile<TILE>::W + tx;
+    const int py = blockIdx.y * Tile<TILE>::H + ty;
     const bool active = px < P.width && py < P.height;
     RayCount rc{0u, 0u};
     if (active) trace_pixel(vols, vfs, nvol, P, out, merge, px, py, rc);
     add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips,
                (active && out.depth && out.depth[(size_t)py * P.width + px] > 0.f) ? 1u : 0u);
+}
+
+static const void *raycast_fn(int tile)
+{
+    switch (tile) {
+    case 1: return (const void *)raycast_kernel<1>;
+    case 2: return (const void *)raycast_kernel<2>;
+    case 3: return (const void *)raycast_kernel<3>;
+    default: return (const void *)raycast_kernel<0>;
+    }
+}
+
+static dim3 raycast_grid(int tile, int width, int height)
+{
+    const int tw = (tile == 0) ? 16 : (tile == 2) ? 8 : 32;
+    const int th = 128 / tw;
+    return dim3((width + tw - 1) / tw, (height + th - 1) / th);
 }
 
 cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
@@ -456,24 +527,29 @@ cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_
 cudaError_t graph_raycast(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[2],
                           cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                           const FrameParams &P, float *depth, float *normal, uint8_t *rgba,
-                          float *vertex, int *vol_id, Stats *stats)
+                          float *vertex, int *vol_id, Stats *stats, int tile)
 {
     cudaError_t e = frame_setup_node(g, exec, &nodes[0], dep, vols, nvol, P, vf);
     if (e != cudaSuccess) return e;
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
     NodeArgs<const VolDev *, const VolFrame *, int, FrameParams, RayOut, int, Stats *> a(
         vols, vf, nvol, P, o, 0, stats);
-    dim3 grid((P.width + 15) / 16, (P.height + 7) / 8);
-    return graph_node(g, exec, &nodes[1], nodes[0], a.params((const void *)raycast_kernel, grid, 128));
+    return graph_node(g, exec, &nodes[1], nodes[0],
+                      a.params(raycast_fn(tile), raycast_grid(tile, P.width, P.height), 128));
 }
 
 cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,
                            float *depth, float *normal, uint8_t *rgba, float *vertex, int *vol_id,
-                           int merge, Stats *stats, cudaStream_t s)
+                           int merge, Stats *stats, int tile, cudaStream_t s)
 {
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
-    dim3 grid((P.width + 15) / 16, (P.height + 7) / 8);
-    raycast_kernel<<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats);
+    const dim3 grid = raycast_grid(tile, P.width, P.height);
+    switch (tile) {
+    case 1: raycast_kernel<1><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
+    case 2: raycast_kernel<2><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
+    case 3: raycast_kernel<3><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
+    default: raycast_kernel<0><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
+    }
     return cudaGetLastError();
 }
 

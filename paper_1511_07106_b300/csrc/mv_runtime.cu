@@ -31,8 +31,9 @@ cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, co
 cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
 cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
-                           float *, uint8_t *, float *, int *, int, Stats *, cudaStream_t);
+                           float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t);
 int integrate_occupancy_grid(int num_sms);
+int integrate_max_ctas_per_sm();
 struct BackwardArgs {
     const VolDev *vols;
     int nvol;
@@ -53,7 +54,7 @@ cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[4], cu
                             unsigned *, const float *, const uint8_t *, Stats *, int, int);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[2], cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
-                          uint8_t *, float *, int *, Stats *);
+                          uint8_t *, float *, int *, Stats *, int);
 }  // namespace mv
 
 using namespace mv;
@@ -86,6 +87,8 @@ struct mv_ctx {
     int device = 0;
     int num_sms = 0;
     int grid_integrate = 0;
+    int ray_tile = 0;
+    int ctas_per_sm = 0;
     std::map<int, Volume *> vols;
     int next_id = 0;
     cudaStream_t swap_stream = nullptr;
@@ -103,7 +106,7 @@ struct mv_ctx {
         cudaGraphExec_t exec = nullptr;
         cudaGraphNode_t nodes[6] = {};
         unsigned long long table_version = ~0ull;
-        int width = 0, height = 0, grid_int = 0;
+        int width = 0, height = 0, grid_int = 0, tile = 0;
     } fg;
     VolDev *d_table = nullptr;
     VolFrame *d_vf = nullptr;
@@ -414,7 +417,8 @@ mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out)
         mv_destroy(x);
         return e == cudaErrorMemoryAllocation ? MV_ERR_OOM : MV_ERR_CUDA;
     }
-    x->grid_integrate = integrate_occupancy_grid(x->num_sms);
+    x->ctas_per_sm = integrate_max_ctas_per_sm();
+    x->grid_integrate = x->num_sms * x->ctas_per_sm;
     *out = x;
     return MV_OK;
 }
@@ -652,7 +656,7 @@ static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_in
             return launch_frame_setup(tab, nvol, P, vf, nullptr, s); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
         return launch_raycast(tab, vf, nvol, P, depth, normal, rgba, vertex, vol_id, merge ? 1 : 0,
-                              c->d_stats, s); }));
+                              c->d_stats, c->ray_tile, s); }));
     return end_call(c, s);
 }
 
@@ -685,13 +689,14 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     if (nvol == 0) {  // nothing to integrate: the maps are all misses
         MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
             return launch_raycast(c->d_table, c->d_vf, 0, P, depth_out, normal, rgba, vertex, vol_id, 0,
-                                  c->d_stats, s); }));
+                                  c->d_stats, c->ray_tile, s); }));
         return end_call(c, s);
     }
     const long long total = c->table.back().brick_base + c->table.back().nbricks;
     auto &fg = c->fg;
     const bool rebuild = !fg.exec || fg.table_version != c->table_version || fg.width != K->width ||
-                         fg.height != K->height || fg.grid_int != c->grid_integrate;
+                         fg.height != K->height || fg.grid_int != c->grid_integrate ||
+                         fg.tile != c->ray_tile;
     if (rebuild) {
         if (fg.exec) cudaGraphExecDestroy(fg.exec);
         if (fg.g) cudaGraphDestroy(fg.g);
@@ -704,19 +709,156 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
                                c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
                                c->num_sms));
     MV_CUDA(c, graph_raycast(fg.g, upd, fg.nodes + 4, fg.nodes[3], c->d_table, nvol, c->d_vf, P,
-                             depth_out, normal, rgba, vertex, vol_id, c->d_stats));
+                             depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile));
     if (rebuild) {
         MV_CUDA(c, cudaGraphInstantiate(&fg.exec, fg.g, 0));
         fg.table_version = c->table_version;
         fg.width = K->width;
         fg.height = K->height;
         fg.grid_int = c->grid_integrate;
+        fg.tile = c->ray_tile;
     }
     MV_CUDA(c, counted_launch(c, MV_KERNEL_FRAME_GRAPH, s, [&] { return cudaGraphLaunch(fg.exec, s); }));
     const int kinds[6] = {MV_KERNEL_SETUP, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE, MV_KERNEL_CELL_FLAGS,
                           MV_KERNEL_SETUP, MV_KERNEL_RAYCAST};
     for (int k : kinds) c->launches[k] += 1;
     return end_call(c, s);
+}
+
+static float time_ms(cudaStream_t s, cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                      const double T[16], mv_tuning *out, void *stream)
+{
+    if (!c || !out) return MV_ERR_ARG;
+    if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    std::memset(out, 0, sizeof(*out));
+    const FrameParams P = make_params(c, K, T);
+    const int nvol = (int)c->table.size();
+    cudaEvent_t a, b;
+    MV_CUDA(c, cudaEventCreate(&a));
+    MV_CUDA(c, cudaEventCreate(&b));
+    const size_t npx = (size_t)K->width * K->height;
+    char *maps = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&maps, npx * 36, s);
+    // raycast tile shapes on the resident volumes (the raycast changes no state)
+    float best = 3.0e38f;
+    int best_tile = c->ray_tile;
+    for (int tile = 0; tile < 4 && e == cudaSuccess; ++tile) {
+        float tbest = 3.0e38f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            e = launch_frame_setup(c->d_table, nvol, P, c->d_vf, nullptr, s);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            if (e == cudaSuccess)
+                e = launch_raycast(c->d_table, c->d_vf, nvol, P, (float *)maps, (float *)(maps + 4 * npx),
+                                   (uint8_t *)(maps + 16 * npx), (float *)(maps + 20 * npx),
+                                   (int *)(maps + 32 * npx), 0, nullptr, tile, s);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess && rep > 0) tbest = fminf(tbest, time_ms(s, a, b));
+        }
+        out->raycast_ms[tile] = tbest;
+        if (tbest < best) { best = tbest; best_tile = tile; }
+    }
+    if (maps) cudaFreeAsync(maps, s);
+    // persistent-grid sizes of the integration, on scratch storage shaped like
+    // the largest resident volume (the map itself is not touched)
+    int best_ctas = c->ctas_per_sm;
+    if (e == cudaSuccess && nvol > 0) {
+        int big = 0;
+        for (int i = 1; i < nvol; ++i)
+            if (c->table[i].nbricks > c->table[big].nbricks) big = i;
+        VolDev sv = c->table[big];
+        const Volume *vol = c->vols.at(sv.id);
+        void *sfw = nullptr, *srgba = nullptr, *sflag = nullptr;
+        VolDev *stab = nullptr;
+        VolFrame *svf = nullptr;
+        uint2 *slist = nullptr;
+        unsigned *scount = nullptr;
+        e = cudaMallocAsync(&sfw, vol->fw_bytes, s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&srgba, vol->rgba_bytes, s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&sflag, vol->flag_bytes, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&stab, sizeof(VolDev), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&svf, sizeof(VolFrame), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&slist, sizeof(uint2) * sv.nbricks, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scount, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sfw, 0, vol->fw_bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(srgba, 0, vol->rgba_bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sflag, kFlagsNew, (size_t)sv.nbricks, s);
+        sv.fw = sfw;
+        sv.rgba = (uint32_t *)srgba;
+        sv.bflag = (uint8_t *)sflag;
+        sv.cflag = nullptr;
+        sv.brick_base = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stab, &sv, sizeof(VolDev), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sv is a stack value
+        const int maxc = integrate_max_ctas_per_sm();
+        const int cands[5] = {2, 4, 6, 8, 10};
+        float ibest = 3.0e38f;
+        for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
+            const int ctas = cands[ci];
+            if (ctas > maxc) break;
+            float tbest = 3.0e38f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = launch_frame_setup(stab, 1, P, svf, scount, s);
+                if (e == cudaSuccess)
+                    e = launch_brick_list(stab, 1, svf, P, 0, sv.nbricks, slist, scount, c->num_sms, s);
+                if (e == cudaSuccess) e = cudaEventRecord(a, s);
+                if (e == cudaSuccess)
+                    e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
+                                         c->num_sms * ctas, s);
+                if (e == cudaSuccess) e = cudaEventRecord(b, s);
+                if (e == cudaSuccess && rep > 0) tbest = fminf(tbest, time_ms(s, a, b));
+            }
+            out->integrate_ms[ci] = tbest;
+            if (tbest < ibest) { ibest = tbest; best_ctas = ctas; }
+        }
+        for (void *p : {sfw, srgba, sflag, (void *)stab, (void *)svf, (void *)slist, (void *)scount})
+            if (p) cudaFreeAsync(p, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, "autotune");
+    }
+    c->ray_tile = best_tile;
+    c->ctas_per_sm = best_ctas;
+    c->grid_integrate = c->num_sms * best_ctas;
+    out->raycast_tile = best_tile;
+    out->integrate_ctas_per_sm = best_ctas;
+    return end_call(c, s);
+}
+
+mv_status mv_set_tuning(mv_ctx *c, const mv_tuning *t)
+{
+    if (!c || !t) return MV_ERR_ARG;
+    if (t->raycast_tile < 0 || t->raycast_tile > 3 || t->integrate_ctas_per_sm < 1 ||
+        t->integrate_ctas_per_sm > integrate_max_ctas_per_sm())
+        return fail(c, MV_ERR_ARG, "bad tuning values");
+    c->ray_tile = t->raycast_tile;
+    c->ctas_per_sm = t->integrate_ctas_per_sm;
+    c->grid_integrate = c->num_sms * t->integrate_ctas_per_sm;
+    return MV_OK;
+}
+
+mv_status mv_get_tuning(mv_ctx *c, mv_tuning *t)
+{
+    if (!c || !t) return MV_ERR_ARG;
+    std::memset(t, 0, sizeof(*t));
+    t->raycast_tile = c->ray_tile;
+    t->integrate_ctas_per_sm = c->ctas_per_sm;
+    return MV_OK;
 }
 
 mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,

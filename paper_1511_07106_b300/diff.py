@@ -137,7 +137,7 @@ def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, l
         loss = l1_loss(depth, colour, ref_depth, ref_colour, colour_weight)
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
         if callback:
-            callback(it, pose_from_twist(xi.detach(), T0).numpy(), float(loss))
+            callback(it, pose_from_twist(xi.detach(), T0).numpy(), losses[-1])
     return pose_from_twist(xi.detach(), T0).numpy(), losses

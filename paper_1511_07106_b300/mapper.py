@@ -303,6 +303,31 @@ class Mapper:
         self._check(self._lib.mv_get_stats(self._h, C.byref(s), int(bool(reset))))
         return {k: getattr(s, k) for k, _ in _abi.mv_stats._fields_}
 
+    def autotune(self, depth, rgb, cam, T, stream=None) -> dict:
+        """Time the raycast tile shapes and integration grid sizes on this
+        frame (the map is not modified) and keep the fastest."""
+        import torch
+        K = intrinsics(cam)
+        n = cam.width * cam.height
+        t = _abi.mv_tuning()
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_autotune(self._h, _dptr(depth, torch.float32, n, "depth"),
+                                          _dptr(rgb, torch.uint8, 3 * n, "rgb"), C.byref(K), Tp,
+                                          C.byref(t), _stream(stream)))
+        del keep
+        return dict(raycast_tile=t.raycast_tile, integrate_ctas_per_sm=t.integrate_ctas_per_sm,
+                    raycast_ms=list(t.raycast_ms), integrate_ms=list(t.integrate_ms))
+
+    def set_tuning(self, raycast_tile: int, integrate_ctas_per_sm: int):
+        t = _abi.mv_tuning()
+        t.raycast_tile, t.integrate_ctas_per_sm = int(raycast_tile), int(integrate_ctas_per_sm)
+        self._check(self._lib.mv_set_tuning(self._h, C.byref(t)))
+
+    def tuning(self) -> dict:
+        t = _abi.mv_tuning()
+        self._check(self._lib.mv_get_tuning(self._h, C.byref(t)))
+        return dict(raycast_tile=t.raycast_tile, integrate_ctas_per_sm=t.integrate_ctas_per_sm)
+
     def set_timing(self, enable: bool):
         self._check(self._lib.mv_set_timing(self._h, int(bool(enable))))
 

@@ -422,3 +422,45 @@ def perturb_poses(poses, seed: int = 6, sigma_t: float = 0.02, sigma_r_deg: floa
         P[:3, 3] = c - D[:3, :3] @ c + D[:3, 3]
         out.append(P @ np.asarray(T))
     return out
+
+
+def uneven_volumes(n_volumes: int = 64, frames: int = 300, seed: int = 4, width: int = 640,
+                   height: int = 480, edges=(128, 192, 256, 384, 512, 768), pitch_mm=(1.0, 8.0),
+                   half_extent: float = 9.0, height_m: float = 8.0) -> Workload:
+    """Batched uneven volumes: n volumes with edge lengths drawn uniformly from
+    `edges` and voxel pitch uniform in `pitch_mm`, placed without overlap
+    (largest first, each on its own pitch lattice) in a hall of
+    2 half_extent x 2 half_extent x height_m metres holding 40 boxes and
+    spheres; 640x480 frames along a handheld path at the hall's centre.  With
+    the defaults the 64 volumes hold about 7 G voxels."""
+    rng = np.random.Generator(np.random.Philox(key=(seed << 32) | 0xABC))
+    specs = []
+    for _ in range(n_volumes):
+        e = int(rng.choice(edges))
+        s = _f32(rng.uniform(*pitch_mm) * 1e-3)
+        specs.append((e, s))
+    specs.sort(key=lambda es: -es[0] * es[1])
+    lo_b = np.array([-half_extent, -half_extent, 0.0])
+    hi_b = np.array([half_extent, half_extent, height_m])
+    boxes_placed = []
+    vols = []
+    for e, s in specs:
+        side = e * s
+        for attempt in range(5000):
+            p = rng.uniform(lo_b, np.maximum(lo_b, hi_b - side))
+            h = np.round(p / s).astype(int)
+            a = h * s
+            b = a + (e - 1) * s
+            if any(np.all(a < bb) and np.all(aa < b) for aa, bb in boxes_placed):
+                continue
+            boxes_placed.append((a, b))
+            vols.append(VolumeSpec(tuple(int(x) for x in h), (e, e, e), s))
+            break
+        else:
+            raise RuntimeError("could not place all volumes; enlarge the hall")
+    scene = _room_scene(rng, tuple(lo_b + 0.05), tuple(hi_b - 0.05), 24, 16, (0.0, 0.0), 1.0)
+    f = 525.0 * width / 640.0
+    cam = Camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
+    poses = handheld_trajectory(frames, seed, (0.0, 0.0, 1.5), (0.6, 0.6, 0.2), 3.0, 1.2)
+    return Workload(f"{n_volumes} uneven volumes (edges {edges[0]}-{edges[-1]}, {pitch_mm[0]:g}-"
+                    f"{pitch_mm[1]:g} mm), {width}x{height}", cam, scene, poses, vols, seed)

@@ -366,3 +366,37 @@ def test_frame_graph_equals_separate_calls():
 
 def _spec(t):
     return t.h, t.r, t.s
+
+
+def test_autotune_changes_speed_not_results():
+    """mv_autotune leaves the map untouched, and every launch shape gives
+    bit-identical volumes and maps."""
+    wl = synth.single_volume_128(frames=4, res=64)
+    (vs,) = wl.volumes
+    a, b = Mapper(), Mapper()
+    va, vb = a.add_volume(vs.h, vs.r, vs.s), b.add_volume(vs.h, vs.r, vs.s)
+    d, c = wl.frame(0)
+    a.integrate(dev(d), dev(c), wl.cam, wl.poses[0])
+    b.integrate(dev(d), dev(c), wl.cam, wl.poses[0])
+    before = b.read_decoded(vb)
+    d1, c1 = wl.frame(1)
+    tun = b.autotune(dev(d1), dev(c1), wl.cam, wl.poses[1])
+    assert tun["raycast_tile"] in range(4) and tun["integrate_ctas_per_sm"] >= 1
+    assert all(t > 0 for t in tun["raycast_ms"])
+    after = b.read_decoded(vb)
+    for x, y in zip(before, after):
+        np.testing.assert_array_equal(x, y)
+    for i in range(1, 4):
+        d, c = wl.frame(i)
+        a.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+        b.frame(dev(d), dev(c), wl.cam, wl.poses[i])
+    for x, y in zip(a.read_decoded(va), b.read_decoded(vb)):
+        np.testing.assert_array_equal(x, y)
+    ref = gpu_maps(a.raycast(wl.cam, wl.poses[2]))
+    for tile in range(4):
+        b.set_tuning(tile, 2)
+        got = gpu_maps(b.raycast(wl.cam, wl.poses[2]))
+        for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+            np.testing.assert_array_equal(ref[key], got[key])
+    a.close()
+    b.close()
