@@ -172,6 +172,7 @@ def bench_storage(torch, Mapper, Config, wl, poses, fmt, warmup, steps, dev_dept
     vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
     maps = m.alloc_maps(cam)
     run_graph_steps(m, poses, cam, maps, 0, warmup, dev_depth, dev_rgb)
+    tuning = m.autotune(dev_depth[warmup - 1], dev_rgb[warmup - 1], cam, poses[warmup - 1])
     m.synchronize()
     m.stats(reset=True)
     m.timings(reset=True)
@@ -179,7 +180,8 @@ def bench_storage(torch, Mapper, Config, wl, poses, fmt, warmup, steps, dev_dept
                     clocks)
     st = m.stats()
     tm_graph = m.timings(reset=True)
-    out = dict(ms=ms, stats=st, graph_timings=tm_graph, clocks=clk, mapper=m, vid=vid, maps=maps)
+    out = dict(ms=ms, stats=st, graph_timings=tm_graph, clocks=clk, mapper=m, vid=vid, maps=maps,
+               tuning=tuning)
     if instrument:
         m.stats(reset=True)
         m.set_timing(True)
@@ -328,6 +330,159 @@ def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
     return st["updated"], dt, h2d, d2h
 
 
+def _render_uneven(i):
+    return synth.uneven_volumes(frames=N_FRAMES_MAX).frame(i)
+
+
+def _render_tiles(i):
+    return synth.room_tiles(frames=N_FRAMES_MAX).frame(i)
+
+
+def _gen(fn, idx, procs):
+    with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, idx))
+
+
+def bench_uneven(torch, Mapper, Config, frames, steps, warmup):
+    """64 volumes of uneven size and pitch (about 7.3 G voxels): one batched
+    graph per frame vs the paper's per-volume loop, and storage formats."""
+    wl = synth.uneven_volumes(frames=N_FRAMES_MAX)
+    cam = wl.cam
+    dd = torch.from_numpy(np.stack([f[0] for f in frames])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames])).cuda()
+    out = {"workload": wl.name, "volumes": len(wl.volumes),
+           "voxels": int(sum(np.prod(v.r) for v in wl.volumes)), "steps": steps}
+    for mode, fmt in (("batched", "f32"), ("per_volume", "f32"), ("batched", "f16"), ("batched", "i16")):
+        m = Mapper(Config())
+        ids = [m.add_volume(v.h, v.r, v.s, fmt) for v in wl.volumes]
+        maps = m.alloc_maps(cam)
+
+        def step(i):
+            if mode == "batched":
+                m.frame(dd[i], dc[i], cam, wl.poses[i], out=maps)
+            else:
+                for vid in ids:
+                    m.integrate_volume(vid, dd[i], dc[i], cam, wl.poses[i])
+                for k, vid in enumerate(ids):
+                    m.raycast_volume(vid, k == 0, cam, wl.poses[i], maps)
+
+        for i in range(warmup):
+            step(i)
+        if mode == "batched":
+            m.autotune(dd[warmup - 1], dc[warmup - 1], cam, wl.poses[warmup - 1])
+        m.synchronize()
+        m.stats(reset=True)
+        ms, _ = timed(torch, lambda: [step(warmup + k) for k in range(steps)])
+        st = m.stats()
+        key = f"{mode}_{fmt}"
+        out[key] = {"ms_per_step": ms / steps, "voxel_updates_per_s": st["updated"] / (ms * 1e-3),
+                    "mrays_per_s": cam.width * cam.height * steps / (ms * 1e-3) / 1e6,
+                    "updated_voxels_per_frame": st["updated"] / steps}
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    out["batched_over_per_volume"] = out["per_volume_f32"]["ms_per_step"] / out["batched_f32"]["ms_per_step"]
+    return out
+
+
+def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
+    """Differentiable raycast: 8 x 256^3 tiles (2 mm) prefilled from the given
+    frames; 16 poses perturbed by N(0, 2 cm) / N(0, 1 deg); forward +
+    backward throughput and 50 Adam steps of pose refinement."""
+    from paper_1511_07106_b300 import diff
+    wl = synth.room_tiles(frames=N_FRAMES_MAX)
+    cam = wl.cam
+    m = Mapper(Config(n_bisect=30))
+    for v in wl.volumes:
+        m.add_volume(v.h, v.r, v.s)
+    for i, (d, c) in enumerate(frames):
+        m.integrate(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), cam, wl.poses[i])
+    idx = np.linspace(0, len(frames) - 1, n_poses).astype(int)
+    T_true = np.stack([wl.poses[i] for i in idx])
+    T_init = np.stack(synth.perturb_poses(list(T_true), seed=6))
+    with torch.no_grad():
+        ref_d, ref_c = diff.render(m, cam, torch.tensor(T_true))
+    # forward + backward timing at the perturbed poses
+    T = torch.tensor(T_init, requires_grad=True)
+    for _ in range(2):
+        dpt, col = diff.render(m, cam, T)
+        diff.l1_loss(dpt, col, ref_d, ref_c).backward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        dpt, col = diff.render(m, cam, T)
+        loss = diff.l1_loss(dpt, col, ref_d, ref_c)
+        loss.backward()
+    torch.cuda.synchronize()
+    fb_ms = (time.perf_counter() - t0) / reps * 1e3
+    m.timings(reset=True)
+    m.set_timing(True)
+    dpt, col = diff.render(m, cam, T)
+    diff.l1_loss(dpt, col, ref_d, ref_c).backward()
+    m.set_timing(False)
+    tm = m.timings()
+
+    def err(Ts):
+        t = float(np.mean([np.linalg.norm(a[:3, 3] - b[:3, 3]) for a, b in zip(Ts, T_true)]))
+        r = float(np.mean([np.degrees(np.arccos(np.clip((np.trace(a[:3, :3].T @ b[:3, :3]) - 1) / 2, -1, 1)))
+                           for a, b in zip(Ts, T_true)]))
+        return t, r
+
+    curve = []
+    T_fin, losses = diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=adam_steps, lr=2e-3,
+                                      callback=lambda it, Ts, l: curve.append(err(Ts)) if it % 10 == 9 else None)
+    m.close()
+    rays = n_poses * cam.width * cam.height
+    return {"workload": wl.name, "poses": n_poses, "prefill_frames": len(frames),
+            "forward_backward_ms": fb_ms, "mrays_per_s_forward_backward": rays / (fb_ms * 1e-3) / 1e6,
+            "backward_kernel_ms": tm["backward"][1] / max(tm["backward"][2], 1),
+            "raycast_kernel_ms": tm["raycast"][1] / max(tm["raycast"][2], 1),
+            "pose_error_m_deg_initial": err(T_init), "pose_error_m_deg_final": err(T_fin),
+            "pose_error_every_10_steps": curve, "loss_initial": losses[0], "loss_final": losses[-1]}
+
+
+def bench_swap(torch, Mapper, Config, frames, steps):
+    """Swap one 512^3 volume out and back in (pinned host memory, side
+    stream) while integrating another: overlap of the copies with compute."""
+    wl = synth.room_512(frames=N_FRAMES_MAX)
+    (vs,) = wl.volumes
+    cam = wl.cam
+    m = Mapper(Config())
+    a = m.add_volume(vs.h, vs.r, vs.s)
+    b = m.add_volume((vs.h[0] + 4096, vs.h[1], vs.h[2]), vs.r, vs.s)  # far away: never in view
+    dd = torch.from_numpy(np.stack([f[0] for f in frames])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames])).cuda()
+    m.swap_out(b)
+    m.swap_in(b)  # first swap allocates the pinned buffers
+    m.synchronize()
+
+    def integ():
+        for k in range(steps):
+            m.integrate(dd[k % len(frames)], dc[k % len(frames)], cam, wl.poses[k % len(frames)])
+
+    def swap():
+        m.swap_out(b)
+        m.swap_in(b)
+
+    t_int, _ = timed(torch, integ)
+    t0 = time.perf_counter()
+    swap()
+    m.synchronize()
+    t_swap = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    swap()
+    integ()
+    m.synchronize()
+    t_both = (time.perf_counter() - t0) * 1e3
+    q = m.query(b)
+    nbytes = 2 * (q["device_bytes"] or q["host_bytes"])
+    m.close()
+    return {"volume_bytes": nbytes // 2, "integrate_ms": t_int, "swap_out_in_ms": t_swap,
+            "both_ms": t_both, "copy_gbs": nbytes / (t_swap * 1e-3) / 1e9,
+            "hidden_fraction": max(0.0, min(1.0, (t_int + t_swap - t_both) / min(t_int, t_swap)))}
+
+
 def main_reference(args, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
     if rank != 0:
@@ -383,6 +538,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the f16/i16 storage runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uneven-volume, differentiable and swap measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -396,6 +553,10 @@ def main():
     n = args.warmup + 2 * args.steps
     procs = max(1, min(16, (os.cpu_count() or 2) // max(world, 1)))
     frames = make_frames(n, procs)  # before any CUDA call
+    extra_steps = 20
+    if not args.no_extra:
+        uneven_frames = _gen(_render_uneven, range(args.warmup + extra_steps), procs)
+        tile_frames = _gen(_render_tiles, range(100), procs)
 
     import torch
     torch.cuda.set_device(local_rank)
@@ -457,6 +618,7 @@ def main():
             "raycast_skips_per_ray": res["stats"]["ray_skips"] / max(res["stats"]["rays"], 1),
             "raycast_hit_fraction": res["stats"]["ray_hits"] / max(res["stats"]["rays"], 1),
             "kernels": kern, "roofline": roofline, "integrate_roofline": integrate_roofline,
+            "tuning": {k: res["tuning"][k] for k in ("raycast_tile", "integrate_ctas_per_sm")},
             "gpu_launches": launches, "clocks": res["clocks"]}
 
     if not args.no_variants:
@@ -484,7 +646,16 @@ def main():
         v, secs, sample, cores = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample, "seconds": secs}
-    m.close()
+    if not args.no_extra:
+        m.close()
+        torch.cuda.empty_cache()
+        line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup)
+        line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
+        line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
+        m = None
+
+    if m is not None:
+        m.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
