@@ -458,8 +458,9 @@ def bench_swap(torch, Mapper, Config, frames, steps):
     m.synchronize()
 
     def integ():
+        # integrating volume a alone does not wait for the copies of volume b
         for k in range(steps):
-            m.integrate(dd[k % len(frames)], dc[k % len(frames)], cam, wl.poses[k % len(frames)])
+            m.integrate_volume(a, dd[k % len(frames)], dc[k % len(frames)], cam, wl.poses[k % len(frames)])
 
     def swap():
         m.swap_out(b)

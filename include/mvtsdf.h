@@ -125,8 +125,9 @@ enum {
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
     MV_KERNEL_CELL_FLAGS = 5,  /* raycast step-over flags refreshed after an integration */
     MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
-    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 kernels are also counted by kind) */
-    MV_KERNEL_KINDS = 8
+    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 7 kernels are also counted by kind) */
+    MV_KERNEL_DEPTH_MAX = 8,   /* farthest accepted depth of the frame (far bound of the brick list) */
+    MV_KERNEL_KINDS = 9
 };
 
 typedef struct {
@@ -202,7 +203,7 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
 
 /* One frame of the paper's per-frame loop: integrate the frame into every
  * resident volume, then raycast every resident volume at the same pose, as
- * one CUDA graph launch (6 kernels).  Same semantics and outputs as
+ * one CUDA graph launch (7 kernels).  Same semantics and outputs as
  * mv_integrate followed by mv_raycast.  The graph is built on the first call
  * and rebuilt when the set of resident volumes or the image size changes;
  * otherwise each call only updates the graph's kernel parameters (pose and
@@ -227,14 +228,17 @@ typedef struct {
     int32_t raycast_tile;          /* 0: 16x8 CTA of 8x4 warps, 1: 32x4 of 8x4, 2: 8x16 of 8x4,
                                       3: 32x4 CTA of 32x1 warps */
     int32_t integrate_ctas_per_sm; /* persistent integration grid = SMs x this */
-    float raycast_ms[4];           /* measured per tile shape (mv_autotune only) */
-    float integrate_ms[5];         /* measured for 2, 4, 6, 8, 10 CTAs per SM (mv_autotune only) */
+    float raycast_ms[4];           /* median per tile shape (mv_autotune only) */
+    float integrate_ms[5];         /* median for 2, 4, 6, 8, 10 CTAs per SM (mv_autotune only;
+                                      0 where not measured) */
 } mv_tuning;
 
 /* Choose the raycast pixel tile and the integration grid size by timing the
- * candidates on this frame and view: the raycast runs on the resident volumes
- * (it changes no state), the integration on temporary scratch storage shaped
- * like the largest resident volume (the map is not modified).  Synchronous;
+ * candidates on this frame and view (median of 5 launches each; the current
+ * choice is kept unless another candidate is more than 3 % faster): the
+ * raycast runs on the resident volumes (it changes no state), the integration
+ * on temporary scratch storage shaped like the largest volume in view (the
+ * map is not modified; with no volume in view the grid is kept).  Synchronous;
  * the choice applies to every later call of the context (results do not
  * depend on it, only speed). */
 mv_status mv_autotune(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,

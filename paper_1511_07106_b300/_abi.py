@@ -48,9 +48,9 @@ class mv_stats(C.Structure):
                 ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64)]
 
 
-MV_KERNEL_KINDS = 8
+MV_KERNEL_KINDS = 9
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
-                5: "cell_flags", 6: "backward", 7: "frame_graph"}
+                5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max"}
 
 
 class mv_timings(C.Structure):

@@ -15,46 +15,18 @@
 namespace mv {
 
 // ---------------------------------------------------------------------------
-// per-call setup: camera position in every volume's voxel units
+// frustum test of a box of voxel positions [lo, hi] given relative to the
+// camera in one volume's voxel units (conservative: never drops a box that
+// holds a voxel the per-voxel test would update, nor a sample of a ray)
 // ---------------------------------------------------------------------------
-__global__ void frame_setup_kernel(const VolDev *__restrict__ vols, int nvol, FrameParams P,
-                                   VolFrame *__restrict__ vf, unsigned *__restrict__ counter)
+__device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3], const FrameParams &P,
+                                            float inv_s, float z_far)
 {
-    for (int v = threadIdx.x; v < nvol; v += blockDim.x) {
-        const double s = (double)vols[v].s;
-        VolFrame f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double q = P.t[a] / s;
-            const double fl = floor(q);
-            f.cam_int[a] = (int)fl;
-            f.cam_frac[a] = (float)(q - fl);
-        }
-        vf[v] = f;
-    }
-    if (threadIdx.x == 0 && counter) *counter = 0u;
-}
-
-// ---------------------------------------------------------------------------
-// frustum test of one brick (conservative: never drops a brick that holds a
-// voxel the per-voxel test would update)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
-                                              const FrameParams &P, int bx, int by, int bz)
-{
-    float lo[3], hi[3];
-    const int bi[3] = {bx, by, bz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int l = bi[a] * kBrick;
-        const int u = min(l + kBrick - 1, v.r[a] - 1);
-        lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
-        hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
-    }
     // plane coefficients (camera frame, voxel units); inside when >= 0
     const float kl = (P.cx + 0.5f) / P.fx, kr = ((float)P.width - 0.5f - P.cx) / P.fx;
     const float kt = (P.cy + 0.5f) / P.fy, kb = ((float)P.height - 0.5f - P.cy) / P.fy;
-    const float zfar = P.z_max * v.inv_s + P.trunc_vox;
+    // a voxel beyond the farthest accepted depth by more than mu is never updated
+    const float zfar = z_far * inv_s + P.trunc_vox;
     bool in_near = false, in_l = false, in_r = false, in_t = false, in_b = false, in_far = false;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -75,17 +47,118 @@ __device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f
     return in_near && in_l && in_r && in_t && in_b && in_far;
 }
 
+__device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
+                                              const FrameParams &P, int bx, int by, int bz, float z_far)
+{
+    float lo[3], hi[3];
+    const int bi[3] = {bx, by, bz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int l = bi[a] * kBrick;
+        const int u = min(l + kBrick - 1, v.r[a] - 1);
+        lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
+        hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
+    }
+    return box_visible(lo, hi, P, v.inv_s, z_far);
+}
+
+// ---------------------------------------------------------------------------
+// per-call setup (one CTA): camera position in every volume's voxel units,
+// the work-list counter, and optionally the list of volumes in view
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) frame_setup_kernel(const VolDev *__restrict__ vols, int nvol,
+                                                          FrameParams P, VolFrame *__restrict__ vf,
+                                                          unsigned *__restrict__ counter,
+                                                          VisList *__restrict__ vis)
+{
+    __shared__ float s_key[kVisSortMax];
+    __shared__ unsigned char s_vis[kMaxVolumes];
+    for (int v = threadIdx.x; v < nvol; v += blockDim.x) {
+        const VolDev &vd = vols[v];
+        const double s = (double)vd.s;
+        VolFrame f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double q = P.t[a] / s;
+            const double fl = floor(q);
+            f.cam_int[a] = (int)fl;
+            f.cam_frac[a] = (float)(q - fl);
+        }
+        vf[v] = f;
+        if (vis) {
+            float lo[3], hi[3], d2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = (float)(vd.h[a] - f.cam_int[a]) - f.cam_frac[a];
+                hi[a] = (float)(vd.h[a] + vd.r[a] - 1 - f.cam_int[a]) - f.cam_frac[a];
+                const float e = fmaxf(fmaxf(lo[a], -hi[a]), 0.f) * vd.s;  // metres outside the box
+                d2 += e * e;
+            }
+            s_vis[v] = box_visible(lo, hi, P, vd.inv_s, P.z_max) ? 1 : 0;
+            if (nvol <= kVisSortMax) s_key[v] = d2;
+        }
+    }
+    if (threadIdx.x == 0 && counter) {
+        counter[0] = 0u;  // work-list length
+        counter[1] = 0u;  // bits of the frame's largest accepted depth (depth_max_kernel)
+    }
+    if (!vis) return;
+    __syncthreads();
+    if (nvol <= kVisSortMax) {
+        // nearest first: rank of each visible volume by (distance, slot)
+        for (int v = threadIdx.x; v < nvol; v += blockDim.x) {
+            if (!s_vis[v]) continue;
+            int rank = 0;
+            for (int u = 0; u < nvol; ++u)
+                rank += s_vis[u] && (s_key[u] < s_key[v] || (s_key[u] == s_key[v] && u < v));
+            vis->slot[rank] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int n = 0;
+            for (int u = 0; u < nvol; ++u) n += s_vis[u];
+            long long acc = 0;
+            for (int i = 0; i < n; ++i) {
+                vis->base[i] = acc;
+                acc += vols[vis->slot[i]].nbricks;
+            }
+            vis->base[n] = acc;
+            vis->count = n;
+            vis->total = acc;
+        }
+    } else if (threadIdx.x == 0) {
+        int n = 0;
+        long long acc = 0;
+        for (int u = 0; u < nvol; ++u) {
+            if (!s_vis[u]) continue;
+            vis->slot[n] = u;
+            vis->base[n] = acc;
+            acc += vols[u].nbricks;
+            ++n;
+        }
+        vis->base[n] = acc;
+        vis->count = n;
+        vis->total = acc;
+    }
+}
+
 // One thread per brick; warp-aggregated append of visible bricks.
 // Bricks are indexed globally over [gb_begin, gb_begin + total) by the
 // prefix sums brick_base of the table.
 __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restrict__ vols, int nvol,
                                                          const VolFrame *__restrict__ vfs,
                                                          FrameParams P, long long gb_begin,
-                                                         long long total, uint2 *__restrict__ list,
-                                                         unsigned *__restrict__ counter)
+                                                         long long total_all, uint2 *__restrict__ list,
+                                                         unsigned *__restrict__ counter,
+                                                         const VisList *__restrict__ vl,
+                                                         const unsigned *__restrict__ dmax_bits)
 {
     const int lane = threadIdx.x & 31;
+    const float z_far = dmax_bits ? fminf(P.z_max, __uint_as_float(*dmax_bits)) : P.z_max;
     const long long stride = (long long)gridDim.x * blockDim.x;
+    // with a view list, only the bricks of volumes in view are examined
+    const long long total = vl ? vl->total : total_all;
+    const int nvis = vl ? vl->count : 0;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
          base += stride) {
         const long long g = base + lane;
@@ -93,20 +166,31 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
         int v = 0;
         unsigned packed = 0;
         if (g < total) {
-            const long long gb = gb_begin + g;
-            int lo = 0, hi = nvol - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (vols[mid].brick_base <= gb) lo = mid; else hi = mid - 1;
+            long long gb;
+            if (vl) {
+                int lo = 0, hi = nvis - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (vl->base[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                v = vl->slot[lo];
+                gb = vols[v].brick_base + (g - vl->base[lo]);
+            } else {
+                gb = gb_begin + g;
+                int lo = 0, hi = nvol - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (vols[mid].brick_base <= gb) lo = mid; else hi = mid - 1;
+                }
+                v = lo;
             }
-            v = lo;
             const VolDev &vd = vols[v];
             const unsigned b = (unsigned)(gb - vd.brick_base);  // < 2^30 bricks per volume
             const unsigned bx = b % (unsigned)vd.nb[0];
             const unsigned byz = b / (unsigned)vd.nb[0];
             const unsigned by = byz % (unsigned)vd.nb[1];
             const unsigned bz = byz / (unsigned)vd.nb[1];
-            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz);
+            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far);
             packed = bx | (by << 10) | (bz << 20);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
@@ -115,6 +199,21 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
         pos = __shfl_sync(0xffffffffu, pos, 0);
         if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, packed);
     }
+}
+
+// Largest accepted depth of the frame (bits of a non-negative float, so the
+// integer maximum is the float maximum); zeroed by the setup kernel.
+__global__ void __launch_bounds__(256) depth_max_kernel(const float *__restrict__ depth, int n,
+                                                        FrameParams P, unsigned *__restrict__ out)
+{
+    float m = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float D = __ldg(depth + i);
+        if (D > 0.f && D >= P.z_min && D <= P.z_max) m = fmaxf(m, D);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
 }
 
 // ---------------------------------------------------------------------------
@@ -288,6 +387,7 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
         if ((old & kFlagEmpty) && !brick_any) nf |= kFlagEmpty;
         if (brick_pos && (brick_all || (old & kFlagNoNeg))) nf |= kFlagNoNeg;
         if (nf != old) v.bflag[b] = nf;
+        if (v.surf && ((old ^ nf) & kFlagNoNeg)) atomicAdd(v.surf, (nf & kFlagNoNeg) ? 0xFFFFFFFFu : 1u);
     }
 }
 
@@ -374,8 +474,10 @@ __global__ void __launch_bounds__(128) brick_flags_kernel(VolDev v)
         const int f = __syncthreads_and(all_free ? 1 : 0);
         const int e = __syncthreads_and(all_empty ? 1 : 0);
         const int nn = __syncthreads_and(no_neg ? 1 : 0);
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             v.bflag[b] = (uint8_t)((f ? kFlagFree : 0) | (e ? kFlagEmpty : 0) | (nn ? kFlagNoNeg : 0));
+            if (!nn && v.surf) atomicAdd(v.surf, 1u);  // zeroed before this kernel
+        }
     }
 }
 
@@ -433,21 +535,44 @@ __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_frame_setup(const VolDev *vols, int nvol, const FrameParams &P, VolFrame *vf,
-                               unsigned *counter, cudaStream_t s)
+                               unsigned *counter, cudaStream_t s, VisList *vis)
 {
-    frame_setup_kernel<<<1, 256, 0, s>>>(vols, nvol, P, vf, counter);
+    frame_setup_kernel<<<1, 256, 0, s>>>(vols, nvol, P, vf, counter, vis);
     return cudaGetLastError();
+}
+
+static long long list_blocks(long long total, int num_sms)
+{
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return blocks;
 }
 
 cudaError_t launch_brick_list(const VolDev *vols, int nvol, const VolFrame *vfs,
                               const FrameParams &P, long long gb_begin, long long total,
-                              uint2 *list, unsigned *counter, int num_sms, cudaStream_t s)
+                              uint2 *list, unsigned *counter, int num_sms, cudaStream_t s,
+                              const VisList *vis, const unsigned *dmax_bits)
 {
     if (total <= 0) return cudaSuccess;
-    long long blocks = (total + 255) / 256;
-    const long long cap = (long long)num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    brick_list_kernel<<<(unsigned)blocks, 256, 0, s>>>(vols, nvol, vfs, P, gb_begin, total, list, counter);
+    brick_list_kernel<<<(unsigned)list_blocks(total, num_sms), 256, 0, s>>>(
+        vols, nvol, vfs, P, gb_begin, total, list, counter, vis, dmax_bits);
+    return cudaGetLastError();
+}
+
+static unsigned depth_max_blocks(int n, int num_sms)
+{
+    int b = (n + 1023) / 1024;
+    if (b > num_sms * 2) b = num_sms * 2;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_depth_max(const float *depth, const FrameParams &P, unsigned *out, int num_sms,
+                             cudaStream_t s)
+{
+    const int n = P.width * P.height;
+    depth_max_kernel<<<depth_max_blocks(n, num_sms), 256, 0, s>>>(depth, n, P, out);
     return cudaGetLastError();
 }
 
@@ -465,6 +590,10 @@ cudaError_t launch_brick_flags(const VolDev &v, int num_sms, cudaStream_t s)
     const long long cap = (long long)num_sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (v.surf) {
+        const cudaError_t z = cudaMemsetAsync(v.surf, 0, sizeof(unsigned), s);
+        if (z != cudaSuccess) return z;
+    }
     brick_flags_kernel<<<(unsigned)blocks, 128, 0, s>>>(v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -484,37 +613,42 @@ cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsig
 
 cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
                              cudaGraphNode_t dep, const VolDev *vols, int nvol, const FrameParams &P,
-                             VolFrame *vf)
+                             VolFrame *vf, VisList *vis)
 {
-    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *> a(vols, nvol, P, vf, nullptr);
+    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a(vols, nvol, P, vf, nullptr,
+                                                                                  vis);
     return graph_node(g, exec, node, dep, a.params((const void *)frame_setup_kernel, 1, 256));
 }
 
-// Graph nodes of one integration: setup -> brick list -> integrate -> cell flags.
-cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[4],
+// Graph nodes of one integration: setup -> depth max -> brick list -> integrate -> cell flags.
+cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[5],
                             cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                             const FrameParams &P, long long total, uint2 *list, unsigned *counter,
                             const float *depth, const uint8_t *rgb, Stats *stats, int grid_int,
-                            int num_sms)
+                            int num_sms, VisList *vis)
 {
-    long long lb = (total + 255) / 256;
-    const long long cap = (long long)num_sms * 8;
-    if (lb > cap) lb = cap;
-    if (lb < 1) lb = 1;
-    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *> a0(vols, nvol, P, vf, counter);
+    const long long lb = list_blocks(total, num_sms);
+    NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a0(vols, nvol, P, vf, counter,
+                                                                                   vis);
     cudaError_t e = graph_node(g, exec, &nodes[0], dep, a0.params((const void *)frame_setup_kernel, 1, 256));
     if (e != cudaSuccess) return e;
-    NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *>
-        a1(vols, nvol, vf, P, 0LL, total, list, counter);
-    e = graph_node(g, exec, &nodes[1], nodes[0], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
+    const int npx = P.width * P.height;
+    NodeArgs<const float *, int, FrameParams, unsigned *> am(depth, npx, P, counter + 1);
+    e = graph_node(g, exec, &nodes[1], nodes[0],
+                   am.params((const void *)depth_max_kernel, depth_max_blocks(npx, num_sms), 256));
+    if (e != cudaSuccess) return e;
+    NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *,
+             const VisList *, const unsigned *>
+        a1(vols, nvol, vf, P, 0LL, total, list, counter, vis, counter + 1);
+    e = graph_node(g, exec, &nodes[2], nodes[1], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,
              const uint8_t *, Stats *>
         a2(vols, vf, list, counter, P, depth, rgb, stats);
-    e = graph_node(g, exec, &nodes[2], nodes[1], a2.params((const void *)integrate_kernel, grid_int, 128));
+    e = graph_node(g, exec, &nodes[3], nodes[2], a2.params((const void *)integrate_kernel, grid_int, 128));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const uint2 *, const unsigned *> a3(vols, list, counter);
-    return graph_node(g, exec, &nodes[3], nodes[2], a3.params((const void *)cell_flags_kernel, num_sms * 4, 256));
+    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_flags_kernel, num_sms * 4, 256));
 }
 
 int integrate_max_ctas_per_sm()

@@ -39,6 +39,7 @@ struct VolDev {
     uint32_t *rgba;    // brick-major RGBA8, A = colour weight
     uint8_t *bflag;    // one flag byte per brick
     uint8_t *cflag;    // one cell-brick byte per brick (may be null where no raycast reads it)
+    unsigned *surf;    // bricks without kFlagNoNeg (0: no hit possible anywhere), may be null
     int h[3];          // lattice offset h_t
     int r[3];          // voxels per axis h_r
     int nb[3];         // bricks per axis
@@ -72,6 +73,26 @@ struct FrameParams {
     float ray_step;
     int n_bisect;
 };
+
+// Volumes in the view of one call, nearest first (when there are at most
+// kVisSortMax of them; table order otherwise), with prefix sums of their
+// brick counts for the work-list kernel.  Built on the device by the per-call
+// setup kernel.
+constexpr int kVisSortMax = 256;
+// candidate volumes per raycast CTA held in shared memory
+constexpr int kTileVolMax = 256;
+struct VisList {
+    int count;
+    int pad;
+    long long total;                 // bricks of the visible volumes
+    int slot[kMaxVolumes];           // table slots
+    long long base[kMaxVolumes + 1]; // prefix sums of nbricks over slot[]
+};
+
+// Flag allocation of a volume: voxel-brick flags, cell-brick flags, then
+// (8-byte aligned) the count of bricks without kFlagNoNeg.
+inline size_t flag_count_offset(long long nbricks) { return ((size_t)(2 * nbricks) + 7) & ~(size_t)7; }
+inline size_t flag_alloc_bytes(long long nbricks) { return flag_count_offset(nbricks) + 8; }
 
 struct Stats {
     unsigned long long swept, updated, band, bricks;

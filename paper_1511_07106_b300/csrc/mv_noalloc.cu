@@ -9,9 +9,12 @@
 #include "mv_internal.cuh"
 
 namespace mv {
-cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t);
+cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t,
+                               VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
-                              long long, uint2 *, unsigned *, int, cudaStream_t);
+                              long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
+                              const unsigned *);
+cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t);
@@ -151,9 +154,12 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MV_ERR_CUDA;
     store_voldev_kernel<<<1, 32, 0, s>>>(v, vdev);
     if (cudaGetLastError() != cudaSuccess) return MV_ERR_CUDA;
-    // the frame setup also zeroes the list counter, the one value that must start at 0
-    if (launch_frame_setup(vdev, 1, P, vframe, counter, s) != cudaSuccess) return MV_ERR_CUDA;
-    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s) != cudaSuccess)
+    // the frame setup zeroes the list counter and the depth maximum, the values
+    // that must start at 0
+    if (launch_frame_setup(vdev, 1, P, vframe, counter, s, nullptr) != cudaSuccess) return MV_ERR_CUDA;
+    if (launch_depth_max(depth, P, counter + 1, sms, s) != cudaSuccess) return MV_ERR_CUDA;
+    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1) !=
+        cudaSuccess)
         return MV_ERR_CUDA;
     if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s) != cudaSuccess)
         return MV_ERR_CUDA;

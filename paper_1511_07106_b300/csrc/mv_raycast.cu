@@ -409,7 +409,7 @@ __device__ __forceinline__ void add_counts(Stats *stats, unsigned rays, unsigned
 }
 
 __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
-                                            const VolFrame *__restrict__ vfs, int nvol,
+                                            const VolFrame *__restrict__ vfs, const int *list, int n,
                                             const FrameParams &P, const RayOut &out, int merge,
                                             int px, int py, RayCount &rc)
 {
@@ -431,8 +431,15 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
         best.id = out.vol_id[p];
         best.slot = -2;  // existing entry
     }
-    for (int i = 0; i < nvol; ++i) {
+    // candidate volumes: the table slots list[0, n) (null list: slots 0..n-1);
+    // with a view list the order is nearest first, so pruning by the current
+    // best hit skips most of the farther ones
+    for (int j = 0; j < n; ++j) {
+        const int i = list ? list[j] : j;
         const VolDev &v = vols[i];
+        // no observed voxel with F <= 0 anywhere in the volume: no sample can
+        // end a bracket, so the volume cannot contribute a hit
+        if (v.surf && __ldg(v.surf) == 0u) continue;
         const VolFrame vf = vfs[i];
         const bool narrow = v.nbricks * kBrickVox <= 0xFFFFFFFFll;
         if (narrow) {
@@ -466,6 +473,45 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     }
 }
 
+// Can a ray of the pixel rectangle [x0, x1] x [y0, y1] hit volume v?  False
+// only when the volume's domain [h_t, h_t + r - 1] lies wholly outside one
+// face of the rectangle's viewing pyramid (widened by half a pixel and a
+// rounding margin) or beyond z_max, or when the volume holds no observed
+// voxel with F <= 0 (no sample can end a bracket there).  Camera frame,
+// this volume's voxel units, camera position split as in the march.
+__device__ __forceinline__ bool tile_sees_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
+                                                 int x0, int x1, int y0, int y1)
+{
+    if (v.surf && __ldg(v.surf) == 0u) return false;
+    const float kl = ((float)x0 - 0.5f - P.cx) / P.fx, kr = ((float)x1 + 0.5f - P.cx) / P.fx;
+    const float kt = ((float)y0 - 0.5f - P.cy) / P.fy, kb = ((float)y1 + 0.5f - P.cy) / P.fy;
+    const float zfar = P.z_max * v.inv_s + 1.0f;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (float)(v.h[a] - vf.cam_int[a]) - vf.cam_frac[a];
+        hi[a] = (float)(v.h[a] + v.r[a] - 1 - vf.cam_int[a]) - vf.cam_frac[a];
+    }
+    bool in_near = false, in_l = false, in_r = false, in_t = false, in_b = false, in_far = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float x = (c & 1) ? hi[0] : lo[0];
+        const float y = (c & 2) ? hi[1] : lo[1];
+        const float z = (c & 4) ? hi[2] : lo[2];
+        const float X = P.Rf[0] * x + P.Rf[3] * y + P.Rf[6] * z;
+        const float Y = P.Rf[1] * x + P.Rf[4] * y + P.Rf[7] * z;
+        const float Z = P.Rf[2] * x + P.Rf[5] * y + P.Rf[8] * z;
+        const float m = 1e-4f * (fabsf(X) + fabsf(Y) + fabsf(Z)) + 1e-3f;
+        in_near |= Z > -m;
+        in_l |= X - kl * Z > -m;
+        in_r |= kr * Z - X > -m;
+        in_t |= Y - kt * Z > -m;
+        in_b |= kb * Z - Y > -m;
+        in_far |= !(Z > zfar + m);
+    }
+    return in_near && in_l && in_r && in_t && in_b && in_far;
+}
+
 // Pixel tiles (128 threads per CTA, selected by the autotuner):
 //   0: 16x8 CTA of 2x2 warps, each warp an 8x4 tile
 //   1: 32x4 CTA of 4x1 warps, each warp an 8x4 tile
@@ -488,16 +534,49 @@ template <int TILE>
 __global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restrict__ vols,
                                                          const VolFrame *__restrict__ vfs, int nvol,
                                                          FrameParams P, RayOut out, int merge,
-                                                         Stats *__restrict__ stats)
+                                                         Stats *__restrict__ stats,
+                                                         const VisList *__restrict__ vl)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int tx, ty;
     Tile<TILE>::pixel(w, lane, tx, ty);
-    const int px = blockIdx.x * Tile<TILE>::W + tx;
-    const int py = blockIdx.y * Tile<TILE>::H + ty;
+    const int x0 = blockIdx.x * Tile<TILE>::W, y0 = blockIdx.y * Tile<TILE>::H;
+    const int px = x0 + tx;
+    const int py = y0 + ty;
     const bool active = px < P.width && py < P.height;
+
+    // candidate volumes of this CTA's pixel rectangle, compacted in order
+    __shared__ int s_list[kTileVolMax];
+    __shared__ int s_warp[4];
+    const int x1 = min(x0 + Tile<TILE>::W, P.width) - 1, y1 = min(y0 + Tile<TILE>::H, P.height) - 1;
+    const int n = vl ? vl->count : nvol;
+    int total = 0;
+    for (int j0 = 0; j0 < n; j0 += 128) {
+        const int j = j0 + (int)threadIdx.x;
+        int i = 0;
+        bool keep = false;
+        if (j < n) {
+            i = vl ? vl->slot[j] : j;
+            keep = tile_sees_volume(vols[i], vfs[i], P, x0, x1, y0, y1);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_warp[w] = __popc(b);
+        __syncthreads();
+        int off = total;
+        for (int k = 0; k < w; ++k) off += s_warp[k];
+        if (keep) {
+            const int pos = off + __popc(b & ((1u << lane) - 1u));
+            if (pos < kTileVolMax) s_list[pos] = i;
+        }
+        total += s_warp[0] + s_warp[1] + s_warp[2] + s_warp[3];
+        __syncthreads();
+    }
+    // the CTA's candidates when they fit in shared memory, else the view list
+    const bool fits = total <= kTileVolMax;
+    const int *list = fits ? s_list : (vl ? vl->slot : nullptr);
+
     RayCount rc{0u, 0u};
-    if (active) trace_pixel(vols, vfs, nvol, P, out, merge, px, py, rc);
+    if (active) trace_pixel(vols, vfs, list, fits ? total : n, P, out, merge, px, py, rc);
     add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips,
                (active && out.depth && out.depth[(size_t)py * P.width + px] > 0.f) ? 1u : 0u);
 }
@@ -521,34 +600,34 @@ static dim3 raycast_grid(int tile, int width, int height)
 
 cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
                              cudaGraphNode_t dep, const VolDev *vols, int nvol, const FrameParams &P,
-                             VolFrame *vf);
+                             VolFrame *vf, VisList *vis);
 
 // Graph nodes of one raycast of all volumes: setup -> raycast.
 cudaError_t graph_raycast(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[2],
                           cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                           const FrameParams &P, float *depth, float *normal, uint8_t *rgba,
-                          float *vertex, int *vol_id, Stats *stats, int tile)
+                          float *vertex, int *vol_id, Stats *stats, int tile, VisList *vis)
 {
-    cudaError_t e = frame_setup_node(g, exec, &nodes[0], dep, vols, nvol, P, vf);
+    cudaError_t e = frame_setup_node(g, exec, &nodes[0], dep, vols, nvol, P, vf, vis);
     if (e != cudaSuccess) return e;
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
-    NodeArgs<const VolDev *, const VolFrame *, int, FrameParams, RayOut, int, Stats *> a(
-        vols, vf, nvol, P, o, 0, stats);
+    NodeArgs<const VolDev *, const VolFrame *, int, FrameParams, RayOut, int, Stats *, const VisList *> a(
+        vols, vf, nvol, P, o, 0, stats, vis);
     return graph_node(g, exec, &nodes[1], nodes[0],
                       a.params(raycast_fn(tile), raycast_grid(tile, P.width, P.height), 128));
 }
 
 cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,
                            float *depth, float *normal, uint8_t *rgba, float *vertex, int *vol_id,
-                           int merge, Stats *stats, int tile, cudaStream_t s)
+                           int merge, Stats *stats, int tile, cudaStream_t s, const VisList *vis)
 {
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
     const dim3 grid = raycast_grid(tile, P.width, P.height);
     switch (tile) {
-    case 1: raycast_kernel<1><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
-    case 2: raycast_kernel<2><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
-    case 3: raycast_kernel<3><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
-    default: raycast_kernel<0><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats); break;
+    case 1: raycast_kernel<1><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
+    case 2: raycast_kernel<2><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
+    case 3: raycast_kernel<3><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
+    default: raycast_kernel<0><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
     }
     return cudaGetLastError();
 }

@@ -22,16 +22,20 @@
 #include "mv_internal.cuh"
 
 namespace mv {
-cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t);
+cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t,
+                               VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
-                              long long, uint2 *, unsigned *, int, cudaStream_t);
+                              long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
+                              const unsigned *);
+cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t);
 cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
 cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
-                           float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t);
+                           float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t,
+                           const VisList *);
 int integrate_occupancy_grid(int num_sms);
 int integrate_max_ctas_per_sm();
 struct BackwardArgs {
@@ -49,12 +53,12 @@ struct BackwardArgs {
     float *grad_pose;
 };
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
-cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[4], cudaGraphNode_t,
+cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
-                            unsigned *, const float *, const uint8_t *, Stats *, int, int);
+                            unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[2], cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
-                          uint8_t *, float *, int *, Stats *, int);
+                          uint8_t *, float *, int *, Stats *, int, VisList *);
 }  // namespace mv
 
 using namespace mv;
@@ -104,7 +108,7 @@ struct mv_ctx {
     struct FrameGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t nodes[6] = {};
+        cudaGraphNode_t nodes[7] = {};
         unsigned long long table_version = ~0ull;
         int width = 0, height = 0, grid_int = 0, tile = 0;
     } fg;
@@ -114,6 +118,7 @@ struct mv_ctx {
     size_t list_cap = 0;  // entries
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
+    VisList *d_vis = nullptr;  // volumes in view of the current batched call
     // raycast backward: per-slot gradient pointers and the poses of one call
     float **d_grad_ptrs = nullptr;
     double *d_poses = nullptr;
@@ -197,6 +202,7 @@ VolDev make_voldev(const Volume &v)
     d.rgba = v.d_rgba;
     d.bflag = v.d_flag;
     d.cflag = v.d_flag ? v.d_flag + v.nbricks : nullptr;
+    d.surf = v.d_flag ? reinterpret_cast<unsigned *>(v.d_flag + flag_count_offset(v.nbricks)) : nullptr;
     for (int a = 0; a < 3; ++a) {
         d.h[a] = v.desc.h_t[a];
         d.r[a] = v.desc.h_r[a];
@@ -210,9 +216,11 @@ VolDev make_voldev(const Volume &v)
     return d;
 }
 
-// Order this call after the previous call and after pending volume copies;
-// refresh the device table when the resident set changed.
-mv_status begin_call(mv_ctx *c, cudaStream_t s)
+// Order this call after the previous call and after the pending copies of
+// the resident volumes it reads (all of them, or only volume `only_id`);
+// copies of volumes the call does not read keep running alongside.  Refresh
+// the device table when the resident set changed.
+mv_status begin_call(mv_ctx *c, cudaStream_t s, int only_id = -1)
 {
     if (c->last_recorded) MV_CUDA(c, cudaStreamWaitEvent(s, c->last_event, 0));
     for (auto &kv : c->vols) {
@@ -222,6 +230,7 @@ mv_status begin_call(mv_ctx *c, cudaStream_t s)
             v->ready_pending = false;
             continue;
         }
+        if (!v->resident || (only_id >= 0 && v->id != only_id)) continue;
         MV_CUDA(c, cudaStreamWaitEvent(s, v->ready, 0));
     }
     if (c->table_dirty) {
@@ -411,6 +420,7 @@ mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out)
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_vf, sizeof(VolFrame) * kMaxVolumes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_counter, sizeof(unsigned) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_stats, sizeof(Stats));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_vis, sizeof(VisList));
     if (e == cudaSuccess) e = cudaMalloc((void **)&x->d_grad_ptrs, sizeof(float *) * kMaxVolumes);
     if (e == cudaSuccess) e = cudaMemset(x->d_stats, 0, sizeof(Stats));
     if (e != cudaSuccess) {
@@ -448,6 +458,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_vf) cudaFree(c->d_vf);
     if (c->d_counter) cudaFree(c->d_counter);
     if (c->d_stats) cudaFree(c->d_stats);
+    if (c->d_vis) cudaFree(c->d_vis);
     if (c->d_grad_ptrs) cudaFree(c->d_grad_ptrs);
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
@@ -489,7 +500,7 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     }
     v->fw_bytes = (size_t)v->nbricks * kBrickVox * fw_elem_bytes(d->fmt);
     v->rgba_bytes = (size_t)v->nbricks * kBrickVox * 4;
-    v->flag_bytes = 2 * (size_t)v->nbricks;  // voxel-brick flags, then cell-brick flags
+    v->flag_bytes = flag_alloc_bytes(v->nbricks);  // voxel-brick flags, cell-brick flags, count
     cudaStream_t s = c->swap_stream;
     cudaError_t e = cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocAsync(&v->d_fw, v->fw_bytes, s);
@@ -499,6 +510,8 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_rgba, 0, v->rgba_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, kFlagsNew, (size_t)v->nbricks, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag + v->nbricks, kCellSkip, (size_t)v->nbricks, s);
+    if (e == cudaSuccess)  // no brick holds an observed voxel yet: the count starts at 0
+        e = cudaMemsetAsync(v->d_flag + flag_count_offset(v->nbricks), 0, 8, s);
     if (e == cudaSuccess) e = cudaEventRecord(v->ready, s);
     if (e != cudaSuccess) {
         if (v->d_fw) cudaFreeAsync(v->d_fw, s);
@@ -585,7 +598,7 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
         if (st) return st;
         if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "volume is swapped out");
     }
-    mv_status st = begin_call(c, s);
+    mv_status st = begin_call(c, s, only_id);
     if (st) return st;
     if (c->table.empty()) return end_call(c, s);
     const FrameParams P = make_params(c, K, T);
@@ -599,10 +612,14 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     const long long gb0 = c->table[slot0].brick_base;
     const long long total = only_id >= 0 ? c->table[slot0].nbricks
                                          : c->table.back().brick_base + c->table.back().nbricks;
+    VisList *vis = only_id >= 0 ? nullptr : c->d_vis;  // batched: only volumes in view
     MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
-        return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s); }));
+        return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s, vis); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
+        return launch_depth_max(depth, P, c->d_counter + 1, c->num_sms, s); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
-        return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s); }));
+        return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s, vis,
+                                 c->d_counter + 1); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
         return launch_integrate(tab, vf, c->d_list, c->d_counter, P, depth, rgb, c->d_stats,
                                 c->grid_integrate, s); }));
@@ -641,7 +658,7 @@ static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_in
         if (st) return st;
         if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "volume is swapped out");
     }
-    mv_status st = begin_call(c, s);
+    mv_status st = begin_call(c, s, only_id);
     if (st) return st;
     const FrameParams P = make_params(c, K, T);
     int slot0 = 0, nvol = (int)c->table.size();
@@ -651,12 +668,13 @@ static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_in
     }
     const VolDev *tab = c->d_table + slot0;
     VolFrame *vf = c->d_vf + slot0;
+    VisList *vis = (only_id >= 0 || nvol == 0) ? nullptr : c->d_vis;
     if (nvol > 0)
         MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
-            return launch_frame_setup(tab, nvol, P, vf, nullptr, s); }));
+            return launch_frame_setup(tab, nvol, P, vf, nullptr, s, vis); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
         return launch_raycast(tab, vf, nvol, P, depth, normal, rgba, vertex, vol_id, merge ? 1 : 0,
-                              c->d_stats, c->ray_tile, s); }));
+                              c->d_stats, c->ray_tile, s, vis); }));
     return end_call(c, s);
 }
 
@@ -689,7 +707,7 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     if (nvol == 0) {  // nothing to integrate: the maps are all misses
         MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
             return launch_raycast(c->d_table, c->d_vf, 0, P, depth_out, normal, rgba, vertex, vol_id, 0,
-                                  c->d_stats, c->ray_tile, s); }));
+                                  c->d_stats, c->ray_tile, s, nullptr); }));
         return end_call(c, s);
     }
     const long long total = c->table.back().brick_base + c->table.back().nbricks;
@@ -707,9 +725,9 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     cudaGraphExec_t upd = rebuild ? nullptr : fg.exec;
     MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
                                c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
-                               c->num_sms));
-    MV_CUDA(c, graph_raycast(fg.g, upd, fg.nodes + 4, fg.nodes[3], c->d_table, nvol, c->d_vf, P,
-                             depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile));
+                               c->num_sms, c->d_vis));
+    MV_CUDA(c, graph_raycast(fg.g, upd, fg.nodes + 5, fg.nodes[4], c->d_table, nvol, c->d_vf, P,
+                             depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
         MV_CUDA(c, cudaGraphInstantiate(&fg.exec, fg.g, 0));
         fg.table_version = c->table_version;
@@ -719,8 +737,8 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
         fg.tile = c->ray_tile;
     }
     MV_CUDA(c, counted_launch(c, MV_KERNEL_FRAME_GRAPH, s, [&] { return cudaGraphLaunch(fg.exec, s); }));
-    const int kinds[6] = {MV_KERNEL_SETUP, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE, MV_KERNEL_CELL_FLAGS,
-                          MV_KERNEL_SETUP, MV_KERNEL_RAYCAST};
+    const int kinds[7] = {MV_KERNEL_SETUP, MV_KERNEL_DEPTH_MAX, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE,
+                          MV_KERNEL_CELL_FLAGS, MV_KERNEL_SETUP, MV_KERNEL_RAYCAST};
     for (int k : kinds) c->launches[k] += 1;
     return end_call(c, s);
 }
@@ -751,32 +769,54 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
     const size_t npx = (size_t)K->width * K->height;
     char *maps = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&maps, npx * 36, s);
-    // raycast tile shapes on the resident volumes (the raycast changes no state)
-    float best = 3.0e38f;
-    int best_tile = c->ray_tile;
+    // raycast tile shapes on the resident volumes (the raycast changes no state);
+    // median of 5 timed launches per shape, the current shape kept unless
+    // another is faster by more than 3 %
+    float best = 3.0e38f, t_cur = 3.0e38f;
+    int best_tile = c->ray_tile, cand_tile = c->ray_tile;
     for (int tile = 0; tile < 4 && e == cudaSuccess; ++tile) {
-        float tbest = 3.0e38f;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-            e = launch_frame_setup(c->d_table, nvol, P, c->d_vf, nullptr, s);
+        float t[5];
+        int nt = 0;
+        for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+            e = launch_frame_setup(c->d_table, nvol, P, c->d_vf, nullptr, s, c->d_vis);
             if (e == cudaSuccess) e = cudaEventRecord(a, s);
             if (e == cudaSuccess)
                 e = launch_raycast(c->d_table, c->d_vf, nvol, P, (float *)maps, (float *)(maps + 4 * npx),
                                    (uint8_t *)(maps + 16 * npx), (float *)(maps + 20 * npx),
-                                   (int *)(maps + 32 * npx), 0, nullptr, tile, s);
+                                   (int *)(maps + 32 * npx), 0, nullptr, tile, s, c->d_vis);
             if (e == cudaSuccess) e = cudaEventRecord(b, s);
-            if (e == cudaSuccess && rep > 0) tbest = fminf(tbest, time_ms(s, a, b));
+            if (e == cudaSuccess && rep > 0) t[nt++] = time_ms(s, a, b);
         }
-        out->raycast_ms[tile] = tbest;
-        if (tbest < best) { best = tbest; best_tile = tile; }
+        if (e != cudaSuccess) break;
+        std::sort(t, t + nt);
+        const float med = t[nt / 2];
+        out->raycast_ms[tile] = med;
+        if (tile == c->ray_tile) t_cur = med;
+        if (med < best) { best = med; cand_tile = tile; }
     }
+    if (best < 0.97f * t_cur) best_tile = cand_tile;
     if (maps) cudaFreeAsync(maps, s);
     // persistent-grid sizes of the integration, on scratch storage shaped like
-    // the largest resident volume (the map itself is not touched)
+    // the largest volume in view (the map itself is not touched)
     int best_ctas = c->ctas_per_sm;
+    int big = -1;
     if (e == cudaSuccess && nvol > 0) {
-        int big = 0;
-        for (int i = 1; i < nvol; ++i)
-            if (c->table[i].nbricks > c->table[big].nbricks) big = i;
+        int nvis = 0;
+        e = cudaMemcpyAsync(&nvis, &c->d_vis->count, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        nvis = std::min(std::max(nvis, 0), nvol);
+        std::vector<int> vis_slots((size_t)nvis);
+        if (e == cudaSuccess && nvis > 0) {
+            e = cudaMemcpyAsync(vis_slots.data(), c->d_vis->slot, sizeof(int) * (size_t)nvis,
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        for (int k = 0; k < nvis && e == cudaSuccess; ++k) {
+            const int i = vis_slots[(size_t)k];
+            if (i >= 0 && i < nvol && (big < 0 || c->table[i].nbricks > c->table[big].nbricks)) big = i;
+        }
+    }
+    if (e == cudaSuccess && big >= 0) {
         VolDev sv = c->table[big];
         const Volume *vol = c->vols.at(sv.id);
         void *sfw = nullptr, *srgba = nullptr, *sflag = nullptr;
@@ -790,7 +830,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&stab, sizeof(VolDev), s);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&svf, sizeof(VolFrame), s);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&slist, sizeof(uint2) * sv.nbricks, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scount, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scount, sizeof(unsigned) * 4, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(sfw, 0, vol->fw_bytes, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(srgba, 0, vol->rgba_bytes, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(sflag, kFlagsNew, (size_t)sv.nbricks, s);
@@ -798,30 +838,42 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
         sv.rgba = (uint32_t *)srgba;
         sv.bflag = (uint8_t *)sflag;
         sv.cflag = nullptr;
+        sv.surf = nullptr;
         sv.brick_base = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(stab, &sv, sizeof(VolDev), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sv is a stack value
         const int maxc = integrate_max_ctas_per_sm();
         const int cands[5] = {2, 4, 6, 8, 10};
-        float ibest = 3.0e38f;
+        // median of 5 timed launches per size; the default size is kept unless
+        // another is faster by more than 3 %
+        float t_default = 3.0e38f, ibest = 3.0e38f;
+        int cand_best = best_ctas;
         for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
             const int ctas = cands[ci];
             if (ctas > maxc) break;
-            float tbest = 3.0e38f;
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                e = launch_frame_setup(stab, 1, P, svf, scount, s);
+            float t[5];
+            int nt = 0;
+            for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+                e = launch_frame_setup(stab, 1, P, svf, scount, s, nullptr);
+                if (e == cudaSuccess) e = launch_depth_max(depth, P, scount + 1, c->num_sms, s);
                 if (e == cudaSuccess)
-                    e = launch_brick_list(stab, 1, svf, P, 0, sv.nbricks, slist, scount, c->num_sms, s);
+                    e = launch_brick_list(stab, 1, svf, P, 0, sv.nbricks, slist, scount, c->num_sms, s,
+                                          nullptr, scount + 1);
                 if (e == cudaSuccess) e = cudaEventRecord(a, s);
                 if (e == cudaSuccess)
                     e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
                                          c->num_sms * ctas, s);
                 if (e == cudaSuccess) e = cudaEventRecord(b, s);
-                if (e == cudaSuccess && rep > 0) tbest = fminf(tbest, time_ms(s, a, b));
+                if (e == cudaSuccess && rep > 0) t[nt++] = time_ms(s, a, b);
             }
-            out->integrate_ms[ci] = tbest;
-            if (tbest < ibest) { ibest = tbest; best_ctas = ctas; }
+            if (e != cudaSuccess) break;
+            std::sort(t, t + nt);
+            const float med = t[nt / 2];
+            out->integrate_ms[ci] = med;
+            if (ctas == best_ctas) t_default = med;
+            if (med < ibest) { ibest = med; cand_best = ctas; }
         }
+        if (ibest < 0.97f * t_default) best_ctas = cand_best;
         for (void *p : {sfw, srgba, sflag, (void *)stab, (void *)svf, (void *)slist, (void *)scount})
             if (p) cudaFreeAsync(p, s);
     }
@@ -1054,6 +1106,7 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
         if (host_rgba) std::memcpy(v->h_rgba, col.data(), v->rgba_bytes);
         // exact flags on the host: voxel-brick summaries, then cell-brick flags
         const long long nb = v->nbricks;
+        unsigned surf = 0;
         for (long long b = 0; b < nb; ++b) {
             bool all_free = true, all_empty = true, no_neg = true;
             for (int k = 0; k < kBrickVox; ++k) {
@@ -1077,7 +1130,9 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
             }
             v->h_flag[b] = (uint8_t)((all_free ? kFlagFree : 0) | (all_empty ? kFlagEmpty : 0) |
                                      (no_neg ? kFlagNoNeg : 0));
+            surf += no_neg ? 0u : 1u;
         }
+        std::memcpy(v->h_flag + flag_count_offset(nb), &surf, sizeof(surf));
         for (long long b = 0; b < nb; ++b) {
             const int cx = (int)(b % v->nb[0]), cy = (int)((b / v->nb[0]) % v->nb[1]);
             const int cz = (int)(b / ((long long)v->nb[0] * v->nb[1]));

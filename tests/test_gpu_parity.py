@@ -400,3 +400,121 @@ def test_autotune_changes_speed_not_results():
             np.testing.assert_array_equal(ref[key], got[key])
     a.close()
     b.close()
+
+
+def test_uneven_volumes_batched_equals_per_volume_and_oracle():
+    """Volumes of different sizes and pitches, some out of view: the batched
+    graph (view list, nearest first) equals the per-volume loop bit for bit,
+    and the merged raycast matches the oracle."""
+    wl = synth.uneven_volumes(n_volumes=12, frames=6, edges=(16, 24, 40), pitch_mm=(15.0, 40.0),
+                              half_extent=1.6, height_m=2.2, width=160, height=120)
+    a, b = Mapper(), Mapper()
+    ida = [a.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    idb = [b.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        ga = gpu_maps(a.frame(dev(d), dev(c), wl.cam, wl.poses[i]))
+        for vid in idb:
+            b.integrate_volume(vid, dev(d), dev(c), wl.cam, wl.poses[i])
+        out = b.alloc_maps(wl.cam)
+        for k, vid in enumerate(idb):
+            b.raycast_volume(vid, k == 0, wl.cam, wl.poses[i], out)
+        gb = gpu_maps(out)
+        for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+            np.testing.assert_array_equal(ga[key], gb[key])
+    seen = 0
+    for x, y, v in zip(ida, idb, wl.volumes):
+        Fa, Wa, Ca = a.read_decoded(x)
+        Fb, Wb, Cb = b.read_decoded(y)
+        np.testing.assert_array_equal(Fa, Fb)
+        np.testing.assert_array_equal(Wa, Wb)
+        seen += (Wa > 0).any()
+    assert 0 < seen < len(ida)  # some volumes were in view, some never
+    ovs = [oracle_volume_from_gpu(a, i, v) for i, v in zip(ida, wl.volumes)]
+    T = wl.poses[3]
+    g = gpu_maps(a.raycast(wl.cam, T))
+    o = oracle.raycast(ovs, wl.cam, T, ocfg(a.config), ids=ida)
+    pitch = min(v.s for v in wl.volumes)
+    compare_raycast(g, o, wl.cam, T, pitch, require_hits=0.05)
+    a.close()
+    b.close()
+
+
+def test_surface_count_skip_and_far_cull_are_exact():
+    """Two exact shortcuts.  (1) A volume in which no brick holds an observed
+    voxel at or behind a surface (every brick flag NO-NEGATIVE) cannot end a
+    bracket; the raycast skips it whole (no samples) and the maps equal those
+    without it.  The per-volume count behind the skip follows every path that
+    changes the flags: integration, device writes, host writes to a swapped-out
+    volume, and the swap.  (2) Bricks farther than the frame's farthest valid
+    depth plus mu are never updated, so they are not listed at all."""
+    s = 0.01
+    scene = synth.Scene()
+    scene.planes = np.array([[0.0, 0.0, 1.0, 1.0]])  # wall z = 1 m
+    cam = synth.Camera(100.0, 100.0, 39.5, 29.5, 80, 60)
+    poses = [synth.look_at((0.01 * i, -0.005 * i, 0.0), (0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0)) for i in range(6)]
+    air = synth.VolumeSpec((-30, -25, 35), (60, 50, 20), s)      # z in [0.35, 0.54]: free space only
+    wall = synth.VolumeSpec((-40, -32, 90), (80, 64, 20), s)     # z in [0.90, 1.09]: holds the wall
+    far = synth.VolumeSpec((-60, -50, 150), (120, 100, 16), s)   # z in [1.50, 1.65]: behind the wall
+    wl = synth.Workload("wall", cam, scene, poses, [air, wall, far], seed=3)
+    m = Mapper()
+    ia, ib, ic = (m.add_volume(v.h, v.r, v.s) for v in wl.volumes)
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        assert np.nanmax(np.where(d > 0, d, np.nan)) < 1.05
+        m.stats(reset=True)
+        m.integrate_volume(ic, dev(d), dev(c), cam, poses[i])
+        assert m.stats()["bricks"] == 0  # every brick of `far` lies beyond max depth + mu
+        m.integrate(dev(d), dev(c), cam, poses[i])
+    assert (m.read_decoded(ic)[1] == 0).all()
+    Fa, Wa, _ = m.read_decoded(ia)
+    assert (Wa > 0).mean() > 0.3 and (Fa[Wa > 0] > 0).all()
+    assert (m.read_brick_flags(ia) & 4).all() and not (m.read_brick_flags(ib) & 4).all()
+    T = poses[2]
+
+    def alone(vid):
+        out = m.alloc_maps(cam)
+        m.stats(reset=True)
+        m.raycast_volume(vid, True, cam, T, out)
+        return m.stats()["ray_samples"], gpu_maps(out)
+
+    sa, ga = alone(ia)
+    assert sa == 0 and (ga["vol_id"] < 0).all()
+    sb, gb = alone(ib)
+    assert sb > 0 and (gb["vol_id"] == ib).mean() > 0.9
+    m.stats(reset=True)
+    g = gpu_maps(m.raycast(cam, T))
+    assert m.stats()["ray_samples"] == sb
+    for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+        np.testing.assert_array_equal(g[key], gb[key])
+
+    # a plane z = 0.45 m written into `air`: now it must be marched and hit
+    z = (air.h[2] + np.arange(air.r[2]))[:, None, None] * s
+    F_plane = np.broadcast_to(np.clip((0.45 - z) / (4 * s), -1, 1), Fa.shape).astype(np.float32)
+    ones = np.ones_like(F_plane)
+    o, dirs = synth.pixel_rays(cam, T)
+    tau = (0.45 - o[..., 2]) / dirs[..., 2]
+
+    def check_plane_hit():
+        sa, ga = alone(ia)
+        assert sa > 0
+        hit = ga["vol_id"] == ia
+        assert hit.mean() > 0.9
+        err = np.abs(ga["depth"] - tau) * np.linalg.norm(dirs, axis=-1) / s
+        assert err[hit].max() < 2e-3
+        np.testing.assert_array_equal(gpu_maps(m.raycast(cam, T))["vol_id"][hit], ia)
+
+    m.write_decoded(ia, F_plane, ones)            # resident: flags recomputed on the device
+    check_plane_hit()
+    m.swap_out(ia)
+    m.write_decoded(ia, np.ones_like(F_plane), ones)  # swapped out: flags recomputed on the host
+    m.swap_in(ia)
+    assert alone(ia)[0] == 0
+    m.swap_out(ia)
+    m.write_decoded(ia, F_plane, ones)
+    m.swap_in(ia)
+    check_plane_hit()
+    m.swap_out(ia)                                # the count travels with the swap
+    m.swap_in(ia)
+    check_plane_hit()
+    m.close()
