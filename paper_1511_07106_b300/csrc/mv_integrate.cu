@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(128) brick_flags_kernel(VolDev v)
 // Cell-brick flag of cell brick (cx, cy, cz): the trilinear cells whose lower
 // corner lies in that brick read voxels of the 8 bricks (cx, cy, cz) + {0,1}^3;
 // bricks beyond the volume only hold cells outside the interpolation domain.
-__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz)
+__device__ __forceinline__ bool cell_skip_of(const VolDev &v, int cx, int cy, int cz)
 {
     bool skip = true;
 #pragma unroll
@@ -493,12 +493,34 @@ __device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy
         if (x < v.nb[0] && y < v.nb[1] && z < v.nb[2])
             skip &= (v.bflag[((long long)z * v.nb[1] + y) * v.nb[0] + x] & kFlagNoNeg) != 0;
     }
-    v.cflag[((long long)cz * v.nb[1] + cy) * v.nb[0] + cx] = skip ? kCellSkip : 0;
+    return skip;
+}
+
+__device__ __forceinline__ unsigned *super_count_of(const VolDev &v, int cx, int cy, int cz)
+{
+    return v.sup + ((long long)(cz / kSuper) * v.nsb[1] + cy / kSuper) * v.nsb[0] + cx / kSuper;
+}
+
+// Incremental refresh: the flag byte is changed by an atomic on its aligned
+// word, whose returned old value tells exactly one of several threads that
+// refresh the same cell brick that the flag changed; that thread moves the
+// super-brick count.
+__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz)
+{
+    const bool skip = cell_skip_of(v, cx, cy, cz);
+    uint8_t *pb = v.cflag + ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
+    if (!v.sup) {
+        *pb = skip ? kCellSkip : 0;
+        return;
+    }
+    unsigned *w = reinterpret_cast<unsigned *>(reinterpret_cast<uintptr_t>(pb) & ~(uintptr_t)3);
+    const unsigned bit = (unsigned)kCellSkip << (8u * (unsigned)(reinterpret_cast<uintptr_t>(pb) & 3u));
+    const unsigned old = skip ? atomicOr(w, bit) : atomicAnd(w, ~bit);
+    if (((old & bit) != 0u) != skip) atomicAdd(super_count_of(v, cx, cy, cz), skip ? 0xFFFFFFFFu : 1u);
 }
 
 // After an integration: refresh the cell-brick flags that the listed bricks
-// feed (each listed brick b is read by the cell bricks b - {0,1}^3).  Cells
-// written by two threads get the same value from the same final voxel flags.
+// feed (each listed brick b is read by the cell bricks b - {0,1}^3).
 __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restrict__ vols,
                                                          const uint2 *__restrict__ list,
                                                          const unsigned *__restrict__ counter)
@@ -519,7 +541,8 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
     }
 }
 
-// Every cell-brick flag of one volume (after a host write).
+// Every cell-brick flag of one volume (after a host write), with the
+// super-brick counts recounted from zero (zeroed before this kernel).
 __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -527,7 +550,9 @@ __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
         const int cx = (int)(b % v.nb[0]);
         const int cy = (int)((b / v.nb[0]) % v.nb[1]);
         const int cz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
-        update_cell_flag(v, cx, cy, cz);
+        const bool skip = cell_skip_of(v, cx, cy, cz);
+        v.cflag[b] = skip ? kCellSkip : 0;
+        if (!skip && v.sup) atomicAdd(super_count_of(v, cx, cy, cz), 1u);
     }
 }
 
@@ -592,6 +617,11 @@ cudaError_t launch_brick_flags(const VolDev &v, int num_sms, cudaStream_t s)
     if (blocks < 1) blocks = 1;
     if (v.surf) {
         const cudaError_t z = cudaMemsetAsync(v.surf, 0, sizeof(unsigned), s);
+        if (z != cudaSuccess) return z;
+    }
+    if (v.sup) {
+        const size_t nsuper = (size_t)v.nsb[0] * v.nsb[1] * v.nsb[2];
+        const cudaError_t z = cudaMemsetAsync(v.sup, 0, sizeof(unsigned) * nsuper, s);
         if (z != cudaSuccess) return z;
     }
     brick_flags_kernel<<<(unsigned)blocks, 128, 0, s>>>(v);

@@ -31,6 +31,9 @@ constexpr uint8_t kFlagEmpty = 2;  // every voxel of the brick has W == 0
 constexpr uint8_t kFlagNoNeg = 4;  // no voxel of the brick has W > 0 and F <= 0
 constexpr uint8_t kFlagsNew = kFlagEmpty | kFlagNoNeg;  // a freshly cleared brick
 constexpr uint8_t kCellSkip = 1;   // the 8 bricks b + {0,1}^3 all carry kFlagNoNeg
+// Super brick: kSuper^3 cell bricks (32^3 voxels).  A super brick whose count
+// of cell bricks without kCellSkip is 0 is crossed by the raycast in one step.
+constexpr int kSuper = 4;
 constexpr int kMaxVolumes = 4096;
 
 // One volume as the kernels see it.
@@ -40,9 +43,11 @@ struct VolDev {
     uint8_t *bflag;    // one flag byte per brick
     uint8_t *cflag;    // one cell-brick byte per brick (may be null where no raycast reads it)
     unsigned *surf;    // bricks without kFlagNoNeg (0: no hit possible anywhere), may be null
+    unsigned *sup;     // per super brick: cell bricks without kCellSkip (may be null)
     int h[3];          // lattice offset h_t
     int r[3];          // voxels per axis h_r
     int nb[3];         // bricks per axis
+    int nsb[3];        // super bricks per axis, ceil(nb / kSuper)
     float s, inv_s;    // pitch and its reciprocal
     int fmt;           // mv_tsdf_fmt
     int id;            // public id (merge tie-break)
@@ -89,10 +94,21 @@ struct VisList {
     long long base[kMaxVolumes + 1]; // prefix sums of nbricks over slot[]
 };
 
-// Flag allocation of a volume: voxel-brick flags, cell-brick flags, then
-// (8-byte aligned) the count of bricks without kFlagNoNeg.
-inline size_t flag_count_offset(long long nbricks) { return ((size_t)(2 * nbricks) + 7) & ~(size_t)7; }
-inline size_t flag_alloc_bytes(long long nbricks) { return flag_count_offset(nbricks) + 8; }
+// Flag allocation of a volume with nbricks bricks and nsuper super bricks:
+// voxel-brick flags (1 B/brick), cell-brick flags (1 B/brick, 4-byte
+// aligned so that a flag byte can be changed by a 32-bit atomic on its word),
+// the count of bricks without kFlagNoNeg (u32, 8-byte aligned), then per
+// super brick the count of its cell bricks without kCellSkip (u32).
+inline size_t cflag_offset(long long nbricks) { return ((size_t)nbricks + 3) & ~(size_t)3; }
+inline size_t flag_count_offset(long long nbricks)
+{
+    return (cflag_offset(nbricks) + (size_t)nbricks + 7) & ~(size_t)7;
+}
+inline size_t super_offset(long long nbricks) { return flag_count_offset(nbricks) + 8; }
+inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
+{
+    return super_offset(nbricks) + 4 * (size_t)nsuper;
+}
 
 struct Stats {
     unsigned long long swept, updated, band, bricks;

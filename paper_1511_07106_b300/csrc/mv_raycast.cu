@@ -237,6 +237,36 @@ __device__ __forceinline__ void dda_axis(float L, float dq, int b0, int r, float
     }
 }
 
+__device__ __forceinline__ bool super_empty(const VolDev &v, int bx, int by, int bz)
+{
+    const unsigned i = (((unsigned)bz >> 2) * (unsigned)v.nsb[1] + ((unsigned)by >> 2)) * (unsigned)v.nsb[0] +
+                       ((unsigned)bx >> 2);
+    return __ldg(v.sup + i) == 0u;
+}
+
+// Brick boundaries along one axis between brick b and the face of its super
+// brick in the step direction.
+__device__ __forceinline__ int inner_faces(int b, int step)
+{
+    return step > 0 ? 3 - (b & 3) : (step < 0 ? (b & 3) : 0);
+}
+
+// Brick boundaries along one axis crossed by parameter texit (next boundary
+// at tmax, spacing tdel = 1 / rdel), at most n.  Rounded down near a
+// boundary: the walk then visits a brick the ray only grazes (an earlier
+// stop), never skips one.
+__device__ __forceinline__ int faces_crossed(float tmax, float rdel, float texit, int n)
+{
+    if (!(tmax <= texit)) return 0;
+    return min(n, (int)floorf(fmaf(texit - tmax, rdel, -1e-4f)) + 1);
+}
+
+// 3D DDA from the sample at L (volume voxel coordinates, cell brick b0,
+// flagged kCellSkip) along dq (voxels per sample) over cell bricks flagged
+// kCellSkip; a super brick (kSuper^3 cell bricks) whose count of cell bricks
+// without kCellSkip is 0 is crossed in one step.  Returns, in samples from L,
+// the end of that run of bricks less m voxels (capped at the domain end less
+// m).
 __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], const float dq[3],
                                           const int b0[3], float m)
 {
@@ -245,21 +275,49 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
     dda_axis(L[0], dq[0], b0[0], v.r[0], m, tx, dx, sx, tdom);
     dda_axis(L[1], dq[1], b0[1], v.r[1], m, ty, dy, sy, tdom);
     dda_axis(L[2], dq[2], b0[2], v.r[2], m, tz, dz, sz, tdom);
+    const float rx = fabsf(dq[0]) * (1.0f / kBrick), ry = fabsf(dq[1]) * (1.0f / kBrick),
+                rz = fabsf(dq[2]) * (1.0f / kBrick);
     int bx = b0[0], by = b0[1], bz = b0[2];
     const int nbx = v.nb[0], nby = v.nb[1], nbz = v.nb[2];
     const int max_steps = nbx + nby + nbz + 3;
     float texit = 0.f, dexit = 1.f;
+    bool empty = v.sup && super_empty(v, bx, by, bz);
     for (int it = 0; it < max_steps; ++it) {
-        bool out;
-        if (tx <= ty && tx <= tz) {
+        bool out, new_super;
+        if (empty) {
+            // to the face of the super brick, every axis advanced to match
+            const int nx = inner_faces(bx, sx), ny = inner_faces(by, sy), nz = inner_faces(bz, sz);
+            const float fx = tx + (float)nx * dx, fy = ty + (float)ny * dy, fz = tz + (float)nz * dz;
+            int jx, jy, jz;
+            if (fx <= fy && fx <= fz) {
+                texit = fx; dexit = fabsf(dq[0]);
+                jx = nx + 1; jy = faces_crossed(ty, ry, texit, ny); jz = faces_crossed(tz, rz, texit, nz);
+            } else if (fy <= fz) {
+                texit = fy; dexit = fabsf(dq[1]);
+                jx = faces_crossed(tx, rx, texit, nx); jy = ny + 1; jz = faces_crossed(tz, rz, texit, nz);
+            } else {
+                texit = fz; dexit = fabsf(dq[2]);
+                jx = faces_crossed(tx, rx, texit, nx); jy = faces_crossed(ty, ry, texit, ny); jz = nz + 1;
+            }
+            bx += sx * jx; tx += (float)jx * dx;
+            by += sy * jy; ty += (float)jy * dy;
+            bz += sz * jz; tz += (float)jz * dz;
+            out = bx < 0 || bx >= nbx || by < 0 || by >= nby || bz < 0 || bz >= nbz;
+            new_super = true;
+        } else if (tx <= ty && tx <= tz) {
             texit = tx; dexit = fabsf(dq[0]); bx += sx; tx += dx; out = bx < 0 || bx >= nbx;
+            new_super = (bx & 3) == (sx > 0 ? 0 : 3);
         } else if (ty <= tz) {
             texit = ty; dexit = fabsf(dq[1]); by += sy; ty += dy; out = by < 0 || by >= nby;
+            new_super = (by & 3) == (sy > 0 ? 0 : 3);
         } else {
             texit = tz; dexit = fabsf(dq[2]); bz += sz; tz += dz; out = bz < 0 || bz >= nbz;
+            new_super = (bz & 3) == (sz > 0 ? 0 : 3);
         }
         if (out) break;
-        if (!(__ldg(v.cflag + ((long long)bz * nby + by) * nbx + bx) & kCellSkip)) break;
+        const uint8_t cf = __ldg(v.cflag + ((long long)bz * nby + by) * nbx + bx);
+        if (new_super) empty = v.sup && super_empty(v, bx, by, bz);
+        if (!empty && !(cf & kCellSkip)) break;
     }
     return fminf(texit - m / dexit, tdom);
 }

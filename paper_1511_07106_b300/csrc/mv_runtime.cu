@@ -69,7 +69,8 @@ struct Volume {
     int id = -1;
     mv_volume_desc desc{};
     int nb[3] = {0, 0, 0};
-    long long nbricks = 0;
+    int nsb[3] = {0, 0, 0};
+    long long nbricks = 0, nsuper = 0;
     size_t fw_bytes = 0, rgba_bytes = 0, flag_bytes = 0;
     void *d_fw = nullptr;
     uint32_t *d_rgba = nullptr;
@@ -201,8 +202,10 @@ VolDev make_voldev(const Volume &v)
     d.fw = v.d_fw;
     d.rgba = v.d_rgba;
     d.bflag = v.d_flag;
-    d.cflag = v.d_flag ? v.d_flag + v.nbricks : nullptr;
+    d.cflag = v.d_flag ? v.d_flag + cflag_offset(v.nbricks) : nullptr;
     d.surf = v.d_flag ? reinterpret_cast<unsigned *>(v.d_flag + flag_count_offset(v.nbricks)) : nullptr;
+    d.sup = v.d_flag ? reinterpret_cast<unsigned *>(v.d_flag + super_offset(v.nbricks)) : nullptr;
+    for (int a = 0; a < 3; ++a) d.nsb[a] = v.nsb[a];
     for (int a = 0; a < 3; ++a) {
         d.h[a] = v.desc.h_t[a];
         d.r[a] = v.desc.h_r[a];
@@ -494,13 +497,16 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     Volume *v = new Volume();
     v->desc = *d;
     v->nbricks = 1;
+    v->nsuper = 1;
     for (int a = 0; a < 3; ++a) {
         v->nb[a] = (d->h_r[a] + kBrick - 1) / kBrick;
         v->nbricks *= v->nb[a];
+        v->nsb[a] = (v->nb[a] + kSuper - 1) / kSuper;
+        v->nsuper *= v->nsb[a];
     }
     v->fw_bytes = (size_t)v->nbricks * kBrickVox * fw_elem_bytes(d->fmt);
     v->rgba_bytes = (size_t)v->nbricks * kBrickVox * 4;
-    v->flag_bytes = flag_alloc_bytes(v->nbricks);  // voxel-brick flags, cell-brick flags, count
+    v->flag_bytes = flag_alloc_bytes(v->nbricks, v->nsuper);  // brick, cell, count, super counts
     cudaStream_t s = c->swap_stream;
     cudaError_t e = cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocAsync(&v->d_fw, v->fw_bytes, s);
@@ -508,10 +514,12 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_flag, v->flag_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_fw, 0, v->fw_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_rgba, 0, v->rgba_bytes, s);
+    // nothing observed yet: every brick NONEG, every cell brick skipped, the
+    // counts (bricks without NONEG, cell bricks without skip) all 0
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, 0, v->flag_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag, kFlagsNew, (size_t)v->nbricks, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_flag + v->nbricks, kCellSkip, (size_t)v->nbricks, s);
-    if (e == cudaSuccess)  // no brick holds an observed voxel yet: the count starts at 0
-        e = cudaMemsetAsync(v->d_flag + flag_count_offset(v->nbricks), 0, 8, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(v->d_flag + cflag_offset(v->nbricks), kCellSkip, (size_t)v->nbricks, s);
     if (e == cudaSuccess) e = cudaEventRecord(v->ready, s);
     if (e != cudaSuccess) {
         if (v->d_fw) cudaFreeAsync(v->d_fw, s);
@@ -839,6 +847,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
         sv.bflag = (uint8_t *)sflag;
         sv.cflag = nullptr;
         sv.surf = nullptr;
+        sv.sup = nullptr;
         sv.brick_base = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(stab, &sv, sizeof(VolDev), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sv is a stack value
@@ -1133,6 +1142,7 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
             surf += no_neg ? 0u : 1u;
         }
         std::memcpy(v->h_flag + flag_count_offset(nb), &surf, sizeof(surf));
+        std::vector<unsigned> sup((size_t)v->nsuper, 0u);
         for (long long b = 0; b < nb; ++b) {
             const int cx = (int)(b % v->nb[0]), cy = (int)((b / v->nb[0]) % v->nb[1]);
             const int cz = (int)(b / ((long long)v->nb[0] * v->nb[1]));
@@ -1142,8 +1152,10 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
                 if (x < v->nb[0] && y < v->nb[1] && z < v->nb[2])
                     skip &= (v->h_flag[((long long)z * v->nb[1] + y) * v->nb[0] + x] & kFlagNoNeg) != 0;
             }
-            v->h_flag[nb + b] = skip ? kCellSkip : 0;
+            v->h_flag[cflag_offset(nb) + b] = skip ? kCellSkip : 0;
+            if (!skip) ++sup[((size_t)(cz / kSuper) * v->nsb[1] + cy / kSuper) * v->nsb[0] + cx / kSuper];
         }
+        std::memcpy(v->h_flag + super_offset(nb), sup.data(), sizeof(unsigned) * sup.size());
     }
     return MV_OK;
 }
