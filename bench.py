@@ -484,6 +484,46 @@ def bench_swap(torch, Mapper, Config, frames, steps):
             "hidden_fraction": max(0.0, min(1.0, (t_int + t_swap - t_both) / min(t_int, t_swap)))}
 
 
+def bench_streamed(torch, Mapper, Config, frames, n_frames=6):
+    """Full-cover out-of-core frames (the paper's per-frame upload, integrate,
+    raycast, download of every volume): 4 tiles of 512^3 (the lower half of
+    the room mapped at 2.93 mm), all swapped out to pinned host memory and
+    streamed through the device every frame."""
+    wl = synth.tiled(synth.room_512(frames=N_FRAMES_MAX, res=1022), split=2)
+    vols = wl.volumes[:4]
+    cam = wl.cam
+    dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_frames + 1]])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames[:n_frames + 1]])).cuda()
+    out = {"workload": "4 x 512^3 tiles at 2.93 mm (lower half of the 3 m room), all swapped out, "
+                       "streamed every frame, 640x480",
+           "volumes": len(vols), "paper_s_per_frame_per_volume": 0.17,
+           "paper_hardware": "GTX 880M (context only)"}
+    for fmt, n_slots in (("f32", 1), ("f32", 2), ("f16", 2)):
+        m = Mapper(Config())
+        ids = [m.add_volume(v.h, v.r, v.s, fmt) for v in vols]
+        for vid in ids:
+            m.swap_out(vid)
+        m.synchronize()
+        maps = m.alloc_maps(cam)
+        m.frame_streamed(dd[0], dc[0], cam, wl.poses[0], out=maps, n_slots=n_slots)  # allocates the slots
+        m.synchronize()
+        m.stats(reset=True)
+        t0 = time.perf_counter()
+        for k in range(1, n_frames + 1):
+            m.frame_streamed(dd[k], dc[k], cam, wl.poses[k], out=maps, n_slots=n_slots)
+        m.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / n_frames
+        st = m.stats()
+        vbytes = m.query(ids[0])["host_bytes"]
+        m.close()
+        torch.cuda.empty_cache()
+        out[f"{fmt}_slots{n_slots}"] = {
+            "ms_per_frame": ms, "s_per_frame_per_volume": ms * 1e-3 / len(vols),
+            "bytes_per_volume": vbytes, "copy_gbs_each_way": len(vols) * vbytes / (ms * 1e-3) / 1e9,
+            "updated_voxels_per_frame": st["updated"] / n_frames}
+    return out
+
+
 def main_reference(args, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
     if rank != 0:
@@ -653,6 +693,7 @@ def main():
         line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup)
         line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
         line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
+        line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
         m = None
 
     if m is not None:

@@ -213,8 +213,26 @@ mv_status mv_frame(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv
                    const double T_c2w[16], float *depth_out, float *normal, uint8_t *rgba,
                    float *vertex, int32_t *vol_id, void *stream);
 
+/* Full-cover out-of-core frame (Sec. Volumetric Integration and
+ * Sec. Raycasting, Algorithm 1: every volume is uploaded, integrated,
+ * raycast and downloaded again in every frame).  Resident volumes are
+ * integrated and raycast in place, as by mv_frame; then every swapped-out
+ * volume passes through one of n_slots (1..4) device staging slots: its host
+ * copy is uploaded on one copy stream, integrated and raycast into the same
+ * maps on `stream` (nearest hit wins, ties to the lower id, so the maps equal
+ * those of all volumes resident), and downloaded back into its host copy on a
+ * second copy stream, so that the copies of one slot overlap the kernels of
+ * another.  The volumes stay swapped out.  The slots (sized for the largest
+ * swapped-out volume) are kept by the context for later calls.  `stream`
+ * waits for the last download; later swap-in, read and write calls wait for
+ * the downloads of their volume.  depth_out and vol_id are required.
+ * MV_ERR_ARG for n_slots outside 1..4; MV_ERR_OOM when the slots do not fit. */
+mv_status mv_frame_streamed(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                            const double T_c2w[16], float *depth_out, float *normal, uint8_t *rgba,
+                            float *vertex, int32_t *vol_id, int32_t n_slots, void *stream);
+
 /* Raycast one volume and merge its hits into the maps (the paper's
- * per-volume raycast: "all raycasting steps modify the same map").  With
+ * per-volume raycast, in which every volume writes into one shared map).  With
  * first != 0 the maps are (re)initialised by this call; otherwise a pixel is
  * overwritten only when this volume's hit is nearer, or equally near with a
  * lower id.  depth and vol_id are required (they carry the merge state);

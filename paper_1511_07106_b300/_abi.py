@@ -91,6 +91,8 @@ _SIGNATURES = {
     "mv_integrate_volume": ([_P, C.c_int32, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_raycast": ([_P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_frame": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
+    "mv_frame_streamed": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, C.c_int32, _P],
+                          C.c_int),
     "mv_raycast_volume": ([_P, C.c_int32, C.c_int32, C.POINTER(mv_intrinsics), _D16, _P, _P, _P,
                            _P, _P, _P], C.c_int),
     "mv_autotune": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, C.POINTER(mv_tuning), _P], C.c_int),

@@ -22,6 +22,7 @@
 #include "mv_internal.cuh"
 
 namespace mv {
+constexpr int kMaxStreamSlots = 4;
 cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFrame *, unsigned *, cudaStream_t,
                                VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
@@ -120,6 +121,23 @@ struct mv_ctx {
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
+    // full-cover streaming (mv_frame_streamed): device staging slots that the
+    // swapped-out volumes pass through, one copy stream per direction
+    struct Slots {
+        int n = 0;
+        size_t fw_cap = 0, rgba_cap = 0, flag_cap = 0;  // bytes per slot
+        long long list_cap = 0;                         // work-list entries
+        void *fw[kMaxStreamSlots] = {};
+        uint32_t *rgba[kMaxStreamSlots] = {};
+        uint8_t *flag[kMaxStreamSlots] = {};
+        VolDev *d_vol = nullptr;   // one descriptor per slot
+        VolFrame *d_vf = nullptr;  // one camera-constant record per slot
+        uint2 *list = nullptr;
+        unsigned *counter = nullptr;
+        cudaStream_t h2d = nullptr, d2h = nullptr;
+        cudaEvent_t loaded[kMaxStreamSlots] = {}, done[kMaxStreamSlots] = {}, freed[kMaxStreamSlots] = {};
+        bool freed_rec[kMaxStreamSlots] = {};
+    } ss;
     // raycast backward: per-slot gradient pointers and the poses of one call
     float **d_grad_ptrs = nullptr;
     double *d_poses = nullptr;
@@ -386,6 +404,87 @@ void free_host(Volume *v)
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// full-cover streaming
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void put_voldev_kernel(VolDev v, VolDev *dst)
+{
+    if (threadIdx.x == 0) *dst = v;
+}
+
+// (Re)allocate the staging slots for n slots of at least the given sizes.
+mv_status ensure_slots(mv_ctx *c, int n, size_t fw, size_t rgba, size_t flag, long long bricks,
+                       cudaStream_t s)
+{
+    auto &ss = c->ss;
+    if (!ss.h2d) MV_CUDA(c, cudaStreamCreateWithFlags(&ss.h2d, cudaStreamNonBlocking));
+    if (!ss.d2h) MV_CUDA(c, cudaStreamCreateWithFlags(&ss.d2h, cudaStreamNonBlocking));
+    if (!ss.d_vol) MV_CUDA(c, cudaMalloc((void **)&ss.d_vol, sizeof(VolDev) * kMaxStreamSlots));
+    if (!ss.d_vf) MV_CUDA(c, cudaMalloc((void **)&ss.d_vf, sizeof(VolFrame) * kMaxStreamSlots));
+    if (!ss.counter) MV_CUDA(c, cudaMalloc((void **)&ss.counter, sizeof(unsigned) * 4));
+    for (int j = 0; j < kMaxStreamSlots; ++j) {
+        if (!ss.loaded[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.loaded[j], cudaEventDisableTiming));
+        if (!ss.done[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.done[j], cudaEventDisableTiming));
+        if (!ss.freed[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.freed[j], cudaEventDisableTiming));
+    }
+    if (bricks > ss.list_cap) {
+        if (ss.list) MV_CUDA(c, cudaFreeAsync(ss.list, s));
+        ss.list = nullptr;
+        ss.list_cap = 0;
+        MV_CUDA(c, cudaMallocAsync((void **)&ss.list, sizeof(uint2) * (size_t)bricks, s));
+        ss.list_cap = bricks;
+    }
+    const bool grow = n > ss.n || fw > ss.fw_cap || rgba > ss.rgba_cap || flag > ss.flag_cap;
+    if (!grow) return MV_OK;
+    // slots in use by earlier calls are released in stream order
+    for (int j = 0; j < ss.n; ++j)
+        if (ss.freed_rec[j]) MV_CUDA(c, cudaStreamWaitEvent(s, ss.freed[j], 0));
+    for (int j = 0; j < kMaxStreamSlots; ++j) {
+        if (ss.fw[j]) MV_CUDA(c, cudaFreeAsync(ss.fw[j], s));
+        if (ss.rgba[j]) MV_CUDA(c, cudaFreeAsync(ss.rgba[j], s));
+        if (ss.flag[j]) MV_CUDA(c, cudaFreeAsync(ss.flag[j], s));
+        ss.fw[j] = nullptr;
+        ss.rgba[j] = nullptr;
+        ss.flag[j] = nullptr;
+        ss.freed_rec[j] = false;
+    }
+    ss.n = 0;
+    ss.fw_cap = std::max(fw, ss.fw_cap);
+    ss.rgba_cap = std::max(rgba, ss.rgba_cap);
+    ss.flag_cap = std::max(flag, ss.flag_cap);
+    for (int j = 0; j < n; ++j) {
+        MV_CUDA(c, cudaMallocAsync(&ss.fw[j], ss.fw_cap, s));
+        MV_CUDA(c, cudaMallocAsync((void **)&ss.rgba[j], ss.rgba_cap, s));
+        MV_CUDA(c, cudaMallocAsync((void **)&ss.flag[j], ss.flag_cap, s));
+    }
+    ss.n = n;
+    return MV_OK;
+}
+
+void free_slots(mv_ctx *c, cudaStream_t s)
+{
+    auto &ss = c->ss;
+    for (int j = 0; j < kMaxStreamSlots; ++j) {
+        if (ss.fw[j]) cudaFreeAsync(ss.fw[j], s);
+        if (ss.rgba[j]) cudaFreeAsync(ss.rgba[j], s);
+        if (ss.flag[j]) cudaFreeAsync(ss.flag[j], s);
+        if (ss.loaded[j]) cudaEventDestroy(ss.loaded[j]);
+        if (ss.done[j]) cudaEventDestroy(ss.done[j]);
+        if (ss.freed[j]) cudaEventDestroy(ss.freed[j]);
+    }
+    if (ss.list) cudaFreeAsync(ss.list, s);
+    if (ss.d_vol) cudaFree(ss.d_vol);
+    if (ss.d_vf) cudaFree(ss.d_vf);
+    if (ss.counter) cudaFree(ss.counter);
+    if (ss.h2d) cudaStreamDestroy(ss.h2d);
+    if (ss.d2h) cudaStreamDestroy(ss.d2h);
+    ss = mv_ctx::Slots{};
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *mv_version(void) { return "mvtsdf 0.1.0 (sm_103a)"; }
@@ -450,6 +549,7 @@ mv_status mv_destroy(mv_ctx *c)
         if (v->d_flag) cudaFreeAsync(v->d_flag, s);
     }
     if (c->d_list) cudaFreeAsync(c->d_list, s);
+    free_slots(c, s);
     if (s) cudaStreamSynchronize(s);
     for (auto &kv : c->vols) {
         Volume *v = kv.second;
@@ -751,6 +851,102 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     return end_call(c, s);
 }
 
+mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                            const double T[16], float *depth_out, float *normal, uint8_t *rgba,
+                            float *vertex, int32_t *vol_id, int32_t n_slots, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    if (!depth_out || !vol_id) return fail(c, MV_ERR_ARG, "depth_out and vol_id are required");
+    if (n_slots < 1 || n_slots > kMaxStreamSlots) return fail(c, MV_ERR_ARG, "n_slots out of range");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // 1. resident volumes: batched integration, then the raycast that
+    //    initialises the maps
+    mv_status st = integrate_impl(c, -1, depth, rgb, K, T, stream);
+    if (st) return st;
+    st = raycast_impl(c, -1, 1, K, T, depth_out, normal, rgba, vertex, vol_id, stream);
+    if (st) return st;
+    std::vector<Volume *> streamed;
+    size_t fw = 0, col = 0, fl = 0;
+    long long bricks = 0;
+    for (auto &kv : c->vols) {
+        Volume *v = kv.second;
+        if (v->resident) continue;
+        streamed.push_back(v);
+        fw = std::max(fw, v->fw_bytes);
+        col = std::max(col, v->rgba_bytes);
+        fl = std::max(fl, v->flag_bytes);
+        bricks = std::max(bricks, v->nbricks);
+    }
+    if (streamed.empty()) return MV_OK;
+    st = begin_call(c, s);
+    if (st) return st;
+    st = ensure_slots(c, n_slots, fw, col, fl, bricks, s);
+    if (st) return st;
+    auto &ss = c->ss;
+    const int n = ss.n < n_slots ? ss.n : n_slots;
+    const FrameParams P = make_params(c, K, T);
+    // the copies start after everything queued on the caller's stream so far
+    MV_CUDA(c, cudaEventRecord(c->last_event, s));
+    MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, c->last_event, 0));
+    // 2. every swapped-out volume: upload into a slot, integrate, raycast
+    //    into the maps (nearest hit wins, as between resident volumes),
+    //    download; slot j is reused once its previous volume is downloaded
+    for (size_t i = 0; i < streamed.size(); ++i) {
+        Volume *v = streamed[i];
+        const int j = (int)(i % (size_t)n);
+        if (ss.freed_rec[j]) MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, ss.freed[j], 0));
+        if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, v->ready, 0));
+        MV_CUDA(c, cudaMemcpyAsync(ss.fw[j], v->h_fw, v->fw_bytes, cudaMemcpyHostToDevice, ss.h2d));
+        MV_CUDA(c, cudaMemcpyAsync(ss.rgba[j], v->h_rgba, v->rgba_bytes, cudaMemcpyHostToDevice, ss.h2d));
+        MV_CUDA(c, cudaMemcpyAsync(ss.flag[j], v->h_flag, v->flag_bytes, cudaMemcpyHostToDevice, ss.h2d));
+        MV_CUDA(c, cudaEventRecord(ss.loaded[j], ss.h2d));
+
+        Volume staged = *v;
+        staged.d_fw = ss.fw[j];
+        staged.d_rgba = ss.rgba[j];
+        staged.d_flag = ss.flag[j];
+        VolDev d = make_voldev(staged);
+        d.brick_base = 0;
+        VolDev *dv = ss.d_vol + j;
+        VolFrame *vf = ss.d_vf + j;
+        MV_CUDA(c, cudaStreamWaitEvent(s, ss.loaded[j], 0));
+        put_voldev_kernel<<<1, 32, 0, s>>>(d, dv);
+        MV_CUDA(c, cudaGetLastError());
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
+            return launch_frame_setup(dv, 1, P, vf, ss.counter, s, nullptr); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
+            return launch_depth_max(depth, P, ss.counter + 1, c->num_sms, s); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
+            return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, ss.list, ss.counter, c->num_sms, s, nullptr,
+                                     ss.counter + 1); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
+            return launch_integrate(dv, vf, ss.list, ss.counter, P, depth, rgb, c->d_stats, c->grid_integrate,
+                                    s); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
+            return launch_cell_flags(dv, ss.list, ss.counter, c->num_sms, s); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
+            return launch_raycast(dv, vf, 1, P, depth_out, normal, rgba, vertex, vol_id, 1, c->d_stats,
+                                  c->ray_tile, s, nullptr); }));
+        MV_CUDA(c, cudaEventRecord(ss.done[j], s));
+
+        MV_CUDA(c, cudaStreamWaitEvent(ss.d2h, ss.done[j], 0));
+        MV_CUDA(c, cudaMemcpyAsync(v->h_fw, ss.fw[j], v->fw_bytes, cudaMemcpyDeviceToHost, ss.d2h));
+        MV_CUDA(c, cudaMemcpyAsync(v->h_rgba, ss.rgba[j], v->rgba_bytes, cudaMemcpyDeviceToHost, ss.d2h));
+        MV_CUDA(c, cudaMemcpyAsync(v->h_flag, ss.flag[j], v->flag_bytes, cudaMemcpyDeviceToHost, ss.d2h));
+        MV_CUDA(c, cudaEventRecord(ss.freed[j], ss.d2h));
+        ss.freed_rec[j] = true;
+        // later readers of the host copy (swap-in, read, write) wait for it
+        MV_CUDA(c, cudaEventRecord(v->ready, ss.d2h));
+        v->ready_pending = true;
+    }
+    // the caller's stream continues once every download has finished
+    for (int j = 0; j < n; ++j)
+        if (ss.freed_rec[j]) MV_CUDA(c, cudaStreamWaitEvent(s, ss.freed[j], 0));
+    return end_call(c, s);
+}
+
 static float time_ms(cudaStream_t s, cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.f;
@@ -1029,6 +1225,8 @@ mv_status mv_swap_in(mv_ctx *c, int32_t id, void *stream)
     cudaSetDevice(c->device);
     cudaStream_t s = c->swap_stream;
     (void)stream;
+    // a download into the host copy (swap-out or streamed frame) may still run
+    if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(s, v->ready, 0));
     void *fw = nullptr, *rgba = nullptr, *flag = nullptr;
     cudaError_t e = cudaMallocAsync(&fw, v->fw_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&rgba, v->rgba_bytes, s);

@@ -223,6 +223,20 @@ class Mapper:
         del keep
         return out
 
+    def frame_streamed(self, depth, rgb, cam, T, out=None, n_slots=2, stream=None) -> dict:
+        """Integrate the frame into every volume and raycast the same view,
+        streaming the swapped-out volumes through n_slots device slots."""
+        import torch
+        out = out if out is not None else self.alloc_maps(cam)
+        K = intrinsics(cam)
+        n = cam.width * cam.height
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_frame_streamed(self._h, _dptr(depth, torch.float32, n, "depth"),
+                                                _dptr(rgb, torch.uint8, 3 * n, "rgb"), C.byref(K), Tp,
+                                                *self._map_ptrs(out, cam), int(n_slots), _stream(stream)))
+        del keep
+        return out
+
     def raycast_volume(self, vid, first, cam, T, out, stream=None) -> dict:
         K = intrinsics(cam)
         _, Tp = keep = _pose(T)
