@@ -338,6 +338,13 @@ def _render_tiles(i):
     return synth.room_tiles(frames=N_FRAMES_MAX).frame(i)
 
 
+PLACEMENT_FRAMES = 90
+
+
+def _render_placement(i):
+    return synth.placement_room(frames=N_FRAMES_MAX).wl.frame(i)
+
+
 def _gen(fn, idx, procs):
     with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(fn, idx))
@@ -524,6 +531,61 @@ def bench_streamed(torch, Mapper, Config, frames, n_frames=6):
     return out
 
 
+def bench_placement(torch, Mapper, Config, frames):
+    """Multi-volume dynamic placement (the paper's Sec. Dynamic Mapping for
+    SLAM): a 6 x 5 x 3 m room, 512^3 volumes of 0.75 m (1.46 mm voxels) placed
+    on the lattice by the ray-endpoint histogram, at most 16 resident, the
+    displaced ones swapped out to pinned host memory.  Per frame: integrate +
+    raycast of the resident volumes (mv_frame), then one placement step."""
+    from paper_1511_07106_b300 import Placer
+    pw = synth.placement_room(frames=N_FRAMES_MAX)
+    wl = pw.wl
+    m = Mapper(Config())
+    p = Placer(m, pw.cell_voxels, pw.volume_voxels, pw.voxel_size, pw.max_volumes, hysteresis=1.5)
+    maps = m.alloc_maps(wl.cam)
+    dd = torch.from_numpy(np.stack([f[0] for f in frames])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames])).cuda()
+    tot = {"added": 0, "restored": 0, "evicted": 0}
+    res_sum, t_frame, t_place, upd = 0, 0.0, 0.0, 0
+    n = len(frames)
+    m.stats(reset=True)
+    for i in range(n):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.frame(dd[i], dc[i], wl.cam, wl.poses[i], out=maps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = p.update(dd[i], wl.cam, wl.poses[i])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if i > 0:  # frame 0 integrates into nothing: the first placement follows it
+            t_frame += t1 - t0
+            t_place += t2 - t1
+            res_sum += r["resident"]
+        for k in tot:
+            tot[k] += r[k]
+    m.synchronize()
+    upd = m.stats()["updated"]
+    nv = len(p.volumes())
+    # the endpoint histogram alone (2 kernels + the copy of c(l) to the host)
+    for _ in range(3):
+        p.histogram(dd[-1], wl.cam, wl.poses[n - 1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        p.histogram(dd[-1], wl.cam, wl.poses[n - 1])
+    hist_ms = (time.perf_counter() - t0) * 1e3 / 20
+    p.close()
+    m.close()
+    torch.cuda.empty_cache()
+    return {"workload": "6x5x3 m room, 40 objects, 640x480; 512^3 volumes of 0.75 m (1.46 mm), "
+                        "at most 16 resident, hysteresis 1.5",
+            "frames": n, "ms_per_frame_integrate_raycast": t_frame * 1e3 / (n - 1),
+            "ms_per_frame_placement": t_place * 1e3 / (n - 1), "ms_histogram": hist_ms,
+            "mean_resident": res_sum / (n - 1), "volumes_placed": nv,
+            "voxel_updates_per_s": upd / (t_frame + 1e-12), **tot}
+
+
 def main_reference(args, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
     if rank != 0:
@@ -598,6 +660,7 @@ def main():
     if not args.no_extra:
         uneven_frames = _gen(_render_uneven, range(args.warmup + extra_steps), procs)
         tile_frames = _gen(_render_tiles, range(100), procs)
+        placement_frames = _gen(_render_placement, range(PLACEMENT_FRAMES), procs)
 
     import torch
     torch.cuda.set_device(local_rank)
@@ -694,6 +757,7 @@ def main():
         line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
         line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
         line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
+        line["placement"] = bench_placement(torch, Mapper, Config, placement_frames)
         m = None
 
     if m is not None:

@@ -391,6 +391,83 @@ mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_config *cfg, 
                                const uint8_t *rgb, const mv_intrinsics *K, const double T_c2w[16],
                                void *stream);
 
+/* The configuration the context was created with. */
+mv_status mv_get_config(const mv_ctx *ctx, mv_config *out);
+
+/* The CUDA device of the context (-1 for NULL). */
+int32_t mv_get_device(const mv_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Dynamic volume placement (Sec. Dynamic Mapping for SLAM; Sec. Insertion and
+ * Removal).  Space is cut into a lattice of cubic cells of cell_voxels voxels
+ * (the paper's d_v - 2); the volume of cell k = (kx, ky, kz) has lattice
+ * offset h_t = k * cell_voxels and volume_voxels voxels per axis (d_v), so
+ * that the volumes of neighbouring cells share two voxel planes.  Each frame
+ * the endpoint e = T (D K^-1 [x, y, 1]^T) of every pixel whose depth D is
+ * valid (> 0, inside the context's [z_min, z_max]) is binned into its cell
+ * l = floor(e / (cell_voxels * voxel_size)), in double precision with a fixed
+ * operation order: xn = (x - cx) / fx, yn = (y - cy) / fy, p = (D xn, D yn, D),
+ * e_a = ((R_a0 p_0 + R_a1 p_1) + R_a2 p_2) + t_a.  c(l) is the number of
+ * endpoints in cell l.
+ *
+ * Policy of one update (after the frame's raycast, as the paper orders it):
+ * cells that are not resident and have at least min_count endpoints are taken
+ * by decreasing count (ties by increasing z, then y, then x).  While fewer
+ * than max_volumes placed volumes are resident, each enters.  Then each
+ * remaining one enters only by displacing the resident cell of lowest count
+ * (ties: increasing z, y, x), and only when its count is larger than that
+ * count times `hysteresis`; the first that is not stops the step.  A cell
+ * enters by creating its volume (mv_add_volume) or, if it had one before, by
+ * mv_swap_in; a displaced cell leaves by mv_swap_out (its volume keeps its
+ * data in pinned host memory).  Placed volumes are ordinary volumes of the
+ * context: every integrate / raycast / frame call sees the resident ones.
+ * The placer does not own them; destroying it leaves them in the context.
+ * ------------------------------------------------------------------------- */
+typedef struct mv_placer mv_placer;
+
+typedef struct {
+    int32_t cell_voxels;   /* lattice spacing in voxels, >= 1 */
+    int32_t volume_voxels; /* voxels per axis of a placed volume, cell_voxels..8192 */
+    float voxel_size;      /* metres, > 0 */
+    int32_t fmt;           /* mv_tsdf_fmt of placed volumes */
+    int32_t max_volumes;   /* resident placed volumes at most, >= 1 */
+    float hysteresis;      /* displacement factor, >= 1 */
+    int32_t min_count;     /* fewest endpoints for a cell to be placed, >= 1 */
+} mv_placement_config;
+
+typedef struct {
+    int32_t cells;    /* distinct cells with endpoints in this frame */
+    int32_t added;    /* volumes created */
+    int32_t restored; /* volumes swapped back in */
+    int32_t evicted;  /* volumes swapped out */
+    int32_t resident; /* placed volumes resident after the step */
+} mv_placement_result;
+
+/* MV_ERR_ARG for a NULL argument or a configuration outside the ranges above. */
+mv_status mv_placer_create(mv_ctx *ctx, const mv_placement_config *cfg, mv_placer **out);
+mv_status mv_placer_destroy(mv_placer *placer);
+const char *mv_placer_last_error(const mv_placer *placer);
+
+/* c(l) of one frame: writes min(n, cap) cells (3 int32 each, x y z) and
+ * counts, sorted by increasing z, then y, then x, and the number of distinct
+ * cells into *n.  depth is a device float32 [height*width] array.  Blocks
+ * until the result is on the host.  MV_ERR_CAPACITY when n > cap (the first
+ * cap are written) or when a cell coordinate is beyond +-2^20. */
+mv_status mv_placer_histogram(mv_placer *placer, const float *depth, const mv_intrinsics *K,
+                              const double T_c2w[16], int32_t *cells, uint32_t *counts, int32_t cap,
+                              int32_t *n, void *stream);
+
+/* One insertion / removal step on this frame's depth (policy above).  The
+ * swaps are asynchronous (side stream, ordered after `stream`); out may be
+ * NULL.  Errors of the add / swap calls are passed on. */
+mv_status mv_placer_update(mv_placer *placer, const float *depth, const mv_intrinsics *K,
+                           const double T_c2w[16], mv_placement_result *out, void *stream);
+
+/* Placed volumes by increasing id: ids, their cells (3 int32 each) and
+ * residency (1 or 0); min(n, cap) entries written, the total into *n. */
+mv_status mv_placer_list(mv_placer *placer, int32_t *ids, int32_t *cells, int32_t *resident, int32_t cap,
+                         int32_t *n);
+
 /* Wait until all work of the context (all streams it used) has finished. */
 mv_status mv_synchronize(mv_ctx *ctx);
 

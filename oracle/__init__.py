@@ -86,6 +86,8 @@ def _load():
         _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
                                           dp, C.POINTER(_Cfg), dp, dp, dp, dp, dp, dp,
                                           C.POINTER(C.POINTER(C.c_double)), u8p]
+        _lib.orc_endpoint_cells.argtypes = [fp, C.POINTER(_Intr), dp, C.c_double, C.c_double, C.c_double,
+                                            i64p, u8p]
     return _lib
 
 
@@ -298,3 +300,81 @@ def se3_exp(xi):
     E = np.eye(4)
     E[:3, :3], E[:3, 3] = Rm, V @ rho
     return E
+
+
+# ---------------------------------------------------------------------------
+# Dynamic placement (Sec. Dynamic Mapping for SLAM)
+# ---------------------------------------------------------------------------
+def endpoint_cells(depth, cam, T, cell_m, z_min=0.0, z_max=np.inf, f32_intrinsics=True):
+    """Per pixel: the lattice cell (int64 x, y, z) of the ray endpoint
+    e = T (D K^-1 [x, y, 1]^T), and whether the depth is valid.  With
+    f32_intrinsics the intrinsics are first rounded to float32, the precision
+    in which the library receives them."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, np.float32)
+    H, W = depth.shape
+    k = [float(np.float32(v)) if f32_intrinsics else float(v) for v in (cam.fx, cam.fy, cam.cx, cam.cy)]
+    K = _Intr(k[0], k[1], k[2], k[3], int(cam.width), int(cam.height))
+    Tm = _pose(T)
+    cells = np.zeros((H, W, 3), np.int64)
+    valid = np.zeros((H, W), np.uint8)
+    lib.orc_endpoint_cells(_ptr(depth, C.c_float), C.byref(K), _ptr(Tm, C.c_double), float(z_min),
+                           float(z_max), float(cell_m), _ptr(cells, C.c_int64), _ptr(valid, C.c_uint8))
+    return cells, valid.astype(bool)
+
+
+def endpoint_histogram(depth, cam, T, cell_m, z_min=0.0, z_max=np.inf):
+    """c(l): the number of valid pixels whose endpoint falls in cell l, as a
+    dict {(x, y, z): count}."""
+    cells, valid = endpoint_cells(depth, cam, T, cell_m, z_min, z_max)
+    keys, counts = np.unique(cells[valid], axis=0, return_counts=True)
+    return {tuple(int(v) for v in k): int(c) for k, c in zip(keys, counts)}
+
+
+@dataclass
+class PlacementState:
+    """Placed volumes by lattice cell: resident ones, and those moved out."""
+    resident: set = field(default_factory=set)
+    evicted: set = field(default_factory=set)
+
+
+def place(state: PlacementState, hist: dict, max_volumes: int, hysteresis: float, min_count: int = 1):
+    """One insertion/removal step (Sec. Insertion and Removal, Sec. Dynamic
+    Mapping for SLAM): keep the cells with the largest counts c(l), at most
+    max_volumes resident; a cell that is not resident enters while a slot is
+    free, otherwise only by displacing the resident cell with the lowest count
+    when its own count exceeds that count times `hysteresis`.  Candidates are
+    taken by decreasing count, ties by increasing (z, y, x); the displaced cell
+    is the resident one with the lowest count, ties by increasing (z, y, x).
+    Returns (added, restored, evicted) lists of cells and updates `state`."""
+    def order(cell):
+        return (cell[2], cell[1], cell[0])
+
+    count = lambda cell: hist.get(cell, 0)
+    cands = [c for c in hist if hist[c] >= min_count and c not in state.resident]
+    cands.sort(key=lambda c: (-hist[c],) + order(c))
+    added, restored, evicted = [], [], []
+
+    def enter(cell):
+        if cell in state.evicted:
+            state.evicted.discard(cell)
+            restored.append(cell)
+        else:
+            added.append(cell)
+        state.resident.add(cell)
+
+    i = 0
+    while i < len(cands) and len(state.resident) < max_volumes:
+        enter(cands[i])
+        i += 1
+    for cell in cands[i:]:
+        if not state.resident:
+            break
+        low = min(state.resident, key=lambda c: (count(c),) + order(c))
+        if not count(cell) > hysteresis * count(low):
+            break
+        state.resident.discard(low)
+        state.evicted.add(low)
+        evicted.append(low)
+        enter(cell)
+    return added, restored, evicted

@@ -660,3 +660,37 @@ ORC_EXPORT void orc_raycast_grad(const orc_volume *vols, const int32_t *ids, int
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Placement lattice (Sec. Dynamic Mapping for SLAM).  For every pixel (x, y)
+ * with a valid depth D the ray endpoint is e = T (D K^-1 [x, y, 1]^T) in
+ * world metres: with xn = (x - cx) / fx and yn = (y - cy) / fy the camera
+ * point is (D xn, D yn, D) and e_a = R_a0 (D xn) + R_a1 (D yn) + R_a2 D + t_a,
+ * summed left to right.  Its lattice cell is l_a = floor(e_a / cell_m), with
+ * cell_m = (d_v - 2) * pitch, the spacing of the volume origins
+ * h_t = k (d_v - 2).  (The paper's printed endpoint formula is garbled; this
+ * is the back-projection it describes.)  valid[p] = 0 where the depth is
+ * not valid (not > 0, or outside [z_min, z_max]); cells then are 0.
+ * ------------------------------------------------------------------------ */
+ORC_EXPORT void orc_endpoint_cells(const float *depth, const orc_intrinsics *K, const double T[16],
+                                   double z_min, double z_max, double cell_m, int64_t *cells,
+                                   uint8_t *valid)
+{
+    const int W = K->width, H = K->height;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            const double D = (double)depth[p];
+            cells[3 * p] = cells[3 * p + 1] = cells[3 * p + 2] = 0;
+            valid[p] = 0;
+            if (!(D > 0.0) || D < z_min || D > z_max) continue;
+            const double xn = ((double)x - K->cx) / K->fx;
+            const double yn = ((double)y - K->cy) / K->fy;
+            const double pc[3] = {D * xn, D * yn, D};
+            for (int a = 0; a < 3; ++a) {
+                const double e = T[4 * a] * pc[0] + T[4 * a + 1] * pc[1] + T[4 * a + 2] * pc[2] + T[4 * a + 3];
+                cells[3 * p + a] = (int64_t)floor(e / cell_m);
+            }
+            valid[p] = 1;
+        }
+}

@@ -12,7 +12,7 @@ of ``include/mvtsdf.h`` (``libmvtsdf.so``, built in-tree by
 """
 from . import synth  # noqa: F401
 
-_LAZY = {"Mapper", "Config", "MVError", "decode", "encode", "intrinsics"}
+_LAZY = {"Mapper", "Placer", "Config", "MVError", "decode", "encode", "intrinsics"}
 
 
 def __getattr__(name):

@@ -75,6 +75,17 @@ class mv_volume_view(C.Structure):
                 ("brick_flags", C.c_void_p)]
 
 
+class mv_placement_config(C.Structure):
+    _fields_ = [("cell_voxels", C.c_int32), ("volume_voxels", C.c_int32), ("voxel_size", C.c_float),
+                ("fmt", C.c_int32), ("max_volumes", C.c_int32), ("hysteresis", C.c_float),
+                ("min_count", C.c_int32)]
+
+
+class mv_placement_result(C.Structure):
+    _fields_ = [("cells", C.c_int32), ("added", C.c_int32), ("restored", C.c_int32),
+                ("evicted", C.c_int32), ("resident", C.c_int32)]
+
+
 _P = C.c_void_p
 _D16 = C.POINTER(C.c_double)
 _SIGNATURES = {
@@ -111,6 +122,17 @@ _SIGNATURES = {
     "mv_synchronize": ([_P], C.c_int),
     "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
                               C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
+    "mv_get_config": ([_P, C.POINTER(mv_config)], C.c_int),
+    "mv_get_device": ([_P], C.c_int32),
+    "mv_placer_create": ([_P, C.POINTER(mv_placement_config), C.POINTER(_P)], C.c_int),
+    "mv_placer_destroy": ([_P], C.c_int),
+    "mv_placer_last_error": ([_P], C.c_char_p),
+    "mv_placer_histogram": ([_P, _P, C.POINTER(mv_intrinsics), _D16, C.POINTER(C.c_int32),
+                             C.POINTER(C.c_uint32), C.c_int32, C.POINTER(C.c_int32), _P], C.c_int),
+    "mv_placer_update": ([_P, _P, C.POINTER(mv_intrinsics), _D16, C.POINTER(mv_placement_result), _P],
+                         C.c_int),
+    "mv_placer_list": ([_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32,
+                        C.POINTER(C.c_int32)], C.c_int),
 }
 
 _lib = None

@@ -577,6 +577,18 @@ mv_status mv_destroy(mv_ctx *c)
     return MV_OK;
 }
 
+mv_status mv_get_config(const mv_ctx *c, mv_config *out)
+{
+    if (!c || !out) return MV_ERR_ARG;
+    *out = c->cfg;
+    return MV_OK;
+}
+
+int32_t mv_get_device(const mv_ctx *c)
+{
+    return c ? c->device : -1;
+}
+
 const char *mv_last_error(const mv_ctx *c)
 {
     if (!c) return "null context";

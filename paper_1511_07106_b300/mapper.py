@@ -353,3 +353,80 @@ class Mapper:
 
     def synchronize(self):
         self._check(self._lib.mv_synchronize(self._h))
+
+
+class Placer:
+    """Dynamic volume placement on a Mapper (the paper's top-n cells of ray
+    endpoints, with hysteresis): see mv_placer_* in include/mvtsdf.h."""
+
+    def __init__(self, mapper: Mapper, cell_voxels: int, volume_voxels: int, voxel_size: float,
+                 max_volumes: int, hysteresis: float = 1.5, min_count: int = 1, fmt="f32"):
+        self._lib = mapper._lib
+        self.mapper = mapper
+        f = _abi.FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        cfg = _abi.mv_placement_config(int(cell_voxels), int(volume_voxels), float(voxel_size), f,
+                                       int(max_volumes), float(hysteresis), int(min_count))
+        h = C.c_void_p()
+        st = self._lib.mv_placer_create(mapper._h, C.byref(cfg), C.byref(h))
+        if st != _abi.MV_OK:
+            raise MVError(st, "mv_placer_create failed")
+        self._h = h
+        self.cell_voxels = int(cell_voxels)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mv_placer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != _abi.MV_OK:
+            msg = self._lib.mv_placer_last_error(self._h)
+            raise MVError(st, msg.decode() if msg else "")
+
+    def histogram(self, depth, cam, T, cap=None, stream=None) -> dict:
+        """c(l) of one frame as {(x, y, z): count}."""
+        import torch
+        n = cam.width * cam.height
+        cap = n if cap is None else int(cap)
+        cells = np.zeros((max(cap, 1), 3), np.int32)
+        counts = np.zeros(max(cap, 1), np.uint32)
+        m = C.c_int32(0)
+        K = intrinsics(cam)
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_placer_histogram(
+            self._h, _dptr(depth, torch.float32, n, "depth"), C.byref(K), Tp,
+            cells.ctypes.data_as(C.POINTER(C.c_int32)), counts.ctypes.data_as(C.POINTER(C.c_uint32)),
+            cap, C.byref(m), _stream(stream)))
+        del keep
+        return {tuple(int(v) for v in cells[i]): int(counts[i]) for i in range(m.value)}
+
+    def update(self, depth, cam, T, stream=None) -> dict:
+        """One insertion / removal step on this frame's depth."""
+        import torch
+        n = cam.width * cam.height
+        r = _abi.mv_placement_result()
+        K = intrinsics(cam)
+        _, Tp = keep = _pose(T)
+        self._check(self._lib.mv_placer_update(self._h, _dptr(depth, torch.float32, n, "depth"), C.byref(K),
+                                               Tp, C.byref(r), _stream(stream)))
+        del keep
+        return {k: getattr(r, k) for k, _ in _abi.mv_placement_result._fields_}
+
+    def volumes(self) -> list:
+        """[(id, (x, y, z) cell, resident)] by increasing id."""
+        m = C.c_int32(0)
+        self._check(self._lib.mv_placer_list(self._h, None, None, None, 0, C.byref(m)))
+        n = max(m.value, 1)
+        ids = np.zeros(n, np.int32)
+        cells = np.zeros((n, 3), np.int32)
+        res = np.zeros(n, np.int32)
+        self._check(self._lib.mv_placer_list(self._h, ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             cells.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             res.ctypes.data_as(C.POINTER(C.c_int32)), n, C.byref(m)))
+        return [(int(ids[i]), tuple(int(v) for v in cells[i]), bool(res[i])) for i in range(m.value)]

@@ -464,3 +464,34 @@ def uneven_volumes(n_volumes: int = 64, frames: int = 300, seed: int = 4, width:
     poses = handheld_trajectory(frames, seed, (0.0, 0.0, 1.5), (0.6, 0.6, 0.2), 3.0, 1.2)
     return Workload(f"{n_volumes} uneven volumes (edges {edges[0]}-{edges[-1]}, {pitch_mm[0]:g}-"
                     f"{pitch_mm[1]:g} mm), {width}x{height}", cam, scene, poses, vols, seed)
+
+
+@dataclass
+class PlacementWorkload:
+    """Frames of a scene to be mapped by dynamically placed volumes: volumes
+    of volume_voxels^3 at voxel_size on the lattice h_t = k cell_voxels
+    (cell_voxels = volume_voxels - 2)."""
+    wl: Workload
+    volume_voxels: int
+    voxel_size: float
+    max_volumes: int
+
+    @property
+    def cell_voxels(self) -> int:
+        return self.volume_voxels - 2
+
+
+def placement_room(frames: int = 1000, seed: int = 3, width: int = 640, height: int = 480,
+                   volume_voxels: int = 512, side_m: float = 0.75, max_volumes: int = 16) -> PlacementWorkload:
+    """Multi-volume dynamic placement: a 6 x 5 x 3 m room with 40 random boxes
+    and spheres, a handheld path through it (640x480), volumes of
+    volume_voxels^3 over side_m metres (1.46 mm voxels at 512 over 0.75 m),
+    at most max_volumes resident."""
+    rng = np.random.Generator(np.random.Philox(key=(seed << 32) | 0xABC))
+    lo, hi = (-3.0, -2.5, 0.0), (3.0, 2.5, 3.0)
+    scene = _room_scene(rng, lo, hi, 24, 16, (0.0, 0.0), 0.8)
+    f = 525.0 * width / 640.0
+    cam = Camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
+    poses = handheld_trajectory(frames, seed, (0.0, 0.0, 1.4), (1.2, 1.0, 0.2), 2.0, 1.0)
+    wl = Workload(f"6x5x3 m room, 40 objects, {width}x{height}", cam, scene, poses, [], seed)
+    return PlacementWorkload(wl, volume_voxels, _f32(side_m / volume_voxels), max_volumes)
