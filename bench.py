@@ -586,6 +586,46 @@ def bench_placement(torch, Mapper, Config, frames):
             "voxel_updates_per_s": upd / (t_frame + 1e-12), **tot}
 
 
+def bench_resolution(torch, Mapper, Config, frames, n_frames=30):
+    """The paper's resolution comparison (Table 1: vertices of one KinectFusion
+    volume vs 8 subvolumes over the same region) on the synthetic room: one
+    512^3 volume over the 3 m cube vs 2 x 2 x 2 tiles of 512^3 (2.93 mm) over
+    the same cube, the same frames integrated into both; surface points
+    counted by mv_extract_points.  Also the extraction time of the 512^3
+    volume."""
+    out = {"workload": f"3 m room, {n_frames} frames at 640x480: one 512^3 volume (5.86 mm) vs "
+                       "8 tiles of 512^3 (2.93 mm)", "paper_vertex_gain_8_volumes": 4.75}
+    dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_frames]])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames[:n_frames]])).cuda()
+    for name, wl in (("single_512", synth.room_512(frames=N_FRAMES_MAX)),
+                     ("tiles_8x512", synth.tiled(synth.room_512(frames=N_FRAMES_MAX, res=1022), split=2))):
+        m = Mapper(Config())
+        ids = [m.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+        for k in range(n_frames):
+            m.integrate(dd[k], dc[k], wl.cam, wl.poses[k])
+        m.synchronize()
+        n = 0
+        for vid in ids:
+            n += int(m.extract_points(vid, rgb=False, edges=False)["xyz"].shape[0])
+        out[name + "_points"] = n
+        if name == "single_512":
+            g = m.extract_points(ids[0])
+            cap = int(g["xyz"].shape[0])
+            for _ in range(3):
+                m.extract_points(ids[0], cap=cap)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(10):
+                m.extract_points(ids[0], cap=cap)
+            ms = (time.perf_counter() - t0) * 1e3 / 10
+            out["extract_ms_512"] = ms
+            out["extract_mpoints_per_s"] = cap / (ms * 1e-3) / 1e6
+        m.close()
+        torch.cuda.empty_cache()
+    out["vertex_gain"] = out["tiles_8x512_points"] / max(out["single_512_points"], 1)
+    return out
+
+
 def main_reference(args, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
     if rank != 0:
@@ -758,6 +798,7 @@ def main():
         line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
         line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
         line["placement"] = bench_placement(torch, Mapper, Config, placement_frames)
+        line["resolution"] = bench_resolution(torch, Mapper, Config, frames)
         m = None
 
     if m is not None:

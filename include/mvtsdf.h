@@ -127,7 +127,8 @@ enum {
     MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
     MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 7 kernels are also counted by kind) */
     MV_KERNEL_DEPTH_MAX = 8,   /* farthest accepted depth of the frame (far bound of the brick list) */
-    MV_KERNEL_KINDS = 9
+    MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
+    MV_KERNEL_KINDS = 10
 };
 
 typedef struct {
@@ -390,6 +391,24 @@ typedef struct {
 mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_config *cfg, const float *depth,
                                const uint8_t *rgb, const mv_intrinsics *K, const double T_c2w[16],
                                void *stream);
+
+/* Surface points of one resident volume: the point cloud that stands for a
+ * volume once it leaves the map (Sec. Insertion and Removal); their number is
+ * the paper's resolution measure (Table 1, vertices).  One point per edge
+ * between 6-neighbour voxels i and i + e_a (a = x, y, z; both inside the
+ * volume) that are both observed (W > 0) and on different sides of the
+ * surface, (F_i > 0) != (F_{i+e_a} > 0): the zero of the linear
+ * interpolation, p = (h_t + i + t e_a) * voxel_size, t = F_i / (F_i - F_{i+e_a}).
+ * Its colour is the linear interpolation of the two voxels' RGB at t, rounded
+ * half up; its edge id is 3 * (z * h_r[1] + y) * h_r[0] + 3 * x + a for
+ * i = (x, y, z).  Outputs are device arrays for cap points, each may be
+ * NULL: xyz float32 [3 cap], rgb uint8 [3 cap], edge uint64 [cap].  Points come
+ * in no particular order; volumes that share voxel planes each report the
+ * points of their own edges.  *n receives the number of points (min(n, cap)
+ * written).  Blocks until done.  MV_ERR_CAPACITY when n > cap;
+ * MV_ERR_NOT_RESIDENT for a swapped-out volume. */
+mv_status mv_extract_points(mv_ctx *ctx, int32_t id, float *xyz, uint8_t *rgb, uint64_t *edge, uint64_t cap,
+                            uint64_t *n, void *stream);
 
 /* The configuration the context was created with. */
 mv_status mv_get_config(const mv_ctx *ctx, mv_config *out);

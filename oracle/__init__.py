@@ -88,6 +88,8 @@ def _load():
                                           C.POINTER(C.POINTER(C.c_double)), u8p]
         _lib.orc_endpoint_cells.argtypes = [fp, C.POINTER(_Intr), dp, C.c_double, C.c_double, C.c_double,
                                             i64p, u8p]
+        _lib.orc_extract_points.argtypes = [C.POINTER(_Volume), dp, u8p, i64p, C.c_int64]
+        _lib.orc_extract_points.restype = C.c_int64
     return _lib
 
 
@@ -378,3 +380,19 @@ def place(state: PlacementState, hist: dict, max_volumes: int, hysteresis: float
         evicted.append(low)
         enter(cell)
     return added, restored, evicted
+
+
+# ---------------------------------------------------------------------------
+# Surface points (Sec. Insertion and Removal; Table 1 vertex counts)
+# ---------------------------------------------------------------------------
+def extract_points(vol: "Volume") -> dict:
+    """Zero crossings of the TSDF along voxel edges: {"xyz" (n, 3) float64,
+    "rgb" (n, 3) uint8, "edge" (n,) int64}, by increasing edge id."""
+    lib = _load()
+    cv = vol._c()
+    n = lib.orc_extract_points(C.byref(cv), None, None, None, 0)
+    xyz = np.zeros((max(n, 1), 3), np.float64)
+    rgb = np.zeros((max(n, 1), 3), np.uint8)
+    edge = np.zeros(max(n, 1), np.int64)
+    lib.orc_extract_points(C.byref(cv), _ptr(xyz, C.c_double), _ptr(rgb, C.c_uint8), _ptr(edge, C.c_int64), n)
+    return {"xyz": xyz[:n], "rgb": rgb[:n], "edge": edge[:n]}

@@ -694,3 +694,51 @@ ORC_EXPORT void orc_endpoint_cells(const float *depth, const orc_intrinsics *K, 
             valid[p] = 1;
         }
 }
+
+/* ------------------------------------------------------------------------
+ * Surface points of a volume (Sec. Insertion and Removal: a volume leaves the
+ * map as a point cloud; Table 1 counts such points).  For every voxel i and
+ * axis a with i + e_a inside the volume, both observed (W > 0) and on
+ * different sides of the surface, (F_i > 0) != (F_{i+e_a} > 0): one point at
+ * the zero of the linear interpolation along the edge, t = F_i / (F_i -
+ * F_{i+e_a}), p = (h + i + t e_a) s, coloured c_i + t (c_{i+e_a} - c_i) per
+ * channel, rounded half up.  Points come by increasing edge id
+ * 3 * lin(i) + a (lin: x fastest).  Returns the number of points; writes at
+ * most cap of them (any output may be NULL).
+ * ------------------------------------------------------------------------ */
+ORC_EXPORT int64_t orc_extract_points(const orc_volume *v, double *xyz, uint8_t *rgb, int64_t *edge,
+                                      int64_t cap)
+{
+    const int64_t rx = v->r[0], ry = v->r[1], rz = v->r[2];
+    int64_t n = 0;
+    for (int64_t z = 0; z < rz; ++z)
+        for (int64_t y = 0; y < ry; ++y)
+            for (int64_t x = 0; x < rx; ++x) {
+                const int64_t i = (z * ry + y) * rx + x;
+                if (!(v->W[i] > 0.0)) continue;
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t q[3] = {x + (a == 0), y + (a == 1), z + (a == 2)};
+                    if (q[0] >= rx || q[1] >= ry || q[2] >= rz) continue;
+                    const int64_t j = (q[2] * ry + q[1]) * rx + q[0];
+                    if (!(v->W[j] > 0.0)) continue;
+                    if ((v->F[i] > 0.0) == (v->F[j] > 0.0)) continue;
+                    const double t = v->F[i] / (v->F[i] - v->F[j]);
+                    if (n < cap) {
+                        const int64_t p[3] = {x, y, z};
+                        if (xyz)
+                            for (int b = 0; b < 3; ++b)
+                                xyz[3 * n + b] = ((double)(v->h[b] + p[b]) + (b == a ? t : 0.0)) * v->s;
+                        if (rgb)
+                            for (int ch = 0; ch < 3; ++ch) {
+                                const double c0 = v->rgba ? v->rgba[4 * i + ch] : 0.0;
+                                const double c1 = v->rgba ? v->rgba[4 * j + ch] : 0.0;
+                                const double cv = floor(c0 + t * (c1 - c0) + 0.5);
+                                rgb[3 * n + ch] = (uint8_t)(cv > 255.0 ? 255.0 : cv);
+                            }
+                        if (edge) edge[n] = 3 * i + a;
+                    }
+                    ++n;
+                }
+            }
+    return n;
+}

@@ -48,9 +48,10 @@ class mv_stats(C.Structure):
                 ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64)]
 
 
-MV_KERNEL_KINDS = 9
+MV_KERNEL_KINDS = 10
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
-                5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max"}
+                5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max",
+                9: "extract"}
 
 
 class mv_timings(C.Structure):
@@ -123,6 +124,7 @@ _SIGNATURES = {
     "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
                               C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_get_config": ([_P, C.POINTER(mv_config)], C.c_int),
+    "mv_extract_points": ([_P, C.c_int32, _P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64), _P], C.c_int),
     "mv_get_device": ([_P], C.c_int32),
     "mv_placer_create": ([_P, C.POINTER(mv_placement_config), C.POINTER(_P)], C.c_int),
     "mv_placer_destroy": ([_P], C.c_int),

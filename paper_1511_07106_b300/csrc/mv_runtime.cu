@@ -54,6 +54,8 @@ struct BackwardArgs {
     float *grad_pose;
 };
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
+cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long long *, unsigned long long,
+                           unsigned long long *, int, cudaStream_t);
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
                             unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *);
@@ -121,6 +123,7 @@ struct mv_ctx {
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
+    unsigned long long *d_points = nullptr;  // point count of mv_extract_points
     // full-cover streaming (mv_frame_streamed): device staging slots that the
     // swapped-out volumes pass through, one copy stream per direction
     struct Slots {
@@ -562,6 +565,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_counter) cudaFree(c->d_counter);
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_vis) cudaFree(c->d_vis);
+    if (c->d_points) cudaFree(c->d_points);
     if (c->d_grad_ptrs) cudaFree(c->d_grad_ptrs);
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
@@ -575,6 +579,33 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->swap_stream) cudaStreamDestroy(c->swap_stream);
     delete c;
     return MV_OK;
+}
+
+mv_status mv_extract_points(mv_ctx *c, int32_t id, float *xyz, uint8_t *rgb, uint64_t *edge, uint64_t cap,
+                            uint64_t *n, void *stream)
+{
+    if (!c || !n) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    if (!v->resident) return fail(c, MV_ERR_NOT_RESIDENT, "volume is swapped out");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = begin_call(c, s, id);
+    if (st) return st;
+    if (!c->d_points) MV_CUDA(c, cudaMalloc((void **)&c->d_points, sizeof(unsigned long long)));
+    MV_CUDA(c, cudaMemsetAsync(c->d_points, 0, sizeof(unsigned long long), s));
+    const VolDev d = make_voldev(*v);
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_EXTRACT, s, [&] {
+        return launch_extract(d, xyz, rgb, reinterpret_cast<unsigned long long *>(edge), cap, c->d_points,
+                              c->num_sms, s); }));
+    unsigned long long count = 0;
+    MV_CUDA(c, cudaMemcpyAsync(&count, c->d_points, sizeof(count), cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaStreamSynchronize(s));
+    *n = count;
+    st = end_call(c, s);
+    if (st) return st;
+    return count > cap ? fail(c, MV_ERR_CAPACITY, "more points than cap") : MV_OK;
 }
 
 mv_status mv_get_config(const mv_ctx *c, mv_config *out)

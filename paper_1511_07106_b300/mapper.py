@@ -237,6 +237,34 @@ class Mapper:
         del keep
         return out
 
+    def extract_points(self, vid, cap=None, rgb=True, edges=True, stream=None) -> dict:
+        """Surface points of a resident volume: {"xyz": (n, 3) float32,
+        "rgb": (n, 3) uint8, "edge": (n,) int64} as CUDA tensors (unordered)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if cap is None:  # a first guess; grown to the exact count if too small
+            cap = int(np.prod(self.query(vid)["h_r"])) // 16 + 4096
+        while True:
+            xyz = torch.empty((max(cap, 1), 3), dtype=torch.float32, device=dev)
+            col = torch.empty((max(cap, 1), 3), dtype=torch.uint8, device=dev) if rgb else None
+            edge = torch.empty(max(cap, 1), dtype=torch.int64, device=dev) if edges else None
+            n = C.c_uint64(0)
+            st = self._lib.mv_extract_points(self._h, int(vid), C.c_void_p(xyz.data_ptr()),
+                                             C.c_void_p(col.data_ptr()) if rgb else None,
+                                             C.c_void_p(edge.data_ptr()) if edges else None, int(cap),
+                                             C.byref(n), _stream(stream))
+            if st == _abi.MV_ERR_CAPACITY:
+                cap = int(n.value)
+                continue
+            self._check(st)
+            k = int(n.value)
+            out = {"xyz": xyz[:k]}
+            if rgb:
+                out["rgb"] = col[:k]
+            if edges:
+                out["edge"] = edge[:k]
+            return out
+
     def raycast_volume(self, vid, first, cam, T, out, stream=None) -> dict:
         K = intrinsics(cam)
         _, Tp = keep = _pose(T)
