@@ -626,6 +626,49 @@ def bench_resolution(torch, Mapper, Config, frames, n_frames=30):
     return out
 
 
+def bench_track(torch, Mapper, Config, frames, n_map=20, n_track=10, iterations=10):
+    """Camera tracking against the raycast model (Sec. Depth Map Conversion,
+    Sec. Camera Tracking): the room's 512^3 volume built from the first n_map
+    frames at their true poses; then each next frame is tracked by
+    point-to-plane ICP against the raycast vertex / normal maps of the
+    previous true pose, from that pose."""
+    wl = synth.room_512(frames=N_FRAMES_MAX)
+    (vs,) = wl.volumes
+    m = Mapper(Config())
+    vid = m.add_volume(vs.h, vs.r, vs.s)
+    dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_map + n_track]])).cuda()
+    dc = torch.from_numpy(np.stack([f[1] for f in frames[:n_map + n_track]])).cuda()
+    for k in range(n_map):
+        m.integrate(dd[k], dc[k], wl.cam, wl.poses[k])
+    maps = m.alloc_maps(wl.cam)
+    errs_t, errs_r, ms = [], [], []
+    m.set_timing(True)
+    m.timings(reset=True)
+    for k in range(n_map, n_map + n_track):
+        T_prev = wl.poses[k - 1]
+        m.raycast(wl.cam, T_prev, out=maps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T, last = m.track(dd[k], wl.cam, maps["vertex"], maps["normal"], T_prev, T_prev, iterations=iterations,
+                          dist=0.1, cos_min=0.8)
+        ms.append((time.perf_counter() - t0) * 1e3)
+        T_true = wl.poses[k]
+        errs_t.append(float(np.linalg.norm(T[:3, 3] - T_true[:3, 3])))
+        R = T[:3, :3] @ T_true[:3, :3].T
+        errs_r.append(float(np.degrees(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)))))
+    tm = m.timings()
+    m.set_timing(False)
+    m.close()
+    torch.cuda.empty_cache()
+    icp = tm.get("icp", (0, 0.0, 0))
+    return {"workload": f"room 512^3 after {n_map} frames, {n_track} frames tracked at 640x480, "
+                        f"{iterations} ICP iterations from the previous pose",
+            "ms_per_track": float(np.median(ms)), "icp_kernel_us": icp[1] / max(icp[2], 1) * 1e3,
+            "translation_error_mm_mean": 1e3 * float(np.mean(errs_t)),
+            "translation_error_mm_max": 1e3 * float(np.max(errs_t)),
+            "rotation_error_deg_mean": float(np.mean(errs_r)), "rotation_error_deg_max": float(np.max(errs_r))}
+
+
 def main_reference(args, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
     if rank != 0:
@@ -799,6 +842,7 @@ def main():
         line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
         line["placement"] = bench_placement(torch, Mapper, Config, placement_frames)
         line["resolution"] = bench_resolution(torch, Mapper, Config, frames)
+        line["tracking"] = bench_track(torch, Mapper, Config, frames)
         m = None
 
     if m is not None:

@@ -128,7 +128,9 @@ enum {
     MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 7 kernels are also counted by kind) */
     MV_KERNEL_DEPTH_MAX = 8,   /* farthest accepted depth of the frame (far bound of the brick list) */
     MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
-    MV_KERNEL_KINDS = 10
+    MV_KERNEL_DEPTH_MAPS = 10, /* vertex / normal maps of a depth frame */
+    MV_KERNEL_ICP = 11,        /* one point-to-plane ICP linearisation */
+    MV_KERNEL_KINDS = 12
 };
 
 typedef struct {
@@ -409,6 +411,61 @@ mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_config *cfg, 
  * MV_ERR_NOT_RESIDENT for a swapped-out volume. */
 mv_status mv_extract_points(mv_ctx *ctx, int32_t id, float *xyz, uint8_t *rgb, uint64_t *edge, uint64_t cap,
                             uint64_t *n, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Depth-map conversion and camera tracking (Sec. Depth Map Conversion;
+ * Sec. Camera Tracking, point-to-plane ICP with projective data association
+ * as in KinectFusion).
+ * ------------------------------------------------------------------------- */
+
+/* Vertex and normal maps of a depth frame: v = K^-1 [x, y, 1]^T D(x, y) for
+ * every pixel with a valid depth (> 0, inside the context's [z_min, z_max]),
+ * and n = (v(x+1, y) - v(x, y)) x (v(x, y+1) - v(x, y)), normalised and turned
+ * to face the camera, where the three depths are valid (not in the last
+ * column or row).  With T_c2w both are moved to the world frame (v -> R v + t,
+ * n -> R n); with T_c2w NULL they stay in the camera frame.  Invalid vertices
+ * and normals are 0.  vertex and normal are device float32 [height*width*3].
+ * Asynchronous on `stream`. */
+mv_status mv_depth_to_maps(mv_ctx *ctx, const float *depth, const mv_intrinsics *K, const double T_c2w[16],
+                           float *vertex, float *normal, void *stream);
+
+typedef struct {
+    int32_t iterations; /* Gauss-Newton steps of mv_track, 0..1000 */
+    float dist;         /* association distance threshold, metres, > 0 */
+    float cos_min;      /* association normal threshold: cos of the largest angle, -1..1 */
+} mv_icp_config;
+
+typedef struct {
+    double A[36];    /* sum of J^T J, row-major */
+    double b[6];     /* sum of J^T r */
+    double error;    /* sum of r^2 */
+    int64_t inliers; /* associated pixels */
+} mv_icp_system;
+
+/* One point-to-plane linearisation.  vertex / normal: the current frame's
+ * maps in its camera frame (mv_depth_to_maps with T NULL); model_vertex /
+ * model_normal: world-frame maps of the same size seen from T_model (e.g.
+ * the raycast of the previous frame; a normal of 0 marks a miss).  Each pixel
+ * with a normal is moved by T_est (v_g = R v + t, n_g = R n), projected into
+ * the model camera, and associated with the model vertex V and normal N at
+ * the nearest pixel (floor(u + 1/2)) when |v_g - V| <= dist and
+ * n_g . N >= cos_min.  With r = N . (V - v_g) and J = [N, v_g x N] (the twist
+ * x = (rho, phi) moves v_g to v_g + rho + phi x v_g, so r changes by -J x)
+ * it adds J^T J, J^T r, r^2 and 1.  Per-pixel terms in FP32, sums in FP64 in
+ * a fixed order.  Blocks until the system is on the host. */
+mv_status mv_icp_linearize(mv_ctx *ctx, const float *vertex, const float *normal, const mv_intrinsics *K,
+                           const double T_est[16], const float *model_vertex, const float *model_normal,
+                           const double T_model[16], const mv_icp_config *cfg, mv_icp_system *out,
+                           void *stream);
+
+/* Track one frame: the depth frame's camera-frame maps, then cfg->iterations
+ * Gauss-Newton steps from T_init: solve A x = b (Cholesky, FP64) and set
+ * T <- exp(x^) T.  Stops early when fewer than 6 pixels associate or the
+ * system is not positive definite.  T_out receives the estimate; last (may be
+ * NULL) the system of the last linearisation.  Blocks until done. */
+mv_status mv_track(mv_ctx *ctx, const float *depth, const mv_intrinsics *K, const float *model_vertex,
+                   const float *model_normal, const double T_model[16], const double T_init[16],
+                   const mv_icp_config *cfg, double T_out[16], mv_icp_system *last, void *stream);
 
 /* The configuration the context was created with. */
 mv_status mv_get_config(const mv_ctx *ctx, mv_config *out);

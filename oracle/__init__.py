@@ -90,6 +90,9 @@ def _load():
                                             i64p, u8p]
         _lib.orc_extract_points.argtypes = [C.POINTER(_Volume), dp, u8p, i64p, C.c_int64]
         _lib.orc_extract_points.restype = C.c_int64
+        _lib.orc_depth_maps.argtypes = [fp, C.POINTER(_Intr), dp, C.c_double, C.c_double, dp, dp]
+        _lib.orc_icp_system.argtypes = [dp, dp, C.POINTER(_Intr), dp, fp, fp, dp, C.c_double, C.c_double,
+                                        dp, dp, dp, i64p, u8p, dp, dp, dp]
     return _lib
 
 
@@ -396,3 +399,73 @@ def extract_points(vol: "Volume") -> dict:
     edge = np.zeros(max(n, 1), np.int64)
     lib.orc_extract_points(C.byref(cv), _ptr(xyz, C.c_double), _ptr(rgb, C.c_uint8), _ptr(edge, C.c_int64), n)
     return {"xyz": xyz[:n], "rgb": rgb[:n], "edge": edge[:n]}
+
+
+# ---------------------------------------------------------------------------
+# Depth-map conversion and tracking (Sec. Depth Map Conversion, Sec. Camera
+# Tracking)
+# ---------------------------------------------------------------------------
+def _intr32(cam) -> _Intr:
+    k = [float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy)]
+    return _Intr(k[0], k[1], k[2], k[3], int(cam.width), int(cam.height))
+
+
+def depth_maps(depth, cam, T=None, z_min=0.0, z_max=np.inf):
+    """Vertex and normal maps (H, W, 3) float64 of a depth frame; world frame
+    with T, camera frame without."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, np.float32)
+    H, W = depth.shape
+    v = np.zeros((H, W, 3), np.float64)
+    n = np.zeros((H, W, 3), np.float64)
+    Tm = None if T is None else _pose(T)
+    lib.orc_depth_maps(_ptr(depth, C.c_float), C.byref(_intr32(cam)), _ptr(Tm, C.c_double), float(z_min),
+                       float(z_max), _ptr(v, C.c_double), _ptr(n, C.c_double))
+    return v, n
+
+
+def icp_system(vertex, normal, cam, T_est, model_vertex, model_normal, T_model, dist, cos_min):
+    """One point-to-plane linearisation: dict A (6, 6), b (6,), error, count,
+    flags (H, W) of marginal association decisions and the sums of |term| over
+    them (absA, absb, abse = (sum r^2, count))."""
+    lib = _load()
+    vertex = np.ascontiguousarray(vertex, np.float64)
+    normal = np.ascontiguousarray(normal, np.float64)
+    mv = np.ascontiguousarray(model_vertex, np.float32)
+    mn = np.ascontiguousarray(model_normal, np.float32)
+    H, W = vertex.shape[:2]
+    A = np.zeros(36)
+    b = np.zeros(6)
+    err = C.c_double(0.0)
+    cnt = C.c_int64(0)
+    flags = np.zeros((H, W), np.uint8)
+    absA, absb, abse = np.zeros(36), np.zeros(6), np.zeros(2)
+    Te, Tm = _pose(T_est), _pose(T_model)
+    lib.orc_icp_system(_ptr(vertex, C.c_double), _ptr(normal, C.c_double), C.byref(_intr32(cam)),
+                       _ptr(Te, C.c_double), _ptr(mv, C.c_float), _ptr(mn, C.c_float), _ptr(Tm, C.c_double),
+                       float(dist), float(cos_min), _ptr(A, C.c_double), _ptr(b, C.c_double), C.byref(err),
+                       C.byref(cnt), _ptr(flags, C.c_uint8), _ptr(absA, C.c_double), _ptr(absb, C.c_double),
+                       _ptr(abse, C.c_double))
+    return {"A": A.reshape(6, 6), "b": b, "error": err.value, "count": cnt.value, "flags": flags.astype(bool),
+            "absA": absA.reshape(6, 6), "absb": absb, "abse": abse}
+
+
+def track(depth, cam, model_vertex, model_normal, T_model, T_init, iterations, dist, cos_min,
+          z_min=0.0, z_max=np.inf):
+    """Gauss-Newton point-to-plane ICP: maps of the frame (camera frame), then
+    `iterations` times solve A x = b and set T <- exp(x^) T; stops early below
+    6 associations or when A is not positive definite.  Returns (T, last)."""
+    v, n = depth_maps(depth, cam, None, z_min, z_max)
+    T = np.array(T_init, np.float64).reshape(4, 4).copy()
+    last = None
+    for _ in range(iterations):
+        last = icp_system(v, n, cam, T, model_vertex, model_normal, T_model, dist, cos_min)
+        if last["count"] < 6:
+            break
+        try:
+            L = np.linalg.cholesky(last["A"])
+        except np.linalg.LinAlgError:
+            break
+        x = np.linalg.solve(L.T, np.linalg.solve(L, last["b"]))
+        T = se3_exp(x) @ T
+    return T, last

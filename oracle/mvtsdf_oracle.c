@@ -742,3 +742,139 @@ ORC_EXPORT int64_t orc_extract_points(const orc_volume *v, double *xyz, uint8_t 
             }
     return n;
 }
+
+/* ------------------------------------------------------------------------
+ * Depth-map conversion (Sec. Depth Map Conversion): v = K^-1 [x, y, 1]^T D
+ * for valid depths (> 0, inside [z_min, z_max]); n = (v(x+1, y) - v(x, y)) x
+ * (v(x, y+1) - v(x, y)) where the three depths are valid, normalised and
+ * turned to face the camera (n . v < 0; the paper's cross product of the
+ * two image-axis differences points away from the camera).  With T non-NULL
+ * both go to the world frame (R v + t, R n).  Invalid entries are 0.
+ * ------------------------------------------------------------------------ */
+static int depth_ok(double D, double z_min, double z_max)
+{
+    return D > 0.0 && D >= z_min && D <= z_max;
+}
+
+ORC_EXPORT void orc_depth_maps(const float *depth, const orc_intrinsics *K, const double *T, double z_min,
+                               double z_max, double *vertex, double *normal)
+{
+    const int W = K->width, H = K->height;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            double v[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+            const double D = depth[p];
+            const int ok = depth_ok(D, z_min, z_max);
+            if (ok) {
+                v[0] = (x - K->cx) / K->fx * D;
+                v[1] = (y - K->cy) / K->fy * D;
+                v[2] = D;
+                if (x + 1 < W && y + 1 < H && depth_ok(depth[p + 1], z_min, z_max) &&
+                    depth_ok(depth[p + W], z_min, z_max)) {
+                    const double Dx = depth[p + 1], Dy = depth[p + W];
+                    const double a[3] = {(x + 1 - K->cx) / K->fx * Dx - v[0], (y - K->cy) / K->fy * Dx - v[1],
+                                         Dx - v[2]};
+                    const double b[3] = {(x - K->cx) / K->fx * Dy - v[0], (y + 1 - K->cy) / K->fy * Dy - v[1],
+                                         Dy - v[2]};
+                    double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+                    const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+                    if (len > 0.0) {
+                        const double sg = (c[0] * v[0] + c[1] * v[1] + c[2] * v[2] > 0.0) ? -1.0 : 1.0;
+                        for (int k = 0; k < 3; ++k) n[k] = sg * c[k] / len;
+                    }
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                double vo = v[a], no = n[a];
+                if (T && ok) {
+                    vo = T[4 * a] * v[0] + T[4 * a + 1] * v[1] + T[4 * a + 2] * v[2] + T[4 * a + 3];
+                    no = T[4 * a] * n[0] + T[4 * a + 1] * n[1] + T[4 * a + 2] * n[2];
+                }
+                vertex[3 * p + a] = ok ? vo : 0.0;
+                normal[3 * p + a] = ok ? no : 0.0;
+            }
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * One point-to-plane ICP linearisation with projective data association
+ * (Sec. Camera Tracking, the KinectFusion tracker it cites).  For each pixel
+ * of the current frame with a normal (camera-frame maps v, n): v_g = R v + t,
+ * n_g = R n with T_est = [R | t]; q = T_model^-1 v_g; the nearest model pixel
+ * (floor(fx q_x / q_z + cx + 1/2), same for y) if q_z > 0 and it is inside
+ * the image; the model vertex V and normal N there (|N|^2 > 1/4, i.e. not a
+ * miss); association when |v_g - V|^2 <= dist^2 and n_g . N >= cos_min.
+ * r = N . (V - v_g), J = [N, v_g x N]; sums of J^T J (A, row-major 6x6),
+ * J^T r (b), r^2 and the count.  flags[p] = 1 for pixels whose association
+ * decision lies within a small margin of a threshold (another evaluation in
+ * lower precision may decide differently); absA / absb / abse receive the
+ * sums of |term| over those flagged pixels.
+ * ------------------------------------------------------------------------ */
+ORC_EXPORT void orc_icp_system(const double *vertex, const double *normal, const orc_intrinsics *K,
+                               const double *T_est, const float *mvertex, const float *mnormal,
+                               const double *T_model, double dist, double cos_min, double *A, double *b,
+                               double *err, int64_t *count, uint8_t *flags, double *absA, double *absb,
+                               double *abse)
+{
+    const int W = K->width, H = K->height;
+    const double eps_px = 2e-3, eps_rel = 1e-4, eps_cos = 1e-3;
+    for (int k = 0; k < 36; ++k) A[k] = absA[k] = 0.0;
+    for (int k = 0; k < 6; ++k) b[k] = absb[k] = 0.0;
+    *err = 0.0;
+    abse[0] = abse[1] = 0.0;
+    *count = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            flags[p] = 0;
+            const double *n = normal + 3 * p, *v = vertex + 3 * p;
+            if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) continue;
+            double vg[3], ng[3], d[3], q[3];
+            for (int a = 0; a < 3; ++a) {
+                vg[a] = T_est[4 * a] * v[0] + T_est[4 * a + 1] * v[1] + T_est[4 * a + 2] * v[2] + T_est[4 * a + 3];
+                ng[a] = T_est[4 * a] * n[0] + T_est[4 * a + 1] * n[1] + T_est[4 * a + 2] * n[2];
+            }
+            for (int a = 0; a < 3; ++a) d[a] = vg[a] - T_model[4 * a + 3];
+            for (int a = 0; a < 3; ++a) q[a] = T_model[a] * d[0] + T_model[4 + a] * d[1] + T_model[8 + a] * d[2];
+            if (!(q[2] > 0.0)) continue;
+            const double u = K->fx * q[0] / q[2] + K->cx, w = K->fy * q[1] / q[2] + K->cy;
+            const double fu = u + 0.5 - floor(u + 0.5), fw = w + 0.5 - floor(w + 0.5);
+            int marginal = fu < eps_px || fu > 1.0 - eps_px || fw < eps_px || fw > 1.0 - eps_px;
+            const int64_t ui = (int64_t)floor(u + 0.5), wi = (int64_t)floor(w + 0.5);
+            if (ui < 0 || wi < 0 || ui >= W || wi >= H) {
+                if (marginal) flags[p] = 1;
+                continue;
+            }
+            const size_t m = (size_t)wi * W + ui;
+            const double N[3] = {mnormal[3 * m], mnormal[3 * m + 1], mnormal[3 * m + 2]};
+            if (!(N[0] * N[0] + N[1] * N[1] + N[2] * N[2] > 0.25)) {
+                if (marginal) flags[p] = 1;
+                continue;
+            }
+            const double V[3] = {mvertex[3 * m], mvertex[3 * m + 1], mvertex[3 * m + 2]};
+            const double e[3] = {V[0] - vg[0], V[1] - vg[1], V[2] - vg[2]};
+            const double d2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+            const double cs = ng[0] * N[0] + ng[1] * N[1] + ng[2] * N[2];
+            marginal |= fabs(d2 - dist * dist) < eps_rel * dist * dist || fabs(cs - cos_min) < eps_cos;
+            if (marginal) flags[p] = 1;
+            if (!(d2 <= dist * dist) || !(cs >= cos_min)) continue;
+            const double r = N[0] * e[0] + N[1] * e[1] + N[2] * e[2];
+            const double J[6] = {N[0], N[1], N[2], vg[1] * N[2] - vg[2] * N[1], vg[2] * N[0] - vg[0] * N[2],
+                                 vg[0] * N[1] - vg[1] * N[0]};
+            for (int i = 0; i < 6; ++i) {
+                for (int j = 0; j < 6; ++j) {
+                    A[6 * i + j] += J[i] * J[j];
+                    if (marginal) absA[6 * i + j] += fabs(J[i] * J[j]);
+                }
+                b[i] += J[i] * r;
+                if (marginal) absb[i] += fabs(J[i] * r);
+            }
+            *err += r * r;
+            *count += 1;
+            if (marginal) {
+                abse[0] += r * r;
+                abse[1] += 1.0;
+            }
+        }
+}

@@ -48,10 +48,10 @@ class mv_stats(C.Structure):
                 ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64)]
 
 
-MV_KERNEL_KINDS = 10
+MV_KERNEL_KINDS = 12
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
                 5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max",
-                9: "extract"}
+                9: "extract", 10: "depth_maps", 11: "icp"}
 
 
 class mv_timings(C.Structure):
@@ -85,6 +85,14 @@ class mv_placement_config(C.Structure):
 class mv_placement_result(C.Structure):
     _fields_ = [("cells", C.c_int32), ("added", C.c_int32), ("restored", C.c_int32),
                 ("evicted", C.c_int32), ("resident", C.c_int32)]
+
+
+class mv_icp_config(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("dist", C.c_float), ("cos_min", C.c_float)]
+
+
+class mv_icp_system(C.Structure):
+    _fields_ = [("A", C.c_double * 36), ("b", C.c_double * 6), ("error", C.c_double), ("inliers", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -124,6 +132,11 @@ _SIGNATURES = {
     "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
                               C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_get_config": ([_P, C.POINTER(mv_config)], C.c_int),
+    "mv_depth_to_maps": ([_P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P], C.c_int),
+    "mv_icp_linearize": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _D16, C.POINTER(mv_icp_config),
+                       C.POINTER(mv_icp_system), _P], C.c_int),
+    "mv_track": ([_P, _P, C.POINTER(mv_intrinsics), _P, _P, _D16, _D16, C.POINTER(mv_icp_config), _D16,
+                  C.POINTER(mv_icp_system), _P], C.c_int),
     "mv_extract_points": ([_P, C.c_int32, _P, _P, _P, C.c_uint64, C.POINTER(C.c_uint64), _P], C.c_int),
     "mv_get_device": ([_P], C.c_int32),
     "mv_placer_create": ([_P, C.POINTER(mv_placement_config), C.POINTER(_P)], C.c_int),

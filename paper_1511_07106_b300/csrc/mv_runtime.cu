@@ -56,6 +56,12 @@ struct BackwardArgs {
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
 cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long long *, unsigned long long,
                            unsigned long long *, int, cudaStream_t);
+cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float, const double *, float *, float *,
+                              cudaStream_t);
+cudaError_t launch_icp_system(const float *, const float *, const mv_intrinsics &, const double *, const float *,
+                              const float *, const double *, float, float, double *, int, cudaStream_t);
+int icp_grid(int num_sms);
+constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
                             unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *);
@@ -124,6 +130,10 @@ struct mv_ctx {
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
     unsigned long long *d_points = nullptr;  // point count of mv_extract_points
+    // tracking scratch: the frame's vertex / normal maps, per-CTA ICP partials
+    float *d_trk_v = nullptr, *d_trk_n = nullptr;
+    size_t trk_px = 0;
+    double *d_trk_part = nullptr;
     // full-cover streaming (mv_frame_streamed): device staging slots that the
     // swapped-out volumes pass through, one copy stream per direction
     struct Slots {
@@ -204,6 +214,8 @@ FrameParams make_params(const mv_ctx *c, const mv_intrinsics *K, const double T[
     P.n_bisect = c->cfg.n_bisect;
     return P;
 }
+
+const double kIdentity[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
 
 bool valid_frame(const mv_intrinsics *K, const double *T)
 {
@@ -408,6 +420,87 @@ void free_host(Volume *v)
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// tracking helpers (host, FP64)
+// ---------------------------------------------------------------------------
+namespace {
+
+// T <- exp(x^) T for the twist x = (rho, phi): rotation by Rodrigues,
+// translation V rho.
+void apply_twist(const double x[6], double T[16])
+{
+    const double p0 = x[3], p1 = x[4], p2 = x[5];
+    const double th2 = p0 * p0 + p1 * p1 + p2 * p2, th = std::sqrt(th2);
+    double A, B, Cc;
+    if (th < 1e-9) {
+        A = 1.0 - th2 / 6.0;
+        B = 0.5 - th2 / 24.0;
+        Cc = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        A = std::sin(th) / th;
+        B = (1.0 - std::cos(th)) / th2;
+        Cc = (th - std::sin(th)) / (th2 * th);
+    }
+    const double P[9] = {0, -p2, p1, p2, 0, -p0, -p1, p0, 0};
+    double P2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += P[3 * i + k] * P[3 * k + j];
+            P2[3 * i + j] = acc;
+        }
+    double R[9], V[9];
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        R[i] = I + A * P[i] + B * P2[i];
+        V[i] = I + B * P[i] + Cc * P2[i];
+    }
+    double t[3];
+    for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * x[0] + V[3 * i + 1] * x[1] + V[3 * i + 2] * x[2];
+    double out[16] = {0};
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * T[4 * k + j];
+            out[4 * i + j] = acc + (j == 3 ? t[i] : 0.0);
+        }
+    }
+    out[15] = 1.0;
+    for (int i = 0; i < 16; ++i) T[i] = out[i];
+}
+
+// Solve the symmetric positive definite 6x6 system A x = b (Cholesky);
+// false when a pivot is not positive.
+bool solve6(const double A[36], const double b[6], double x[6])
+{
+    double L[36] = {0};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double acc = A[6 * i + j];
+            for (int k = 0; k < j; ++k) acc -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(acc > 0.0)) return false;
+                L[6 * i + i] = std::sqrt(acc);
+            } else {
+                L[6 * i + j] = acc / L[6 * j + j];
+            }
+        }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double acc = b[i];
+        for (int k = 0; k < i; ++k) acc -= L[6 * i + k] * y[k];
+        y[i] = acc / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double acc = y[i];
+        for (int k = i + 1; k < 6; ++k) acc -= L[6 * k + i] * x[k];
+        x[i] = acc / L[6 * i + i];
+    }
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // full-cover streaming
 // ---------------------------------------------------------------------------
 namespace {
@@ -566,6 +659,9 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_vis) cudaFree(c->d_vis);
     if (c->d_points) cudaFree(c->d_points);
+    if (c->d_trk_v) cudaFree(c->d_trk_v);
+    if (c->d_trk_n) cudaFree(c->d_trk_n);
+    if (c->d_trk_part) cudaFree(c->d_trk_part);
     if (c->d_grad_ptrs) cudaFree(c->d_grad_ptrs);
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
@@ -606,6 +702,111 @@ mv_status mv_extract_points(mv_ctx *c, int32_t id, float *xyz, uint8_t *rgb, uin
     st = end_call(c, s);
     if (st) return st;
     return count > cap ? fail(c, MV_ERR_CAPACITY, "more points than cap") : MV_OK;
+}
+
+static mv_status track_scratch(mv_ctx *c, const mv_intrinsics *K, cudaStream_t s)
+{
+    const size_t px = (size_t)K->width * K->height;
+    if (px > c->trk_px) {
+        if (c->d_trk_v) MV_CUDA(c, cudaFreeAsync(c->d_trk_v, s));
+        if (c->d_trk_n) MV_CUDA(c, cudaFreeAsync(c->d_trk_n, s));
+        c->d_trk_v = c->d_trk_n = nullptr;
+        c->trk_px = 0;
+        MV_CUDA(c, cudaMallocAsync((void **)&c->d_trk_v, 3 * sizeof(float) * px, s));
+        MV_CUDA(c, cudaMallocAsync((void **)&c->d_trk_n, 3 * sizeof(float) * px, s));
+        c->trk_px = px;
+    }
+    if (!c->d_trk_part)
+        MV_CUDA(c, cudaMalloc((void **)&c->d_trk_part, sizeof(double) * kIcpTerms * icp_grid(c->num_sms)));
+    return MV_OK;
+}
+
+// One ICP linearisation on device maps; the partials are added on the host
+// in CTA order (deterministic).
+static mv_status icp_linearise(mv_ctx *c, const float *v, const float *n, const mv_intrinsics *K,
+                               const double T_est[16], const float *mv_, const float *mn, const double T_model[16],
+                               const mv_icp_config *cfg, mv_icp_system *out, cudaStream_t s)
+{
+    const int grid = icp_grid(c->num_sms);
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_ICP, s, [&] {
+        return launch_icp_system(v, n, *K, T_est, mv_, mn, T_model, cfg->dist, cfg->cos_min, c->d_trk_part, grid,
+                                 s); }));
+    std::vector<double> part((size_t)grid * kIcpTerms);
+    MV_CUDA(c, cudaMemcpyAsync(part.data(), c->d_trk_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaStreamSynchronize(s));
+    double sum[kIcpTerms] = {0};
+    for (int g = 0; g < grid; ++g)
+        for (int k = 0; k < kIcpTerms; ++k) sum[k] += part[(size_t)g * kIcpTerms + k];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) out->A[6 * i + j] = out->A[6 * j + i] = sum[k];
+    for (int i = 0; i < 6; ++i) out->b[i] = sum[21 + i];
+    out->error = sum[27];
+    out->inliers = (int64_t)std::llround(sum[28]);
+    return MV_OK;
+}
+
+static bool valid_icp(const mv_icp_config *cfg)
+{
+    return cfg && cfg->iterations >= 0 && cfg->iterations <= 1000 && cfg->dist > 0.f && std::isfinite(cfg->dist) &&
+           cfg->cos_min >= -1.f && cfg->cos_min <= 1.f;
+}
+
+mv_status mv_depth_to_maps(mv_ctx *c, const float *depth, const mv_intrinsics *K, const double T[16],
+                           float *vertex, float *normal, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !vertex || !normal || !valid_frame(K, T ? T : kIdentity))
+        return fail(c, MV_ERR_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAPS, s, [&] {
+        return launch_depth_maps(depth, *K, c->cfg.z_min, c->cfg.z_max, T, vertex, normal, s); }));
+    return MV_OK;
+}
+
+mv_status mv_icp_linearize(mv_ctx *c, const float *vertex, const float *normal, const mv_intrinsics *K,
+                        const double T_est[16], const float *model_vertex, const float *model_normal,
+                        const double T_model[16], const mv_icp_config *cfg, mv_icp_system *out, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!vertex || !normal || !model_vertex || !model_normal || !out || !valid_frame(K, T_est) ||
+        !valid_frame(K, T_model) || !valid_icp(cfg))
+        return fail(c, MV_ERR_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = track_scratch(c, K, s);
+    if (st) return st;
+    return icp_linearise(c, vertex, normal, K, T_est, model_vertex, model_normal, T_model, cfg, out, s);
+}
+
+mv_status mv_track(mv_ctx *c, const float *depth, const mv_intrinsics *K, const float *model_vertex,
+                   const float *model_normal, const double T_model[16], const double T_init[16],
+                   const mv_icp_config *cfg, double T_out[16], mv_icp_system *last, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !model_vertex || !model_normal || !T_out || !valid_frame(K, T_model) ||
+        !valid_frame(K, T_init) || !valid_icp(cfg))
+        return fail(c, MV_ERR_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = track_scratch(c, K, s);
+    if (st) return st;
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAPS, s, [&] {
+        return launch_depth_maps(depth, *K, c->cfg.z_min, c->cfg.z_max, nullptr, c->d_trk_v, c->d_trk_n, s); }));
+    double T[16];
+    for (int i = 0; i < 16; ++i) T[i] = T_init[i];
+    mv_icp_system sys{};
+    for (int it = 0; it < cfg->iterations; ++it) {
+        st = icp_linearise(c, c->d_trk_v, c->d_trk_n, K, T, model_vertex, model_normal, T_model, cfg, &sys, s);
+        if (st) return st;
+        double x[6];
+        if (sys.inliers < 6 || !solve6(sys.A, sys.b, x)) break;
+        apply_twist(x, T);
+    }
+    for (int i = 0; i < 16; ++i) T_out[i] = T[i];
+    if (last) *last = sys;
+    return MV_OK;
 }
 
 mv_status mv_get_config(const mv_ctx *c, mv_config *out)

@@ -1,0 +1,206 @@
+// mv_track.cu -- depth-map conversion and point-to-plane ICP (sm_103a).
+//
+// Sec. Depth Map Conversion: every pixel's vertex v = K^-1 [x, y, 1]^T D(x, y)
+// and the normal (v(x+1, y) - v(x, y)) x (v(x, y+1) - v(x, y)), here
+// normalised and turned to face the camera; Sec. Camera Tracking: the pose
+// that aligns these vertices with the model maps of the previous raycast, by
+// iterated point-to-plane ICP with projective data association.
+//
+// One linearisation is one kernel: every pixel of the current frame is moved
+// by the current estimate, projected into the model's camera, associated with
+// the model vertex / normal at the nearest pixel (rejected beyond a distance
+// or normal-angle threshold), and contributes J^T J, J^T r, r^2 and a count
+// (29 values) to a per-CTA partial in FP64; the host adds the partials in a
+// fixed order and solves the 6x6 system.
+#include "mv_internal.cuh"
+
+namespace mv {
+
+struct Mat34f {
+    float r[9];  // row-major rotation
+    float t[3];
+};
+
+__global__ void __launch_bounds__(256) depth_maps_kernel(const float *__restrict__ depth, int W, int H, float fx,
+                                                         float fy, float cx, float cy, float z_min, float z_max,
+                                                         Mat34f T, float *__restrict__ vertex,
+                                                         float *__restrict__ normal)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= W * H) return;
+    const int x = p % W, y = p / W;
+    auto valid = [&](float D) { return D > 0.f && D >= z_min && D <= z_max; };
+    auto backproject = [&](int xx, int yy, float D, float v[3]) {
+        v[0] = ((float)xx - cx) / fx * D;
+        v[1] = ((float)yy - cy) / fy * D;
+        v[2] = D;
+    };
+    const float D = __ldg(depth + p);
+    float v[3] = {0.f, 0.f, 0.f}, n[3] = {0.f, 0.f, 0.f};
+    if (valid(D)) {
+        backproject(x, y, D, v);
+        if (x + 1 < W && y + 1 < H) {
+            const float Dx = __ldg(depth + p + 1), Dy = __ldg(depth + p + W);
+            if (valid(Dx) && valid(Dy)) {
+                float vx[3], vy[3];
+                backproject(x + 1, y, Dx, vx);
+                backproject(x, y + 1, Dy, vy);
+                const float a0 = vx[0] - v[0], a1 = vx[1] - v[1], a2 = vx[2] - v[2];
+                const float b0 = vy[0] - v[0], b1 = vy[1] - v[1], b2 = vy[2] - v[2];
+                float c0 = a1 * b2 - a2 * b1, c1 = a2 * b0 - a0 * b2, c2 = a0 * b1 - a1 * b0;
+                const float len = sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+                if (len > 0.f) {
+                    // face the camera (the side the raycast normals face)
+                    const float sgn = (c0 * v[0] + c1 * v[1] + c2 * v[2] > 0.f) ? -1.f : 1.f;
+                    n[0] = sgn * c0 / len;
+                    n[1] = sgn * c1 / len;
+                    n[2] = sgn * c2 / len;
+                }
+            }
+        }
+    }
+    float vo[3] = {0.f, 0.f, 0.f}, no[3] = {0.f, 0.f, 0.f};
+    if (valid(D)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            vo[a] = T.r[3 * a] * v[0] + T.r[3 * a + 1] * v[1] + T.r[3 * a + 2] * v[2] + T.t[a];
+            no[a] = T.r[3 * a] * n[0] + T.r[3 * a + 1] * n[1] + T.r[3 * a + 2] * n[2];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vertex[3 * (size_t)p + a] = vo[a];
+        normal[3 * (size_t)p + a] = no[a];
+    }
+}
+
+cudaError_t launch_depth_maps(const float *depth, const mv_intrinsics &K, float z_min, float z_max,
+                              const double *T, float *vertex, float *normal, cudaStream_t s)
+{
+    Mat34f M;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) M.r[3 * a + b] = T ? (float)T[4 * a + b] : (a == b ? 1.f : 0.f);
+        M.t[a] = T ? (float)T[4 * a + 3] : 0.f;
+    }
+    const int n = K.width * K.height;
+    depth_maps_kernel<<<(n + 255) / 256, 256, 0, s>>>(depth, K.width, K.height, K.fx, K.fy, K.cx, K.cy, z_min,
+                                                      z_max, M, vertex, normal);
+    return cudaGetLastError();
+}
+
+constexpr int kIcpTerms = 29;  // 21 of J^T J (upper triangle, row-major), 6 of J^T r, r^2, count
+
+struct IcpArgs {
+    const float *vertex;   // current frame, camera frame
+    const float *normal;
+    int W, H;
+    Mat34f est;            // current estimate, camera to world
+    const float *mvertex;  // model maps (world frame), same size as the frame
+    const float *mnormal;
+    Mat34f model_inv;      // world to model camera
+    float fx, fy, cx, cy;
+    float dist2, cos_min;
+    double *partials;      // gridDim.x x kIcpTerms
+};
+
+__global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A)
+{
+    float acc[kIcpTerms];
+#pragma unroll
+    for (int k = 0; k < kIcpTerms; ++k) acc[k] = 0.f;
+    const int n = A.W * A.H;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float nl0 = A.normal[3 * p], nl1 = A.normal[3 * p + 1], nl2 = A.normal[3 * p + 2];
+        if (nl0 == 0.f && nl1 == 0.f && nl2 == 0.f) continue;
+        const float vl0 = A.vertex[3 * p], vl1 = A.vertex[3 * p + 1], vl2 = A.vertex[3 * p + 2];
+        float v[3], nn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[a] = A.est.r[3 * a] * vl0 + A.est.r[3 * a + 1] * vl1 + A.est.r[3 * a + 2] * vl2 + A.est.t[a];
+            nn[a] = A.est.r[3 * a] * nl0 + A.est.r[3 * a + 1] * nl1 + A.est.r[3 * a + 2] * nl2;
+        }
+        float q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            q[a] = A.model_inv.r[3 * a] * v[0] + A.model_inv.r[3 * a + 1] * v[1] + A.model_inv.r[3 * a + 2] * v[2] +
+                   A.model_inv.t[a];
+        if (!(q[2] > 0.f)) continue;
+        const float u = A.fx * q[0] / q[2] + A.cx, w = A.fy * q[1] / q[2] + A.cy;
+        const int ui = (int)floorf(u + 0.5f), wi = (int)floorf(w + 0.5f);
+        if (ui < 0 || wi < 0 || ui >= A.W || wi >= A.H) continue;
+        const size_t m = (size_t)wi * A.W + ui;
+        const float N0 = A.mnormal[3 * m], N1 = A.mnormal[3 * m + 1], N2 = A.mnormal[3 * m + 2];
+        if (!(N0 * N0 + N1 * N1 + N2 * N2 > 0.25f)) continue;  // model miss (normal 0)
+        const float V0 = A.mvertex[3 * m], V1 = A.mvertex[3 * m + 1], V2 = A.mvertex[3 * m + 2];
+        const float d0 = V0 - v[0], d1 = V1 - v[1], d2 = V2 - v[2];
+        if (!(d0 * d0 + d1 * d1 + d2 * d2 <= A.dist2)) continue;
+        if (!(nn[0] * N0 + nn[1] * N1 + nn[2] * N2 >= A.cos_min)) continue;
+        const float r = N0 * d0 + N1 * d1 + N2 * d2;
+        // x = (rho, phi): v -> v + rho + phi x v, so dr/dx = -[N, v x N]
+        const float J[6] = {N0, N1, N2, v[1] * N2 - v[2] * N1, v[2] * N0 - v[0] * N2, v[0] * N1 - v[1] * N0};
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = i; j < 6; ++j) acc[k++] += J[i] * J[j];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[21 + i] += J[i] * r;
+        acc[27] += r * r;
+        acc[28] += 1.f;
+    }
+    // CTA sum in FP64: warps by shuffles, then across the 8 warps in shared memory
+    __shared__ double s_part[8][kIcpTerms];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kIcpTerms; ++k) {
+        double x = (double)acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) s_part[wid][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kIcpTerms) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_part[w][threadIdx.x];
+        A.partials[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = x;
+    }
+}
+
+int icp_grid(int num_sms) { return num_sms * 2; }
+
+cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv_intrinsics &K,
+                              const double *T_est, const float *mvertex, const float *mnormal,
+                              const double *T_model, float dist, float cos_min, double *partials, int grid,
+                              cudaStream_t s)
+{
+    IcpArgs A;
+    A.vertex = vertex;
+    A.normal = normal;
+    A.W = K.width;
+    A.H = K.height;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            A.est.r[3 * a + b] = (float)T_est[4 * a + b];
+            A.model_inv.r[3 * a + b] = (float)T_model[4 * b + a];  // R^T
+        }
+        A.est.t[a] = (float)T_est[4 * a + 3];
+    }
+    for (int a = 0; a < 3; ++a) {  // -R^T t in FP64, then rounded
+        double x = 0.0;
+        for (int b = 0; b < 3; ++b) x -= T_model[4 * b + a] * T_model[4 * b + 3];
+        A.model_inv.t[a] = (float)x;
+    }
+    A.mvertex = mvertex;
+    A.mnormal = mnormal;
+    A.fx = K.fx;
+    A.fy = K.fy;
+    A.cx = K.cx;
+    A.cy = K.cy;
+    A.dist2 = dist * dist;
+    A.cos_min = cos_min;
+    A.partials = partials;
+    icp_system_kernel<<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace mv

@@ -265,6 +265,69 @@ class Mapper:
                 out["edge"] = edge[:k]
             return out
 
+    # -- tracking -------------------------------------------------------------
+    def depth_to_maps(self, depth, cam, T=None, stream=None):
+        """(vertex, normal) float32 CUDA tensors (H, W, 3) of a depth frame;
+        world frame with T, camera frame without."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        n = cam.width * cam.height
+        v = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device=dev)
+        nn = torch.empty_like(v)
+        K = intrinsics(cam)
+        if T is None:
+            Tp, keep = None, None
+        else:
+            keep = _pose(T)
+            Tp = keep[1]
+        self._check(self._lib.mv_depth_to_maps(self._h, _dptr(depth, torch.float32, n, "depth"), C.byref(K), Tp,
+                                               C.c_void_p(v.data_ptr()), C.c_void_p(nn.data_ptr()),
+                                               _stream(stream)))
+        del keep
+        return v, nn
+
+    @staticmethod
+    def _icp_cfg(iterations, dist, cos_min):
+        return _abi.mv_icp_config(int(iterations), float(dist), float(cos_min))
+
+    @staticmethod
+    def _icp_out(r):
+        return {"A": np.array(r.A[:]).reshape(6, 6), "b": np.array(r.b[:]), "error": r.error, "count": r.inliers}
+
+    def icp_linearize(self, vertex, normal, cam, T_est, model_vertex, model_normal, T_model, dist=0.1,
+                      cos_min=0.8, stream=None) -> dict:
+        """One point-to-plane linearisation (see mv_icp_linearize)."""
+        import torch
+        n = 3 * cam.width * cam.height
+        r = _abi.mv_icp_system()
+        cfg = self._icp_cfg(1, dist, cos_min)
+        ke, Te = _pose(T_est)
+        km, Tm = _pose(T_model)
+        self._check(self._lib.mv_icp_linearize(
+            self._h, _dptr(vertex, torch.float32, n, "vertex"), _dptr(normal, torch.float32, n, "normal"),
+            C.byref(intrinsics(cam)), Te, _dptr(model_vertex, torch.float32, n, "model_vertex"),
+            _dptr(model_normal, torch.float32, n, "model_normal"), Tm, C.byref(cfg), C.byref(r), _stream(stream)))
+        del ke, km
+        return self._icp_out(r)
+
+    def track(self, depth, cam, model_vertex, model_normal, T_model, T_init, iterations=10, dist=0.1,
+              cos_min=0.8, stream=None):
+        """Track a depth frame against model maps: (T (4, 4) float64, last system)."""
+        import torch
+        n = cam.width * cam.height
+        r = _abi.mv_icp_system()
+        cfg = self._icp_cfg(iterations, dist, cos_min)
+        km, Tm = _pose(T_model)
+        ki, Ti = _pose(T_init)
+        out = np.zeros(16)
+        self._check(self._lib.mv_track(
+            self._h, _dptr(depth, torch.float32, n, "depth"), C.byref(intrinsics(cam)),
+            _dptr(model_vertex, torch.float32, 3 * n, "model_vertex"),
+            _dptr(model_normal, torch.float32, 3 * n, "model_normal"), Tm, Ti, C.byref(cfg),
+            out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(r), _stream(stream)))
+        del km, ki
+        return out.reshape(4, 4), self._icp_out(r)
+
     def raycast_volume(self, vid, first, cam, T, out, stream=None) -> dict:
         K = intrinsics(cam)
         _, Tp = keep = _pose(T)
