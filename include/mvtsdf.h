@@ -13,7 +13,7 @@
  *     vertex maps, all volumes writing one map where the shortest ray distance
  *     wins (Sec. Raycasting; Algorithm 1, second loop);
  *   - moving a volume between GPU memory and host memory
- *     (Sec. Memory Passing; Algorithm 1, uploadToGPU / uploadToCPU).
+ *     (Sec. Memory Passing; the upload and download steps of Algorithm 1).
  *
  * Conventions shared by every call:
  *   - Poses are 4x4 row-major camera-to-world matrices T = [R | t] in double
@@ -24,7 +24,7 @@
  *     Volumes whose offsets differ by integer multiples of (h_r - 2) tile space
  *     with the paper's two-voxel overlap (Sec. Initialization).
  *   - Depth is float32 z-depth in metres, row-major height x width; a value
- *     <= 0, NaN, or outside [z_min, z_max] is "no measurement".  RGB is uint8
+ *     <= 0, NaN, or outside [z_min, z_max] is no measurement.  RGB is uint8
  *     height x width x 3, registered to depth with the same intrinsics.
  *   - TSDF values are stored in units of the truncation distance mu
  *     (range [-1, 1]); weights count frames, capped at w_max.
@@ -300,14 +300,14 @@ mv_status mv_raycast_backward(mv_ctx *ctx, const mv_intrinsics *K, const double 
                               const float *grad_depth, const float *grad_rgb, float *grad_pose,
                               const mv_grad_target *targets, int32_t n_targets, void *stream);
 
-/* Move a volume to pinned host memory (the paper's download, "uploadToCPU")
+/* Move a volume to pinned host memory (the paper's download to the CPU, Algorithm 1)
  * on the library's swap stream, after the work already queued on `stream`;
  * its GPU memory is released once the copy has finished.  From this call on
  * the volume is skipped by mv_integrate / mv_raycast.  MV_ERR_OOM if pinned
  * memory cannot be allocated (the volume then stays resident). */
 mv_status mv_swap_out(mv_ctx *ctx, int32_t id, void *stream);
 
-/* Bring a swapped-out volume back to GPU memory ("uploadToGPU") on the swap
+/* Bring a swapped-out volume back to GPU memory (the paper's upload to the GPU, Algorithm 1) on the swap
  * stream; later calls on any stream wait for the copy.  MV_ERR_OOM if GPU
  * memory is exhausted (the volume stays on the host). */
 mv_status mv_swap_in(mv_ctx *ctx, int32_t id, void *stream);

@@ -17,13 +17,13 @@
  *     (h_t + i) * s, s = voxel pitch (Sec. Volumetric Integration, t_s = t_l + h_t;
  *     Sec. Dynamic Mapping for SLAM, h_t on an integer lattice);
  *   - the pose T = [R|t] maps camera to world (Sec. Depth Map Conversion);
- *   - the "measured distance" is the projective distance along the voxel's
+ *   - the measured distance of a voxel is the projective distance along its
  *     ray seen from the current camera: sdf = (D - z) * |p_c| / z
  *     (Sec. Volumetric Integration, dist = D - d_m, read with d_m measured
  *     from the camera of the current frame);
- *   - "constrained to truncation bounds": voxels with sdf < -mu are not
- *     updated, otherwise f = min(1, sdf / mu) in units of mu;
- *   - "linearly increasing weight up to some maximum": per-frame weight 1,
+ *   - truncation: voxels with sdf < -mu are not updated, otherwise
+ *     f = min(1, sdf / mu) in units of mu;
+ *   - weights grow by one per frame up to a cap: per-frame weight 1,
  *     F' = (F W + f) / (W + 1), W' = min(W + 1, W_max);
  *   - colour (the paper shows coloured models but gives no rule): a running
  *     average inside the band |sdf| < mu, rounded half up, colour weight in
@@ -37,7 +37,7 @@
  *     brackets the surface; an invalid sample breaks the pair.  The root of
  *     the trilinear interpolant inside the bracket is found by bisection.
  *   - normal = normalised analytic gradient of the trilinear interpolant in
- *     the hit cell (the "derivative of the TSDF at the zero crossing");
+ *     the hit cell (the TSDF derivative at the zero crossing);
  *     colour = trilinear RGB in the hit cell, rounded half up;
  *   - all volumes write one map; the smallest ray distance wins, exact ties
  *     go to the lower volume id (Sec. Raycasting, last paragraph).
