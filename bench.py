@@ -198,22 +198,27 @@ def barrier(torch):
         dist.barrier()
 
 
-def allreduce_max(torch, x):
+def _allreduce(torch, x, op, device):
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
-        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=getattr(dist.ReduceOp, op))
         return float(t.item())
     return float(x)
 
 
-def allreduce_sum(torch, x):
-    import torch.distributed as dist
-    if dist.is_available() and dist.is_initialized():
-        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-    return float(x)
+def allreduce_max(torch, x, device="cuda"):
+    return _allreduce(torch, x, "MAX", device)
+
+
+def allreduce_sum(torch, x, device="cuda"):
+    return _allreduce(torch, x, "SUM", device)
+
+
+def weak_scaling_value(torch, units, ms, device="cuda"):
+    """Whole-job throughput of independent per-rank jobs: the units all ranks
+    processed over the slowest rank's time."""
+    return allreduce_sum(torch, units, device) / (allreduce_max(torch, ms, device) * 1e-3)
 
 
 def integrate_bytes_per_voxel(fmt):
@@ -766,8 +771,7 @@ def main():
     res = bench_storage(torch, Mapper, Config, wl, poses, "f32", args.warmup, args.steps,
                         dev_depth, dev_rgb, clocks=clocks)
     ms_max = allreduce_max(torch, res["ms"])
-    upd_sum = allreduce_sum(torch, res["stats"]["updated"])
-    value = upd_sum / (ms_max * 1e-3)
+    value = weak_scaling_value(torch, res["stats"]["updated"], res["ms"])
     kern = kernel_summary(res, "f32", cam, args.steps)
     peak, peak_kind = measured_peaks()
     dom = max(kern, key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])

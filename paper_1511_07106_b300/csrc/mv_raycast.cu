@@ -15,9 +15,11 @@
 //
 // B300 design: one thread per pixel, 8x4-pixel warp tiles for gather
 // locality, every volume of the view in one launch with the nearest hit kept
-// in registers.  Space that cannot hold a surface crossing is crossed brick by
-// brick with a 3D DDA over per-brick flags (see march_volume): an exact
-// shortcut, not an approximation.
+// in registers; each CTA first keeps only the volumes its pixel rectangle can
+// hit.  Space that cannot hold a surface crossing is crossed by a 3D DDA over
+// 8^3-voxel cell bricks and 32^3-voxel super bricks using exact per-brick
+// summaries (see march_volume): a shortcut, not an approximation.  The
+// bisection keeps the corners of its current cell in registers.
 #include <float.h>
 #include <limits.h>
 
@@ -213,11 +215,9 @@ __device__ __forceinline__ void shade(const VolDev &v, const Geo<Off> &geo, cons
     h.rgba = out;
 }
 
-// Length (in grid samples from the current one, at local position L inside
-// cell brick b0) of the run of consecutive step-over cell bricks along the
-// ray, minus a safety margin of m voxels before the run's exit face and
-// before the volume's last voxel plane (where cells are clamped).  3D DDA
-// over bricks, at most nb0 + nb1 + nb2 + 3 steps.
+// DDA set-up along one axis: parameter (in samples) of the first brick face
+// crossed from L, spacing of the faces, step direction, and the domain end
+// (the last voxel plane less m) for positive directions.
 __device__ __forceinline__ void dda_axis(float L, float dq, int b0, int r, float m, float &tmax,
                                          float &tdel, int &step, float &tdom)
 {
@@ -423,11 +423,40 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
         if (state == 1 && F <= 0.f) {
             // bracket (k-1, k]: bisection on the interpolant, then a secant step
             float a = k - 1.0f, b = k, ga = Fprev, gb = F;
+            // the corners of the cell last read stay in registers: a midpoint in
+            // the same cell re-reads no memory (same arithmetic as trilinear)
+            int c0 = -1, c1 = 0, c2 = 0;
+            float Fc0 = 0.f, Fc1 = 0.f, Fc2 = 0.f, Fc3 = 0.f, Fc4 = 0.f, Fc5 = 0.f, Fc6 = 0.f, Fc7 = 0.f;
             for (int it = 0; it < P.n_bisect; ++it) {
                 const float mid = 0.5f * (a + b);
                 if (mid <= a || mid >= b) break;  // interval at float resolution
-                bool vv;
-                const float gm = eval_at<FMT>(v, g, vr, mid, vv);
+                float rm[3], fm[3];
+                int cm[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) rm[e] = fmaf(mid, vr.dq[e], vr.fr[e]);
+                locate(v, vr, rm, cm, fm);
+                if (cm[0] != c0 || cm[1] != c1 || cm[2] != c2) {
+                    c0 = cm[0];
+                    c1 = cm[1];
+                    c2 = cm[2];
+                    const Corners<Off> q = cell_corners(g, c0, c1, c2);
+                    float Wd;
+                    load_fw<FMT>(v, q.base, Fc0, Wd);
+                    load_fw<FMT>(v, q.base + q.ox, Fc1, Wd);
+                    load_fw<FMT>(v, q.base + q.oy, Fc2, Wd);
+                    load_fw<FMT>(v, q.base + q.ox + q.oy, Fc3, Wd);
+                    load_fw<FMT>(v, q.base + q.oz, Fc4, Wd);
+                    load_fw<FMT>(v, q.base + q.ox + q.oz, Fc5, Wd);
+                    load_fw<FMT>(v, q.base + q.oy + q.oz, Fc6, Wd);
+                    load_fw<FMT>(v, q.base + q.ox + q.oy + q.oz, Fc7, Wd);
+                }
+                const float x00 = fmaf(fm[0], Fc1 - Fc0, Fc0);
+                const float x10 = fmaf(fm[0], Fc3 - Fc2, Fc2);
+                const float x01 = fmaf(fm[0], Fc5 - Fc4, Fc4);
+                const float x11 = fmaf(fm[0], Fc7 - Fc6, Fc6);
+                const float y0 = fmaf(fm[1], x10 - x00, x00);
+                const float y1 = fmaf(fm[1], x11 - x01, x01);
+                const float gm = fmaf(fm[2], y1 - y0, y0);
                 if (gm > 0.f) { a = mid; ga = gm; } else { b = mid; gb = gm; }
             }
             const float den = ga - gb;
