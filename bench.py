@@ -500,7 +500,8 @@ def bench_streamed(torch, Mapper, Config, frames, n_frames=6):
     """Full-cover out-of-core frames (the paper's per-frame upload, integrate,
     raycast, download of every volume): 4 tiles of 512^3 (the lower half of
     the room mapped at 2.93 mm), all swapped out to pinned host memory and
-    streamed through the device every frame."""
+    streamed through the device every frame; only the bricks a frame can read
+    go up and only those it changed come back (plus the flags)."""
     wl = synth.tiled(synth.room_512(frames=N_FRAMES_MAX, res=1022), split=2)
     vols = wl.volumes[:4]
     cam = wl.cam
@@ -527,11 +528,17 @@ def bench_streamed(torch, Mapper, Config, frames, n_frames=6):
         ms = (time.perf_counter() - t0) * 1e3 / n_frames
         st = m.stats()
         vbytes = m.query(ids[0])["host_bytes"]
+        nb = int(np.prod([(r + 7) // 8 for r in vols[0].r]))
+        brick_bytes = 512 * ((8 if fmt == "f32" else 4) + 4)
+        up = st["stream_up"] / n_frames * brick_bytes
+        down = st["stream_down"] / n_frames * brick_bytes
         m.close()
         torch.cuda.empty_cache()
         out[f"{fmt}_slots{n_slots}"] = {
             "ms_per_frame": ms, "s_per_frame_per_volume": ms * 1e-3 / len(vols),
-            "bytes_per_volume": vbytes, "copy_gbs_each_way": len(vols) * vbytes / (ms * 1e-3) / 1e9,
+            "bytes_per_volume": vbytes, "bricks_per_volume": nb,
+            "upload_bytes_per_frame": up, "writeback_bytes_per_frame": down,
+            "upload_gbs": up / (ms * 1e-3) / 1e9, "writeback_gbs": down / (ms * 1e-3) / 1e9,
             "updated_voxels_per_frame": st["updated"] / n_frames}
     return out
 

@@ -114,6 +114,8 @@ typedef struct {
     uint64_t ray_samples; /* raycast: grid samples evaluated by trilinear interpolation */
     uint64_t ray_skips;   /* raycast: whole-brick shortcuts taken */
     uint64_t ray_hits;    /* raycast: pixels with a surface hit */
+    uint64_t stream_up;   /* mv_frame_streamed: bricks uploaded to a staging slot */
+    uint64_t stream_down; /* mv_frame_streamed: bricks written back to host copies */
 } mv_stats;
 
 /* Kernel kinds counted and timed by mv_get_timings. */
@@ -130,7 +132,8 @@ enum {
     MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
     MV_KERNEL_DEPTH_MAPS = 10, /* vertex / normal maps of a depth frame */
     MV_KERNEL_ICP = 11,        /* one point-to-plane ICP linearisation */
-    MV_KERNEL_KINDS = 12
+    MV_KERNEL_STREAM = 12,     /* brick gather / scatter of mv_frame_streamed */
+    MV_KERNEL_KINDS = 13
 };
 
 typedef struct {
@@ -220,12 +223,15 @@ mv_status mv_frame(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv
  * Sec. Raycasting, Algorithm 1: every volume is uploaded, integrated,
  * raycast and downloaded again in every frame).  Resident volumes are
  * integrated and raycast in place, as by mv_frame; then every swapped-out
- * volume passes through one of n_slots (1..4) device staging slots: its host
- * copy is uploaded on one copy stream, integrated and raycast into the same
- * maps on `stream` (nearest hit wins, ties to the lower id, so the maps equal
- * those of all volumes resident), and downloaded back into its host copy on a
- * second copy stream, so that the copies of one slot overlap the kernels of
- * another.  The volumes stay swapped out.  The slots (sized for the largest
+ * volume passes through one of n_slots (1..4) device staging slots: on one
+ * side stream its flags and the bricks the frame can read (those whose cells
+ * meet the view frustum, found from the pose) are uploaded, the bricks by a
+ * kernel that reads the pinned host copy directly; it is integrated and raycast
+ * into the same maps on `stream` (nearest hit wins, ties to the lower id, so
+ * the maps equal those of all volumes resident); on a second side stream its
+ * flags and the bricks the integration changed are written back to the host
+ * copy.  The uploads and write-backs of one slot overlap the kernels of
+ * another.  mv_get_stats counts the bricks moved (stream_up, stream_down).  The volumes stay swapped out.  The slots (sized for the largest
  * swapped-out volume) are kept by the context for later calls.  `stream`
  * waits for the last download; later swap-in, read and write calls wait for
  * the downloads of their volume.  depth_out and vol_id are required.

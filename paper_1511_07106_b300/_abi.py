@@ -45,13 +45,15 @@ class mv_volume_info(C.Structure):
 class mv_stats(C.Structure):
     _fields_ = [("swept", C.c_uint64), ("updated", C.c_uint64), ("band", C.c_uint64),
                 ("bricks", C.c_uint64), ("rays", C.c_uint64), ("ray_samples", C.c_uint64),
-                ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64)]
+                ("ray_skips", C.c_uint64), ("ray_hits", C.c_uint64), ("stream_up", C.c_uint64),
+                ("stream_down", C.c_uint64)]
 
 
-MV_KERNEL_KINDS = 12
+MV_KERNEL_KINDS = 13
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
                 5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max",
-                9: "extract", 10: "depth_maps", 11: "icp"}
+                9: "extract", 10: "depth_maps", 11: "icp",
+                12: "stream"}
 
 
 class mv_timings(C.Structure):

@@ -557,6 +557,91 @@ __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
 }
 
 // ---------------------------------------------------------------------------
+// full-cover streaming: brick gather / scatter between the host copy of a
+// swapped-out volume (pinned, mapped) and a device staging slot
+// ---------------------------------------------------------------------------
+// A frame reads, of a staged volume, the bricks holding the cells along the
+// pixel rays inside [z_min, z_max] (and the integration's bricks, a subset):
+// a cell whose lower corner lies in brick b covers positions [8b, 8b + 8)
+// and reads bricks b and b + 1, so brick b' is needed when the box
+// [8b' - 8, 8b' + 8] meets the view frustum.  Those bricks are copied from
+// the host copy into the slot, one warp per brick; the slot's other bricks
+// are never read by the frame's kernels.
+__global__ void __launch_bounds__(128) stream_gather_kernel(VolDev v, const VolFrame *__restrict__ vf,
+                                                            FrameParams P, const uint4 *__restrict__ h_fw,
+                                                            const uint4 *__restrict__ h_rgba,
+                                                            unsigned long long *__restrict__ count)
+{
+    const VolFrame f = *vf;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int fw_vec = kBrickVox * (v.fmt == MV_TSDF_F32 ? 8 : 4) / 16;
+    const int col_vec = kBrickVox * 4 / 16;
+    uint4 *dfw = reinterpret_cast<uint4 *>(v.fw);
+    uint4 *dcol = reinterpret_cast<uint4 *>(v.rgba);
+    unsigned long long n = 0;
+    for (long long b = warp; b < v.nbricks; b += nwarps) {
+        const int bi[3] = {(int)(b % v.nb[0]), (int)((b / v.nb[0]) % v.nb[1]),
+                           (int)(b / ((long long)v.nb[0] * v.nb[1]))};
+        float lo[3], hi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int l = max(0, bi[a] * kBrick - kBrick), u = min(v.r[a] - 1, bi[a] * kBrick + kBrick);
+            lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
+            hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
+        }
+        if (!box_visible(lo, hi, P, v.inv_s, P.z_max)) continue;
+        // all of a lane's loads first (many host reads in flight), then the stores
+        uint4 a[8], c[4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k * 32 < fw_vec) a[k] = h_fw[b * fw_vec + k * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = h_rgba[b * col_vec + k * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k * 32 < fw_vec) dfw[b * fw_vec + k * 32 + lane] = a[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dcol[b * col_vec + k * 32 + lane] = c[k];
+        ++n;
+    }
+    if (lane == 0 && n) atomicAdd(count, n);
+}
+
+// The bricks the integration changed (its work list) back to the host copy.
+__global__ void __launch_bounds__(128) stream_scatter_kernel(VolDev v, const uint2 *__restrict__ list,
+                                                             const unsigned *__restrict__ counter,
+                                                             uint4 *__restrict__ h_fw, uint4 *__restrict__ h_rgba,
+                                                             unsigned long long *__restrict__ count)
+{
+    const unsigned n = *counter;
+    const int lane = threadIdx.x & 31;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int fw_vec = kBrickVox * (v.fmt == MV_TSDF_F32 ? 8 : 4) / 16;
+    const int col_vec = kBrickVox * 4 / 16;
+    const uint4 *sfw = reinterpret_cast<const uint4 *>(v.fw);
+    const uint4 *scol = reinterpret_cast<const uint4 *>(v.rgba);
+    for (unsigned i = warp; i < n; i += nwarps) {
+        const unsigned pk = list[i].y;
+        const long long b = ((long long)(pk >> 20) * v.nb[1] + ((pk >> 10) & 1023u)) * v.nb[0] + (pk & 1023u);
+        uint4 a[8], c[4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k * 32 < fw_vec) a[k] = sfw[b * fw_vec + k * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = scol[b * col_vec + k * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k * 32 < fw_vec) h_fw[b * fw_vec + k * 32 + lane] = a[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h_rgba[b * col_vec + k * 32 + lane] = c[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, (unsigned long long)n);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_frame_setup(const VolDev *vols, int nvol, const FrameParams &P, VolFrame *vf,
@@ -691,5 +776,28 @@ int integrate_max_ctas_per_sm()
 }
 
 int integrate_occupancy_grid(int num_sms) { return num_sms * integrate_max_ctas_per_sm(); }
+
+}  // namespace mv
+
+namespace mv {
+
+// Gather and scatter are bound by the host link, not the SMs: two CTAs per SM
+// keep enough reads in flight and leave the SMs to the kernels of the other
+// slots, which run at the same time on other streams.
+cudaError_t launch_stream_gather(const VolDev &v, const VolFrame *vf, const FrameParams &P, const void *h_fw,
+                                 const void *h_rgba, unsigned long long *count, int num_sms, cudaStream_t s)
+{
+    stream_gather_kernel<<<num_sms * 2, 128, 0, s>>>(v, vf, P, reinterpret_cast<const uint4 *>(h_fw),
+                                                     reinterpret_cast<const uint4 *>(h_rgba), count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_scatter(const VolDev &v, const uint2 *list, const unsigned *counter, void *h_fw,
+                                  void *h_rgba, unsigned long long *count, int num_sms, cudaStream_t s)
+{
+    stream_scatter_kernel<<<num_sms * 2, 128, 0, s>>>(v, list, counter, reinterpret_cast<uint4 *>(h_fw),
+                                                      reinterpret_cast<uint4 *>(h_rgba), count);
+    return cudaGetLastError();
+}
 
 }  // namespace mv

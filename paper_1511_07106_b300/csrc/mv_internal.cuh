@@ -113,6 +113,7 @@ inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
 struct Stats {
     unsigned long long swept, updated, band, bricks;
     unsigned long long rays, ray_samples, ray_skips, ray_hits;
+    unsigned long long stream_up, stream_down;
 };
 
 // ---------------------------------------------------------------------------

@@ -61,6 +61,10 @@ cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float
 cudaError_t launch_icp_system(const float *, const float *, const mv_intrinsics &, const double *, const float *,
                               const float *, const double *, float, float, double *, int, cudaStream_t);
 int icp_grid(int num_sms);
+cudaError_t launch_stream_gather(const VolDev &, const VolFrame *, const FrameParams &, const void *, const void *,
+                                 unsigned long long *, int, cudaStream_t);
+cudaError_t launch_stream_scatter(const VolDev &, const uint2 *, const unsigned *, void *, void *,
+                                  unsigned long long *, int, cudaStream_t);
 constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
@@ -145,8 +149,8 @@ struct mv_ctx {
         uint8_t *flag[kMaxStreamSlots] = {};
         VolDev *d_vol = nullptr;   // one descriptor per slot
         VolFrame *d_vf = nullptr;  // one camera-constant record per slot
-        uint2 *list = nullptr;
-        unsigned *counter = nullptr;
+        uint2 *list[kMaxStreamSlots] = {};  // per slot: the integration's work list
+        unsigned *counter = nullptr;        // 4 per slot
         cudaStream_t h2d = nullptr, d2h = nullptr;
         cudaEvent_t loaded[kMaxStreamSlots] = {}, done[kMaxStreamSlots] = {}, freed[kMaxStreamSlots] = {};
         bool freed_rec[kMaxStreamSlots] = {};
@@ -519,20 +523,14 @@ mv_status ensure_slots(mv_ctx *c, int n, size_t fw, size_t rgba, size_t flag, lo
     if (!ss.d2h) MV_CUDA(c, cudaStreamCreateWithFlags(&ss.d2h, cudaStreamNonBlocking));
     if (!ss.d_vol) MV_CUDA(c, cudaMalloc((void **)&ss.d_vol, sizeof(VolDev) * kMaxStreamSlots));
     if (!ss.d_vf) MV_CUDA(c, cudaMalloc((void **)&ss.d_vf, sizeof(VolFrame) * kMaxStreamSlots));
-    if (!ss.counter) MV_CUDA(c, cudaMalloc((void **)&ss.counter, sizeof(unsigned) * 4));
+    if (!ss.counter) MV_CUDA(c, cudaMalloc((void **)&ss.counter, sizeof(unsigned) * 4 * kMaxStreamSlots));
     for (int j = 0; j < kMaxStreamSlots; ++j) {
         if (!ss.loaded[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.loaded[j], cudaEventDisableTiming));
         if (!ss.done[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.done[j], cudaEventDisableTiming));
         if (!ss.freed[j]) MV_CUDA(c, cudaEventCreateWithFlags(&ss.freed[j], cudaEventDisableTiming));
     }
-    if (bricks > ss.list_cap) {
-        if (ss.list) MV_CUDA(c, cudaFreeAsync(ss.list, s));
-        ss.list = nullptr;
-        ss.list_cap = 0;
-        MV_CUDA(c, cudaMallocAsync((void **)&ss.list, sizeof(uint2) * (size_t)bricks, s));
-        ss.list_cap = bricks;
-    }
-    const bool grow = n > ss.n || fw > ss.fw_cap || rgba > ss.rgba_cap || flag > ss.flag_cap;
+    const bool grow = n > ss.n || fw > ss.fw_cap || rgba > ss.rgba_cap || flag > ss.flag_cap ||
+                      bricks > ss.list_cap;
     if (!grow) return MV_OK;
     // slots in use by earlier calls are released in stream order
     for (int j = 0; j < ss.n; ++j)
@@ -541,19 +539,24 @@ mv_status ensure_slots(mv_ctx *c, int n, size_t fw, size_t rgba, size_t flag, lo
         if (ss.fw[j]) MV_CUDA(c, cudaFreeAsync(ss.fw[j], s));
         if (ss.rgba[j]) MV_CUDA(c, cudaFreeAsync(ss.rgba[j], s));
         if (ss.flag[j]) MV_CUDA(c, cudaFreeAsync(ss.flag[j], s));
+        if (ss.list[j]) MV_CUDA(c, cudaFreeAsync(ss.list[j], s));
         ss.fw[j] = nullptr;
         ss.rgba[j] = nullptr;
         ss.flag[j] = nullptr;
+        ss.list[j] = nullptr;
         ss.freed_rec[j] = false;
     }
     ss.n = 0;
     ss.fw_cap = std::max(fw, ss.fw_cap);
     ss.rgba_cap = std::max(rgba, ss.rgba_cap);
     ss.flag_cap = std::max(flag, ss.flag_cap);
+    ss.list_cap = std::max(bricks, ss.list_cap);
+    n = std::max(n, 1);
     for (int j = 0; j < n; ++j) {
         MV_CUDA(c, cudaMallocAsync(&ss.fw[j], ss.fw_cap, s));
         MV_CUDA(c, cudaMallocAsync((void **)&ss.rgba[j], ss.rgba_cap, s));
         MV_CUDA(c, cudaMallocAsync((void **)&ss.flag[j], ss.flag_cap, s));
+        MV_CUDA(c, cudaMallocAsync((void **)&ss.list[j], sizeof(uint2) * (size_t)ss.list_cap, s));
     }
     ss.n = n;
     return MV_OK;
@@ -570,7 +573,8 @@ void free_slots(mv_ctx *c, cudaStream_t s)
         if (ss.done[j]) cudaEventDestroy(ss.done[j]);
         if (ss.freed[j]) cudaEventDestroy(ss.freed[j]);
     }
-    if (ss.list) cudaFreeAsync(ss.list, s);
+    for (int j = 0; j < kMaxStreamSlots; ++j)
+        if (ss.list[j]) cudaFreeAsync(ss.list[j], s);
     if (ss.d_vol) cudaFree(ss.d_vol);
     if (ss.d_vf) cudaFree(ss.d_vf);
     if (ss.counter) cudaFree(ss.counter);
@@ -1134,19 +1138,20 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
     // the copies start after everything queued on the caller's stream so far
     MV_CUDA(c, cudaEventRecord(c->last_event, s));
     MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, c->last_event, 0));
-    // 2. every swapped-out volume: upload into a slot, integrate, raycast
-    //    into the maps (nearest hit wins, as between resident volumes),
-    //    download; slot j is reused once its previous volume is downloaded
+    // 2. every swapped-out volume passes through a slot: its flags and the
+    //    bricks the frame can read are uploaded (the bricks by a gather kernel
+    //    reading the mapped host copy), it is integrated and raycast into the
+    //    maps (nearest hit wins, as between resident volumes), and its flags
+    //    and the bricks the integration changed are written back; slot j is
+    //    reused once its previous volume is written back
     for (size_t i = 0; i < streamed.size(); ++i) {
         Volume *v = streamed[i];
         const int j = (int)(i % (size_t)n);
-        if (ss.freed_rec[j]) MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, ss.freed[j], 0));
-        if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(ss.h2d, v->ready, 0));
-        MV_CUDA(c, cudaMemcpyAsync(ss.fw[j], v->h_fw, v->fw_bytes, cudaMemcpyHostToDevice, ss.h2d));
-        MV_CUDA(c, cudaMemcpyAsync(ss.rgba[j], v->h_rgba, v->rgba_bytes, cudaMemcpyHostToDevice, ss.h2d));
-        MV_CUDA(c, cudaMemcpyAsync(ss.flag[j], v->h_flag, v->flag_bytes, cudaMemcpyHostToDevice, ss.h2d));
-        MV_CUDA(c, cudaEventRecord(ss.loaded[j], ss.h2d));
-
+        unsigned *cnt = ss.counter + 4 * j;
+        uint2 *list = ss.list[j];
+        void *hfw = nullptr, *hcol = nullptr;
+        MV_CUDA(c, cudaHostGetDevicePointer(&hfw, v->h_fw, 0));
+        MV_CUDA(c, cudaHostGetDevicePointer(&hcol, v->h_rgba, 0));
         Volume staged = *v;
         staged.d_fw = ss.fw[j];
         staged.d_rgba = ss.rgba[j];
@@ -1155,34 +1160,42 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
         d.brick_base = 0;
         VolDev *dv = ss.d_vol + j;
         VolFrame *vf = ss.d_vf + j;
-        MV_CUDA(c, cudaStreamWaitEvent(s, ss.loaded[j], 0));
-        put_voldev_kernel<<<1, 32, 0, s>>>(d, dv);
+
+        cudaStream_t up = ss.h2d;
+        if (ss.freed_rec[j]) MV_CUDA(c, cudaStreamWaitEvent(up, ss.freed[j], 0));
+        if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(up, v->ready, 0));
+        MV_CUDA(c, cudaMemcpyAsync(ss.flag[j], v->h_flag, v->flag_bytes, cudaMemcpyHostToDevice, up));
+        put_voldev_kernel<<<1, 32, 0, up>>>(d, dv);
         MV_CUDA(c, cudaGetLastError());
-        MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
-            return launch_frame_setup(dv, 1, P, vf, ss.counter, s, nullptr); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, up, [&] {
+            return launch_frame_setup(dv, 1, P, vf, cnt, up, nullptr); }));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_STREAM, up, [&] {
+            return launch_stream_gather(d, vf, P, hfw, hcol, &c->d_stats->stream_up, c->num_sms, up); }));
+        MV_CUDA(c, cudaEventRecord(ss.loaded[j], up));
+
+        MV_CUDA(c, cudaStreamWaitEvent(s, ss.loaded[j], 0));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
-            return launch_depth_max(depth, P, ss.counter + 1, c->num_sms, s); }));
+            return launch_depth_max(depth, P, cnt + 1, c->num_sms, s); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
-            return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, ss.list, ss.counter, c->num_sms, s, nullptr,
-                                     ss.counter + 1); }));
+            return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, list, cnt, c->num_sms, s, nullptr, cnt + 1); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
-            return launch_integrate(dv, vf, ss.list, ss.counter, P, depth, rgb, c->d_stats, c->grid_integrate,
-                                    s); }));
+            return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
-            return launch_cell_flags(dv, ss.list, ss.counter, c->num_sms, s); }));
+            return launch_cell_flags(dv, list, cnt, c->num_sms, s); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
             return launch_raycast(dv, vf, 1, P, depth_out, normal, rgba, vertex, vol_id, 1, c->d_stats,
                                   c->ray_tile, s, nullptr); }));
         MV_CUDA(c, cudaEventRecord(ss.done[j], s));
 
-        MV_CUDA(c, cudaStreamWaitEvent(ss.d2h, ss.done[j], 0));
-        MV_CUDA(c, cudaMemcpyAsync(v->h_fw, ss.fw[j], v->fw_bytes, cudaMemcpyDeviceToHost, ss.d2h));
-        MV_CUDA(c, cudaMemcpyAsync(v->h_rgba, ss.rgba[j], v->rgba_bytes, cudaMemcpyDeviceToHost, ss.d2h));
-        MV_CUDA(c, cudaMemcpyAsync(v->h_flag, ss.flag[j], v->flag_bytes, cudaMemcpyDeviceToHost, ss.d2h));
-        MV_CUDA(c, cudaEventRecord(ss.freed[j], ss.d2h));
+        cudaStream_t down = ss.d2h;
+        MV_CUDA(c, cudaStreamWaitEvent(down, ss.done[j], 0));
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_STREAM, down, [&] {
+            return launch_stream_scatter(d, list, cnt, hfw, hcol, &c->d_stats->stream_down, c->num_sms, down); }));
+        MV_CUDA(c, cudaMemcpyAsync(v->h_flag, ss.flag[j], v->flag_bytes, cudaMemcpyDeviceToHost, down));
+        MV_CUDA(c, cudaEventRecord(ss.freed[j], down));
         ss.freed_rec[j] = true;
         // later readers of the host copy (swap-in, read, write) wait for it
-        MV_CUDA(c, cudaEventRecord(v->ready, ss.d2h));
+        MV_CUDA(c, cudaEventRecord(v->ready, down));
         v->ready_pending = true;
     }
     // the caller's stream continues once every download has finished
@@ -1428,9 +1441,9 @@ mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)
     if (!v->resident) return MV_OK;
     cudaSetDevice(c->device);
     if (!v->h_fw) {
-        cudaError_t e = cudaHostAlloc(&v->h_fw, v->fw_bytes, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_rgba, v->rgba_bytes, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_flag, v->flag_bytes, cudaHostAllocDefault);
+        cudaError_t e = cudaHostAlloc(&v->h_fw, v->fw_bytes, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_rgba, v->rgba_bytes, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_flag, v->flag_bytes, cudaHostAllocMapped);
         if (e != cudaSuccess) {
             free_host(v);
             cudaGetLastError();
@@ -1636,6 +1649,8 @@ mv_status mv_get_stats(mv_ctx *c, mv_stats *out, int32_t reset)
     out->ray_samples = h.ray_samples;
     out->ray_skips = h.ray_skips;
     out->ray_hits = h.ray_hits;
+    out->stream_up = h.stream_up;
+    out->stream_down = h.stream_down;
     if (reset) MV_CUDA(c, cudaMemset(c->d_stats, 0, sizeof(Stats)));
     return MV_OK;
 }

@@ -46,7 +46,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(_abi.mv_intrinsics) == 24
     assert C.sizeof(_abi.mv_config) == 28
     assert C.sizeof(_abi.mv_volume_desc) == 32
-    assert C.sizeof(_abi.mv_stats) == 64
+    assert C.sizeof(_abi.mv_stats) == 80
 
 
 def test_version_and_defaults(lib):
