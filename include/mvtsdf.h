@@ -473,6 +473,15 @@ mv_status mv_track(mv_ctx *ctx, const float *depth, const mv_intrinsics *K, cons
                    const float *model_normal, const double T_model[16], const double T_init[16],
                    const mv_icp_config *cfg, double T_out[16], mv_icp_system *last, void *stream);
 
+/* Hold `count` (0..4096) spare sets of pinned host buffers for volumes
+ * shaped like `desc` (h_r and fmt), pinning the missing ones now (this call
+ * takes as long as pinning them), so that a later first mv_swap_out of such a
+ * volume need not wait while gigabytes of host memory are pinned.  Swap-outs
+ * take spares first; buffers of removed volumes return to the spares while
+ * fewer than `count` are held; 0 frees the spares.  MV_ERR_OOM when the host
+ * cannot pin that much (the sets pinned so far are kept). */
+mv_status mv_reserve_host(mv_ctx *ctx, const mv_volume_desc *desc, int32_t count);
+
 /* The configuration the context was created with. */
 mv_status mv_get_config(const mv_ctx *ctx, mv_config *out);
 

@@ -134,6 +134,7 @@ _SIGNATURES = {
     "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
                               C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_get_config": ([_P, C.POINTER(mv_config)], C.c_int),
+    "mv_reserve_host": ([_P, C.POINTER(mv_volume_desc), C.c_int32], C.c_int),
     "mv_depth_to_maps": ([_P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P], C.c_int),
     "mv_icp_linearize": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _D16, C.POINTER(mv_icp_config),
                        C.POINTER(mv_icp_system), _P], C.c_int),

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "mv_internal.cuh"
+#include "mv_pinned.h"
 
 namespace mv {
 constexpr int kMaxStreamSlots = 4;
@@ -134,6 +135,7 @@ struct mv_ctx {
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
     unsigned long long *d_points = nullptr;  // point count of mv_extract_points
+    mv::PinnedPool *pool = nullptr;          // pinned host buffers of swapped-out volumes
     // tracking scratch: the frame's vertex / normal maps, per-CTA ICP partials
     float *d_trk_v = nullptr, *d_trk_n = nullptr;
     size_t trk_px = 0;
@@ -411,11 +413,11 @@ void linear_to_bricks(const Volume &v, const T *src, T *dst)
         }
 }
 
-void free_host(Volume *v)
+void free_host(mv_ctx *c, Volume *v)
 {
-    if (v->h_fw) cudaFreeHost(v->h_fw);
-    if (v->h_rgba) cudaFreeHost(v->h_rgba);
-    if (v->h_flag) cudaFreeHost(v->h_flag);
+    c->pool->give(v->h_fw, v->fw_bytes);
+    c->pool->give(v->h_rgba, v->rgba_bytes);
+    c->pool->give(v->h_flag, v->flag_bytes);
     v->h_fw = nullptr;
     v->h_rgba = nullptr;
     v->h_flag = nullptr;
@@ -615,6 +617,7 @@ mv_status mv_create(const mv_config *cfg, int32_t device, mv_ctx **out)
     mv_ctx *x = new mv_ctx();
     x->cfg = c;
     x->device = device;
+    x->pool = new mv::PinnedPool();
     cudaError_t e = cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x->swap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->last_event, cudaEventDisableTiming);
@@ -653,7 +656,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (s) cudaStreamSynchronize(s);
     for (auto &kv : c->vols) {
         Volume *v = kv.second;
-        free_host(v);
+        free_host(c, v);
         if (v->ready) cudaEventDestroy(v->ready);
         delete v;
     }
@@ -677,6 +680,7 @@ mv_status mv_destroy(mv_ctx *c)
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->last_event) cudaEventDestroy(c->last_event);
     if (c->swap_stream) cudaStreamDestroy(c->swap_stream);
+    delete c->pool;  // after the volumes gave their host buffers back
     delete c;
     return MV_OK;
 }
@@ -813,6 +817,28 @@ mv_status mv_track(mv_ctx *c, const float *depth, const mv_intrinsics *K, const 
     return MV_OK;
 }
 
+mv_status mv_reserve_host(mv_ctx *c, const mv_volume_desc *d, int32_t count)
+{
+    if (!c || !d || count < 0 || count > 4096) return fail(c, MV_ERR_ARG, "bad arguments");
+    Volume shape;
+    shape.desc = *d;
+    shape.nbricks = 1;
+    shape.nsuper = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d->h_r[a] < 2 || d->h_r[a] > 8192) return fail(c, MV_ERR_ARG, "bad volume size");
+        shape.nb[a] = (d->h_r[a] + kBrick - 1) / kBrick;
+        shape.nbricks *= shape.nb[a];
+        shape.nsb[a] = (shape.nb[a] + kSuper - 1) / kSuper;
+        shape.nsuper *= shape.nsb[a];
+    }
+    if (d->fmt < MV_TSDF_F32 || d->fmt > MV_TSDF_I16) return fail(c, MV_ERR_ARG, "bad format");
+    cudaSetDevice(c->device);
+    const bool ok = c->pool->reserve((size_t)shape.nbricks * kBrickVox * fw_elem_bytes(d->fmt), count) &&
+                    c->pool->reserve((size_t)shape.nbricks * kBrickVox * 4, count) &&
+                    c->pool->reserve(flag_alloc_bytes(shape.nbricks, shape.nsuper), count);
+    return ok ? MV_OK : fail(c, MV_ERR_OOM, "pinned host allocation failed");
+}
+
 mv_status mv_get_config(const mv_ctx *c, mv_config *out)
 {
     if (!c || !out) return MV_ERR_ARG;
@@ -902,7 +928,7 @@ mv_status mv_remove_volume(mv_ctx *c, int32_t id)
     if (v->d_flag) MV_CUDA(c, cudaFreeAsync(v->d_flag, s));
     if (v->h_fw || v->h_rgba || v->h_flag) {
         MV_CUDA(c, cudaStreamSynchronize(s));  // in-flight copies may still read the host copy
-        free_host(v);
+        free_host(c, v);
     }
     if (v->ready) {
         cudaEventSynchronize(v->ready);
@@ -1441,12 +1467,11 @@ mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)
     if (!v->resident) return MV_OK;
     cudaSetDevice(c->device);
     if (!v->h_fw) {
-        cudaError_t e = cudaHostAlloc(&v->h_fw, v->fw_bytes, cudaHostAllocMapped);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_rgba, v->rgba_bytes, cudaHostAllocMapped);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&v->h_flag, v->flag_bytes, cudaHostAllocMapped);
-        if (e != cudaSuccess) {
-            free_host(v);
-            cudaGetLastError();
+        v->h_fw = c->pool->take(v->fw_bytes);
+        v->h_rgba = (uint32_t *)c->pool->take(v->rgba_bytes);
+        v->h_flag = (uint8_t *)c->pool->take(v->flag_bytes);
+        if (!v->h_fw || !v->h_rgba || !v->h_flag) {
+            free_host(c, v);
             return fail(c, MV_ERR_OOM, "pinned host allocation failed");
         }
     }

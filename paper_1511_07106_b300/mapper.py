@@ -138,6 +138,13 @@ class Mapper:
         self._fmt[out.value] = f
         return out.value
 
+    def reserve_host(self, h_r, fmt="f32", count=2):
+        """Pin `count` spare host buffer sets now for volumes of h_r voxels (see
+        mv_reserve_host)."""
+        f = _abi.FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        d = _abi.mv_volume_desc((C.c_int32 * 3)(0, 0, 0), (C.c_int32 * 3)(*[int(a) for a in h_r]), 1.0, f)
+        self._check(self._lib.mv_reserve_host(self._h, C.byref(d), int(count)))
+
     def remove_volume(self, vid: int):
         self._check(self._lib.mv_remove_volume(self._h, int(vid)))
         self._fmt.pop(vid, None)

@@ -518,3 +518,29 @@ def test_surface_count_skip_and_far_cull_are_exact():
     m.swap_in(ia)
     check_plane_hit()
     m.close()
+
+
+def test_reserved_pinned_buffers_roundtrip():
+    """Swap-outs served from reserved pinned buffers (and from buffers that
+    removed volumes gave back) keep the volumes bit for bit."""
+    wl = synth.single_volume_128(frames=4, res=64)
+    (vs,) = wl.volumes
+    m = Mapper()
+    m.reserve_host(vs.r, "f32", 1)
+    ids = [m.add_volume(vs.h, vs.r, vs.s) for _ in range(3)]
+    for i in range(4):
+        d, c = wl.frame(i)
+        m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+    ref = m.read_decoded(ids[0])
+    for vid in ids:
+        m.swap_out(vid)
+    m.remove_volume(ids[2])  # its host buffers go back to the spares
+    extra = m.add_volume(vs.h, vs.r, vs.s)
+    m.write_decoded(extra, *ref)
+    m.swap_out(extra)
+    for vid in (ids[0], ids[1], extra):
+        m.swap_in(vid)
+        for a, b in zip(m.read_decoded(vid), ref):
+            np.testing.assert_array_equal(a, b)
+    m.reserve_host(vs.r, "f32", 0)
+    m.close()
