@@ -291,9 +291,12 @@ def cpu_baseline_sample(wl, frames, m, vid, first):
 
 
 def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
-    """Same metric through the public API with host buffers: per step, copy the
-    frame from pinned host memory, integrate, raycast, read depth/normal/colour
-    back to pinned host memory."""
+    """Same metric through the public API with host buffers: every step copies
+    its frame from pinned host memory, integrates and raycasts it (mv_frame),
+    and reads depth / normal / colour back to pinned host memory, where the
+    host reads them.  Steps are pipelined over three streams with two buffer
+    sets: the upload of step i+1 and the read-back of step i-1 overlap the
+    kernels of step i."""
     (vs,) = wl.volumes
     cam = wl.cam
     m = Mapper(Config())
@@ -301,30 +304,55 @@ def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
     H, W = cam.height, cam.width
     hd = [torch.from_numpy(f[0]).pin_memory() for f in frames]
     hc = [torch.from_numpy(f[1]).pin_memory() for f in frames]
-    dd = torch.empty((H, W), dtype=torch.float32, device="cuda")
-    dc = torch.empty((H, W, 3), dtype=torch.uint8, device="cuda")
-    maps = m.alloc_maps(cam, vertex=False)
-    out_d = torch.empty((H, W), dtype=torch.float32).pin_memory()
-    out_n = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
-    out_c = torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()
+    dd = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(2)]
+    dc = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    maps = [m.alloc_maps(cam, vertex=False) for _ in range(2)]
+    out = [(torch.empty((H, W), dtype=torch.float32).pin_memory(),
+            torch.empty((H, W, 3), dtype=torch.float32).pin_memory(),
+            torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()) for _ in range(2)]
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    loaded, used, ran, read = ([ev() for _ in range(2)] for _ in range(4))
+    seen = [False, False]
+    checksum = 0.0
 
     def step(i):
-        dd.copy_(hd[i], non_blocking=True)
-        dc.copy_(hc[i], non_blocking=True)
-        m.frame(dd, dc, cam, wl.poses[i % N_FRAMES_MAX], out=maps)
-        out_d.copy_(maps["depth"], non_blocking=True)
-        out_n.copy_(maps["normal"], non_blocking=True)
-        out_c.copy_(maps["rgba"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        nonlocal checksum
+        b = i % 2
+        if seen[b]:
+            read[b].synchronize()        # the host has step i-2's result
+            checksum += float(out[b][0][0, 0])
+        with torch.cuda.stream(s_in):
+            if seen[b]:
+                s_in.wait_event(used[b])  # step i-2 is done with this input buffer
+            dd[b].copy_(hd[i], non_blocking=True)
+            dc[b].copy_(hc[i], non_blocking=True)
+            loaded[b].record(s_in)
+        s_run.wait_event(loaded[b])
+        if seen[b]:
+            s_run.wait_event(read[b])     # the maps of step i-2 were read back
+        m.frame(dd[b], dc[b], cam, wl.poses[i % N_FRAMES_MAX], out=maps[b], stream=s_run)
+        used[b].record(s_run)
+        ran[b].record(s_run)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ran[b])
+            out[b][0].copy_(maps[b]["depth"], non_blocking=True)
+            out[b][1].copy_(maps[b]["normal"], non_blocking=True)
+            out[b][2].copy_(maps[b]["rgba"], non_blocking=True)
+            read[b].record(s_out)
+        seen[b] = True
 
     for i in range(warmup):
         step(i)
+    torch.cuda.synchronize()
     m.stats(reset=True)
     barrier(torch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(steps):
         step(warmup + k)
+    for b in range(2):
+        read[b].synchronize()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     barrier(torch)
