@@ -127,7 +127,7 @@ enum {
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
     MV_KERNEL_CELL_FLAGS = 5,  /* raycast step-over flags refreshed after an integration */
     MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
-    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 7 kernels are also counted by kind) */
+    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 kernels are also counted by kind) */
     MV_KERNEL_DEPTH_MAX = 8,   /* farthest accepted depth of the frame (far bound of the brick list) */
     MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
     MV_KERNEL_DEPTH_MAPS = 10, /* vertex / normal maps of a depth frame */
@@ -209,7 +209,7 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
 
 /* One frame of the paper's per-frame loop: integrate the frame into every
  * resident volume, then raycast every resident volume at the same pose, as
- * one CUDA graph launch (7 kernels).  Same semantics and outputs as
+ * one CUDA graph launch (6 kernels).  Same semantics and outputs as
  * mv_integrate followed by mv_raycast.  The graph is built on the first call
  * and rebuilt when the set of resident volumes or the image size changes;
  * otherwise each call only updates the graph's kernel parameters (pose and

@@ -685,23 +685,18 @@ static dim3 raycast_grid(int tile, int width, int height)
     return dim3((width + tw - 1) / tw, (height + th - 1) / th);
 }
 
-cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node,
-                             cudaGraphNode_t dep, const VolDev *vols, int nvol, const FrameParams &P,
-                             VolFrame *vf, VisList *vis);
-
-// Graph nodes of one raycast of all volumes: setup -> raycast.
-cudaError_t graph_raycast(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[2],
-                          cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
-                          const FrameParams &P, float *depth, float *normal, uint8_t *rgba,
-                          float *vertex, int *vol_id, Stats *stats, int tile, VisList *vis)
+// Graph node of the raycast of all volumes, after `dep`, reusing the camera
+// constants and view list that the frame's setup node computed for the same
+// view (the integration changes neither).
+cudaError_t graph_raycast(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t *node, cudaGraphNode_t dep,
+                          const VolDev *vols, int nvol, VolFrame *vf, const FrameParams &P, float *depth,
+                          float *normal, uint8_t *rgba, float *vertex, int *vol_id, Stats *stats, int tile,
+                          VisList *vis)
 {
-    cudaError_t e = frame_setup_node(g, exec, &nodes[0], dep, vols, nvol, P, vf, vis);
-    if (e != cudaSuccess) return e;
     RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
     NodeArgs<const VolDev *, const VolFrame *, int, FrameParams, RayOut, int, Stats *, const VisList *> a(
         vols, vf, nvol, P, o, 0, stats, vis);
-    return graph_node(g, exec, &nodes[1], nodes[0],
-                      a.params(raycast_fn(tile), raycast_grid(tile, P.width, P.height), 128));
+    return graph_node(g, exec, node, dep, a.params(raycast_fn(tile), raycast_grid(tile, P.width, P.height), 128));
 }
 
 cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams &P,

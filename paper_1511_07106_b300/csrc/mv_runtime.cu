@@ -70,7 +70,7 @@ constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
                             unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *);
-cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[2], cudaGraphNode_t,
+cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
                           uint8_t *, float *, int *, Stats *, int, VisList *);
 }  // namespace mv
@@ -123,7 +123,7 @@ struct mv_ctx {
     struct FrameGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t nodes[7] = {};
+        cudaGraphNode_t nodes[6] = {};
         unsigned long long table_version = ~0ull;
         int width = 0, height = 0, grid_int = 0, tile = 0;
     } fg;
@@ -1108,7 +1108,7 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
                                c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
                                c->num_sms, c->d_vis));
-    MV_CUDA(c, graph_raycast(fg.g, upd, fg.nodes + 5, fg.nodes[4], c->d_table, nvol, c->d_vf, P,
+    MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[5], fg.nodes[4], c->d_table, nvol, c->d_vf, P,
                              depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
         MV_CUDA(c, cudaGraphInstantiate(&fg.exec, fg.g, 0));
@@ -1119,8 +1119,8 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
         fg.tile = c->ray_tile;
     }
     MV_CUDA(c, counted_launch(c, MV_KERNEL_FRAME_GRAPH, s, [&] { return cudaGraphLaunch(fg.exec, s); }));
-    const int kinds[7] = {MV_KERNEL_SETUP, MV_KERNEL_DEPTH_MAX, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE,
-                          MV_KERNEL_CELL_FLAGS, MV_KERNEL_SETUP, MV_KERNEL_RAYCAST};
+    const int kinds[6] = {MV_KERNEL_SETUP, MV_KERNEL_DEPTH_MAX, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE,
+                          MV_KERNEL_CELL_FLAGS, MV_KERNEL_RAYCAST};
     for (int k : kinds) c->launches[k] += 1;
     return end_call(c, s);
 }
