@@ -284,7 +284,7 @@ def cpu_baseline_sample(wl, frames, m, vid, first):
     t0 = time.perf_counter()
     oracle.raycast([full], wl.cam, T, cfg, ids=[vid], pixels=pix)
     t_ray = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     sample = ("one step: frame integrated into 8 z-slabs x 8 voxels (1/8 of the 512^3 volume) + "
               "raycast of every 8th pixel (1/8 of 640x480); FP64 C oracle, OpenMP")
     return upd / (t_int + t_ray), t_int + t_ray, sample, cores
@@ -747,7 +747,7 @@ def main_reference(args, rank):
             upd_total += int(cnt[0])
             t_total += dt
     value = upd_total / t_total if t_total > 0 else 0.0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     sample = ("per step: the frame integrated into one 8-voxel z-slab (1/64 of the 512^3 volume) and "
               "every 64th pixel raycast; FP64 C oracle, OpenMP")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -875,9 +875,14 @@ def main():
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         v, secs, sample, cores = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
+        oracle.set_threads(1)
+        v1, secs1, _, _ = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
+        oracle.set_threads(cores)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample, "seconds": secs}
+                                "sample": sample, "seconds": secs, "one_core_value": v1,
+                                "one_core_seconds": secs1}
     if not args.no_extra:
         m.close()
         torch.cuda.empty_cache()

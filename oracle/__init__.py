@@ -90,6 +90,8 @@ def _load():
                                             i64p, u8p]
         _lib.orc_extract_points.argtypes = [C.POINTER(_Volume), dp, u8p, i64p, C.c_int64]
         _lib.orc_extract_points.restype = C.c_int64
+        _lib.orc_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_depth_maps.argtypes = [fp, C.POINTER(_Intr), dp, C.c_double, C.c_double, dp, dp]
         _lib.orc_icp_system.argtypes = [dp, dp, C.POINTER(_Intr), dp, fp, fp, dp, C.c_double, C.c_double,
                                         dp, dp, dp, i64p, u8p, dp, dp, dp]
@@ -469,3 +471,13 @@ def track(depth, cam, model_vertex, model_normal, T_model, T_init, iterations, d
         x = np.linalg.solve(L.T, np.linalg.solve(L, last["b"]))
         T = se3_exp(x) @ T
     return T, last
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(_load().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's OpenMP loops."""
+    _load().orc_set_threads(int(n))

@@ -46,6 +46,9 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_EXPORT __attribute__((visibility("default")))
 
@@ -877,4 +880,24 @@ ORC_EXPORT void orc_icp_system(const double *vertex, const double *normal, const
                 abse[1] += 1.0;
             }
         }
+}
+
+/* Threads an OpenMP loop of this library uses (1 without OpenMP). */
+ORC_EXPORT int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Set the threads of this library's OpenMP loops (n >= 1). */
+ORC_EXPORT void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
