@@ -246,31 +246,48 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     const float mu = P.trunc_vox, inv_mu = 1.0f / P.trunc_vox;
     const bool row_in = gy < v.r[1] && gz < v.r[2];
     u.upd = u.band = u.inside = 0u;
+    // three phases so that the four depth loads are in flight together:
+    // projections, loads (pixel 0 stands in for voxels that project nowhere),
+    // then the distance and gating
+    float Xj[4], Yj[4], Zj[4], izj[4];
+    int pj[4];
+    bool okj[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        u.f[j] = 0.f;
-        u.pix[j] = 0;
-        if (!(row_in && gx + j < v.r[0])) continue;
-        u.inside |= 1u << j;
         const float X = X0 + (float)j * P.Rf[0];
         const float Y = Y0 + (float)j * P.Rf[1];
         const float Z = Z0 + (float)j * P.Rf[2];
-        if (!(Z > 0.f)) continue;
+        const bool in = row_in && gx + j < v.r[0];
+        if (in) u.inside |= 1u << j;
         const float iz = __fdividef(1.0f, Z);  // ~2 ulp; decisions near pixel edges are margins
         const float uf = fmaf(P.fx * X, iz, P.cx);
         const float vf = fmaf(P.fy * Y, iz, P.cy);
         const int ui = __float2int_rd(uf + 0.5f), vi = __float2int_rd(vf + 0.5f);
-        if (ui < 0 || vi < 0 || ui >= P.width || vi >= P.height) continue;
-        const int p = vi * P.width + ui;
-        const float D = __ldg(depth + p);
-        if (!(D > 0.f) || D < P.z_min || D > P.z_max) continue;
+        const bool ok = in && (Z > 0.f) && ui >= 0 && vi >= 0 && ui < P.width && vi < P.height;
+        Xj[j] = X;
+        Yj[j] = Y;
+        Zj[j] = Z;
+        izj[j] = iz;
+        okj[j] = ok;
+        pj[j] = ok ? vi * P.width + ui : 0;
+    }
+    float Dj[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Dj[j] = __ldg(depth + pj[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        u.f[j] = 0.f;
+        u.pix[j] = 0;
+        const float D = Dj[j];
+        if (!okj[j] || !(D > 0.f) || D < P.z_min || D > P.z_max) continue;
+        const float X = Xj[j], Y = Yj[j], Z = Zj[j];
         // projective distance along the voxel's ray, in voxels
         const float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-        const float lam = n2 * rsqrtf(n2) * iz;  // |p_c| / z
+        const float lam = n2 * rsqrtf(n2) * izj[j];  // |p_c| / z
         const float sdf = (D * v.inv_s - Z) * lam;
         if (sdf < -mu) continue;
         u.f[j] = fminf(1.0f, sdf * inv_mu);
-        u.pix[j] = p;
+        u.pix[j] = pj[j];
         u.upd |= 1u << j;
         if (fabsf(sdf) < mu) u.band |= 1u << j;
     }
