@@ -162,7 +162,7 @@ def timed(torch, fn, clocks=None):
 
 
 def bench_storage(torch, Mapper, Config, wl, poses, fmt, warmup, steps, dev_depth, dev_rgb,
-                  clocks=None, instrument=True):
+                  clocks=None, instrument=True, tuning=None):
     """Device-timed steps for one storage format: `steps` graph steps (the
     measured throughput), then `steps` eager steps on the following frames
     with per-kernel CUDA events (the per-kernel roofline)."""
@@ -172,7 +172,11 @@ def bench_storage(torch, Mapper, Config, wl, poses, fmt, warmup, steps, dev_dept
     vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
     maps = m.alloc_maps(cam)
     run_graph_steps(m, poses, cam, maps, 0, warmup, dev_depth, dev_rgb)
-    tuning = m.autotune(dev_depth[warmup - 1], dev_rgb[warmup - 1], cam, poses[warmup - 1])
+    if tuning is None:
+        tuning = m.autotune(dev_depth[warmup - 1], dev_rgb[warmup - 1], cam, poses[warmup - 1])
+    else:  # fixed launch shapes (profiling runs: timings under a profiler mislead the autotuner)
+        m.set_tuning(*tuning)
+        tuning = m.tuning()
     m.synchronize()
     m.stats(reset=True)
     m.timings(reset=True)
@@ -770,6 +774,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the f16/i16 storage runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--tuning", type=lambda t: tuple(int(x) for x in t.split(",")), default=None,
+                    help="fixed raycast tile and integration CTAs per SM (e.g. 0,8) instead of autotuning")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the uneven-volume, differentiable and swap measurements")
     args = ap.parse_args()
@@ -810,7 +816,7 @@ def main():
     except Exception:
         clocks = ClockSampler(local_rank)
     res = bench_storage(torch, Mapper, Config, wl, poses, "f32", args.warmup, args.steps,
-                        dev_depth, dev_rgb, clocks=clocks)
+                        dev_depth, dev_rgb, clocks=clocks, tuning=args.tuning)
     ms_max = allreduce_max(torch, res["ms"])
     value = weak_scaling_value(torch, res["stats"]["updated"], res["ms"])
     kern = kernel_summary(res, "f32", cam, args.steps)
