@@ -100,7 +100,8 @@ typedef struct {
     mv_volume_desc desc;
     int32_t resident;    /* 1: in GPU memory, 0: swapped out to pinned host memory */
     int32_t reserved;
-    uint64_t device_bytes; /* GPU bytes held by the volume */
+    uint64_t device_bytes; /* GPU bytes held by the volume (voxels, colour, flags and the raycast's
+                              derived bit masks of 256 bytes per 8^3 brick) */
     uint64_t host_bytes;   /* pinned host bytes held by the volume */
 } mv_volume_info;
 

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(256) frame_setup_kernel(const VolDev *__restri
     if (threadIdx.x == 0 && counter) {
         counter[0] = 0u;  // work-list length
         counter[1] = 0u;  // bits of the frame's largest accepted depth (depth_max_kernel)
+        counter[2] = 0u;  // bricks whose voxel masks the integration changed
     }
     if (!vis) return;
     __syncthreads();
@@ -311,6 +312,33 @@ __device__ __forceinline__ uint32_t blend_rgba(uint32_t old, const uint8_t *__re
     return out;
 }
 
+// Where an integration lists the bricks whose voxel masks it changed (count
+// null: the volume set keeps no masks or nothing needs the list).
+struct MaskOut {
+    uint2 *list;
+    unsigned *count;
+    unsigned stamp_id;
+};
+
+// A CTA collects the bricks whose voxel masks it changed in shared memory and
+// appends them to the global list in one piece (no atomic round trip on the
+// per-brick critical path).
+constexpr int kChgBuf = 128;
+struct ChgBuf {
+    int flag[2];           // "voxel masks changed" of the current and the next brick
+    unsigned n;            // entries in `items`
+    unsigned base;         // global position of the final flush
+    uint2 items[kChgBuf];
+};
+
+// Thread 0 only: append the collected entries to the global list.
+__device__ __forceinline__ void flush_changed(ChgBuf &cb, const MaskOut &mo)
+{
+    const unsigned base = atomicAdd(mo.count, cb.n);
+    for (unsigned k = 0; k < cb.n; ++k) mo.list[base + k] = cb.items[k];
+    cb.n = 0;
+}
+
 template <int FMT>
 __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame &fr,
                                                 const FrameParams &P, unsigned packed,
@@ -318,12 +346,15 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
                                                 const uint8_t *__restrict__ rgb,
                                                 unsigned long long &n_swept,
                                                 unsigned long long &n_upd,
-                                                unsigned long long &n_band)
+                                                unsigned long long &n_band,
+                                                const MaskOut &mo, uint2 item, ChgBuf &cb, int parity)
 {
     const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = (int)(packed >> 20);
     const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
     const int t = threadIdx.x;
     const long long vox0 = b * kBrickVox + 4 * t;  // first of this thread's 4 voxels
+    // the brick's old flag byte, read early: thread 0 updates it after the barriers
+    const uint8_t old_flag = t == 0 ? v.bflag[b] : 0;
     // issue this thread's 32 (16) bytes of brick storage before the projection
     // so that the HBM latency overlaps the depth-image gather
     float4 a32, c32;
@@ -338,43 +369,86 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
     VoxelUpdate u;
     project_voxels(v, fr, P, bx, by, bz, depth, u);
     bool all_pos = true;  // every voxel this thread updated is stored > 0
+    bool mchg = false;    // the update changed a voxel's "observed" or "F <= 0" bit
+    bool pair_chg = false;  // ... of this thread or of its partner (same 8-voxel row)
+    unsigned mine = 0u;   // after a change: "observed" bits of the 4 voxels, "F <= 0" bits << 4
+    const bool track = mo.count && v.vmask;  // voxel masks kept and changes listed
 
-    if (u.upd) {
+    {
         const float wmax = P.w_max;
         if (FMT == MV_TSDF_F32) {
-            float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(v.fw) + vox0);
             float F[4] = {a32.x, a32.z, c32.x, c32.z}, W[4] = {a32.y, a32.w, c32.y, c32.w};
+            if (u.upd) {
+                float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(v.fw) + vox0);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (!((u.upd >> j) & 1u)) continue;
-                // (F W + f) / (W + 1) in increment form
-                const float Fn = F[j] + __fdividef(u.f[j] - F[j], W[j] + 1.0f);
-                W[j] = fminf(W[j] + 1.0f, wmax);
-                F[j] = Fn;
-                all_pos &= Fn > 0.f;
+                for (int j = 0; j < 4; ++j) {
+                    if (!((u.upd >> j) & 1u)) continue;
+                    // (F W + f) / (W + 1) in increment form
+                    const float Fn = F[j] + __fdividef(u.f[j] - F[j], W[j] + 1.0f);
+                    mchg |= !(W[j] > 0.f) || ((F[j] <= 0.f) != (Fn <= 0.f));
+                    W[j] = fminf(W[j] + 1.0f, wmax);
+                    F[j] = Fn;
+                    all_pos &= Fn > 0.f;
+                }
+                p[0] = make_float4(F[0], W[0], F[1], W[1]);
+                p[1] = make_float4(F[2], W[2], F[3], W[3]);
             }
-            p[0] = make_float4(F[0], W[0], F[1], W[1]);
-            p[1] = make_float4(F[2], W[2], F[3], W[3]);
-        } else {
-            uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(v.fw) + vox0);
-            uint32_t q[4] = {a16.x, a16.y, a16.z, a16.w};
+            if (track) pair_chg = __shfl_xor_sync(0xffffffffu, (int)mchg, 1) || mchg;
+            if (pair_chg) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (!((u.upd >> j) & 1u)) continue;
-                float F, W;
-                if (FMT == MV_TSDF_F16) decode_f16(q[j], F, W); else decode_i16(q[j], F, W);
-                const float Fn = F + __fdividef(u.f[j] - F, W + 1.0f);
-                const float Wn = fminf(W + 1.0f, wmax);
-                if (FMT == MV_TSDF_F16) {
-                    q[j] = encode_f16(Fn, Wn);
-                    all_pos &= stored_f16(Fn) > 0.f;
-                } else {
-                    q[j] = encode_i16(Fn, Wn);
-                    all_pos &= stored_i16(Fn) > 0.f;
+                for (int j = 0; j < 4; ++j)
+                    mine |= ((W[j] > 0.f ? 1u : 0u) | ((W[j] > 0.f) & (F[j] <= 0.f) ? 16u : 0u)) << j;
+            }
+        } else {
+            uint32_t q[4] = {a16.x, a16.y, a16.z, a16.w};
+            // both codes store F in the low 16 bits with the sign of an int16
+            // (a half's sign bit; +-0 and the int16 code 0 compare <= 0)
+            if (u.upd) {
+                uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(v.fw) + vox0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (!((u.upd >> j) & 1u)) continue;
+                    float F, W;
+                    if (FMT == MV_TSDF_F16) decode_f16(q[j], F, W); else decode_i16(q[j], F, W);
+                    const float Fn = F + __fdividef(u.f[j] - F, W + 1.0f);
+                    const float Wn = fminf(W + 1.0f, wmax);
+                    const uint32_t q0 = q[j];
+                    if (FMT == MV_TSDF_F16) {
+                        q[j] = encode_f16(Fn, Wn);
+                        all_pos &= stored_f16(Fn) > 0.f;
+                    } else {
+                        q[j] = encode_i16(Fn, Wn);
+                        all_pos &= stored_i16(Fn) > 0.f;
+                    }
+                    mchg |= (q0 >> 16) == 0u || (((short)(q0 & 0xFFFFu) <= 0) != ((short)(q[j] & 0xFFFFu) <= 0));
+                }
+                *p = make_uint4(q[0], q[1], q[2], q[3]);
+            }
+            if (track) pair_chg = __shfl_xor_sync(0xffffffffu, (int)mchg, 1) || mchg;
+            if (pair_chg) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool obs = (q[j] >> 16) != 0u;
+                    mine |= ((obs ? 1u : 0u) | (obs & ((short)(q[j] & 0xFFFFu) <= 0) ? 16u : 0u)) << j;
                 }
             }
-            *p = make_uint4(q[0], q[1], q[2], q[3]);
         }
+    }
+    // a brick whose voxel masks changed raises its flag in cb.flag[parity]
+    // (read after the barriers below; see integrate_kernel for its reset),
+    // and each changed 8-voxel row (held by the thread pair 2k, 2k + 1) is
+    // stored by the even thread: its "observed" and "F <= 0" bytes
+    if (pair_chg) {
+        const unsigned other = __shfl_xor_sync(__activemask(), mine, 1);
+        if ((t & 1) == 0) {
+            uint8_t *row = reinterpret_cast<uint8_t *>(v.vmask + b * 16) + (t >> 1);
+            row[0] = (uint8_t)((mine & 0xFu) | ((other & 0xFu) << 4));
+            row[64] = (uint8_t)((mine >> 4) | (other & 0xF0u));
+        }
+        if (mchg) cb.flag[parity] = 1;
+    }
+
+    if (u.upd) {
         if (rgb && u.band) {
             uint4 *pc = reinterpret_cast<uint4 *>(v.rgba + vox0);
             uint4 c = *pc;
@@ -395,10 +469,19 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
     // every updated voxel stayed positive; EMPTY while no voxel was ever
     // updated; NONEG like FREE but without requiring every voxel observed
     const int brick_all = __syncthreads_and(u.upd == 0xFu ? 1 : 0);
+    if (t == 0) cb.flag[parity ^ 1] = 0;  // the next brick's flag, read by everyone before this barrier
     const int brick_any = __syncthreads_or(u.upd != 0u ? 1 : 0);
     const int brick_pos = __syncthreads_and(all_pos ? 1 : 0);
+    if (track && cb.flag[parity]) {
+        // the brick is stamped and listed for the cell-mask refresh
+        if (t == 0) {
+            v.stamp[b] = mo.stamp_id;
+            if (cb.n == kChgBuf) flush_changed(cb, mo);
+            cb.items[cb.n++] = item;
+        }
+    }
     if (t == 0) {
-        const uint8_t old = v.bflag[b];
+        const uint8_t old = old_flag;
         uint8_t nf = 0;
         if (brick_pos && (brick_all || (old & kFlagFree))) nf |= kFlagFree;
         if ((old & kFlagEmpty) && !brick_any) nf |= kFlagEmpty;
@@ -414,10 +497,21 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
                                                         const unsigned *__restrict__ counter,
                                                         FrameParams P, const float *__restrict__ depth,
                                                         const uint8_t *__restrict__ rgb,
-                                                        Stats *__restrict__ stats)
+                                                        Stats *__restrict__ stats, MaskOut mo)
 {
     __shared__ VolDev s_v;
     __shared__ VolFrame s_f;
+    // per-brick "voxel masks changed" flags, used alternately by consecutive
+    // bricks: brick k raises cb.flag[k & 1] before its first barrier, reads it
+    // after its third, and thread 0 clears cb.flag[(k + 1) & 1] after brick
+    // k's first barrier (all reads of it by brick k - 1 are done, no write of
+    // brick k + 1 has started)
+    __shared__ ChgBuf cb;
+    if (threadIdx.x == 0) {  // published by the first volume-change barrier (or the final one)
+        cb.flag[0] = cb.flag[1] = 0;
+        cb.n = 0;
+    }
+    int parity = 0;
     int cached = -1;
     const unsigned n = *counter;
     unsigned long long n_swept = 0, n_upd = 0, n_band = 0, n_bricks = 0;
@@ -437,11 +531,19 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
         const VolDev &v = s_v;
         const VolFrame fr = s_f;
         switch (v.fmt) {
-        case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
-        case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
-        default: integrate_brick<MV_TSDF_I16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band); break;
+        case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
+        case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
+        default: integrate_brick<MV_TSDF_I16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
         }
+        parity ^= 1;
         ++n_bricks;
+    }
+    if (mo.count) {
+        // the CTA's remaining changed bricks, appended together
+        __syncthreads();
+        if (threadIdx.x == 0 && cb.n) cb.base = atomicAdd(mo.count, cb.n);
+        __syncthreads();
+        for (unsigned k = threadIdx.x; k < cb.n; k += blockDim.x) mo.list[cb.base + k] = cb.items[k];
     }
     // one atomic per warp
 #pragma unroll
@@ -522,9 +624,8 @@ __device__ __forceinline__ unsigned *super_count_of(const VolDev &v, int cx, int
 // word, whose returned old value tells exactly one of several threads that
 // refresh the same cell brick that the flag changed; that thread moves the
 // super-brick count.
-__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz)
+__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz, bool skip)
 {
-    const bool skip = cell_skip_of(v, cx, cy, cz);
     uint8_t *pb = v.cflag + ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
     if (!v.sup) {
         *pb = skip ? kCellSkip : 0;
@@ -536,8 +637,48 @@ __device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy
     if (((old & bit) != 0u) != skip) atomicAdd(super_count_of(v, cx, cy, cz), skip ? 0xFFFFFFFFu : 1u);
 }
 
-// After an integration: refresh the cell-brick flags that the listed bricks
-// feed (each listed brick b is read by the cell bricks b - {0,1}^3).
+// Row z (0..7) of the voxel mask `plane` (0 observed, 1 observed with F <= 0)
+// of brick (bx, by, bz); bricks beyond the volume hold no observed voxel.
+__device__ __forceinline__ unsigned long long vmask_row(const VolDev &v, int bx, int by, int bz, int plane,
+                                                        int z)
+{
+    if (bx >= v.nb[0] || by >= v.nb[1] || bz >= v.nb[2]) return 0ull;
+    const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
+    return __ldg(v.vmask + b * 16 + plane * 8 + z);
+}
+
+// Cell masks of slice z of cell brick (cx, cy, cz) from the voxel masks of
+// the bricks (cx, cy, cz) + {0,1}^3: the corners of cell (x, y, z) are the
+// voxels (x + i, y + j, z + k); the +x / +y / +xy corners of a voxel row are
+// the row shifted by one bit / one byte, with the bits that leave the brick
+// taken from the neighbour brick's first column / row.
+__device__ __forceinline__ ulonglong2 cell_mask_slice(const VolDev &v, int cx, int cy, int cz, int z)
+{
+    constexpr unsigned long long kCol0 = 0x0101010101010101ull, kCol7 = 0x8080808080808080ull;
+    unsigned long long V = ~0ull, N = 0ull;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+        const int zz = z + dz, bz = cz + (zz >> 3), sz = zz & 7;
+#pragma unroll
+        for (int plane = 0; plane < 2; ++plane) {
+            const unsigned long long a = vmask_row(v, cx, cy, bz, plane, sz);
+            const unsigned long long ax = vmask_row(v, cx + 1, cy, bz, plane, sz);
+            const unsigned long long ay = vmask_row(v, cx, cy + 1, bz, plane, sz);
+            const unsigned long long axy = vmask_row(v, cx + 1, cy + 1, bz, plane, sz);
+            const unsigned long long sx = ((a >> 1) & ~kCol7) | ((ax & kCol0) << 7);   // (x + 1, y)
+            const unsigned long long ux = ((ay >> 1) & ~kCol7) | ((axy & kCol0) << 7); // (x + 1, y) of +y
+            const unsigned long long sy = (a >> 8) | (ay << 56);                      // (x, y + 1)
+            const unsigned long long sxy = (sx >> 8) | (ux << 56);                    // (x + 1, y + 1)
+            if (plane == 0) V &= a & sx & sy & sxy;
+            else N |= a | sx | sy | sxy;
+        }
+    }
+    return make_ulonglong2(V, N);
+}
+
+// After an integration, for volumes without cell masks: refresh the
+// cell-brick flags that the listed bricks feed (each listed brick b is read
+// by the cell bricks b - {0,1}^3) from the brick summaries.
 __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restrict__ vols,
                                                          const uint2 *__restrict__ list,
                                                          const unsigned *__restrict__ counter)
@@ -549,12 +690,97 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
         const uint2 it = list[i >> 3];
         const int d = (int)(i & 7);
         const VolDev &v = vols[it.x];
-        if (!v.cflag) continue;
+        if (!v.cflag || v.cmask) continue;
         const int cx = (int)(it.y & 1023u) - (d & 1);
         const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
         const int cz = (int)(it.y >> 20) - ((d >> 2) & 1);
         if (cx < 0 || cy < 0 || cz < 0) continue;
-        update_cell_flag(v, cx, cy, cz);
+        update_cell_flag(v, cx, cy, cz, cell_skip_of(v, cx, cy, cz));
+    }
+}
+
+// After an integration, for volumes with cell masks: the integration listed
+// the bricks whose voxel masks changed (and stamped them with stamp_id);
+// every cell brick c that reads one of them (c = b - d, d in {0,1}^3) gets its
+// cell masks and its flag recomputed, once: by the smallest d for which
+// c + d changed.  One thread per (changed brick, d, slice).
+__global__ void __launch_bounds__(256) cell_masks_kernel(const VolDev *__restrict__ vols,
+                                                         const uint2 *__restrict__ changed,
+                                                         const unsigned *__restrict__ counter,
+                                                         unsigned stamp_id)
+{
+    const unsigned long long n = 64ull * (*counter);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const uint2 it = changed[i >> 6];
+        const int d = (int)((i >> 3) & 7), z = (int)(i & 7);
+        const VolDev &v = vols[it.x];
+        const int cx = (int)(it.y & 1023u) - (d & 1);
+        const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
+        const int cz = (int)(it.y >> 20) - ((d >> 2) & 1);
+        if (cx < 0 || cy < 0 || cz < 0) continue;  // uniform over the 8 slices
+        const unsigned group = 0xFFu << (threadIdx.x & 24u);  // the 8 slices of this cell brick
+        if (d) {
+            // lane z tests whether c + z (z < d) changed too
+            bool earlier = false;
+            const int x = cx + (z & 1), y = cy + ((z >> 1) & 1), w = cz + (z >> 2);
+            if (z < d && x < v.nb[0] && y < v.nb[1] && w < v.nb[2])
+                earlier = __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) == stamp_id;
+            if (__ballot_sync(group, earlier)) continue;
+        }
+        const long long c = ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
+        const ulonglong2 m = cell_mask_slice(v, cx, cy, cz, z);
+        v.cmask[c * 8 + z] = m;
+        // the cell brick can be stepped over when none of its cells has an
+        // observed corner with F <= 0 (OR of the 8 slices' N rows)
+        unsigned long long nz = m.y;
+        nz |= __shfl_xor_sync(group, nz, 1);
+        nz |= __shfl_xor_sync(group, nz, 2);
+        nz |= __shfl_xor_sync(group, nz, 4);
+        if (z == 0) update_cell_flag(v, cx, cy, cz, nz == 0ull);
+    }
+}
+
+// Voxel masks of every brick of one volume from its stored voxels (after a
+// host write or a swap-in); 128 threads per brick, one ballot per 4 rows.
+__global__ void __launch_bounds__(128) vmask_all_kernel(VolDev v)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long b = blockIdx.x; b < v.nbricks; b += gridDim.x) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = i * 128 + (int)threadIdx.x;  // voxel (k & 7, (k >> 3) & 7, k >> 6)
+            bool valid, pos;
+            const long long off = b * kBrickVox + k;
+            if (v.fmt == MV_TSDF_F32) voxel_state<MV_TSDF_F32>(v, off, valid, pos);
+            else if (v.fmt == MV_TSDF_F16) voxel_state<MV_TSDF_F16>(v, off, valid, pos);
+            else voxel_state<MV_TSDF_I16>(v, off, valid, pos);
+            const unsigned o = __ballot_sync(0xffffffffu, valid);
+            const unsigned ng = __ballot_sync(0xffffffffu, valid && !pos);
+            if (lane == 0) {
+                // 32 voxels = rows 4 (w & 1) .. + 3 of slice 2 i + (w >> 1)
+                unsigned *rows = reinterpret_cast<unsigned *>(v.vmask + b * 16);
+                const int word = 2 * (2 * i + (w >> 1)) + (w & 1);
+                rows[word] = o;
+                rows[16 + word] = ng;
+            }
+        }
+    }
+}
+
+// Cell masks of every brick of one volume (after vmask_all_kernel).
+__global__ void __launch_bounds__(256) cmask_all_kernel(VolDev v)
+{
+    const long long n = v.nbricks * 8;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const long long b = i >> 3;
+        const int z = (int)(i & 7);
+        const int cx = (int)(b % v.nb[0]);
+        const int cy = (int)((b / v.nb[0]) % v.nb[1]);
+        const int cz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
+        v.cmask[i] = cell_mask_slice(v, cx, cy, cz, z);
     }
 }
 
@@ -705,9 +931,29 @@ cudaError_t launch_depth_max(const float *depth, const FrameParams &P, unsigned 
 
 cudaError_t launch_integrate(const VolDev *vols, const VolFrame *vfs, const uint2 *list,
                              const unsigned *counter, const FrameParams &P, const float *depth,
-                             const uint8_t *rgb, Stats *stats, int grid, cudaStream_t s)
+                             const uint8_t *rgb, Stats *stats, int grid, cudaStream_t s,
+                             uint2 *changed, unsigned *chg_count, unsigned stamp_id)
 {
-    integrate_kernel<<<grid, 128, 0, s>>>(vols, vfs, list, counter, P, depth, rgb, stats);
+    integrate_kernel<<<grid, 128, 0, s>>>(vols, vfs, list, counter, P, depth, rgb, stats,
+                                          MaskOut{changed, chg_count, stamp_id});
+    return cudaGetLastError();
+}
+
+// Voxel and cell masks of a whole volume from its stored voxels.
+cudaError_t launch_mask_rebuild(const VolDev &v, int num_sms, cudaStream_t s)
+{
+    if (!v.vmask || !v.cmask) return cudaSuccess;
+    long long blocks = v.nbricks;
+    const long long cap = (long long)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    vmask_all_kernel<<<(unsigned)blocks, 128, 0, s>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long cblocks = (v.nbricks * 8 + 255) / 256;
+    if (cblocks > cap) cblocks = cap;
+    if (cblocks < 1) cblocks = 1;
+    cmask_all_kernel<<<(unsigned)cblocks, 256, 0, s>>>(v);
     return cudaGetLastError();
 }
 
@@ -733,13 +979,22 @@ cudaError_t launch_brick_flags(const VolDev &v, int num_sms, cudaStream_t s)
     if (cblocks > cap) cblocks = cap;
     if (cblocks < 1) cblocks = 1;
     cell_flags_all_kernel<<<(unsigned)cblocks, 256, 0, s>>>(v);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !v.vmask) return e;
+    return launch_mask_rebuild(v, num_sms, s);
 }
 
 cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsigned *counter,
                               int num_sms, cudaStream_t s)
 {
     cell_flags_kernel<<<num_sms * 4, 256, 0, s>>>(vols, list, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_masks(const VolDev *vols, const uint2 *changed, const unsigned *counter,
+                              unsigned stamp_id, int num_sms, cudaStream_t s)
+{
+    cell_masks_kernel<<<num_sms * 4, 256, 0, s>>>(vols, changed, counter, stamp_id);
     return cudaGetLastError();
 }
 
@@ -757,7 +1012,7 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
                             cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                             const FrameParams &P, long long total, uint2 *list, unsigned *counter,
                             const float *depth, const uint8_t *rgb, Stats *stats, int grid_int,
-                            int num_sms, VisList *vis)
+                            int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id)
 {
     const long long lb = list_blocks(total, num_sms);
     NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a0(vols, nvol, P, vf, counter,
@@ -775,12 +1030,12 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
     e = graph_node(g, exec, &nodes[2], nodes[1], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,
-             const uint8_t *, Stats *>
-        a2(vols, vf, list, counter, P, depth, rgb, stats);
+             const uint8_t *, Stats *, MaskOut>
+        a2(vols, vf, list, counter, P, depth, rgb, stats, MaskOut{changed, counter + 2, stamp_id});
     e = graph_node(g, exec, &nodes[3], nodes[2], a2.params((const void *)integrate_kernel, grid_int, 128));
     if (e != cudaSuccess) return e;
-    NodeArgs<const VolDev *, const uint2 *, const unsigned *> a3(vols, list, counter);
-    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_flags_kernel, num_sms * 4, 256));
+    NodeArgs<const VolDev *, const uint2 *, const unsigned *, unsigned> a3(vols, changed, counter + 2, stamp_id);
+    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_masks_kernel, num_sms * 4, 256));
 }
 
 int integrate_max_ctas_per_sm()

@@ -11,6 +11,23 @@
 // byte saying whether the trilinear cells whose lower corner lies in the brick
 // can be stepped over by the raycast (see mv_raycast.cu).  Both byte arrays
 // live in one allocation: voxel-brick flags first, then cell-brick flags.
+//
+// Resident volumes also carry per-voxel and per-cell bit masks (derived data,
+// rebuilt from the voxels after a host write or a swap-in, never swapped):
+//   vmask, 16 x u64 per brick: rows [0, 8) = "observed" (W > 0) of slice z,
+//          rows [8, 16) = "observed with stored F <= 0" of slice z; bit
+//          8 y + x is voxel (x, y, z) of the brick;
+//   cmask, 8 x (u64 V, u64 N) per brick: for the trilinear cell whose lower
+//          corner is voxel (x, y, z) of the brick, bit 8 y + x of V is set when
+//          all 8 corners are observed and of N when some corner is observed
+//          with F <= 0 (corners beyond the brick come from its neighbours);
+//   stamp, 1 x u32 per brick: the id of the last integration call whose work
+//          list held the brick (lets the cell-mask refresh visit each cell
+//          brick once).
+// The raycast decides most samples from one 16-byte cmask load: a cell with
+// N clear cannot end a bracket, and its V bit gives the march state.  With
+// masks, a cell brick carries kCellSkip exactly when none of its cells has N
+// set (a finer test than the brick summaries, which are used without masks).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -30,7 +47,11 @@ constexpr uint8_t kFlagFree = 1;   // every voxel of the brick has W > 0 and F >
 constexpr uint8_t kFlagEmpty = 2;  // every voxel of the brick has W == 0
 constexpr uint8_t kFlagNoNeg = 4;  // no voxel of the brick has W > 0 and F <= 0
 constexpr uint8_t kFlagsNew = kFlagEmpty | kFlagNoNeg;  // a freshly cleared brick
-constexpr uint8_t kCellSkip = 1;   // the 8 bricks b + {0,1}^3 all carry kFlagNoNeg
+// Cell-brick flag: no trilinear cell whose lower corner lies in the brick has
+// an observed corner with F <= 0 (taken from the cell masks where the volume
+// has them, else from the brick summaries: the 8 bricks b + {0,1}^3 all carry
+// kFlagNoNeg, a stronger condition).
+constexpr uint8_t kCellSkip = 1;
 // Super brick: kSuper^3 cell bricks (32^3 voxels).  A super brick whose count
 // of cell bricks without kCellSkip is 0 is crossed by the raycast in one step.
 constexpr int kSuper = 4;
@@ -44,6 +65,9 @@ struct VolDev {
     uint8_t *cflag;    // one cell-brick byte per brick (may be null where no raycast reads it)
     unsigned *surf;    // bricks without kFlagNoNeg (0: no hit possible anywhere), may be null
     unsigned *sup;     // per super brick: cell bricks without kCellSkip (may be null)
+    unsigned long long *vmask;  // per-voxel masks, 16 x u64 per brick (may be null)
+    ulonglong2 *cmask;          // per-cell masks, 8 x (V, N) per brick (may be null)
+    unsigned *stamp;            // per brick: id of the last integration that listed it (may be null)
     int h[3];          // lattice offset h_t
     int r[3];          // voxels per axis h_r
     int nb[3];         // bricks per axis
@@ -109,6 +133,11 @@ inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
 {
     return super_offset(nbricks) + 4 * (size_t)nsuper;
 }
+
+// Mask allocation of a volume: vmask (128 B per brick), cmask (128 B per
+// brick), then the listing stamps (4 B per brick).
+constexpr size_t kMaskBytesPerBrick = 260;
+inline size_t mask_alloc_bytes(long long nbricks) { return (size_t)nbricks * kMaskBytesPerBrick; }
 
 struct Stats {
     unsigned long long swept, updated, band, bricks;

@@ -17,7 +17,7 @@ cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const Frame
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
-                             cudaStream_t);
+                             cudaStream_t, uint2 *, unsigned *, unsigned);
 int integrate_occupancy_grid(int num_sms);
 }  // namespace mv
 
@@ -161,7 +161,7 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1) !=
         cudaSuccess)
         return MV_ERR_CUDA;
-    if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s) != cudaSuccess)
+    if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s, nullptr, nullptr, 0u) != cudaSuccess)
         return MV_ERR_CUDA;
     return MV_OK;
 }

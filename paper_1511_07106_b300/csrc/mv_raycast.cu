@@ -375,6 +375,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
 
     int state = 0;  // 0: no valid previous sample, 1: previous valid > 0, -1: previous valid <= 0
     float Fprev = 0.f;
+    bool prev_read = false;  // Fprev holds the previous sample's value (not decided by its mask)
     int cur_b = -1;
     for (int kk = 0; kk <= nk; ++kk) {
         float k = k0 + (float)kk;
@@ -409,19 +410,36 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                         for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
                         locate(v, vr, rr, cell, f);
                         cur_b = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
+                        bidx = cur_b;
                         state = 0;
                         ++rc.skips;
                     }
                 }
             }
         }
+        if (v.cmask) {
+            // a cell without an observed corner with F <= 0 cannot end a
+            // bracket (its interpolant is > 0 where valid): the march state
+            // follows from its "all corners observed" bit alone
+            const ulonglong2 cm = __ldg(v.cmask + (size_t)bidx * 8 + (cell[2] & 7));
+            const int bit = ((cell[1] & 7) << 3) | (cell[0] & 7);
+            if (!((cm.y >> bit) & 1ull)) {
+                state = ((cm.x >> bit) & 1ull) ? 1 : 0;
+                prev_read = false;
+                continue;
+            }
+        }
         const Corners<Off> c = cell_corners(g, cell[0], cell[1], cell[2]);
         bool valid;
         const float F = trilinear<FMT>(v, c, f[0], f[1], f[2], valid);
         ++rc.samples;
-        if (!valid) { state = 0; continue; }
+        if (!valid) { state = 0; prev_read = false; continue; }
         if (state == 1 && F <= 0.f) {
             // bracket (k-1, k]: bisection on the interpolant, then a secant step
+            if (!prev_read) {
+                bool pv;
+                Fprev = eval_at<FMT>(v, g, vr, k - 1.0f, pv);
+            }
             float a = k - 1.0f, b = k, ga = Fprev, gb = F;
             // the corners of the cell last read stay in registers: a midpoint in
             // the same cell re-reads no memory (same arithmetic as trilinear)
@@ -472,6 +490,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
         }
         state = (F > 0.f) ? 1 : -1;
         Fprev = F;
+        prev_read = true;
     }
 }
 

@@ -32,9 +32,11 @@ cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const Frame
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
-                             cudaStream_t);
+                             cudaStream_t, uint2 *, unsigned *, unsigned);
 cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
+cudaError_t launch_mask_rebuild(const VolDev &, int, cudaStream_t);
 cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
+cudaError_t launch_cell_masks(const VolDev *, const uint2 *, const unsigned *, unsigned, int, cudaStream_t);
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
                            float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t,
                            const VisList *);
@@ -69,7 +71,8 @@ cudaError_t launch_stream_scatter(const VolDev &, const uint2 *, const unsigned 
 constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
-                            unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *);
+                            unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
+                            uint2 *, unsigned);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
                           uint8_t *, float *, int *, Stats *, int, VisList *);
@@ -89,6 +92,7 @@ struct Volume {
     void *d_fw = nullptr;
     uint32_t *d_rgba = nullptr;
     uint8_t *d_flag = nullptr;
+    void *d_mask = nullptr;  // voxel + cell masks while resident (derived, never swapped)
     void *h_fw = nullptr;
     uint32_t *h_rgba = nullptr;
     uint8_t *h_flag = nullptr;
@@ -110,6 +114,7 @@ struct mv_ctx {
     int ctas_per_sm = 0;
     std::map<int, Volume *> vols;
     int next_id = 0;
+    unsigned integrations = 0;  // id of the last integration call (brick listing stamps)
     cudaStream_t swap_stream = nullptr;
     cudaEvent_t last_event = nullptr;
     bool last_recorded = false;
@@ -244,6 +249,13 @@ VolDev make_voldev(const Volume &v)
     d.cflag = v.d_flag ? v.d_flag + cflag_offset(v.nbricks) : nullptr;
     d.surf = v.d_flag ? reinterpret_cast<unsigned *>(v.d_flag + flag_count_offset(v.nbricks)) : nullptr;
     d.sup = v.d_flag ? reinterpret_cast<unsigned *>(v.d_flag + super_offset(v.nbricks)) : nullptr;
+    d.vmask = v.d_mask ? reinterpret_cast<unsigned long long *>(v.d_mask) : nullptr;
+    d.cmask = v.d_mask ? reinterpret_cast<ulonglong2 *>(reinterpret_cast<uint8_t *>(v.d_mask) +
+                                                         (size_t)v.nbricks * 128)
+                       : nullptr;
+    d.stamp = v.d_mask ? reinterpret_cast<unsigned *>(reinterpret_cast<uint8_t *>(v.d_mask) +
+                                                      (size_t)v.nbricks * 256)
+                       : nullptr;
     for (int a = 0; a < 3; ++a) d.nsb[a] = v.nsb[a];
     for (int a = 0; a < 3; ++a) {
         d.h[a] = v.desc.h_t[a];
@@ -291,12 +303,13 @@ mv_status begin_call(mv_ctx *c, cudaStream_t s, int only_id = -1)
         if (!c->table.empty())
             MV_CUDA(c, cudaMemcpyAsync(c->d_table, c->table.data(), c->table.size() * sizeof(VolDev),
                                        cudaMemcpyHostToDevice, s));
-        // the work list holds at most one entry per resident brick
+        // the work list holds at most one entry per resident brick; the list of
+        // bricks whose voxel masks changed follows it in the same buffer
         if ((size_t)base > c->list_cap) {
             if (c->d_list) MV_CUDA(c, cudaFreeAsync(c->d_list, s));
             c->d_list = nullptr;
             c->list_cap = 0;
-            MV_CUDA(c, cudaMallocAsync((void **)&c->d_list, (size_t)base * sizeof(uint2), s));
+            MV_CUDA(c, cudaMallocAsync((void **)&c->d_list, 2 * (size_t)base * sizeof(uint2), s));
             c->list_cap = (size_t)base;
         }
         c->table_dirty = false;
@@ -650,6 +663,7 @@ mv_status mv_destroy(mv_ctx *c)
         if (v->d_fw) cudaFreeAsync(v->d_fw, s);
         if (v->d_rgba) cudaFreeAsync(v->d_rgba, s);
         if (v->d_flag) cudaFreeAsync(v->d_flag, s);
+        if (v->d_mask) cudaFreeAsync(v->d_mask, s);
     }
     if (c->d_list) cudaFreeAsync(c->d_list, s);
     free_slots(c, s);
@@ -886,7 +900,9 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
     if (e == cudaSuccess) e = cudaMallocAsync(&v->d_fw, v->fw_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_rgba, v->rgba_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&v->d_flag, v->flag_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&v->d_mask, mask_alloc_bytes(v->nbricks), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_fw, 0, v->fw_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_mask, 0, mask_alloc_bytes(v->nbricks), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_rgba, 0, v->rgba_bytes, s);
     // nothing observed yet: every brick NONEG, every cell brick skipped, the
     // counts (bricks without NONEG, cell bricks without skip) all 0
@@ -899,6 +915,7 @@ mv_status mv_add_volume(mv_ctx *c, const mv_volume_desc *d, int32_t *out_id)
         if (v->d_fw) cudaFreeAsync(v->d_fw, s);
         if (v->d_rgba) cudaFreeAsync(v->d_rgba, s);
         if (v->d_flag) cudaFreeAsync(v->d_flag, s);
+        if (v->d_mask) cudaFreeAsync(v->d_mask, s);
         cudaStreamSynchronize(s);
         if (v->ready) cudaEventDestroy(v->ready);
         delete v;
@@ -926,6 +943,7 @@ mv_status mv_remove_volume(mv_ctx *c, int32_t id)
     if (v->d_fw) MV_CUDA(c, cudaFreeAsync(v->d_fw, s));
     if (v->d_rgba) MV_CUDA(c, cudaFreeAsync(v->d_rgba, s));
     if (v->d_flag) MV_CUDA(c, cudaFreeAsync(v->d_flag, s));
+    if (v->d_mask) MV_CUDA(c, cudaFreeAsync(v->d_mask, s));
     if (v->h_fw || v->h_rgba || v->h_flag) {
         MV_CUDA(c, cudaStreamSynchronize(s));  // in-flight copies may still read the host copy
         free_host(c, v);
@@ -950,7 +968,7 @@ mv_status mv_query(mv_ctx *c, int32_t id, mv_volume_info *out)
     out->resident = v->resident ? 1 : 0;
     out->reserved = 0;
     const size_t tot = v->fw_bytes + v->rgba_bytes + v->flag_bytes;
-    out->device_bytes = v->resident ? tot : 0;
+    out->device_bytes = v->resident ? tot + mask_alloc_bytes(v->nbricks) : 0;
     out->host_bytes = v->h_fw ? tot : 0;
     return MV_OK;
 }
@@ -995,6 +1013,7 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     const long long total = only_id >= 0 ? c->table[slot0].nbricks
                                          : c->table.back().brick_base + c->table.back().nbricks;
     VisList *vis = only_id >= 0 ? nullptr : c->d_vis;  // batched: only volumes in view
+    const unsigned stamp = ++c->integrations;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
         return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s, vis); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
@@ -1002,11 +1021,15 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
         return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s, vis,
                                  c->d_counter + 1); }));
+    // every resident volume keeps cell masks: the integration lists the bricks
+    // whose voxel masks changed (second half of the work-list buffer) and the
+    // refresh recomputes the cell masks and flags that read them
+    uint2 *changed = c->d_list + c->list_cap;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
         return launch_integrate(tab, vf, c->d_list, c->d_counter, P, depth, rgb, c->d_stats,
-                                c->grid_integrate, s); }));
+                                c->grid_integrate, s, changed, c->d_counter + 2, stamp); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
-        return launch_cell_flags(tab, c->d_list, c->d_counter, c->num_sms, s); }));
+        return launch_cell_masks(tab, changed, c->d_counter + 2, stamp, c->num_sms, s); }));
     return end_call(c, s);
 }
 
@@ -1107,7 +1130,7 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     cudaGraphExec_t upd = rebuild ? nullptr : fg.exec;
     MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
                                c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
-                               c->num_sms, c->d_vis));
+                               c->num_sms, c->d_vis, c->d_list + c->list_cap, ++c->integrations));
     MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[5], fg.nodes[4], c->d_table, nvol, c->d_vf, P,
                              depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
@@ -1205,7 +1228,8 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
             return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, list, cnt, c->num_sms, s, nullptr, cnt + 1); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
-            return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s); }));
+            return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s,
+                                    nullptr, nullptr, 0u); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
             return launch_cell_flags(dv, list, cnt, c->num_sms, s); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
@@ -1327,6 +1351,9 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
         sv.cflag = nullptr;
         sv.surf = nullptr;
         sv.sup = nullptr;
+        sv.vmask = nullptr;
+        sv.cmask = nullptr;
+        sv.stamp = nullptr;
         sv.brick_base = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(stab, &sv, sizeof(VolDev), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sv is a stack value
@@ -1350,7 +1377,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
                 if (e == cudaSuccess) e = cudaEventRecord(a, s);
                 if (e == cudaSuccess)
                     e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
-                                         c->num_sms * ctas, s);
+                                         c->num_sms * ctas, s, nullptr, nullptr, 0u);
                 if (e == cudaSuccess) e = cudaEventRecord(b, s);
                 if (e == cudaSuccess && rep > 0) t[nt++] = time_ms(s, a, b);
             }
@@ -1487,11 +1514,13 @@ mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)
     MV_CUDA(c, cudaFreeAsync(v->d_fw, s));
     MV_CUDA(c, cudaFreeAsync(v->d_rgba, s));
     MV_CUDA(c, cudaFreeAsync(v->d_flag, s));
+    if (v->d_mask) MV_CUDA(c, cudaFreeAsync(v->d_mask, s));
     MV_CUDA(c, cudaEventRecord(v->ready, s));
     v->ready_pending = true;
     v->d_fw = nullptr;
     v->d_rgba = nullptr;
     v->d_flag = nullptr;
+    v->d_mask = nullptr;
     v->resident = false;
     c->table_dirty = true;
     return MV_OK;
@@ -1509,25 +1538,31 @@ mv_status mv_swap_in(mv_ctx *c, int32_t id, void *stream)
     (void)stream;
     // a download into the host copy (swap-out or streamed frame) may still run
     if (v->ready_pending) MV_CUDA(c, cudaStreamWaitEvent(s, v->ready, 0));
-    void *fw = nullptr, *rgba = nullptr, *flag = nullptr;
+    void *fw = nullptr, *rgba = nullptr, *flag = nullptr, *mask = nullptr;
     cudaError_t e = cudaMallocAsync(&fw, v->fw_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&rgba, v->rgba_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&flag, v->flag_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&mask, mask_alloc_bytes(v->nbricks), s);
     if (e != cudaSuccess) {
         if (fw) cudaFreeAsync(fw, s);
         if (rgba) cudaFreeAsync(rgba, s);
         if (flag) cudaFreeAsync(flag, s);
+        if (mask) cudaFreeAsync(mask, s);
         cudaGetLastError();
         return cuda_fail(c, e, "allocating GPU memory for swap-in");
     }
     MV_CUDA(c, cudaMemcpyAsync(fw, v->h_fw, v->fw_bytes, cudaMemcpyHostToDevice, s));
     MV_CUDA(c, cudaMemcpyAsync(rgba, v->h_rgba, v->rgba_bytes, cudaMemcpyHostToDevice, s));
     MV_CUDA(c, cudaMemcpyAsync(flag, v->h_flag, v->flag_bytes, cudaMemcpyHostToDevice, s));
-    MV_CUDA(c, cudaEventRecord(v->ready, s));
-    v->ready_pending = true;
     v->d_fw = fw;
     v->d_rgba = (uint32_t *)rgba;
     v->d_flag = (uint8_t *)flag;
+    v->d_mask = mask;
+    // the masks are rebuilt from the voxels just uploaded
+    const VolDev dv = make_voldev(*v);
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_FLAGS, s, [&] { return launch_mask_rebuild(dv, c->num_sms, s); }));
+    MV_CUDA(c, cudaEventRecord(v->ready, s));
+    v->ready_pending = true;
     v->resident = true;
     c->table_dirty = true;
     return MV_OK;
