@@ -47,8 +47,52 @@ __device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3]
     return in_near && in_l && in_r && in_t && in_b && in_far;
 }
 
+// A brick none of whose voxels the frame can update because each lies farther
+// than every accepted depth of the pixels it can project to by more than mu
+// (sdf = (D - z) |p_c| / z < -mu, as |p_c| / z >= 1), or projects outside the
+// image.  The pixels are bounded by the projected corners (all in front of
+// the camera) widened by one pixel; their largest depth comes from the
+// smallest pyramid level whose tiles are at least as large as that range.
+// Conservative: margins far above the float rounding of the per-voxel test.
+__device__ __forceinline__ bool brick_behind_surface(const float lo[3], const float hi[3], const FrameParams &P,
+                                                     float inv_s, const unsigned *__restrict__ pyr)
+{
+    float u0 = 3.0e38f, u1 = -3.0e38f, v0 = 3.0e38f, v1 = -3.0e38f, zmin = 3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float x = (c & 1) ? hi[0] : lo[0];
+        const float y = (c & 2) ? hi[1] : lo[1];
+        const float z = (c & 4) ? hi[2] : lo[2];
+        const float X = P.Rf[0] * x + P.Rf[3] * y + P.Rf[6] * z;
+        const float Y = P.Rf[1] * x + P.Rf[4] * y + P.Rf[7] * z;
+        const float Z = P.Rf[2] * x + P.Rf[5] * y + P.Rf[8] * z;
+        if (!(Z > 0.5f)) return false;  // at or behind the camera plane: keep
+        const float iz = 1.0f / Z;
+        const float u = fminf(1.0e6f, fmaxf(-1.0e6f, fmaf(P.fx * X, iz, P.cx)));
+        const float v = fminf(1.0e6f, fmaxf(-1.0e6f, fmaf(P.fy * Y, iz, P.cy)));
+        u0 = fminf(u0, u); u1 = fmaxf(u1, u);
+        v0 = fminf(v0, v); v1 = fmaxf(v1, v);
+        zmin = fminf(zmin, Z);
+    }
+    const int x0 = max(0, (int)floorf(u0 + 0.5f) - 1), x1 = min(P.width - 1, (int)floorf(u1 + 0.5f) + 1);
+    const int y0 = max(0, (int)floorf(v0 + 0.5f) - 1), y1 = min(P.height - 1, (int)floorf(v1 + 0.5f) + 1);
+    if (x0 > x1 || y0 > y1) return true;  // no voxel projects into the image
+    const int span = max(x1 - x0, y1 - y0) + 1;
+    int l = 0;
+    while (l < kPyrLevels - 1 && (8 << l) < span) ++l;
+    if ((8 << l) < span) return false;  // wider than the coarsest tile: the frame-wide far test only
+    const unsigned *lev = pyr + pyr_level_off(P.width, P.height, l);
+    const int nx = pyr_tiles(P.width, l), sh = 3 + l;
+    float dmax = 0.f;
+    for (int ty = y0 >> sh; ty <= (y1 >> sh); ++ty)
+        for (int tx = x0 >> sh; tx <= (x1 >> sh); ++tx)
+            dmax = fmaxf(dmax, __uint_as_float(__ldg(lev + (long long)ty * nx + tx)));
+    return zmin > fmaf(dmax, inv_s, P.trunc_vox) + 1e-4f * zmin + 1e-3f;
+}
+
 __device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
-                                              const FrameParams &P, int bx, int by, int bz, float z_far)
+                                              const FrameParams &P, int bx, int by, int bz, float z_far,
+                                              const unsigned *__restrict__ pyr)
 {
     float lo[3], hi[3];
     const int bi[3] = {bx, by, bz};
@@ -59,7 +103,8 @@ __device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f
         lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
         hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
     }
-    return box_visible(lo, hi, P, v.inv_s, z_far);
+    if (!box_visible(lo, hi, P, v.inv_s, z_far)) return false;
+    return !(pyr && brick_behind_surface(lo, hi, P, v.inv_s, pyr));
 }
 
 // ---------------------------------------------------------------------------
@@ -152,7 +197,8 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
                                                          long long total_all, uint2 *__restrict__ list,
                                                          unsigned *__restrict__ counter,
                                                          const VisList *__restrict__ vl,
-                                                         const unsigned *__restrict__ dmax_bits)
+                                                         const unsigned *__restrict__ dmax_bits,
+                                                         const unsigned *__restrict__ pyr)
 {
     const int lane = threadIdx.x & 31;
     const float z_far = dmax_bits ? fminf(P.z_max, __uint_as_float(*dmax_bits)) : P.z_max;
@@ -191,7 +237,7 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
             const unsigned byz = b / (unsigned)vd.nb[0];
             const unsigned by = byz % (unsigned)vd.nb[1];
             const unsigned bz = byz / (unsigned)vd.nb[1];
-            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far);
+            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far, pyr);
             packed = bx | (by << 10) | (bz << 20);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
@@ -215,6 +261,59 @@ __global__ void __launch_bounds__(256) depth_max_kernel(const float *__restrict_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+// The depth-tile pyramid of the frame (one CTA per 32 x 32 pixels) and its
+// largest accepted depth (bits in *out, zeroed by the setup kernel).
+__global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restrict__ depth, FrameParams P,
+                                                          unsigned *__restrict__ pyr, unsigned *__restrict__ out)
+{
+    __shared__ unsigned s_t[4][4];  // level 0: the block's 4 x 4 tiles of 8 x 8 pixels
+    __shared__ unsigned s_1[2][2];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t < 16) s_t[t >> 2][t & 3] = 0u;
+    __syncthreads();
+    // warp w reads rows w + 8 i (tile row i) of the block, lane = column
+    const int x = blockIdx.x * 32 + lane;
+    float m[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        m[i] = 0.f;
+        const int y = blockIdx.y * 32 + w + 8 * i;
+        if (x < P.width && y < P.height) {
+            const float D = __ldg(depth + (size_t)y * P.width + x);
+            if (D > 0.f && D >= P.z_min && D <= P.z_max) m[i] = D;
+        }
+    }
+    // the 8 columns of a tile are 8 consecutive lanes; the 8 warps meet in shared memory
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float v = m[i];
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+        if ((lane & 7) == 0 && v > 0.f) atomicMax(&s_t[i][lane >> 3], __float_as_uint(v));
+    }
+    __syncthreads();
+    if (t < 16) {
+        const int tx = blockIdx.x * 4 + (t & 3), ty = blockIdx.y * 4 + (t >> 2);
+        if (tx < pyr_tiles(P.width, 0) && ty < pyr_tiles(P.height, 0))
+            pyr[(long long)ty * pyr_tiles(P.width, 0) + tx] = s_t[t >> 2][t & 3];
+    } else if (t < 20) {
+        const int k = t - 16, lx = k & 1, ly = k >> 1;
+        const unsigned mx = max(max(s_t[2 * ly][2 * lx], s_t[2 * ly][2 * lx + 1]),
+                                max(s_t[2 * ly + 1][2 * lx], s_t[2 * ly + 1][2 * lx + 1]));
+        s_1[ly][lx] = mx;
+        const int tx = blockIdx.x * 2 + lx, ty = blockIdx.y * 2 + ly;
+        if (tx < pyr_tiles(P.width, 1) && ty < pyr_tiles(P.height, 1))
+            pyr[pyr_level_off(P.width, P.height, 1) + (long long)ty * pyr_tiles(P.width, 1) + tx] = mx;
+    }
+    __syncthreads();
+    if (t == 0) {
+        const unsigned mx = max(max(s_1[0][0], s_1[0][1]), max(s_1[1][0], s_1[1][1]));
+        pyr[pyr_level_off(P.width, P.height, 2) + (long long)blockIdx.y * pyr_tiles(P.width, 2) + blockIdx.x] = mx;
+        if (mx) atomicMax(out, mx);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -906,11 +1005,11 @@ static long long list_blocks(long long total, int num_sms)
 cudaError_t launch_brick_list(const VolDev *vols, int nvol, const VolFrame *vfs,
                               const FrameParams &P, long long gb_begin, long long total,
                               uint2 *list, unsigned *counter, int num_sms, cudaStream_t s,
-                              const VisList *vis, const unsigned *dmax_bits)
+                              const VisList *vis, const unsigned *dmax_bits, const unsigned *pyr)
 {
     if (total <= 0) return cudaSuccess;
     brick_list_kernel<<<(unsigned)list_blocks(total, num_sms), 256, 0, s>>>(
-        vols, nvol, vfs, P, gb_begin, total, list, counter, vis, dmax_bits);
+        vols, nvol, vfs, P, gb_begin, total, list, counter, vis, dmax_bits, pyr);
     return cudaGetLastError();
 }
 
@@ -921,9 +1020,16 @@ static unsigned depth_max_blocks(int n, int num_sms)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+static dim3 depth_tiles_grid(const FrameParams &P) { return dim3((P.width + 31) / 32, (P.height + 31) / 32); }
+
+// The frame's largest accepted depth, and with pyr its depth-tile pyramid.
 cudaError_t launch_depth_max(const float *depth, const FrameParams &P, unsigned *out, int num_sms,
-                             cudaStream_t s)
+                             cudaStream_t s, unsigned *pyr)
 {
+    if (pyr) {
+        depth_tiles_kernel<<<depth_tiles_grid(P), 256, 0, s>>>(depth, P, pyr, out);
+        return cudaGetLastError();
+    }
     const int n = P.width * P.height;
     depth_max_kernel<<<depth_max_blocks(n, num_sms), 256, 0, s>>>(depth, n, P, out);
     return cudaGetLastError();
@@ -1012,21 +1118,19 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
                             cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                             const FrameParams &P, long long total, uint2 *list, unsigned *counter,
                             const float *depth, const uint8_t *rgb, Stats *stats, int grid_int,
-                            int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id)
+                            int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id, unsigned *pyr)
 {
     const long long lb = list_blocks(total, num_sms);
     NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a0(vols, nvol, P, vf, counter,
                                                                                    vis);
     cudaError_t e = graph_node(g, exec, &nodes[0], dep, a0.params((const void *)frame_setup_kernel, 1, 256));
     if (e != cudaSuccess) return e;
-    const int npx = P.width * P.height;
-    NodeArgs<const float *, int, FrameParams, unsigned *> am(depth, npx, P, counter + 1);
-    e = graph_node(g, exec, &nodes[1], nodes[0],
-                   am.params((const void *)depth_max_kernel, depth_max_blocks(npx, num_sms), 256));
+    NodeArgs<const float *, FrameParams, unsigned *, unsigned *> am(depth, P, pyr, counter + 1);
+    e = graph_node(g, exec, &nodes[1], nodes[0], am.params((const void *)depth_tiles_kernel, depth_tiles_grid(P), 256));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *,
-             const VisList *, const unsigned *>
-        a1(vols, nvol, vf, P, 0LL, total, list, counter, vis, counter + 1);
+             const VisList *, const unsigned *, const unsigned *>
+        a1(vols, nvol, vf, P, 0LL, total, list, counter, vis, counter + 1, pyr);
     e = graph_node(g, exec, &nodes[2], nodes[1], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,

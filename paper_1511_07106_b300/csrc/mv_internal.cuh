@@ -139,6 +139,38 @@ inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
 constexpr size_t kMaskBytesPerBrick = 260;
 inline size_t mask_alloc_bytes(long long nbricks) { return (size_t)nbricks * kMaskBytesPerBrick; }
 
+// Per-frame pyramid of the largest accepted depth over square pixel tiles of
+// 8, 16 and 32 pixels (float bits, 0 where no pixel of the tile has an
+// accepted depth): level L is a row-major grid of ceil(W / 2^(L+3)) x
+// ceil(H / 2^(L+3)) tiles, the levels stored one after the other.
+constexpr int kPyrLevels = 3;
+struct PyrDims {
+    int nx[kPyrLevels], ny[kPyrLevels];
+    long long off[kPyrLevels + 1];  // off[kPyrLevels] = words of the whole pyramid
+};
+__host__ __device__ inline PyrDims pyr_dims(int width, int height)
+{
+    PyrDims d;
+    long long acc = 0;
+    for (int l = 0; l < kPyrLevels; ++l) {
+        const int t = 8 << l;
+        d.nx[l] = (width + t - 1) / t;
+        d.ny[l] = (height + t - 1) / t;
+        d.off[l] = acc;
+        acc += (long long)d.nx[l] * d.ny[l];
+    }
+    d.off[kPyrLevels] = acc;
+    return d;
+}
+// the same per level, without arrays (device code indexes levels at run time)
+__host__ __device__ inline int pyr_tiles(int extent, int level) { return (extent + (8 << level) - 1) / (8 << level); }
+__host__ __device__ inline long long pyr_level_off(int width, int height, int level)
+{
+    long long acc = 0;
+    for (int l = 0; l < level; ++l) acc += (long long)pyr_tiles(width, l) * pyr_tiles(height, l);
+    return acc;
+}
+
 struct Stats {
     unsigned long long swept, updated, band, bricks;
     unsigned long long rays, ray_samples, ray_skips, ray_hits;

@@ -13,8 +13,8 @@ cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFram
                                VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
                               long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
-                              const unsigned *);
-cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
+                              const unsigned *, const unsigned *);
+cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t, uint2 *, unsigned *, unsigned);
@@ -157,8 +157,8 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     // the frame setup zeroes the list counter and the depth maximum, the values
     // that must start at 0
     if (launch_frame_setup(vdev, 1, P, vframe, counter, s, nullptr) != cudaSuccess) return MV_ERR_CUDA;
-    if (launch_depth_max(depth, P, counter + 1, sms, s) != cudaSuccess) return MV_ERR_CUDA;
-    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1) !=
+    if (launch_depth_max(depth, P, counter + 1, sms, s, nullptr) != cudaSuccess) return MV_ERR_CUDA;
+    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1, nullptr) !=
         cudaSuccess)
         return MV_ERR_CUDA;
     if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s, nullptr, nullptr, 0u) != cudaSuccess)

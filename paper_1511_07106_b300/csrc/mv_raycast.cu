@@ -119,6 +119,13 @@ struct VolRay {
 };
 
 // Cell (local, clamped) and fractions of the point rr (camera-relative).
+// Cell only (the march decides most samples from the cell's masks).
+__device__ __forceinline__ void locate_cell(const VolDev &v, const VolRay &vr, const float rr[3], int cell[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cell[a] = max(0, min(v.r[a] - 2, __float2int_rd(rr[a]) + vr.oi[a]));
+}
+
 __device__ __forceinline__ void locate(const VolDev &v, const VolRay &vr, const float rr[3],
                                        int cell[3], float f[3])
 {
@@ -379,11 +386,11 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
     int cur_b = -1;
     for (int kk = 0; kk <= nk; ++kk) {
         float k = k0 + (float)kk;
-        float rr[3], f[3];
+        float rr[3];
         int cell[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
-        locate(v, vr, rr, cell, f);
+        locate_cell(v, vr, rr, cell);
         // brick of the sample's cell (its lower corner)
         int bidx = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
         if (bidx != cur_b) {
@@ -408,7 +415,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                         k = k0 + (float)kk;
 #pragma unroll
                         for (int a = 0; a < 3; ++a) rr[a] = fmaf(k, vr.dq[a], vr.fr[a]);
-                        locate(v, vr, rr, cell, f);
+                        locate_cell(v, vr, rr, cell);
                         cur_b = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
                         bidx = cur_b;
                         state = 0;
@@ -429,6 +436,9 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                 continue;
             }
         }
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[a] = rr[a] - (float)(cell[a] - vr.oi[a]);
         const Corners<Off> c = cell_corners(g, cell[0], cell[1], cell[2]);
         bool valid;
         const float F = trilinear<FMT>(v, c, f[0], f[1], f[2], valid);

@@ -28,8 +28,8 @@ cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFram
                                VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
                               long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
-                              const unsigned *);
-cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t);
+                              const unsigned *, const unsigned *);
+cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t, uint2 *, unsigned *, unsigned);
@@ -72,7 +72,7 @@ constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
                             unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
-                            uint2 *, unsigned);
+                            uint2 *, unsigned, unsigned *);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
                           uint8_t *, float *, int *, Stats *, int, VisList *);
@@ -139,6 +139,8 @@ struct mv_ctx {
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
+    unsigned *d_pyr = nullptr;  // depth-tile pyramid of the current frame
+    size_t pyr_words = 0;
     unsigned long long *d_points = nullptr;  // point count of mv_extract_points
     mv::PinnedPool *pool = nullptr;          // pinned host buffers of swapped-out volumes
     // tracking scratch: the frame's vertex / normal maps, per-CTA ICP partials
@@ -679,6 +681,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_counter) cudaFree(c->d_counter);
     if (c->d_stats) cudaFree(c->d_stats);
     if (c->d_vis) cudaFree(c->d_vis);
+    if (c->d_pyr) cudaFree(c->d_pyr);
     if (c->d_points) cudaFree(c->d_points);
     if (c->d_trk_v) cudaFree(c->d_trk_v);
     if (c->d_trk_n) cudaFree(c->d_trk_n);
@@ -985,6 +988,21 @@ mv_status mv_list_volumes(mv_ctx *c, int32_t *ids, int32_t cap, int32_t *count)
     return MV_OK;
 }
 
+// The depth-tile pyramid buffer, grown to the frame size (before any graph
+// or launch of the call uses it).
+static mv_status ensure_pyramid(mv_ctx *c, const mv_intrinsics *K)
+{
+    const size_t words = (size_t)pyr_dims(K->width, K->height).off[kPyrLevels];
+    if (words <= c->pyr_words) return MV_OK;
+    MV_CUDA(c, cudaDeviceSynchronize());  // an earlier call may still read the old buffer
+    if (c->d_pyr) MV_CUDA(c, cudaFree(c->d_pyr));
+    c->d_pyr = nullptr;
+    c->pyr_words = 0;
+    MV_CUDA(c, cudaMalloc((void **)&c->d_pyr, words * sizeof(unsigned)));
+    c->pyr_words = words;
+    return MV_OK;
+}
+
 static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, const uint8_t *rgb,
                                 const mv_intrinsics *K, const double T[16], void *stream)
 {
@@ -1013,14 +1031,16 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     const long long total = only_id >= 0 ? c->table[slot0].nbricks
                                          : c->table.back().brick_base + c->table.back().nbricks;
     VisList *vis = only_id >= 0 ? nullptr : c->d_vis;  // batched: only volumes in view
+    st = ensure_pyramid(c, K);
+    if (st) return st;
     const unsigned stamp = ++c->integrations;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
         return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s, vis); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
-        return launch_depth_max(depth, P, c->d_counter + 1, c->num_sms, s); }));
+        return launch_depth_max(depth, P, c->d_counter + 1, c->num_sms, s, c->d_pyr); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
         return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s, vis,
-                                 c->d_counter + 1); }));
+                                 c->d_counter + 1, c->d_pyr); }));
     // every resident volume keeps cell masks: the integration lists the bricks
     // whose voxel masks changed (second half of the work-list buffer) and the
     // refresh recomputes the cell masks and flags that read them
@@ -1107,6 +1127,8 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
     if (st) return st;
+    st = ensure_pyramid(c, K);
+    if (st) return st;
     const FrameParams P = make_params(c, K, T);
     const int nvol = (int)c->table.size();
     if (nvol == 0) {  // nothing to integrate: the maps are all misses
@@ -1130,7 +1152,7 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     cudaGraphExec_t upd = rebuild ? nullptr : fg.exec;
     MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
                                c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
-                               c->num_sms, c->d_vis, c->d_list + c->list_cap, ++c->integrations));
+                               c->num_sms, c->d_vis, c->d_list + c->list_cap, ++c->integrations, c->d_pyr));
     MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[5], fg.nodes[4], c->d_table, nvol, c->d_vf, P,
                              depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
@@ -1224,9 +1246,10 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
 
         MV_CUDA(c, cudaStreamWaitEvent(s, ss.loaded[j], 0));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
-            return launch_depth_max(depth, P, cnt + 1, c->num_sms, s); }));
+            return launch_depth_max(depth, P, cnt + 1, c->num_sms, s, c->d_pyr); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
-            return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, list, cnt, c->num_sms, s, nullptr, cnt + 1); }));
+            return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, list, cnt, c->num_sms, s, nullptr, cnt + 1,
+                                     c->d_pyr); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
             return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s,
                                     nullptr, nullptr, 0u); }));
@@ -1270,6 +1293,8 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
+    if (st) return st;
+    st = ensure_pyramid(c, K);
     if (st) return st;
     std::memset(out, 0, sizeof(*out));
     const FrameParams P = make_params(c, K, T);
@@ -1370,10 +1395,10 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
             int nt = 0;
             for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
                 e = launch_frame_setup(stab, 1, P, svf, scount, s, nullptr);
-                if (e == cudaSuccess) e = launch_depth_max(depth, P, scount + 1, c->num_sms, s);
+                if (e == cudaSuccess) e = launch_depth_max(depth, P, scount + 1, c->num_sms, s, c->d_pyr);
                 if (e == cudaSuccess)
                     e = launch_brick_list(stab, 1, svf, P, 0, sv.nbricks, slist, scount, c->num_sms, s,
-                                          nullptr, scount + 1);
+                                          nullptr, scount + 1, c->d_pyr);
                 if (e == cudaSuccess) e = cudaEventRecord(a, s);
                 if (e == cudaSuccess)
                     e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
