@@ -157,10 +157,18 @@ struct RayCount {
     unsigned samples, skips;
 };
 
+// Nearest hit so far: ray distance, volume id and table slot, and the sample
+// parameter of the refined root in that volume's grid (the shading happens
+// once, after every volume has been marched).
 struct Hit {
     float tau;
     int id;
     int slot;
+    float ks;
+};
+
+// Normal and colour of a hit.
+struct Shade {
     float n[3];
     uint32_t rgba;
 };
@@ -168,7 +176,7 @@ struct Hit {
 // Gradient (normal) and colour in the hit cell.
 template <int FMT, typename Off>
 __device__ __forceinline__ void shade(const VolDev &v, const Geo<Off> &geo, const VolRay &vr, float ks,
-                                      Hit &h)
+                                      Shade &h)
 {
     float rr[3];
 #pragma unroll
@@ -339,6 +347,24 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
 // the run's last sample alone.  The march therefore jumps to that last sample
 // (at least m voxels inside the run) and evaluates it normally: the result is
 // that of the dense march, not an approximation.
+// Ray state of one volume: camera lattice point and fraction, the direction
+// in voxels, and (after the domain is known) the grid step dq = dirv * Delta.
+__device__ __forceinline__ void vol_ray(const VolDev &v, const VolFrame &vf, const float d[3], VolRay &vr,
+                                        float dirv[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vr.fr[a] = vf.cam_frac[a];
+        vr.oi[a] = vf.cam_int[a] - v.h[a];
+        dirv[a] = d[a] * v.inv_s;
+    }
+}
+
+__device__ __forceinline__ float grid_step(const VolDev &v, const FrameParams &P, float dn)
+{
+    return P.ray_step * v.s / dn;
+}
+
 template <int FMT, typename Off>
 __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
                              const float d[3], float dn, int slot, Hit &best, RayCount &rc)
@@ -346,12 +372,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
     const Geo<Off> g = make_geo<Off>(v);
     VolRay vr;
     float dirv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        vr.fr[a] = vf.cam_frac[a];
-        vr.oi[a] = vf.cam_int[a] - v.h[a];
-        dirv[a] = d[a] * v.inv_s;
-    }
+    vol_ray(v, vf, d, vr, dirv);
     // domain [h_t, h_t + r - 1] in camera-relative coordinates
     float lo = P.z_min, hi = P.z_max;
 #pragma unroll
@@ -370,7 +391,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
     }
     if (!(lo <= hi)) return;
     if (lo > best.tau) return;  // cannot beat the current nearest hit
-    const float Delta = P.ray_step * v.s / dn;
+    const float Delta = grid_step(v, P, dn);
 #pragma unroll
     for (int a = 0; a < 3; ++a) vr.dq[a] = dirv[a] * Delta;
     const float k0 = ceilf(lo / Delta), k1 = floorf(hi / Delta);
@@ -494,7 +515,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                 best.tau = tau;
                 best.id = v.id;
                 best.slot = slot;
-                shade<FMT>(v, g, vr, ks, best);
+                best.ks = ks;
             }
             return;
         }
@@ -539,8 +560,7 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     best.tau = FLT_MAX;
     best.id = INT_MAX;
     best.slot = -1;
-    best.n[0] = best.n[1] = best.n[2] = 0.f;
-    best.rgba = 0u;
+    best.ks = 0.f;
     const size_t p = (size_t)py * P.width + px;
     if (merge && out.depth[p] > 0.f) {
         best.tau = out.depth[p];
@@ -574,14 +594,42 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     }
     if (best.slot == -2) return;  // merge: the existing entry stays
     const bool hit = best.slot >= 0;
+    // normal and colour of the nearest hit, in its volume's grid
+    Shade sh;
+    sh.n[0] = sh.n[1] = sh.n[2] = 0.f;
+    sh.rgba = 0u;
+    if (hit) {
+        const VolDev &v = vols[best.slot];
+        VolRay vr;
+        float dirv[3];
+        vol_ray(v, vfs[best.slot], d, vr, dirv);
+        const float Delta = grid_step(v, P, dn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vr.dq[a] = dirv[a] * Delta;
+        if (v.nbricks * kBrickVox <= 0xFFFFFFFFll) {
+            const Geo<uint32_t> g = make_geo<uint32_t>(v);
+            switch (v.fmt) {
+            case MV_TSDF_F32: shade<MV_TSDF_F32>(v, g, vr, best.ks, sh); break;
+            case MV_TSDF_F16: shade<MV_TSDF_F16>(v, g, vr, best.ks, sh); break;
+            default: shade<MV_TSDF_I16>(v, g, vr, best.ks, sh); break;
+            }
+        } else {
+            const Geo<long long> g = make_geo<long long>(v);
+            switch (v.fmt) {
+            case MV_TSDF_F32: shade<MV_TSDF_F32>(v, g, vr, best.ks, sh); break;
+            case MV_TSDF_F16: shade<MV_TSDF_F16>(v, g, vr, best.ks, sh); break;
+            default: shade<MV_TSDF_I16>(v, g, vr, best.ks, sh); break;
+            }
+        }
+    }
     if (out.depth) out.depth[p] = hit ? best.tau : 0.f;
     if (out.vol_id) out.vol_id[p] = hit ? best.id : -1;
     if (out.normal) {
-        out.normal[3 * p + 0] = hit ? best.n[0] : 0.f;
-        out.normal[3 * p + 1] = hit ? best.n[1] : 0.f;
-        out.normal[3 * p + 2] = hit ? best.n[2] : 0.f;
+        out.normal[3 * p + 0] = sh.n[0];
+        out.normal[3 * p + 1] = sh.n[1];
+        out.normal[3 * p + 2] = sh.n[2];
     }
-    if (out.rgba) out.rgba[p] = hit ? best.rgba : 0u;
+    if (out.rgba) out.rgba[p] = sh.rgba;
     if (out.vertex) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
