@@ -393,19 +393,32 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     }
 }
 
+// Division by the invariant divisors d = 2 (w + 1), w = 0..255, as a
+// multiplication (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): with M = ceil(2^32 / d) = (2^32 + e) / d,
+// 0 <= e < d, n M / 2^32 = n / d + n e / (d 2^32), and for n < 2^17 the
+// added term is below 2^-15 while the fractional part of n / d is at most
+// 1 - 1/512, so floor(n M / 2^32) = floor(n / d) exactly.
+__device__ __forceinline__ unsigned colour_rcp(int w)
+{
+    const unsigned long long d = 2ull * (unsigned long long)(w + 1);
+    return (unsigned)(((1ull << 32) + d - 1) / d);
+}
+
 __device__ __forceinline__ uint32_t blend_rgba(uint32_t old, const uint8_t *__restrict__ rgb, int p,
-                                               int cw_max)
+                                               int cw_max, const unsigned *__restrict__ rcp)
 {
     const int wc = (int)(old >> 24);
+    const unsigned m = rcp[wc];
     uint32_t out = 0u;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         const int c = (int)((old >> (8 * ch)) & 0xFFu);
         const int x = (int)__ldg(rgb + 3 * p + ch);
         const int num = c * wc + x;
-        // round half up of num / (wc + 1), in integers
-        const int nc = (2 * num + wc + 1) / (2 * (wc + 1));
-        out |= (uint32_t)nc << (8 * ch);
+        // round half up of num / (wc + 1) = floor((2 num + wc + 1) / (2 (wc + 1)))
+        const unsigned nc = __umulhi((unsigned)(2 * num + wc + 1), m);
+        out |= nc << (8 * ch);
     }
     out |= (uint32_t)min(wc + 1, cw_max) << 24;
     return out;
@@ -446,7 +459,8 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
                                                 unsigned long long &n_swept,
                                                 unsigned long long &n_upd,
                                                 unsigned long long &n_band,
-                                                const MaskOut &mo, uint2 item, ChgBuf &cb, int parity)
+                                                const MaskOut &mo, uint2 item, ChgBuf &cb, int parity,
+                                                const unsigned *__restrict__ rcp)
 {
     const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = (int)(packed >> 20);
     const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
@@ -554,7 +568,7 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
             uint32_t cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if ((u.band >> j) & 1u) cc[j] = blend_rgba(cc[j], rgb, u.pix[j], P.color_w_max);
+                if ((u.band >> j) & 1u) cc[j] = blend_rgba(cc[j], rgb, u.pix[j], P.color_w_max, rcp);
             *pc = make_uint4(cc[0], cc[1], cc[2], cc[3]);
         }
     }
@@ -606,6 +620,8 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
     // k's first barrier (all reads of it by brick k - 1 are done, no write of
     // brick k + 1 has started)
     __shared__ ChgBuf cb;
+    __shared__ unsigned s_rcp[256];  // colour_rcp(w), published by the first volume-change barrier
+    for (int w = threadIdx.x; w < 256; w += blockDim.x) s_rcp[w] = colour_rcp(w);
     if (threadIdx.x == 0) {  // published by the first volume-change barrier (or the final one)
         cb.flag[0] = cb.flag[1] = 0;
         cb.n = 0;
@@ -630,9 +646,9 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
         const VolDev &v = s_v;
         const VolFrame fr = s_f;
         switch (v.fmt) {
-        case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
-        case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
-        default: integrate_brick<MV_TSDF_I16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity); break;
+        case MV_TSDF_F32: integrate_brick<MV_TSDF_F32>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity, s_rcp); break;
+        case MV_TSDF_F16: integrate_brick<MV_TSDF_F16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity, s_rcp); break;
+        default: integrate_brick<MV_TSDF_I16>(v, fr, P, it.y, depth, rgb, n_swept, n_upd, n_band, mo, it, cb, parity, s_rcp); break;
         }
         parity ^= 1;
         ++n_bricks;
