@@ -47,17 +47,22 @@ __device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3]
     return in_near && in_l && in_r && in_t && in_b && in_far;
 }
 
-// A brick none of whose voxels the frame can update because each lies farther
-// than every accepted depth of the pixels it can project to by more than mu
-// (sdf = (D - z) |p_c| / z < -mu, as |p_c| / z >= 1), or projects outside the
-// image.  The pixels are bounded by the projected corners (all in front of
-// the camera) widened by one pixel; their largest depth comes from the
-// smallest pyramid level whose tiles are at least as large as that range.
+// Where a brick lies against the depths of the pixels it can project to
+// (bounded by the projected corners, all in front of the camera, widened by
+// one pixel; their largest and smallest depth come from the smallest pyramid
+// level whose tiles are at least as large as that range):
+//   kDepthBehind: every voxel lies farther than every accepted depth by more
+//     than mu (sdf = (D - z) |p_c| / z < -mu, as |p_c| / z >= 1), or none
+//     projects into the image: the frame updates none of them;
+//   kDepthFront: every voxel lies nearer than every accepted depth by more
+//     than mu: each voxel it updates gets f = min(1, sdf / mu) = 1, no colour;
+//   kDepthMixed: otherwise.
 // Conservative: margins far above the float rounding of the per-voxel test.
-__device__ __forceinline__ bool brick_behind_surface(const float lo[3], const float hi[3], const FrameParams &P,
-                                                     float inv_s, const unsigned *__restrict__ pyr)
+constexpr int kDepthMixed = 0, kDepthBehind = 1, kDepthFront = 2;
+__device__ __forceinline__ int brick_depth_class(const float lo[3], const float hi[3], const FrameParams &P,
+                                                 float inv_s, const unsigned *__restrict__ pyr)
 {
-    float u0 = 3.0e38f, u1 = -3.0e38f, v0 = 3.0e38f, v1 = -3.0e38f, zmin = 3.0e38f;
+    float u0 = 3.0e38f, u1 = -3.0e38f, v0 = 3.0e38f, v1 = -3.0e38f, zmin = 3.0e38f, zmax = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const float x = (c & 1) ? hi[0] : lo[0];
@@ -66,33 +71,41 @@ __device__ __forceinline__ bool brick_behind_surface(const float lo[3], const fl
         const float X = P.Rf[0] * x + P.Rf[3] * y + P.Rf[6] * z;
         const float Y = P.Rf[1] * x + P.Rf[4] * y + P.Rf[7] * z;
         const float Z = P.Rf[2] * x + P.Rf[5] * y + P.Rf[8] * z;
-        if (!(Z > 0.5f)) return false;  // at or behind the camera plane: keep
+        if (!(Z > 0.5f)) return kDepthMixed;  // at or behind the camera plane
         const float iz = 1.0f / Z;
         const float u = fminf(1.0e6f, fmaxf(-1.0e6f, fmaf(P.fx * X, iz, P.cx)));
         const float v = fminf(1.0e6f, fmaxf(-1.0e6f, fmaf(P.fy * Y, iz, P.cy)));
         u0 = fminf(u0, u); u1 = fmaxf(u1, u);
         v0 = fminf(v0, v); v1 = fmaxf(v1, v);
         zmin = fminf(zmin, Z);
+        zmax = fmaxf(zmax, Z);
     }
     const int x0 = max(0, (int)floorf(u0 + 0.5f) - 1), x1 = min(P.width - 1, (int)floorf(u1 + 0.5f) + 1);
     const int y0 = max(0, (int)floorf(v0 + 0.5f) - 1), y1 = min(P.height - 1, (int)floorf(v1 + 0.5f) + 1);
-    if (x0 > x1 || y0 > y1) return true;  // no voxel projects into the image
+    if (x0 > x1 || y0 > y1) return kDepthBehind;  // no voxel projects into the image
     const int span = max(x1 - x0, y1 - y0) + 1;
     int l = 0;
     while (l < kPyrLevels - 1 && (8 << l) < span) ++l;
-    if ((8 << l) < span) return false;  // wider than the coarsest tile: the frame-wide far test only
-    const unsigned *lev = pyr + pyr_level_off(P.width, P.height, l);
+    if ((8 << l) < span) return kDepthMixed;  // wider than the coarsest tile: the frame-wide far test only
+    const long long off = pyr_level_off(P.width, P.height, l);
+    const unsigned *lev_max = pyr + off;
+    const unsigned *lev_min = pyr + pyr_level_off(P.width, P.height, kPyrLevels) + off;
     const int nx = pyr_tiles(P.width, l), sh = 3 + l;
-    float dmax = 0.f;
+    float dmax = 0.f, dmin = 3.0e38f;
     for (int ty = y0 >> sh; ty <= (y1 >> sh); ++ty)
-        for (int tx = x0 >> sh; tx <= (x1 >> sh); ++tx)
-            dmax = fmaxf(dmax, __uint_as_float(__ldg(lev + (long long)ty * nx + tx)));
-    return zmin > fmaf(dmax, inv_s, P.trunc_vox) + 1e-4f * zmin + 1e-3f;
+        for (int tx = x0 >> sh; tx <= (x1 >> sh); ++tx) {
+            dmax = fmaxf(dmax, __uint_as_float(__ldg(lev_max + (long long)ty * nx + tx)));
+            dmin = fminf(dmin, __uint_as_float(__ldg(lev_min + (long long)ty * nx + tx)));
+        }
+    if (zmin > fmaf(dmax, inv_s, P.trunc_vox) + 1e-4f * zmin + 1e-3f) return kDepthBehind;
+    if (fminf(dmin, 3.0e37f) * inv_s - zmax > P.trunc_vox + 1e-4f * zmax + 1e-3f) return kDepthFront;
+    return kDepthMixed;
 }
 
-__device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f,
-                                              const FrameParams &P, int bx, int by, int bz, float z_far,
-                                              const unsigned *__restrict__ pyr)
+// 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu
+__device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
+                                             const FrameParams &P, int bx, int by, int bz, float z_far,
+                                             const unsigned *__restrict__ pyr)
 {
     float lo[3], hi[3];
     const int bi[3] = {bx, by, bz};
@@ -103,8 +116,10 @@ __device__ __forceinline__ bool brick_visible(const VolDev &v, const VolFrame &f
         lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
         hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
     }
-    if (!box_visible(lo, hi, P, v.inv_s, z_far)) return false;
-    return !(pyr && brick_behind_surface(lo, hi, P, v.inv_s, pyr));
+    if (!box_visible(lo, hi, P, v.inv_s, z_far)) return 0;
+    if (!pyr) return 1;
+    const int cls = brick_depth_class(lo, hi, P, v.inv_s, pyr);
+    return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,8 +252,9 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
             const unsigned byz = b / (unsigned)vd.nb[0];
             const unsigned by = byz % (unsigned)vd.nb[1];
             const unsigned bz = byz / (unsigned)vd.nb[1];
-            vis = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far, pyr);
-            packed = bx | (by << 10) | (bz << 20);
+            const int cls = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far, pyr);
+            vis = cls != 0;
+            packed = bx | (by << 10) | (bz << 20) | (cls == 2 ? kListFree : 0u);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
         unsigned pos = 0;
@@ -263,55 +279,79 @@ __global__ void __launch_bounds__(256) depth_max_kernel(const float *__restrict_
     if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
 }
 
-// The depth-tile pyramid of the frame (one CTA per 32 x 32 pixels) and its
-// largest accepted depth (bits in *out, zeroed by the setup kernel).
+// The depth-tile pyramids of the frame (one CTA per 32 x 32 pixels) and its
+// largest accepted depth (bits in *out, zeroed by the setup kernel).  The
+// accepted depths are positive floats, ordered like their bits.
 __global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restrict__ depth, FrameParams P,
                                                           unsigned *__restrict__ pyr, unsigned *__restrict__ out)
 {
-    __shared__ unsigned s_t[4][4];  // level 0: the block's 4 x 4 tiles of 8 x 8 pixels
-    __shared__ unsigned s_1[2][2];
+    constexpr unsigned kInf = 0x7F800000u;
+    __shared__ unsigned s_t[4][4], s_n[4][4];  // level 0: the block's 4 x 4 tiles of 8 x 8 pixels
+    __shared__ unsigned s_1[2][2], s_1n[2][2];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t < 16) s_t[t >> 2][t & 3] = 0u;
+    if (t < 16) {
+        s_t[t >> 2][t & 3] = 0u;
+        s_n[t >> 2][t & 3] = kInf;
+    }
     __syncthreads();
     // warp w reads rows w + 8 i (tile row i) of the block, lane = column
     const int x = blockIdx.x * 32 + lane;
-    float m[4];
+    float m[4], n[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         m[i] = 0.f;
+        n[i] = __uint_as_float(kInf);
         const int y = blockIdx.y * 32 + w + 8 * i;
         if (x < P.width && y < P.height) {
             const float D = __ldg(depth + (size_t)y * P.width + x);
-            if (D > 0.f && D >= P.z_min && D <= P.z_max) m[i] = D;
+            if (D > 0.f && D >= P.z_min && D <= P.z_max) m[i] = n[i] = D;
         }
     }
     // the 8 columns of a tile are 8 consecutive lanes; the 8 warps meet in shared memory
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        float v = m[i];
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
-        if ((lane & 7) == 0 && v > 0.f) atomicMax(&s_t[i][lane >> 3], __float_as_uint(v));
+        float v = m[i], u = n[i];
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            u = fminf(u, __shfl_xor_sync(0xffffffffu, u, o));
+        }
+        if ((lane & 7) == 0) {
+            if (v > 0.f) atomicMax(&s_t[i][lane >> 3], __float_as_uint(v));
+            if (__float_as_uint(u) != kInf) atomicMin(&s_n[i][lane >> 3], __float_as_uint(u));
+        }
     }
     __syncthreads();
+    const long long min_off = pyr_level_off(P.width, P.height, kPyrLevels);  // the smallest-depth pyramid
     if (t < 16) {
         const int tx = blockIdx.x * 4 + (t & 3), ty = blockIdx.y * 4 + (t >> 2);
-        if (tx < pyr_tiles(P.width, 0) && ty < pyr_tiles(P.height, 0))
-            pyr[(long long)ty * pyr_tiles(P.width, 0) + tx] = s_t[t >> 2][t & 3];
+        if (tx < pyr_tiles(P.width, 0) && ty < pyr_tiles(P.height, 0)) {
+            const long long i = (long long)ty * pyr_tiles(P.width, 0) + tx;
+            pyr[i] = s_t[t >> 2][t & 3];
+            pyr[min_off + i] = s_n[t >> 2][t & 3];
+        }
     } else if (t < 20) {
         const int k = t - 16, lx = k & 1, ly = k >> 1;
         const unsigned mx = max(max(s_t[2 * ly][2 * lx], s_t[2 * ly][2 * lx + 1]),
                                 max(s_t[2 * ly + 1][2 * lx], s_t[2 * ly + 1][2 * lx + 1]));
+        const unsigned mn = min(min(s_n[2 * ly][2 * lx], s_n[2 * ly][2 * lx + 1]),
+                                min(s_n[2 * ly + 1][2 * lx], s_n[2 * ly + 1][2 * lx + 1]));
         s_1[ly][lx] = mx;
+        s_1n[ly][lx] = mn;
         const int tx = blockIdx.x * 2 + lx, ty = blockIdx.y * 2 + ly;
-        if (tx < pyr_tiles(P.width, 1) && ty < pyr_tiles(P.height, 1))
-            pyr[pyr_level_off(P.width, P.height, 1) + (long long)ty * pyr_tiles(P.width, 1) + tx] = mx;
+        if (tx < pyr_tiles(P.width, 1) && ty < pyr_tiles(P.height, 1)) {
+            const long long i = pyr_level_off(P.width, P.height, 1) + (long long)ty * pyr_tiles(P.width, 1) + tx;
+            pyr[i] = mx;
+            pyr[min_off + i] = mn;
+        }
     }
     __syncthreads();
     if (t == 0) {
         const unsigned mx = max(max(s_1[0][0], s_1[0][1]), max(s_1[1][0], s_1[1][1]));
-        pyr[pyr_level_off(P.width, P.height, 2) + (long long)blockIdx.y * pyr_tiles(P.width, 2) + blockIdx.x] = mx;
+        const unsigned mn = min(min(s_1n[0][0], s_1n[0][1]), min(s_1n[1][0], s_1n[1][1]));
+        const long long i = pyr_level_off(P.width, P.height, 2) + (long long)blockIdx.y * pyr_tiles(P.width, 2) + blockIdx.x;
+        pyr[i] = mx;
+        pyr[min_off + i] = mn;
         if (mx) atomicMax(out, mx);
     }
 }
@@ -329,7 +369,7 @@ struct VoxelUpdate {
 
 __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &fr,
                                                const FrameParams &P, int bx, int by, int bz,
-                                               const float *__restrict__ depth, VoxelUpdate &u)
+                                               const float *__restrict__ depth, VoxelUpdate &u, bool front)
 {
     const int t = threadIdx.x;
     const int lx0 = (t & 1) * 4, ly = (t >> 1) & 7, lz = t >> 4;
@@ -380,6 +420,13 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         u.pix[j] = 0;
         const float D = Dj[j];
         if (!okj[j] || !(D > 0.f) || D < P.z_min || D > P.z_max) continue;
+        if (front) {
+            // the brick lies nearer than every depth of its pixels by more
+            // than mu: sdf >= mu, so f = 1 and no colour, as computed below
+            u.f[j] = 1.0f;
+            u.upd |= 1u << j;
+            continue;
+        }
         const float X = Xj[j], Y = Yj[j], Z = Zj[j];
         // projective distance along the voxel's ray, in voxels
         const float n2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
@@ -462,7 +509,7 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
                                                 const MaskOut &mo, uint2 item, ChgBuf &cb, int parity,
                                                 const unsigned *__restrict__ rcp)
 {
-    const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = (int)(packed >> 20);
+    const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = packed_bz(packed);
     const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
     const int t = threadIdx.x;
     const long long vox0 = b * kBrickVox + 4 * t;  // first of this thread's 4 voxels
@@ -480,7 +527,7 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
         a16 = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint32_t *>(v.fw) + vox0);
     }
     VoxelUpdate u;
-    project_voxels(v, fr, P, bx, by, bz, depth, u);
+    project_voxels(v, fr, P, bx, by, bz, depth, u, (packed & kListFree) != 0u);
     bool all_pos = true;  // every voxel this thread updated is stored > 0
     bool mchg = false;    // the update changed a voxel's "observed" or "F <= 0" bit
     bool pair_chg = false;  // ... of this thread or of its partner (same 8-voxel row)
@@ -808,7 +855,7 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
         if (!v.cflag || v.cmask) continue;
         const int cx = (int)(it.y & 1023u) - (d & 1);
         const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
-        const int cz = (int)(it.y >> 20) - ((d >> 2) & 1);
+        const int cz = packed_bz(it.y) - ((d >> 2) & 1);
         if (cx < 0 || cy < 0 || cz < 0) continue;
         update_cell_flag(v, cx, cy, cz, cell_skip_of(v, cx, cy, cz));
     }
@@ -833,7 +880,7 @@ __global__ void __launch_bounds__(256) cell_masks_kernel(const VolDev *__restric
         const VolDev &v = vols[it.x];
         const int cx = (int)(it.y & 1023u) - (d & 1);
         const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
-        const int cz = (int)(it.y >> 20) - ((d >> 2) & 1);
+        const int cz = packed_bz(it.y) - ((d >> 2) & 1);
         if (cx < 0 || cy < 0 || cz < 0) continue;  // uniform over the 8 slices
         const unsigned group = 0xFFu << (threadIdx.x & 24u);  // the 8 slices of this cell brick
         if (d) {
@@ -983,7 +1030,7 @@ __global__ void __launch_bounds__(128) stream_scatter_kernel(VolDev v, const uin
     const uint4 *scol = reinterpret_cast<const uint4 *>(v.rgba);
     for (unsigned i = warp; i < n; i += nwarps) {
         const unsigned pk = list[i].y;
-        const long long b = ((long long)(pk >> 20) * v.nb[1] + ((pk >> 10) & 1023u)) * v.nb[0] + (pk & 1023u);
+        const long long b = ((long long)packed_bz(pk) * v.nb[1] + ((pk >> 10) & 1023u)) * v.nb[0] + (pk & 1023u);
         uint4 a[8], c[4];
 #pragma unroll
         for (int k = 0; k < 8; ++k)

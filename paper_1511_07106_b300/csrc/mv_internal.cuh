@@ -139,10 +139,12 @@ inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
 constexpr size_t kMaskBytesPerBrick = 260;
 inline size_t mask_alloc_bytes(long long nbricks) { return (size_t)nbricks * kMaskBytesPerBrick; }
 
-// Per-frame pyramid of the largest accepted depth over square pixel tiles of
-// 8, 16 and 32 pixels (float bits, 0 where no pixel of the tile has an
-// accepted depth): level L is a row-major grid of ceil(W / 2^(L+3)) x
-// ceil(H / 2^(L+3)) tiles, the levels stored one after the other.
+// Per-frame pyramids of the largest and of the smallest accepted depth over
+// square pixel tiles of 8, 16 and 32 pixels (float bits; where no pixel of the
+// tile has an accepted depth, 0 in the largest and +inf in the smallest):
+// level L is a row-major grid of ceil(W / 2^(L+3)) x ceil(H / 2^(L+3)) tiles,
+// the levels stored one after the other, the smallest-depth pyramid after the
+// largest-depth one.
 constexpr int kPyrLevels = 3;
 struct PyrDims {
     int nx[kPyrLevels], ny[kPyrLevels];
@@ -170,6 +172,12 @@ __host__ __device__ inline long long pyr_level_off(int width, int height, int le
     for (int l = 0; l < level; ++l) acc += (long long)pyr_tiles(width, l) * pyr_tiles(height, l);
     return acc;
 }
+
+// Work-list entry (table slot, packed brick coordinates bx | by << 10 | bz << 20):
+// bit 30 marks a brick in front of every accepted depth of its pixels by
+// more than mu, whose updated voxels all take f = 1 and no colour.
+constexpr unsigned kListFree = 1u << 30;
+__host__ __device__ inline int packed_bz(unsigned packed) { return (int)((packed >> 20) & 1023u); }
 
 struct Stats {
     unsigned long long swept, updated, band, bricks;

@@ -992,7 +992,8 @@ mv_status mv_list_volumes(mv_ctx *c, int32_t *ids, int32_t cap, int32_t *count)
 // or launch of the call uses it).
 static mv_status ensure_pyramid(mv_ctx *c, const mv_intrinsics *K)
 {
-    const size_t words = (size_t)pyr_dims(K->width, K->height).off[kPyrLevels];
+    // the largest-depth pyramid, then the smallest-depth one
+    const size_t words = 2 * (size_t)pyr_dims(K->width, K->height).off[kPyrLevels];
     if (words <= c->pyr_words) return MV_OK;
     MV_CUDA(c, cudaDeviceSynchronize());  // an earlier call may still read the old buffer
     if (c->d_pyr) MV_CUDA(c, cudaFree(c->d_pyr));
