@@ -126,10 +126,10 @@ enum {
     MV_KERNEL_INTEGRATE = 2,   /* TSDF + colour update of the listed bricks */
     MV_KERNEL_RAYCAST = 3,     /* per-pixel march, refinement, shading and merge */
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
-    MV_KERNEL_CELL_FLAGS = 5,  /* raycast step-over flags refreshed after an integration */
+    MV_KERNEL_CELL_FLAGS = 5,  /* raycast cell masks and step-over flags refreshed after an integration */
     MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
     MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 kernels are also counted by kind) */
-    MV_KERNEL_DEPTH_MAX = 8,   /* farthest accepted depth of the frame (far bound of the brick list) */
+    MV_KERNEL_DEPTH_MAX = 8,   /* the frame's depth-tile pyramids and farthest accepted depth (brick list bounds) */
     MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
     MV_KERNEL_DEPTH_MAPS = 10, /* vertex / normal maps of a depth frame */
     MV_KERNEL_ICP = 11,        /* one point-to-plane ICP linearisation */

@@ -51,7 +51,7 @@ class mv_stats(C.Structure):
 
 MV_KERNEL_KINDS = 13
 KERNEL_NAMES = {0: "setup", 1: "brick_list", 2: "integrate", 3: "raycast", 4: "flags",
-                5: "cell_flags", 6: "backward", 7: "frame_graph", 8: "depth_max",
+                5: "cell_masks", 6: "backward", 7: "frame_graph", 8: "depth_tiles",
                 9: "extract", 10: "depth_maps", 11: "icp",
                 12: "stream"}
 
