@@ -232,18 +232,21 @@ __device__ __forceinline__ void shade(const VolDev &v, const Geo<Off> &geo, cons
 
 // DDA set-up along one axis: parameter (in samples) of the first brick face
 // crossed from L, spacing of the faces, step direction, and the domain end
-// (the last voxel plane less m) for positive directions.
+// (the last voxel plane less m) for positive directions.  Products with the
+// rounded reciprocal of dq instead of quotients: a few ulp of the parameters,
+// far inside the margin m of the landing.
 __device__ __forceinline__ void dda_axis(float L, float dq, int b0, int r, float m, float &tmax,
                                          float &tdel, int &step, float &tdom)
 {
+    const float rq = __frcp_rn(dq);
     if (dq > 0.f) {
-        tmax = ((float)((b0 + 1) * kBrick) - L) / dq;
-        tdel = (float)kBrick / dq;
+        tmax = ((float)((b0 + 1) * kBrick) - L) * rq;
+        tdel = (float)kBrick * rq;
         step = 1;
-        tdom = fminf(tdom, ((float)(r - 1) - m - L) / dq);
+        tdom = fminf(tdom, ((float)(r - 1) - m - L) * rq);
     } else if (dq < 0.f) {
-        tmax = ((float)(b0 * kBrick) - L) / dq;
-        tdel = -(float)kBrick / dq;
+        tmax = ((float)(b0 * kBrick) - L) * rq;
+        tdel = -(float)kBrick * rq;
         step = -1;
     } else {
         tmax = 3.0e38f;
@@ -334,19 +337,9 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
         if (new_super) empty = v.sup && super_empty(v, bx, by, bz);
         if (!empty && !(cf & kCellSkip)) break;
     }
-    return fminf(texit - m / dexit, tdom);
+    return fminf(texit - m * __frcp_rn(dexit), tdom);
 }
 
-// March one ray through one volume; updates `best` when this volume's hit is
-// nearer (or equally near with a lower id).
-//
-// Step-over rule: a sample can end a bracket only if it is valid with F <= 0,
-// which needs an observed voxel with F <= 0 among its cell's corners.  Inside
-// a run of cell bricks flagged kCellSkip no such voxel exists, so no sample in
-// the run can end a bracket, and the march state after the run is fixed by
-// the run's last sample alone.  The march therefore jumps to that last sample
-// (at least m voxels inside the run) and evaluates it normally: the result is
-// that of the dense march, not an approximation.
 // Ray state of one volume: camera lattice point and fraction, the direction
 // in voxels, and (after the domain is known) the grid step dq = dirv * Delta.
 __device__ __forceinline__ void vol_ray(const VolDev &v, const VolFrame &vf, const float d[3], VolRay &vr,
@@ -364,6 +357,28 @@ __device__ __forceinline__ float grid_step(const VolDev &v, const FrameParams &P
 {
     return P.ray_step * v.s / dn;
 }
+
+// March one ray through one volume; updates `best` when this volume's hit is
+// nearer (or equally near with a lower id).
+//
+// Step-over rule: a sample can end a bracket only if it is valid with F <= 0,
+// which needs an observed voxel with F <= 0 among its cell's corners.  Inside
+// a run of cell bricks flagged kCellSkip no such voxel exists, so no sample in
+// the run can end a bracket, and the march state after the run is fixed by
+// the run's last sample alone.  The march therefore jumps to that last sample
+// (at least m voxels inside the run) and evaluates it normally: the result is
+// that of the dense march, not an approximation.
+//
+// Step-over policy: stepping over a run and walking through it sample by
+// sample (each sample decided by its cell masks) end in the same state, so
+// whether a run is stepped over changes the cost, never the result.  A DDA
+// taken by a few lanes of a warp holds the other lanes, and runs met after a
+// landing are often short, so with cell masks a later run is stepped over
+// only kSkipGap samples after the last landing, or while at most kSkipLanes
+// lanes of the warp are still marching (the warp's stragglers).  Without
+// masks a walk evaluates every sample, so every run is stepped over.
+constexpr int kSkipGap = 48;
+constexpr int kSkipLanes = 8;
 
 template <int FMT, typename Off>
 __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FrameParams &P,
@@ -405,7 +420,9 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
     float Fprev = 0.f;
     bool prev_read = false;  // Fprev holds the previous sample's value (not decided by its mask)
     int cur_b = -1;
+    int last_land = -kSkipGap;  // the first run is always stepped over
     for (int kk = 0; kk <= nk; ++kk) {
+        const int lanes = __popc(__activemask());
         float k = k0 + (float)kk;
         float rr[3];
         int cell[3];
@@ -416,7 +433,8 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
         int bidx = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
         if (bidx != cur_b) {
             cur_b = bidx;
-            if (__ldg(v.cflag + bidx) & kCellSkip) {
+            const bool may_skip = !v.cmask || kk - last_land >= kSkipGap || lanes <= kSkipLanes;
+            if (may_skip && (__ldg(v.cflag + bidx) & kCellSkip)) {
                 float L[3];
                 int bi[3];
                 bool inside = true;
@@ -440,6 +458,7 @@ __device__ void march_volume(const VolDev &v, const VolFrame &vf, const FramePar
                         cur_b = ((cell[2] >> 3) * g.nby + (cell[1] >> 3)) * (int)g.nb0 + (cell[0] >> 3);
                         bidx = cur_b;
                         state = 0;
+                        last_land = kk;
                         ++rc.skips;
                     }
                 }
