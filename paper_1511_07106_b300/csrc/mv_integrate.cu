@@ -782,21 +782,53 @@ __device__ __forceinline__ unsigned *super_count_of(const VolDev &v, int cx, int
     return v.sup + ((long long)(cz / kSuper) * v.nsb[1] + cy / kSuper) * v.nsb[0] + cx / kSuper;
 }
 
+// The count of super brick (sx, sy, sz) became non-zero (up = true) or zero:
+// every super brick within Chebyshev distance kSupReach moves its
+// neighbour counts.  Additions and subtractions commute, so the words are
+// exact once every change of the kernel has been applied, whatever the
+// order (a field may wrap in between; nothing reads them in between).  The
+// (2 kSupReach + 1)^3 neighbours k = first, first + stride, ... are done
+// here (several threads may share them).
+__device__ void super_occupancy_changed(const VolDev &v, int sx, int sy, int sz, bool up, int first, int stride)
+{
+    constexpr int kSide = 2 * kSupReach + 1;
+    for (int k = first; k < kSide * kSide * kSide; k += stride) {
+        const int dx = k % kSide - kSupReach, dy = (k / kSide) % kSide - kSupReach, dz = k / (kSide * kSide) - kSupReach;
+        const int x = sx + dx, y = sy + dy, z = sz + dz;
+        if (x < 0 || y < 0 || z < 0 || x >= v.nsb[0] || y >= v.nsb[1] || z >= v.nsb[2]) continue;
+        const int d = max(abs(dx), max(abs(dy), abs(dz)));
+        const unsigned inc = (d <= 1 ? kSupNear1 : 0u) + kSupNear2;
+        atomicAdd(v.sup + ((long long)z * v.nsb[1] + y) * v.nsb[0] + x, up ? inc : 0u - inc);
+    }
+}
+
+// Moves the count of the super brick holding cell brick (cx, cy, cz) by one
+// (up: a cell brick lost kCellSkip).  The count never drops below zero (a
+// decrement follows the increment of the same cell brick), so the returned
+// old value tells exactly one thread of each change to or from zero: +1 when
+// the count left zero, -1 when it reached zero, else 0.
+__device__ __forceinline__ int move_super_count(const VolDev &v, int cx, int cy, int cz, bool up)
+{
+    const unsigned old = atomicAdd(super_count_of(v, cx, cy, cz), up ? 1u : 0xFFFFFFFFu);
+    return (old & kSupCount) == (up ? 0u : 1u) ? (up ? 1 : -1) : 0;
+}
+
 // Incremental refresh: the flag byte is changed by an atomic on its aligned
 // word, whose returned old value tells exactly one of several threads that
 // refresh the same cell brick that the flag changed; that thread moves the
-// super-brick count.
-__device__ __forceinline__ void update_cell_flag(const VolDev &v, int cx, int cy, int cz, bool skip)
+// super-brick count.  Returns move_super_count's change to or from zero
+// (the caller updates the neighbour counts).
+__device__ __forceinline__ int update_cell_flag(const VolDev &v, int cx, int cy, int cz, bool skip)
 {
     uint8_t *pb = v.cflag + ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
     if (!v.sup) {
         *pb = skip ? kCellSkip : 0;
-        return;
+        return 0;
     }
     unsigned *w = reinterpret_cast<unsigned *>(reinterpret_cast<uintptr_t>(pb) & ~(uintptr_t)3);
     const unsigned bit = (unsigned)kCellSkip << (8u * (unsigned)(reinterpret_cast<uintptr_t>(pb) & 3u));
     const unsigned old = skip ? atomicOr(w, bit) : atomicAnd(w, ~bit);
-    if (((old & bit) != 0u) != skip) atomicAdd(super_count_of(v, cx, cy, cz), skip ? 0xFFFFFFFFu : 1u);
+    return ((old & bit) != 0u) != skip ? move_super_count(v, cx, cy, cz, !skip) : 0;
 }
 
 // Row z (0..7) of the voxel mask `plane` (0 observed, 1 observed with F <= 0)
@@ -857,7 +889,8 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
         const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
         const int cz = packed_bz(it.y) - ((d >> 2) & 1);
         if (cx < 0 || cy < 0 || cz < 0) continue;
-        update_cell_flag(v, cx, cy, cz, cell_skip_of(v, cx, cy, cz));
+        const int ch = update_cell_flag(v, cx, cy, cz, cell_skip_of(v, cx, cy, cz));
+        if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, 0, 1);
     }
 }
 
@@ -900,7 +933,11 @@ __global__ void __launch_bounds__(256) cell_masks_kernel(const VolDev *__restric
         nz |= __shfl_xor_sync(group, nz, 1);
         nz |= __shfl_xor_sync(group, nz, 2);
         nz |= __shfl_xor_sync(group, nz, 4);
-        if (z == 0) update_cell_flag(v, cx, cy, cz, nz == 0ull);
+        int ch = z == 0 ? update_cell_flag(v, cx, cy, cz, nz == 0ull) : 0;
+        // a change of the super count to or from zero: the 8 slice threads
+        // share the neighbour updates
+        ch = __shfl_sync(group, ch, (int)(threadIdx.x & 24u));
+        if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, z, 8);
     }
 }
 
@@ -947,7 +984,7 @@ __global__ void __launch_bounds__(256) cmask_all_kernel(VolDev v)
 }
 
 // Every cell-brick flag of one volume (after a host write), with the
-// super-brick counts recounted from zero (zeroed before this kernel).
+// super-brick words recounted from zero (zeroed before this kernel).
 __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -957,7 +994,8 @@ __global__ void __launch_bounds__(256) cell_flags_all_kernel(VolDev v)
         const int cz = (int)(b / ((long long)v.nb[0] * v.nb[1]));
         const bool skip = cell_skip_of(v, cx, cy, cz);
         v.cflag[b] = skip ? kCellSkip : 0;
-        if (!skip && v.sup) atomicAdd(super_count_of(v, cx, cy, cz), 1u);
+        if (!skip && v.sup && move_super_count(v, cx, cy, cz, true))
+            super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, true, 0, 1);
     }
 }
 

@@ -54,7 +54,16 @@ constexpr uint8_t kFlagsNew = kFlagEmpty | kFlagNoNeg;  // a freshly cleared bri
 constexpr uint8_t kCellSkip = 1;
 // Super brick: kSuper^3 cell bricks (32^3 voxels).  A super brick whose count
 // of cell bricks without kCellSkip is 0 is crossed by the raycast in one step.
+// Its 32-bit word holds that count in bits 0-7 (at most 64) and, for the
+// super bricks within Chebyshev distance 1 (the 3^3 block around it, itself
+// included, clipped to the grid) and 2 (the 5^3 block), how many have a
+// non-zero count, in bits 8-15 (at most 27) and 16-23 (at most 125): with
+// such a count 0 the raycast crosses the whole block in one step.
 constexpr int kSuper = 4;
+constexpr unsigned kSupCount = 0xFFu;
+constexpr unsigned kSupNear1 = 1u << 8;
+constexpr unsigned kSupNear2 = 1u << 16;
+constexpr int kSupReach = 2;
 constexpr int kMaxVolumes = 4096;
 
 // One volume as the kernels see it.
@@ -64,7 +73,7 @@ struct VolDev {
     uint8_t *bflag;    // one flag byte per brick
     uint8_t *cflag;    // one cell-brick byte per brick (may be null where no raycast reads it)
     unsigned *surf;    // bricks without kFlagNoNeg (0: no hit possible anywhere), may be null
-    unsigned *sup;     // per super brick: cell bricks without kCellSkip (may be null)
+    unsigned *sup;     // per super brick: counts of non-skippable cell bricks and neighbours (may be null)
     unsigned long long *vmask;  // per-voxel masks, 16 x u64 per brick (may be null)
     ulonglong2 *cmask;          // per-cell masks, 8 x (V, N) per brick (may be null)
     unsigned *stamp;            // per brick: id of the last integration that listed it (may be null)
@@ -122,7 +131,7 @@ struct VisList {
 // voxel-brick flags (1 B/brick), cell-brick flags (1 B/brick, 4-byte
 // aligned so that a flag byte can be changed by a 32-bit atomic on its word),
 // the count of bricks without kFlagNoNeg (u32, 8-byte aligned), then per
-// super brick the count of its cell bricks without kCellSkip (u32).
+// super brick its word of counts (u32, see kSupCount).
 inline size_t cflag_offset(long long nbricks) { return ((size_t)nbricks + 3) & ~(size_t)3; }
 inline size_t flag_count_offset(long long nbricks)
 {

@@ -255,18 +255,22 @@ __device__ __forceinline__ void dda_axis(float L, float dq, int b0, int r, float
     }
 }
 
-__device__ __forceinline__ bool super_empty(const VolDev &v, int bx, int by, int bz)
+// Word of the super brick holding cell brick (bx, by, bz); volumes without
+// super bricks read as "not empty".
+__device__ __forceinline__ unsigned super_word(const VolDev &v, int bx, int by, int bz)
 {
+    if (!v.sup) return 1u;
     const unsigned i = (((unsigned)bz >> 2) * (unsigned)v.nsb[1] + ((unsigned)by >> 2)) * (unsigned)v.nsb[0] +
                        ((unsigned)bx >> 2);
-    return __ldg(v.sup + i) == 0u;
+    return __ldg(v.sup + i);
 }
 
-// Brick boundaries along one axis between brick b and the face of its super
-// brick in the step direction.
-__device__ __forceinline__ int inner_faces(int b, int step)
+// Brick boundaries along one axis between brick b and the face, in the step
+// direction, of the block of super bricks within Chebyshev distance `reach`
+// of b's super brick, clipped to the grid of nb bricks.
+__device__ __forceinline__ int inner_faces(int b, int step, int reach, int nb)
 {
-    return step > 0 ? 3 - (b & 3) : (step < 0 ? (b & 3) : 0);
+    return step > 0 ? min(3 - (b & 3) + 4 * reach, nb - 1 - b) : (step < 0 ? min((b & 3) + 4 * reach, b) : 0);
 }
 
 // Brick boundaries along one axis crossed by parameter texit (next boundary
@@ -282,7 +286,9 @@ __device__ __forceinline__ int faces_crossed(float tmax, float rdel, float texit
 // 3D DDA from the sample at L (volume voxel coordinates, cell brick b0,
 // flagged kCellSkip) along dq (voxels per sample) over cell bricks flagged
 // kCellSkip; a super brick (kSuper^3 cell bricks) whose count of cell bricks
-// without kCellSkip is 0 is crossed in one step.  Returns, in samples from L,
+// without kCellSkip is 0 is crossed in one step, and so is the block of super
+// bricks within distance 1 or 2 of it when their counts are all 0 (the
+// neighbour counts of its word).  Returns, in samples from L,
 // the end of that run of bricks less m voxels (capped at the domain end less
 // m).
 __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], const float dq[3],
@@ -299,12 +305,15 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
     const int nbx = v.nb[0], nby = v.nb[1], nbz = v.nb[2];
     const int max_steps = nbx + nby + nbz + 3;
     float texit = 0.f, dexit = 1.f;
-    bool empty = v.sup && super_empty(v, bx, by, bz);
+    unsigned sw = super_word(v, bx, by, bz);
     for (int it = 0; it < max_steps; ++it) {
         bool out, new_super;
-        if (empty) {
-            // to the face of the super brick, every axis advanced to match
-            const int nx = inner_faces(bx, sx), ny = inner_faces(by, sy), nz = inner_faces(bz, sz);
+        if ((sw & kSupCount) == 0u) {
+            // to the face of the super brick, or of the empty block around it,
+            // every axis advanced to match
+            const int reach = (sw & (0xFFu * kSupNear2)) == 0u ? 2 : ((sw & (0xFFu * kSupNear1)) == 0u ? 1 : 0);
+            const int nx = inner_faces(bx, sx, reach, nbx), ny = inner_faces(by, sy, reach, nby),
+                      nz = inner_faces(bz, sz, reach, nbz);
             const float fx = tx + (float)nx * dx, fy = ty + (float)ny * dy, fz = tz + (float)nz * dz;
             int jx, jy, jz;
             if (fx <= fy && fx <= fz) {
@@ -334,8 +343,8 @@ __device__ __forceinline__ float skip_run(const VolDev &v, const float L[3], con
         }
         if (out) break;
         const uint8_t cf = __ldg(v.cflag + ((long long)bz * nby + by) * nbx + bx);
-        if (new_super) empty = v.sup && super_empty(v, bx, by, bz);
-        if (!empty && !(cf & kCellSkip)) break;
+        if (new_super) sw = super_word(v, bx, by, bz);
+        if ((sw & kSupCount) != 0u && !(cf & kCellSkip)) break;
     }
     return fminf(texit - m * __frcp_rn(dexit), tdom);
 }

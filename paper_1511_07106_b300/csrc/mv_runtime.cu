@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -1696,7 +1697,22 @@ mv_status mv_write_volume(mv_ctx *c, int32_t id, const void *host_fw, const uint
             v->h_flag[cflag_offset(nb) + b] = skip ? kCellSkip : 0;
             if (!skip) ++sup[((size_t)(cz / kSuper) * v->nsb[1] + cy / kSuper) * v->nsb[0] + cx / kSuper];
         }
-        std::memcpy(v->h_flag + super_offset(nb), sup.data(), sizeof(unsigned) * sup.size());
+        // neighbour counts of the super-brick words (see kSupCount)
+        std::vector<unsigned> word(sup);
+        for (int sz = 0; sz < v->nsb[2]; ++sz)
+            for (int sy = 0; sy < v->nsb[1]; ++sy)
+                for (int sx = 0; sx < v->nsb[0]; ++sx) {
+                    if (!sup[((size_t)sz * v->nsb[1] + sy) * v->nsb[0] + sx]) continue;
+                    for (int z = std::max(0, sz - kSupReach); z <= std::min(v->nsb[2] - 1, sz + kSupReach); ++z)
+                        for (int y = std::max(0, sy - kSupReach); y <= std::min(v->nsb[1] - 1, sy + kSupReach); ++y)
+                            for (int x = std::max(0, sx - kSupReach); x <= std::min(v->nsb[0] - 1, sx + kSupReach);
+                                 ++x) {
+                                const int d = std::max(std::abs(x - sx), std::max(std::abs(y - sy), std::abs(z - sz)));
+                                word[((size_t)z * v->nsb[1] + y) * v->nsb[0] + x] +=
+                                    (d <= 1 ? kSupNear1 : 0u) + kSupNear2;
+                            }
+                }
+        std::memcpy(v->h_flag + super_offset(nb), word.data(), sizeof(unsigned) * word.size());
     }
     return MV_OK;
 }
