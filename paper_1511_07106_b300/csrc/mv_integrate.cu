@@ -898,46 +898,65 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
 // the bricks whose voxel masks changed (and stamped them with stamp_id);
 // every cell brick c that reads one of them (c = b - d, d in {0,1}^3) gets its
 // cell masks and its flag recomputed, once: by the smallest d for which
-// c + d changed.  One thread per (changed brick, d, slice).
-__global__ void __launch_bounds__(256) cell_masks_kernel(const VolDev *__restrict__ vols,
-                                                         const uint2 *__restrict__ changed,
-                                                         const unsigned *__restrict__ counter,
-                                                         unsigned stamp_id)
+// c + d changed.  Each CTA first gives one thread to each of kCellMaskPairs
+// (changed brick, d) pairs and collects the cell bricks they own in shared
+// memory, then refreshes those with 8 threads each (one per slice), so that
+// pairs owned elsewhere hold no lanes during the refresh.
+constexpr int kCellMaskCta = 256;
+constexpr int kCellMaskPairs = 64;
+__global__ void __launch_bounds__(kCellMaskCta) cell_masks_kernel(const VolDev *__restrict__ vols,
+                                                                const uint2 *__restrict__ changed,
+                                                                const unsigned *__restrict__ counter,
+                                                                unsigned stamp_id)
 {
-    const unsigned long long n = 64ull * (*counter);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += stride) {
-        const uint2 it = changed[i >> 6];
-        const int d = (int)((i >> 3) & 7), z = (int)(i & 7);
-        const VolDev &v = vols[it.x];
-        const int cx = (int)(it.y & 1023u) - (d & 1);
-        const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
-        const int cz = packed_bz(it.y) - ((d >> 2) & 1);
-        if (cx < 0 || cy < 0 || cz < 0) continue;  // uniform over the 8 slices
-        const unsigned group = 0xFFu << (threadIdx.x & 24u);  // the 8 slices of this cell brick
-        if (d) {
-            // lane z tests whether c + z (z < d) changed too
-            bool earlier = false;
-            const int x = cx + (z & 1), y = cy + ((z >> 1) & 1), w = cz + (z >> 2);
-            if (z < d && x < v.nb[0] && y < v.nb[1] && w < v.nb[2])
-                earlier = __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) == stamp_id;
-            if (__ballot_sync(group, earlier)) continue;
+    __shared__ uint2 s_item[kCellMaskPairs];  // (table slot, packed cell brick) owned by this CTA
+    __shared__ unsigned s_n;
+    const unsigned long long n = 8ull * (*counter);
+    const int t = threadIdx.x, z = t & 7;
+    const unsigned group = 0xFFu << (t & 24);  // the 8 slice threads of one cell brick
+    for (unsigned long long base = (unsigned long long)blockIdx.x * kCellMaskPairs; base < n;
+         base += (unsigned long long)gridDim.x * kCellMaskPairs) {
+        if (t == 0) s_n = 0;
+        __syncthreads();
+        const unsigned long long i = base + t;
+        if (t < kCellMaskPairs && i < n) {
+            const uint2 it = changed[i >> 3];
+            const int d = (int)(i & 7);
+            const VolDev &v = vols[it.x];
+            const int cx = (int)(it.y & 1023u) - (d & 1);
+            const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
+            const int cz = packed_bz(it.y) - ((d >> 2) & 1);
+            bool own = cx >= 0 && cy >= 0 && cz >= 0;
+            // not the owner when c + e changed for some e < d
+            for (int e = 0; own && e < d; ++e) {
+                const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), w = cz + (e >> 2);
+                if (x < v.nb[0] && y < v.nb[1] && w < v.nb[2])
+                    own = __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) != stamp_id;
+            }
+            if (own) s_item[atomicAdd(&s_n, 1u)] = make_uint2(it.x, (unsigned)cx | ((unsigned)cy << 10) | ((unsigned)cz << 20));
         }
-        const long long c = ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
-        const ulonglong2 m = cell_mask_slice(v, cx, cy, cz, z);
-        v.cmask[c * 8 + z] = m;
-        // the cell brick can be stepped over when none of its cells has an
-        // observed corner with F <= 0 (OR of the 8 slices' N rows)
-        unsigned long long nz = m.y;
-        nz |= __shfl_xor_sync(group, nz, 1);
-        nz |= __shfl_xor_sync(group, nz, 2);
-        nz |= __shfl_xor_sync(group, nz, 4);
-        int ch = z == 0 ? update_cell_flag(v, cx, cy, cz, nz == 0ull) : 0;
-        // a change of the super count to or from zero: the 8 slice threads
-        // share the neighbour updates
-        ch = __shfl_sync(group, ch, (int)(threadIdx.x & 24u));
-        if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, z, 8);
+        __syncthreads();
+        const unsigned m = s_n;
+        for (unsigned k = (unsigned)t >> 3; k < m; k += kCellMaskCta / 8) {
+            const uint2 it = s_item[k];
+            const VolDev &v = vols[it.x];
+            const int cx = (int)(it.y & 1023u), cy = (int)((it.y >> 10) & 1023u), cz = (int)(it.y >> 20);
+            const long long c = ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
+            const ulonglong2 mk = cell_mask_slice(v, cx, cy, cz, z);
+            v.cmask[c * 8 + z] = mk;
+            // the cell brick can be stepped over when none of its cells has an
+            // observed corner with F <= 0 (OR of the 8 slices' N rows)
+            unsigned long long nz = mk.y;
+            nz |= __shfl_xor_sync(group, nz, 1);
+            nz |= __shfl_xor_sync(group, nz, 2);
+            nz |= __shfl_xor_sync(group, nz, 4);
+            int ch = z == 0 ? update_cell_flag(v, cx, cy, cz, nz == 0ull) : 0;
+            // a change of the super count to or from zero: the 8 slice threads
+            // share the neighbour updates
+            ch = __shfl_sync(group, ch, t & 24);
+            if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, z, 8);
+        }
+        __syncthreads();
     }
 }
 
@@ -1201,7 +1220,7 @@ cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsig
 cudaError_t launch_cell_masks(const VolDev *vols, const uint2 *changed, const unsigned *counter,
                               unsigned stamp_id, int num_sms, cudaStream_t s)
 {
-    cell_masks_kernel<<<num_sms * 4, 256, 0, s>>>(vols, changed, counter, stamp_id);
+    cell_masks_kernel<<<num_sms * 8, kCellMaskCta, 0, s>>>(vols, changed, counter, stamp_id);
     return cudaGetLastError();
 }
 
@@ -1240,7 +1259,7 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
     e = graph_node(g, exec, &nodes[3], nodes[2], a2.params((const void *)integrate_kernel, grid_int, 128));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const uint2 *, const unsigned *, unsigned> a3(vols, changed, counter + 2, stamp_id);
-    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_masks_kernel, num_sms * 4, 256));
+    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_masks_kernel, num_sms * 8, kCellMaskCta));
 }
 
 int integrate_max_ctas_per_sm()
