@@ -122,13 +122,13 @@ typedef struct {
 /* Kernel kinds counted and timed by mv_get_timings. */
 enum {
     MV_KERNEL_SETUP = 0,       /* per-call camera constants of every volume */
-    MV_KERNEL_BRICK_LIST = 1,  /* frustum work list of bricks */
+    MV_KERNEL_BRICK_LIST = 1,  /* frustum work list of bricks (batched calls: super bricks, then their bricks) */
     MV_KERNEL_INTEGRATE = 2,   /* TSDF + colour update of the listed bricks */
     MV_KERNEL_RAYCAST = 3,     /* per-pixel march, refinement, shading and merge */
     MV_KERNEL_FLAGS = 4,       /* brick summaries recomputed after a host write */
     MV_KERNEL_CELL_FLAGS = 5,  /* raycast cell masks and step-over flags refreshed after an integration */
     MV_KERNEL_BACKWARD = 6,    /* raycast gradients */
-    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 kernels are also counted by kind) */
+    MV_KERNEL_FRAME_GRAPH = 7, /* one mv_frame graph (its 6 or 7 kernels are also counted by kind) */
     MV_KERNEL_DEPTH_MAX = 8,   /* the frame's depth-tile pyramids and farthest accepted depth (brick list bounds) */
     MV_KERNEL_EXTRACT = 9,     /* surface points of a volume */
     MV_KERNEL_DEPTH_MAPS = 10, /* vertex / normal maps of a depth frame */
@@ -210,7 +210,7 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
 
 /* One frame of the paper's per-frame loop: integrate the frame into every
  * resident volume, then raycast every resident volume at the same pose, as
- * one CUDA graph launch (6 kernels).  Same semantics and outputs as
+ * one CUDA graph launch (6 kernels; 7 with the two-level work list).  Same semantics and outputs as
  * mv_integrate followed by mv_raycast.  The graph is built on the first call
  * and rebuilt when the set of resident volumes or the image size changes;
  * otherwise each call only updates the graph's kernel parameters (pose and
@@ -259,6 +259,9 @@ typedef struct {
     float raycast_ms[4];           /* median per tile shape (mv_autotune only) */
     float integrate_ms[5];         /* median for 2, 4, 6, 8, 10 CTAs per SM (mv_autotune only;
                                       0 where not measured) */
+    int32_t work_list_levels;      /* work list of the batched calls: 1 one thread per brick,
+                                      2 super bricks in view first, then their bricks; 0 automatic
+                                      (2 from 2^20 resident bricks on).  Same list either way. */
 } mv_tuning;
 
 /* Choose the raycast pixel tile and the integration grid size by timing the
@@ -272,7 +275,8 @@ typedef struct {
 mv_status mv_autotune(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
                       const double T_c2w[16], mv_tuning *out, void *stream);
 
-/* Set / read the launch shapes (raycast_tile, integrate_ctas_per_sm). */
+/* Set / read the launch shapes (raycast_tile, integrate_ctas_per_sm,
+ * work_list_levels); mv_autotune keeps work_list_levels. */
 mv_status mv_set_tuning(mv_ctx *ctx, const mv_tuning *t);
 mv_status mv_get_tuning(mv_ctx *ctx, mv_tuning *t);
 

@@ -63,7 +63,8 @@ class mv_timings(C.Structure):
 
 class mv_tuning(C.Structure):
     _fields_ = [("raycast_tile", C.c_int32), ("integrate_ctas_per_sm", C.c_int32),
-                ("raycast_ms", C.c_float * 4), ("integrate_ms", C.c_float * 5)]
+                ("raycast_ms", C.c_float * 4), ("integrate_ms", C.c_float * 5),
+                ("work_list_levels", C.c_int32)]
 
 
 class mv_grad_target(C.Structure):

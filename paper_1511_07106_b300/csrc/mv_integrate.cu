@@ -102,17 +102,17 @@ __device__ __forceinline__ int brick_depth_class(const float lo[3], const float 
     return kDepthMixed;
 }
 
-// 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu
-__device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
-                                             const FrameParams &P, int bx, int by, int bz, float z_far,
-                                             const unsigned *__restrict__ pyr)
+// The box of voxels n * bi .. n * bi + n - 1 per axis (clipped to the volume):
+// 0 when the frame updates none of them; 1 when it may; 2 when it may and
+// every voxel lies in front of every depth of its pixels by more than mu.
+__device__ __forceinline__ int box_class(const VolDev &v, const VolFrame &f, const FrameParams &P, int n,
+                                         const int bi[3], float z_far, const unsigned *__restrict__ pyr)
 {
     float lo[3], hi[3];
-    const int bi[3] = {bx, by, bz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int l = bi[a] * kBrick;
-        const int u = min(l + kBrick - 1, v.r[a] - 1);
+        const int l = bi[a] * n;
+        const int u = min(l + n - 1, v.r[a] - 1);
         lo[a] = (float)(v.h[a] + l - f.cam_int[a]) - f.cam_frac[a];
         hi[a] = (float)(v.h[a] + u - f.cam_int[a]) - f.cam_frac[a];
     }
@@ -120,6 +120,15 @@ __device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
     if (!pyr) return 1;
     const int cls = brick_depth_class(lo, hi, P, v.inv_s, pyr);
     return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : 1);
+}
+
+// 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu
+__device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
+                                             const FrameParams &P, int bx, int by, int bz, float z_far,
+                                             const unsigned *__restrict__ pyr)
+{
+    const int bi[3] = {bx, by, bz};
+    return box_class(v, f, P, kBrick, bi, z_far, pyr);
 }
 
 // ---------------------------------------------------------------------------
@@ -162,6 +171,7 @@ __global__ void __launch_bounds__(256) frame_setup_kernel(const VolDev *__restri
         counter[0] = 0u;  // work-list length
         counter[1] = 0u;  // bits of the frame's largest accepted depth (depth_max_kernel)
         counter[2] = 0u;  // bricks whose voxel masks the integration changed
+        counter[3] = 0u;  // super bricks in view (the two-level work list)
     }
     if (!vis) return;
     __syncthreads();
@@ -178,28 +188,37 @@ __global__ void __launch_bounds__(256) frame_setup_kernel(const VolDev *__restri
         if (threadIdx.x == 0) {
             int n = 0;
             for (int u = 0; u < nvol; ++u) n += s_vis[u];
-            long long acc = 0;
+            long long acc = 0, sacc = 0;
             for (int i = 0; i < n; ++i) {
+                const VolDev &vd = vols[vis->slot[i]];
                 vis->base[i] = acc;
-                acc += vols[vis->slot[i]].nbricks;
+                vis->sbase[i] = sacc;
+                acc += vd.nbricks;
+                sacc += (long long)vd.nsb[0] * vd.nsb[1] * vd.nsb[2];
             }
             vis->base[n] = acc;
+            vis->sbase[n] = sacc;
             vis->count = n;
             vis->total = acc;
+            vis->stotal = sacc;
         }
     } else if (threadIdx.x == 0) {
         int n = 0;
-        long long acc = 0;
+        long long acc = 0, sacc = 0;
         for (int u = 0; u < nvol; ++u) {
             if (!s_vis[u]) continue;
             vis->slot[n] = u;
             vis->base[n] = acc;
+            vis->sbase[n] = sacc;
             acc += vols[u].nbricks;
+            sacc += (long long)vols[u].nsb[0] * vols[u].nsb[1] * vols[u].nsb[2];
             ++n;
         }
         vis->base[n] = acc;
+        vis->sbase[n] = sacc;
         vis->count = n;
         vis->total = acc;
+        vis->stotal = sacc;
     }
 }
 
@@ -261,6 +280,95 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
         if (lane == 0 && mask) pos = atomicAdd(counter, (unsigned)__popc(mask));
         pos = __shfl_sync(0xffffffffu, pos, 0);
         if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, packed);
+    }
+}
+
+// Two-level work list of the volumes in view (the batched calls).  First one
+// thread per super brick (kSuper^3 bricks): the same frustum and depth-tile
+// tests on its box, which holds every brick of it, so a super brick that
+// fails them holds no brick that passes (both tests only widen with the box:
+// more corners on the inside of each plane, a wider pixel range whose depth
+// range holds the smaller one's).  The super bricks that pass are listed
+// (table slot, sx | sy << 10 | sz << 20).
+__global__ void __launch_bounds__(256) super_list_kernel(const VolDev *__restrict__ vols,
+                                                         const VolFrame *__restrict__ vfs, FrameParams P,
+                                                         uint2 *__restrict__ slist, unsigned *__restrict__ scounter,
+                                                         const VisList *__restrict__ vl,
+                                                         const unsigned *__restrict__ dmax_bits,
+                                                         const unsigned *__restrict__ pyr)
+{
+    const int lane = threadIdx.x & 31;
+    const float z_far = dmax_bits ? fminf(P.z_max, __uint_as_float(*dmax_bits)) : P.z_max;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long total = vl->stotal;
+    const int nvis = vl->count;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += stride) {
+        const long long g = base + lane;
+        bool vis = false;
+        int v = 0;
+        unsigned packed = 0;
+        if (g < total) {
+            int lo = 0, hi = nvis - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (vl->sbase[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            v = vl->slot[lo];
+            const VolDev &vd = vols[v];
+            const unsigned si = (unsigned)(g - vl->sbase[lo]);  // < 2^24 super bricks per volume
+            const int si3[3] = {(int)(si % (unsigned)vd.nsb[0]), (int)((si / (unsigned)vd.nsb[0]) % (unsigned)vd.nsb[1]),
+                                (int)(si / ((unsigned)vd.nsb[0] * (unsigned)vd.nsb[1]))};
+            vis = box_class(vd, vfs[v], P, kSuper * kBrick, si3, z_far, pyr) != 0;
+            packed = (unsigned)si3[0] | ((unsigned)si3[1] << 10) | ((unsigned)si3[2] << 20);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, vis);
+        unsigned pos = 0;
+        if (lane == 0 && mask) pos = atomicAdd(scounter, (unsigned)__popc(mask));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (vis) slist[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2((unsigned)v, packed);
+    }
+}
+
+// Then one thread per brick of each listed super brick, tested and listed as
+// by brick_list_kernel.
+__global__ void __launch_bounds__(256) brick_list_super_kernel(const VolDev *__restrict__ vols,
+                                                               const VolFrame *__restrict__ vfs, FrameParams P,
+                                                               const uint2 *__restrict__ slist,
+                                                               const unsigned *__restrict__ scounter,
+                                                               uint2 *__restrict__ list, unsigned *__restrict__ counter,
+                                                               const unsigned *__restrict__ dmax_bits,
+                                                               const unsigned *__restrict__ pyr)
+{
+    constexpr int kPer = kSuper * kSuper * kSuper;
+    const int lane = threadIdx.x & 31;
+    const float z_far = dmax_bits ? fminf(P.z_max, __uint_as_float(*dmax_bits)) : P.z_max;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long total = (long long)kPer * (*scounter);
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += stride) {
+        const long long g = base + lane;
+        bool vis = false;
+        unsigned v = 0, packed = 0;
+        if (g < total) {
+            const uint2 it = slist[g / kPer];
+            const int l = (int)(g % kPer);
+            v = it.x;
+            const VolDev &vd = vols[v];
+            const int bx = (int)(it.y & 1023u) * kSuper + (l % kSuper);
+            const int by = (int)((it.y >> 10) & 1023u) * kSuper + ((l / kSuper) % kSuper);
+            const int bz = (int)(it.y >> 20) * kSuper + l / (kSuper * kSuper);
+            if (bx < vd.nb[0] && by < vd.nb[1] && bz < vd.nb[2]) {
+                const int cls = brick_visible(vd, vfs[v], P, bx, by, bz, z_far, pyr);
+                vis = cls != 0;
+                packed = (unsigned)bx | ((unsigned)by << 10) | ((unsigned)bz << 20) | (cls == 2 ? kListFree : 0u);
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, vis);
+        unsigned pos = 0;
+        if (lane == 0 && mask) pos = atomicAdd(counter, (unsigned)__popc(mask));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (vis) list[pos + __popc(mask & ((1u << lane) - 1u))] = make_uint2(v, packed);
     }
 }
 
@@ -1122,12 +1230,27 @@ static long long list_blocks(long long total, int num_sms)
     return blocks;
 }
 
+// With a view list (the batched calls) and a super-brick list buffer
+// (slist, total_sup entries, its length in counter[3]): the two-level list;
+// otherwise one thread per brick.  The second kernel and its launch cost
+// about 3 us; the first saves about 5.5 us per million bricks in view, so the
+// callers pass slist from about a million resident bricks on.
 cudaError_t launch_brick_list(const VolDev *vols, int nvol, const VolFrame *vfs,
                               const FrameParams &P, long long gb_begin, long long total,
                               uint2 *list, unsigned *counter, int num_sms, cudaStream_t s,
-                              const VisList *vis, const unsigned *dmax_bits, const unsigned *pyr)
+                              const VisList *vis, const unsigned *dmax_bits, const unsigned *pyr,
+                              uint2 *slist, long long total_sup)
 {
     if (total <= 0) return cudaSuccess;
+    if (vis && slist) {
+        super_list_kernel<<<(unsigned)list_blocks(total_sup, num_sms), 256, 0, s>>>(
+            vols, vfs, P, slist, counter + 3, vis, dmax_bits, pyr);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        brick_list_super_kernel<<<(unsigned)num_sms * 8, 256, 0, s>>>(vols, vfs, P, slist, counter + 3, list,
+                                                                     counter, dmax_bits, pyr);
+        return cudaGetLastError();
+    }
     brick_list_kernel<<<(unsigned)list_blocks(total, num_sms), 256, 0, s>>>(
         vols, nvol, vfs, P, gb_begin, total, list, counter, vis, dmax_bits, pyr);
     return cudaGetLastError();
@@ -1234,13 +1357,16 @@ cudaError_t frame_setup_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_
 }
 
 // Graph nodes of one integration: setup -> depth max -> brick list -> integrate -> cell flags.
-cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[5],
+// Nodes: 0 setup, 1 depth tiles, 2 (and 3) the work list, 4 integration,
+// 5 cell-mask refresh.  With slist the work list is two-level (2: super
+// bricks, 3: their bricks), else one kernel over total bricks (node 3 unused).
+cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t nodes[6],
                             cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
-                            const FrameParams &P, long long total, uint2 *list, unsigned *counter,
-                            const float *depth, const uint8_t *rgb, Stats *stats, int grid_int,
-                            int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id, unsigned *pyr)
+                            const FrameParams &P, long long total, long long total_sup, uint2 *slist,
+                            uint2 *list, unsigned *counter, const float *depth, const uint8_t *rgb, Stats *stats,
+                            int grid_int, int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id,
+                            unsigned *pyr)
 {
-    const long long lb = list_blocks(total, num_sms);
     NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a0(vols, nvol, P, vf, counter,
                                                                                    vis);
     cudaError_t e = graph_node(g, exec, &nodes[0], dep, a0.params((const void *)frame_setup_kernel, 1, 256));
@@ -1248,18 +1374,34 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
     NodeArgs<const float *, FrameParams, unsigned *, unsigned *> am(depth, P, pyr, counter + 1);
     e = graph_node(g, exec, &nodes[1], nodes[0], am.params((const void *)depth_tiles_kernel, depth_tiles_grid(P), 256));
     if (e != cudaSuccess) return e;
-    NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *,
-             const VisList *, const unsigned *, const unsigned *>
-        a1(vols, nvol, vf, P, 0LL, total, list, counter, vis, counter + 1, pyr);
-    e = graph_node(g, exec, &nodes[2], nodes[1], a1.params((const void *)brick_list_kernel, (unsigned)lb, 256));
+    if (slist) {
+        NodeArgs<const VolDev *, const VolFrame *, FrameParams, uint2 *, unsigned *, const VisList *,
+                 const unsigned *, const unsigned *>
+            as(vols, vf, P, slist, counter + 3, vis, counter + 1, pyr);
+        e = graph_node(g, exec, &nodes[2], nodes[1],
+                       as.params((const void *)super_list_kernel, (unsigned)list_blocks(total_sup, num_sms), 256));
+        if (e != cudaSuccess) return e;
+        NodeArgs<const VolDev *, const VolFrame *, FrameParams, const uint2 *, const unsigned *, uint2 *, unsigned *,
+                 const unsigned *, const unsigned *>
+            a1(vols, vf, P, slist, counter + 3, list, counter, counter + 1, pyr);
+        e = graph_node(g, exec, &nodes[3], nodes[2],
+                       a1.params((const void *)brick_list_super_kernel, (unsigned)num_sms * 8, 256));
+    } else {
+        NodeArgs<const VolDev *, int, const VolFrame *, FrameParams, long long, long long, uint2 *, unsigned *,
+                 const VisList *, const unsigned *, const unsigned *>
+            a1(vols, nvol, vf, P, 0LL, total, list, counter, vis, counter + 1, pyr);
+        e = graph_node(g, exec, &nodes[2], nodes[1],
+                       a1.params((const void *)brick_list_kernel, (unsigned)list_blocks(total, num_sms), 256));
+    }
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,
              const uint8_t *, Stats *, MaskOut>
         a2(vols, vf, list, counter, P, depth, rgb, stats, MaskOut{changed, counter + 2, stamp_id});
-    e = graph_node(g, exec, &nodes[3], nodes[2], a2.params((const void *)integrate_kernel, grid_int, 128));
+    e = graph_node(g, exec, &nodes[4], slist ? nodes[3] : nodes[2],
+                   a2.params((const void *)integrate_kernel, grid_int, 128));
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const uint2 *, const unsigned *, unsigned> a3(vols, changed, counter + 2, stamp_id);
-    return graph_node(g, exec, &nodes[4], nodes[3], a3.params((const void *)cell_masks_kernel, num_sms * 8, kCellMaskCta));
+    return graph_node(g, exec, &nodes[5], nodes[4], a3.params((const void *)cell_masks_kernel, num_sms * 8, kCellMaskCta));
 }
 
 int integrate_max_ctas_per_sm()

@@ -117,14 +117,19 @@ struct FrameParams {
 // brick counts for the work-list kernel.  Built on the device by the per-call
 // setup kernel.
 constexpr int kVisSortMax = 256;
+// Resident bricks from which the batched calls build their work list in two
+// levels (super bricks in view, then their bricks).
+constexpr long long kTwoLevelBricks = 1ll << 20;
 // candidate volumes per raycast CTA held in shared memory
 constexpr int kTileVolMax = 256;
 struct VisList {
     int count;
     int pad;
-    long long total;                 // bricks of the visible volumes
-    int slot[kMaxVolumes];           // table slots
-    long long base[kMaxVolumes + 1]; // prefix sums of nbricks over slot[]
+    long long total;                  // bricks of the visible volumes
+    long long stotal;                 // super bricks of the visible volumes
+    int slot[kMaxVolumes];            // table slots
+    long long base[kMaxVolumes + 1];  // prefix sums of nbricks over slot[]
+    long long sbase[kMaxVolumes + 1]; // prefix sums of the super-brick counts over slot[]
 };
 
 // Flag allocation of a volume with nbricks bricks and nsuper super bricks:

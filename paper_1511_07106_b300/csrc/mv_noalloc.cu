@@ -13,7 +13,7 @@ cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFram
                                VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
                               long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
-                              const unsigned *, const unsigned *);
+                              const unsigned *, const unsigned *, uint2 *, long long);
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
@@ -158,7 +158,8 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     // that must start at 0
     if (launch_frame_setup(vdev, 1, P, vframe, counter, s, nullptr) != cudaSuccess) return MV_ERR_CUDA;
     if (launch_depth_max(depth, P, counter + 1, sms, s, nullptr) != cudaSuccess) return MV_ERR_CUDA;
-    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1, nullptr) !=
+    if (launch_brick_list(vdev, 1, vframe, P, 0, nbricks, list, counter, sms, s, nullptr, counter + 1, nullptr,
+                          nullptr, 0) !=
         cudaSuccess)
         return MV_ERR_CUDA;
     if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s, nullptr, nullptr, 0u) != cudaSuccess)

@@ -29,7 +29,7 @@ cudaError_t launch_frame_setup(const VolDev *, int, const FrameParams &, VolFram
                                VisList *);
 cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const FrameParams &, long long,
                               long long, uint2 *, unsigned *, int, cudaStream_t, const VisList *,
-                              const unsigned *, const unsigned *);
+                              const unsigned *, const unsigned *, uint2 *, long long);
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
@@ -70,9 +70,9 @@ cudaError_t launch_stream_gather(const VolDev &, const VolFrame *, const FramePa
 cudaError_t launch_stream_scatter(const VolDev &, const uint2 *, const unsigned *, void *, void *,
                                   unsigned long long *, int, cudaStream_t);
 constexpr int kIcpTerms = 29;
-cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[5], cudaGraphNode_t,
-                            const VolDev *, int, VolFrame *, const FrameParams &, long long, uint2 *,
-                            unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
+cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[6], cudaGraphNode_t,
+                            const VolDev *, int, VolFrame *, const FrameParams &, long long, long long, uint2 *,
+                            uint2 *, unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
                             uint2 *, unsigned, unsigned *);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
@@ -129,14 +129,20 @@ struct mv_ctx {
     struct FrameGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t nodes[6] = {};
+        cudaGraphNode_t nodes[7] = {};
         unsigned long long table_version = ~0ull;
         int width = 0, height = 0, grid_int = 0, tile = 0;
+        bool two_level = false;
     } fg;
     VolDev *d_table = nullptr;
     VolFrame *d_vf = nullptr;
     uint2 *d_list = nullptr;
     size_t list_cap = 0;  // entries
+    uint2 *d_slist = nullptr;  // super bricks in view (two-level work list)
+    size_t slist_cap = 0;      // entries
+    long long total_sup = 0;   // super bricks of the resident volumes
+    long long resident_bricks = 0;  // bricks of the resident volumes
+    int list_levels = 0;            // mv_tuning::work_list_levels
     unsigned *d_counter = nullptr;
     Stats *d_stats = nullptr;
     VisList *d_vis = nullptr;  // volumes in view of the current batched call
@@ -293,13 +299,14 @@ mv_status begin_call(mv_ctx *c, cudaStream_t s, int only_id = -1)
     if (c->table_dirty) {
         c->table.clear();
         c->table_ids.clear();
-        long long base = 0;
+        long long base = 0, sbase = 0;
         for (auto &kv : c->vols) {
             Volume *v = kv.second;
             if (!v->resident) continue;
             VolDev d = make_voldev(*v);
             d.brick_base = base;
             base += v->nbricks;
+            sbase += v->nsuper;
             c->table.push_back(d);
             c->table_ids.push_back(v->id);
         }
@@ -315,10 +322,28 @@ mv_status begin_call(mv_ctx *c, cudaStream_t s, int only_id = -1)
             MV_CUDA(c, cudaMallocAsync((void **)&c->d_list, 2 * (size_t)base * sizeof(uint2), s));
             c->list_cap = (size_t)base;
         }
+        // the super bricks in view: at most one entry per resident super brick
+        if ((size_t)sbase > c->slist_cap) {
+            if (c->d_slist) MV_CUDA(c, cudaFreeAsync(c->d_slist, s));
+            c->d_slist = nullptr;
+            c->slist_cap = 0;
+            MV_CUDA(c, cudaMallocAsync((void **)&c->d_slist, (size_t)sbase * sizeof(uint2), s));
+            c->slist_cap = (size_t)sbase;
+        }
+        c->total_sup = sbase;
+        c->resident_bricks = base;
         c->table_dirty = false;
         c->table_version += 1;
     }
     return MV_OK;
+}
+
+// The batched calls build their work list in two levels (super bricks in
+// view, then their bricks) when so tuned, or automatically from
+// kTwoLevelBricks resident bricks on.
+bool two_level_list(const mv_ctx *c)
+{
+    return c->list_levels == 2 || (c->list_levels == 0 && c->resident_bricks >= kTwoLevelBricks);
 }
 
 mv_status end_call(mv_ctx *c, cudaStream_t s)
@@ -669,6 +694,7 @@ mv_status mv_destroy(mv_ctx *c)
         if (v->d_mask) cudaFreeAsync(v->d_mask, s);
     }
     if (c->d_list) cudaFreeAsync(c->d_list, s);
+    if (c->d_slist) cudaFreeAsync(c->d_slist, s);
     free_slots(c, s);
     if (s) cudaStreamSynchronize(s);
     for (auto &kv : c->vols) {
@@ -1033,6 +1059,7 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     const long long total = only_id >= 0 ? c->table[slot0].nbricks
                                          : c->table.back().brick_base + c->table.back().nbricks;
     VisList *vis = only_id >= 0 ? nullptr : c->d_vis;  // batched: only volumes in view
+    const bool two_level = vis && two_level_list(c);
     st = ensure_pyramid(c, K);
     if (st) return st;
     const unsigned stamp = ++c->integrations;
@@ -1042,7 +1069,8 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
         return launch_depth_max(depth, P, c->d_counter + 1, c->num_sms, s, c->d_pyr); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
         return launch_brick_list(tab, nvol, vf, P, gb0, total, c->d_list, c->d_counter, c->num_sms, s, vis,
-                                 c->d_counter + 1, c->d_pyr); }));
+                                 c->d_counter + 1, c->d_pyr, two_level ? c->d_slist : nullptr, c->total_sup); }));
+    if (two_level) c->launches[MV_KERNEL_BRICK_LIST] += 1;  // the two-level list is two kernels
     // every resident volume keeps cell masks: the integration lists the bricks
     // whose voxel masks changed (second half of the work-list buffer) and the
     // refresh recomputes the cell masks and flags that read them
@@ -1140,10 +1168,11 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
         return end_call(c, s);
     }
     const long long total = c->table.back().brick_base + c->table.back().nbricks;
+    const bool two_level = two_level_list(c);
     auto &fg = c->fg;
     const bool rebuild = !fg.exec || fg.table_version != c->table_version || fg.width != K->width ||
                          fg.height != K->height || fg.grid_int != c->grid_integrate ||
-                         fg.tile != c->ray_tile;
+                         fg.tile != c->ray_tile || fg.two_level != two_level;
     if (rebuild) {
         if (fg.exec) cudaGraphExecDestroy(fg.exec);
         if (fg.g) cudaGraphDestroy(fg.g);
@@ -1152,10 +1181,11 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
         MV_CUDA(c, cudaGraphCreate(&fg.g, 0));
     }
     cudaGraphExec_t upd = rebuild ? nullptr : fg.exec;
-    MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total,
-                               c->d_list, c->d_counter, depth, rgb, c->d_stats, c->grid_integrate,
+    MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total, c->total_sup,
+                               two_level ? c->d_slist : nullptr, c->d_list, c->d_counter, depth, rgb,
+                               c->d_stats, c->grid_integrate,
                                c->num_sms, c->d_vis, c->d_list + c->list_cap, ++c->integrations, c->d_pyr));
-    MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[5], fg.nodes[4], c->d_table, nvol, c->d_vf, P,
+    MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[6], fg.nodes[5], c->d_table, nvol, c->d_vf, P,
                              depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
         MV_CUDA(c, cudaGraphInstantiate(&fg.exec, fg.g, 0));
@@ -1164,11 +1194,13 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
         fg.height = K->height;
         fg.grid_int = c->grid_integrate;
         fg.tile = c->ray_tile;
+        fg.two_level = two_level;
     }
     MV_CUDA(c, counted_launch(c, MV_KERNEL_FRAME_GRAPH, s, [&] { return cudaGraphLaunch(fg.exec, s); }));
     const int kinds[6] = {MV_KERNEL_SETUP, MV_KERNEL_DEPTH_MAX, MV_KERNEL_BRICK_LIST, MV_KERNEL_INTEGRATE,
                           MV_KERNEL_CELL_FLAGS, MV_KERNEL_RAYCAST};
     for (int k : kinds) c->launches[k] += 1;
+    if (two_level) c->launches[MV_KERNEL_BRICK_LIST] += 1;
     return end_call(c, s);
 }
 
@@ -1251,7 +1283,7 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
             return launch_depth_max(depth, P, cnt + 1, c->num_sms, s, c->d_pyr); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BRICK_LIST, s, [&] {
             return launch_brick_list(dv, 1, vf, P, 0, v->nbricks, list, cnt, c->num_sms, s, nullptr, cnt + 1,
-                                     c->d_pyr); }));
+                                     c->d_pyr, nullptr, 0); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
             return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s,
                                     nullptr, nullptr, 0u); }));
@@ -1400,7 +1432,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
                 if (e == cudaSuccess) e = launch_depth_max(depth, P, scount + 1, c->num_sms, s, c->d_pyr);
                 if (e == cudaSuccess)
                     e = launch_brick_list(stab, 1, svf, P, 0, sv.nbricks, slist, scount, c->num_sms, s,
-                                          nullptr, scount + 1, c->d_pyr);
+                                          nullptr, scount + 1, c->d_pyr, nullptr, 0);
                 if (e == cudaSuccess) e = cudaEventRecord(a, s);
                 if (e == cudaSuccess)
                     e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
@@ -1431,6 +1463,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
     c->grid_integrate = c->num_sms * best_ctas;
     out->raycast_tile = best_tile;
     out->integrate_ctas_per_sm = best_ctas;
+    out->work_list_levels = c->list_levels;
     return end_call(c, s);
 }
 
@@ -1438,8 +1471,10 @@ mv_status mv_set_tuning(mv_ctx *c, const mv_tuning *t)
 {
     if (!c || !t) return MV_ERR_ARG;
     if (t->raycast_tile < 0 || t->raycast_tile > 3 || t->integrate_ctas_per_sm < 1 ||
-        t->integrate_ctas_per_sm > integrate_max_ctas_per_sm())
+        t->integrate_ctas_per_sm > integrate_max_ctas_per_sm() || t->work_list_levels < 0 ||
+        t->work_list_levels > 2)
         return fail(c, MV_ERR_ARG, "bad tuning values");
+    c->list_levels = t->work_list_levels;
     c->ray_tile = t->raycast_tile;
     c->ctas_per_sm = t->integrate_ctas_per_sm;
     c->grid_integrate = c->num_sms * t->integrate_ctas_per_sm;
@@ -1452,6 +1487,7 @@ mv_status mv_get_tuning(mv_ctx *c, mv_tuning *t)
     std::memset(t, 0, sizeof(*t));
     t->raycast_tile = c->ray_tile;
     t->integrate_ctas_per_sm = c->ctas_per_sm;
+    t->work_list_levels = c->list_levels;
     return MV_OK;
 }
 

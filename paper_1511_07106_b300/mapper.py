@@ -430,15 +430,20 @@ class Mapper:
         return dict(raycast_tile=t.raycast_tile, integrate_ctas_per_sm=t.integrate_ctas_per_sm,
                     raycast_ms=list(t.raycast_ms), integrate_ms=list(t.integrate_ms))
 
-    def set_tuning(self, raycast_tile: int, integrate_ctas_per_sm: int):
+    def set_tuning(self, raycast_tile: int, integrate_ctas_per_sm: int, work_list_levels: int = None):
+        """Launch shapes; work_list_levels (0 automatic, 1, 2) is kept when None."""
         t = _abi.mv_tuning()
+        self._check(self._lib.mv_get_tuning(self._h, C.byref(t)))
         t.raycast_tile, t.integrate_ctas_per_sm = int(raycast_tile), int(integrate_ctas_per_sm)
+        if work_list_levels is not None:
+            t.work_list_levels = int(work_list_levels)
         self._check(self._lib.mv_set_tuning(self._h, C.byref(t)))
 
     def tuning(self) -> dict:
         t = _abi.mv_tuning()
         self._check(self._lib.mv_get_tuning(self._h, C.byref(t)))
-        return dict(raycast_tile=t.raycast_tile, integrate_ctas_per_sm=t.integrate_ctas_per_sm)
+        return dict(raycast_tile=t.raycast_tile, integrate_ctas_per_sm=t.integrate_ctas_per_sm,
+                    work_list_levels=t.work_list_levels)
 
     def set_timing(self, enable: bool):
         self._check(self._lib.mv_set_timing(self._h, int(bool(enable))))

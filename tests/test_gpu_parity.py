@@ -427,13 +427,18 @@ def test_autotune_changes_speed_not_results():
     b.close()
 
 
-def test_uneven_volumes_batched_equals_per_volume_and_oracle():
+@pytest.mark.parametrize("levels", [1, 2])
+def test_uneven_volumes_batched_equals_per_volume_and_oracle(levels):
     """Volumes of different sizes and pitches, some out of view: the batched
-    graph (view list, nearest first) equals the per-volume loop bit for bit,
-    and the merged raycast matches the oracle."""
+    graph (view list, nearest first; work list built per brick or from the
+    super bricks in view first) equals the per-volume loop bit for bit, and
+    the merged raycast matches the oracle."""
     wl = synth.uneven_volumes(n_volumes=12, frames=6, edges=(16, 24, 40), pitch_mm=(15.0, 40.0),
                               half_extent=1.6, height_m=2.2, width=160, height=120)
     a, b = Mapper(), Mapper()
+    t = a.tuning()
+    a.set_tuning(t["raycast_tile"], t["integrate_ctas_per_sm"], levels)
+    assert a.tuning()["work_list_levels"] == levels
     ida = [a.add_volume(v.h, v.r, v.s) for v in wl.volumes]
     idb = [b.add_volume(v.h, v.r, v.s) for v in wl.volumes]
     for i in range(wl.n_frames):
