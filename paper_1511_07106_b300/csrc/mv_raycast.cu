@@ -154,7 +154,7 @@ __device__ __forceinline__ float eval_at(const VolDev &v, const Geo<Off> &g, con
 }
 
 struct RayCount {
-    unsigned samples, skips;
+    unsigned samples, skips, hits;
 };
 
 // Nearest hit so far: ray distance, volume id and table slot, and the sample
@@ -620,8 +620,12 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
             }
         }
     }
-    if (best.slot == -2) return;  // merge: the existing entry stays
+    if (best.slot == -2) {  // merge: the existing entry (a hit) stays
+        ++rc.hits;
+        return;
+    }
     const bool hit = best.slot >= 0;
+    rc.hits += hit ? 1u : 0u;
     // normal and colour of the nearest hit, in its volume's grid
     Shade sh;
     sh.n[0] = sh.n[1] = sh.n[2] = 0.f;
@@ -737,13 +741,15 @@ __global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restric
     const int py = y0 + ty;
     const bool active = px < P.width && py < P.height;
 
-    // candidate volumes of this CTA's pixel rectangle, compacted in order
+    // candidate volumes of this CTA's pixel rectangle, compacted in order (a
+    // single volume in view is marched directly: its per-ray tests prune it
+    // as the tile test would, without the CTA's barriers)
     __shared__ int s_list[kTileVolMax];
     __shared__ int s_warp[4];
     const int x1 = min(x0 + Tile<TILE>::W, P.width) - 1, y1 = min(y0 + Tile<TILE>::H, P.height) - 1;
     const int n = vl ? vl->count : nvol;
     int total = 0;
-    for (int j0 = 0; j0 < n; j0 += 128) {
+    for (int j0 = 0; n > 1 && j0 < n; j0 += 128) {
         const int j = j0 + (int)threadIdx.x;
         int i = 0;
         bool keep = false;
@@ -764,13 +770,12 @@ __global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restric
         __syncthreads();
     }
     // the CTA's candidates when they fit in shared memory, else the view list
-    const bool fits = total <= kTileVolMax;
+    const bool fits = n > 1 && total <= kTileVolMax;
     const int *list = fits ? s_list : (vl ? vl->slot : nullptr);
 
-    RayCount rc{0u, 0u};
+    RayCount rc{0u, 0u, 0u};
     if (active) trace_pixel(vols, vfs, list, fits ? total : n, P, out, merge, px, py, rc);
-    add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips,
-               (active && out.depth && out.depth[(size_t)py * P.width + px] > 0.f) ? 1u : 0u);
+    add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips, rc.hits);
 }
 
 static const void *raycast_fn(int tile)
