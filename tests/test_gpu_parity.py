@@ -470,6 +470,37 @@ def test_uneven_volumes_batched_equals_per_volume_and_oracle(levels):
     b.close()
 
 
+def test_two_level_list_at_scale_equals_one_level():
+    """Eight 512^3 tiles (2.1 M resident bricks, above the automatic
+    threshold): the frame graph's two-level work list (super bricks in view,
+    then their bricks) gives the same volumes' brick flags, the same counts
+    of listed bricks and updated voxels, and the same maps as the one-level
+    list, frame after frame."""
+    wl = synth.room_tiles(res=512, pitch=0.003, split=2, frames=4)
+    a, b = Mapper(), Mapper()
+    ida = [a.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    idb = [b.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    t = b.tuning()
+    b.set_tuning(t["raycast_tile"], t["integrate_ctas_per_sm"], 1)
+    assert a.tuning()["work_list_levels"] == 0  # automatic: two levels at this size
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        a.timings(reset=True)
+        ga = gpu_maps(a.frame(dev(d), dev(c), wl.cam, wl.poses[i]))
+        gb = gpu_maps(b.frame(dev(d), dev(c), wl.cam, wl.poses[i]))
+        assert a.timings()["brick_list"][0] == 2  # super bricks, then their bricks
+        for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+            np.testing.assert_array_equal(ga[key], gb[key])
+        sa, sb = a.stats(reset=True), b.stats(reset=True)
+        for key in ("swept", "updated", "band", "bricks", "ray_hits"):
+            assert sa[key] == sb[key], key
+        assert sa["updated"] > 0 and sa["ray_hits"] > 0
+    for x, y in zip(ida, idb):
+        np.testing.assert_array_equal(a.read_brick_flags(x), b.read_brick_flags(y))
+    a.close()
+    b.close()
+
+
 def test_surface_count_skip_and_far_cull_are_exact():
     """Two exact shortcuts.  (1) A volume in which no brick holds an observed
     voxel at or behind a surface (every brick flag NO-NEGATIVE) cannot end a
