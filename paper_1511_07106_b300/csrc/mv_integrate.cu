@@ -511,7 +511,7 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         const float uf = fmaf(P.fx * X, iz, P.cx);
         const float vf = fmaf(P.fy * Y, iz, P.cy);
         const int ui = __float2int_rd(uf + 0.5f), vi = __float2int_rd(vf + 0.5f);
-        const bool ok = in && (Z > 0.f) && ui >= 0 && vi >= 0 && ui < P.width && vi < P.height;
+        const bool ok = in && (Z > 0.f) && (unsigned)ui < (unsigned)P.width && (unsigned)vi < (unsigned)P.height;
         Xj[j] = X;
         Yj[j] = Y;
         Zj[j] = Z;
@@ -611,14 +611,15 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
                                                 const FrameParams &P, unsigned packed,
                                                 const float *__restrict__ depth,
                                                 const uint8_t *__restrict__ rgb,
-                                                unsigned long long &n_swept,
-                                                unsigned long long &n_upd,
-                                                unsigned long long &n_band,
+                                                unsigned &n_swept,
+                                                unsigned &n_upd,
+                                                unsigned &n_band,
                                                 const MaskOut &mo, uint2 item, ChgBuf &cb, int parity,
                                                 const unsigned *__restrict__ rcp)
 {
     const int bx = (int)(packed & 1023u), by = (int)((packed >> 10) & 1023u), bz = packed_bz(packed);
-    const long long b = ((long long)bz * v.nb[1] + by) * v.nb[0] + bx;
+    const long long b = (long long)(((unsigned)bz * (unsigned)v.nb[1] + (unsigned)by) * (unsigned)v.nb[0] +
+                                    (unsigned)bx);  // < 2^30 bricks per volume
     const int t = threadIdx.x;
     const long long vox0 = b * kBrickVox + 4 * t;  // first of this thread's 4 voxels
     // the brick's old flag byte, read early: thread 0 updates it after the barriers
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
     int parity = 0;
     int cached = -1;
     const unsigned n = *counter;
-    unsigned long long n_swept = 0, n_upd = 0, n_band = 0, n_bricks = 0;
+    unsigned n_swept = 0, n_upd = 0, n_band = 0, n_bricks = 0;  // per thread: < 2^32
     for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
         const uint2 it = list[i];
         // the volume descriptor and camera constants are staged in shared
@@ -823,10 +824,10 @@ __global__ void __launch_bounds__(128) integrate_kernel(const VolDev *__restrict
         n_band += __shfl_down_sync(0xffffffffu, n_band, o);
     }
     if ((threadIdx.x & 31) == 0 && stats) {
-        if (n_swept) atomicAdd(&stats->swept, n_swept);
-        if (n_upd) atomicAdd(&stats->updated, n_upd);
-        if (n_band) atomicAdd(&stats->band, n_band);
-        if (threadIdx.x == 0 && n_bricks) atomicAdd(&stats->bricks, n_bricks);
+        if (n_swept) atomicAdd(&stats->swept, (unsigned long long)n_swept);
+        if (n_upd) atomicAdd(&stats->updated, (unsigned long long)n_upd);
+        if (n_band) atomicAdd(&stats->band, (unsigned long long)n_band);
+        if (threadIdx.x == 0 && n_bricks) atomicAdd(&stats->bricks, (unsigned long long)n_bricks);
     }
 }
 
