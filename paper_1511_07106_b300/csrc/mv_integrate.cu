@@ -56,9 +56,13 @@ __device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3]
 //     projects into the image: the frame updates none of them;
 //   kDepthFront: every voxel lies nearer than every accepted depth by more
 //     than mu: each voxel it updates gets f = min(1, sdf / mu) = 1, no colour;
+//   kDepthFull: kDepthFront, and every voxel projects into the image onto a
+//     pixel with an accepted depth (the widened range lies inside the image
+//     and no tile of it holds a pixel without one): each voxel is updated
+//     with f = 1;
 //   kDepthMixed: otherwise.
 // Conservative: margins far above the float rounding of the per-voxel test.
-constexpr int kDepthMixed = 0, kDepthBehind = 1, kDepthFront = 2;
+constexpr int kDepthMixed = 0, kDepthBehind = 1, kDepthFront = 2, kDepthFull = 3;
 __device__ __forceinline__ int brick_depth_class(const float lo[3], const float hi[3], const FrameParams &P,
                                                  float inv_s, const unsigned *__restrict__ pyr)
 {
@@ -80,8 +84,11 @@ __device__ __forceinline__ int brick_depth_class(const float lo[3], const float 
         zmin = fminf(zmin, Z);
         zmax = fmaxf(zmax, Z);
     }
-    const int x0 = max(0, (int)floorf(u0 + 0.5f) - 1), x1 = min(P.width - 1, (int)floorf(u1 + 0.5f) + 1);
-    const int y0 = max(0, (int)floorf(v0 + 0.5f) - 1), y1 = min(P.height - 1, (int)floorf(v1 + 0.5f) + 1);
+    const int rx0 = (int)floorf(u0 + 0.5f) - 1, rx1 = (int)floorf(u1 + 0.5f) + 1;
+    const int ry0 = (int)floorf(v0 + 0.5f) - 1, ry1 = (int)floorf(v1 + 0.5f) + 1;
+    const bool within = rx0 >= 0 && ry0 >= 0 && rx1 < P.width && ry1 < P.height;
+    const int x0 = max(0, rx0), x1 = min(P.width - 1, rx1);
+    const int y0 = max(0, ry0), y1 = min(P.height - 1, ry1);
     if (x0 > x1 || y0 > y1) return kDepthBehind;  // no voxel projects into the image
     const int span = max(x1 - x0, y1 - y0) + 1;
     int l = 0;
@@ -92,19 +99,24 @@ __device__ __forceinline__ int brick_depth_class(const float lo[3], const float 
     const unsigned *lev_min = pyr + pyr_level_off(P.width, P.height, kPyrLevels) + off;
     const int nx = pyr_tiles(P.width, l), sh = 3 + l;
     float dmax = 0.f, dmin = 3.0e38f;
+    unsigned holes = 0u;  // sign bits: a tile holds a pixel without an accepted depth
     for (int ty = y0 >> sh; ty <= (y1 >> sh); ++ty)
         for (int tx = x0 >> sh; tx <= (x1 >> sh); ++tx) {
             dmax = fmaxf(dmax, __uint_as_float(__ldg(lev_max + (long long)ty * nx + tx)));
-            dmin = fminf(dmin, __uint_as_float(__ldg(lev_min + (long long)ty * nx + tx)));
+            const unsigned wmin = __ldg(lev_min + (long long)ty * nx + tx);
+            holes |= wmin;
+            dmin = fminf(dmin, __uint_as_float(wmin & 0x7FFFFFFFu));
         }
     if (zmin > fmaf(dmax, inv_s, P.trunc_vox) + 1e-4f * zmin + 1e-3f) return kDepthBehind;
-    if (fminf(dmin, 3.0e37f) * inv_s - zmax > P.trunc_vox + 1e-4f * zmax + 1e-3f) return kDepthFront;
+    if (fminf(dmin, 3.0e37f) * inv_s - zmax > P.trunc_vox + 1e-4f * zmax + 1e-3f)
+        return within && !(holes >> 31) ? kDepthFull : kDepthFront;
     return kDepthMixed;
 }
 
 // The box of voxels n * bi .. n * bi + n - 1 per axis (clipped to the volume):
 // 0 when the frame updates none of them; 1 when it may; 2 when it may and
-// every voxel lies in front of every depth of its pixels by more than mu.
+// every voxel lies in front of every depth of its pixels by more than mu; 3
+// when, besides, every voxel projects onto an accepted depth (all updated).
 __device__ __forceinline__ int box_class(const VolDev &v, const VolFrame &f, const FrameParams &P, int n,
                                          const int bi[3], float z_far, const unsigned *__restrict__ pyr)
 {
@@ -119,10 +131,11 @@ __device__ __forceinline__ int box_class(const VolDev &v, const VolFrame &f, con
     if (!box_visible(lo, hi, P, v.inv_s, z_far)) return 0;
     if (!pyr) return 1;
     const int cls = brick_depth_class(lo, hi, P, v.inv_s, pyr);
-    return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : 1);
+    return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : (cls == kDepthFull ? 3 : 1));
 }
 
-// 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu
+// 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu;
+// 3: listed, every voxel updated with f = 1
 __device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
                                              const FrameParams &P, int bx, int by, int bz, float z_far,
                                              const unsigned *__restrict__ pyr)
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
             const unsigned bz = byz / (unsigned)vd.nb[1];
             const int cls = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far, pyr);
             vis = cls != 0;
-            packed = bx | (by << 10) | (bz << 20) | (cls == 2 ? kListFree : 0u);
+            packed = bx | (by << 10) | (bz << 20) | (cls >= 2 ? kListFree : 0u) | (cls == 3 ? kListFull : 0u);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
         unsigned pos = 0;
@@ -361,7 +374,7 @@ __global__ void __launch_bounds__(256) brick_list_super_kernel(const VolDev *__r
             if (bx < vd.nb[0] && by < vd.nb[1] && bz < vd.nb[2]) {
                 const int cls = brick_visible(vd, vfs[v], P, bx, by, bz, z_far, pyr);
                 vis = cls != 0;
-                packed = (unsigned)bx | ((unsigned)by << 10) | ((unsigned)bz << 20) | (cls == 2 ? kListFree : 0u);
+                packed = (unsigned)bx | ((unsigned)by << 10) | ((unsigned)bz << 20) | (cls >= 2 ? kListFree : 0u) | (cls == 3 ? kListFull : 0u);
             }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
@@ -393,26 +406,32 @@ __global__ void __launch_bounds__(256) depth_max_kernel(const float *__restrict_
 __global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restrict__ depth, FrameParams P,
                                                           unsigned *__restrict__ pyr, unsigned *__restrict__ out)
 {
-    constexpr unsigned kInf = 0x7F800000u;
-    __shared__ unsigned s_t[4][4], s_n[4][4];  // level 0: the block's 4 x 4 tiles of 8 x 8 pixels
+    constexpr unsigned kInf = 0x7F800000u, kHole = 0x80000000u;
+    // level 0: the block's 4 x 4 tiles of 8 x 8 pixels (largest, smallest
+    // depth, and kHole where a pixel inside the image has no accepted depth)
+    __shared__ unsigned s_t[4][4], s_n[4][4], s_h[4][4];
     __shared__ unsigned s_1[2][2], s_1n[2][2];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t < 16) {
         s_t[t >> 2][t & 3] = 0u;
         s_n[t >> 2][t & 3] = kInf;
+        s_h[t >> 2][t & 3] = 0u;
     }
     __syncthreads();
     // warp w reads rows w + 8 i (tile row i) of the block, lane = column
     const int x = blockIdx.x * 32 + lane;
     float m[4], n[4];
+    bool hole[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         m[i] = 0.f;
         n[i] = __uint_as_float(kInf);
+        hole[i] = false;
         const int y = blockIdx.y * 32 + w + 8 * i;
         if (x < P.width && y < P.height) {
             const float D = __ldg(depth + (size_t)y * P.width + x);
             if (D > 0.f && D >= P.z_min && D <= P.z_max) m[i] = n[i] = D;
+            else hole[i] = true;
         }
     }
     // the 8 columns of a tile are 8 consecutive lanes; the 8 warps meet in shared memory
@@ -424,9 +443,11 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restric
             v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
             u = fminf(u, __shfl_xor_sync(0xffffffffu, u, o));
         }
+        const bool h = (__ballot_sync(0xffffffffu, hole[i]) >> (lane & 24)) & 0xFFu;  // the tile's 8 lanes
         if ((lane & 7) == 0) {
             if (v > 0.f) atomicMax(&s_t[i][lane >> 3], __float_as_uint(v));
             if (__float_as_uint(u) != kInf) atomicMin(&s_n[i][lane >> 3], __float_as_uint(u));
+            if (h) atomicOr(&s_h[i][lane >> 3], kHole);
         }
     }
     __syncthreads();
@@ -436,14 +457,16 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restric
         if (tx < pyr_tiles(P.width, 0) && ty < pyr_tiles(P.height, 0)) {
             const long long i = (long long)ty * pyr_tiles(P.width, 0) + tx;
             pyr[i] = s_t[t >> 2][t & 3];
-            pyr[min_off + i] = s_n[t >> 2][t & 3];
+            pyr[min_off + i] = s_n[t >> 2][t & 3] | s_h[t >> 2][t & 3];
         }
     } else if (t < 20) {
         const int k = t - 16, lx = k & 1, ly = k >> 1;
         const unsigned mx = max(max(s_t[2 * ly][2 * lx], s_t[2 * ly][2 * lx + 1]),
                                 max(s_t[2 * ly + 1][2 * lx], s_t[2 * ly + 1][2 * lx + 1]));
         const unsigned mn = min(min(s_n[2 * ly][2 * lx], s_n[2 * ly][2 * lx + 1]),
-                                min(s_n[2 * ly + 1][2 * lx], s_n[2 * ly + 1][2 * lx + 1]));
+                                min(s_n[2 * ly + 1][2 * lx], s_n[2 * ly + 1][2 * lx + 1])) |
+                            s_h[2 * ly][2 * lx] | s_h[2 * ly][2 * lx + 1] | s_h[2 * ly + 1][2 * lx] |
+                            s_h[2 * ly + 1][2 * lx + 1];
         s_1[ly][lx] = mx;
         s_1n[ly][lx] = mn;
         const int tx = blockIdx.x * 2 + lx, ty = blockIdx.y * 2 + ly;
@@ -456,7 +479,10 @@ __global__ void __launch_bounds__(256) depth_tiles_kernel(const float *__restric
     __syncthreads();
     if (t == 0) {
         const unsigned mx = max(max(s_1[0][0], s_1[0][1]), max(s_1[1][0], s_1[1][1]));
-        const unsigned mn = min(min(s_1n[0][0], s_1n[0][1]), min(s_1n[1][0], s_1n[1][1]));
+        // the hole bit survives the minimum of the low 31 bits
+        const unsigned hl = (s_1n[0][0] | s_1n[0][1] | s_1n[1][0] | s_1n[1][1]) & kHole;
+        const unsigned mn = min(min(s_1n[0][0] & ~kHole, s_1n[0][1] & ~kHole),
+                                min(s_1n[1][0] & ~kHole, s_1n[1][1] & ~kHole)) | hl;
         const long long i = pyr_level_off(P.width, P.height, 2) + (long long)blockIdx.y * pyr_tiles(P.width, 2) + blockIdx.x;
         pyr[i] = mx;
         pyr[min_off + i] = mn;
@@ -548,6 +574,25 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     }
 }
 
+// A brick listed with kListFull: every voxel projects onto an accepted depth
+// nearer than it by more than mu, so each voxel inside the volume takes
+// f = 1 and no colour, as project_voxels would find voxel by voxel.
+__device__ __forceinline__ void full_front_voxels(const VolDev &v, int bx, int by, int bz, VoxelUpdate &u)
+{
+    const int t = threadIdx.x;
+    const int gx = bx * kBrick + (t & 1) * 4, gy = by * kBrick + ((t >> 1) & 7), gz = bz * kBrick + (t >> 4);
+    const bool row_in = gy < v.r[1] && gz < v.r[2];
+    unsigned in = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (row_in && gx + j < v.r[0]) in |= 1u << j;
+        u.f[j] = 1.0f;
+        u.pix[j] = 0;
+    }
+    u.inside = u.upd = in;
+    u.band = 0u;
+}
+
 // Division by the invariant divisors d = 2 (w + 1), w = 0..255, as a
 // multiplication (Granlund and Montgomery, "Division by invariant integers
 // using multiplication", 1994): with M = ceil(2^32 / d) = (2^32 + e) / d,
@@ -636,7 +681,10 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
         a16 = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint32_t *>(v.fw) + vox0);
     }
     VoxelUpdate u;
-    project_voxels(v, fr, P, bx, by, bz, depth, u, (packed & kListFree) != 0u);
+    if (packed & kListFull)
+        full_front_voxels(v, bx, by, bz, u);
+    else
+        project_voxels(v, fr, P, bx, by, bz, depth, u, (packed & kListFree) != 0u);
     bool all_pos = true;  // every voxel this thread updated is stored > 0
     bool mchg = false;    // the update changed a voxel's "observed" or "F <= 0" bit
     bool pair_chg = false;  // ... of this thread or of its partner (same 8-voxel row)

@@ -155,7 +155,9 @@ inline size_t mask_alloc_bytes(long long nbricks) { return (size_t)nbricks * kMa
 
 // Per-frame pyramids of the largest and of the smallest accepted depth over
 // square pixel tiles of 8, 16 and 32 pixels (float bits; where no pixel of the
-// tile has an accepted depth, 0 in the largest and +inf in the smallest):
+// tile has an accepted depth, 0 in the largest and +inf in the smallest; the
+// sign bit of a smallest-depth word is set when a pixel of the tile inside
+// the image has no accepted depth):
 // level L is a row-major grid of ceil(W / 2^(L+3)) x ceil(H / 2^(L+3)) tiles,
 // the levels stored one after the other, the smallest-depth pyramid after the
 // largest-depth one.
@@ -189,8 +191,11 @@ __host__ __device__ inline long long pyr_level_off(int width, int height, int le
 
 // Work-list entry (table slot, packed brick coordinates bx | by << 10 | bz << 20):
 // bit 30 marks a brick in front of every accepted depth of its pixels by
-// more than mu, whose updated voxels all take f = 1 and no colour.
+// more than mu, whose updated voxels all take f = 1 and no colour; bit 31
+// (with bit 30) one whose voxels all project into the image onto accepted
+// depths, so that every voxel inside the volume is updated with f = 1.
 constexpr unsigned kListFree = 1u << 30;
+constexpr unsigned kListFull = 1u << 31;
 __host__ __device__ inline int packed_bz(unsigned packed) { return (int)((packed >> 20) & 1023u); }
 
 struct Stats {
