@@ -50,7 +50,8 @@ __device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3]
 // Where a brick lies against the depths of the pixels it can project to
 // (bounded by the projected corners, all in front of the camera, widened by
 // one pixel; their largest and smallest depth come from the smallest pyramid
-// level whose tiles are at least as large as that range):
+// level whose tiles are at least as large as that range, or from the
+// coarsest level for ranges up to twice its tile):
 //   kDepthBehind: every voxel lies farther than every accepted depth by more
 //     than mu (sdf = (D - z) |p_c| / z < -mu, as |p_c| / z >= 1), or none
 //     projects into the image: the frame updates none of them;
@@ -93,7 +94,9 @@ __device__ __forceinline__ int brick_depth_class(const float lo[3], const float 
     const int span = max(x1 - x0, y1 - y0) + 1;
     int l = 0;
     while (l < kPyrLevels - 1 && (8 << l) < span) ++l;
-    if ((8 << l) < span) return kDepthMixed;  // wider than the coarsest tile: the frame-wide far test only
+    // up to two coarsest tiles wide (at most 3 x 3 of them read); wider ranges
+    // (bricks close to the camera) keep the frame-wide far test only
+    if ((8 << l) * 2 < span) return kDepthMixed;
     const long long off = pyr_level_off(P.width, P.height, l);
     const unsigned *lev_max = pyr + off;
     const unsigned *lev_min = pyr + pyr_level_off(P.width, P.height, kPyrLevels) + off;
