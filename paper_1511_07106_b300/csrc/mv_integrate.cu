@@ -61,9 +61,12 @@ __device__ __forceinline__ bool box_visible(const float lo[3], const float hi[3]
 //     pixel with an accepted depth (the widened range lies inside the image
 //     and no tile of it holds a pixel without one): each voxel is updated
 //     with f = 1;
+//   kDepthMixedClean: neither of the above, but every voxel projects into the
+//     image onto a pixel with an accepted depth (the voxel's own distance
+//     test decides);
 //   kDepthMixed: otherwise.
 // Conservative: margins far above the float rounding of the per-voxel test.
-constexpr int kDepthMixed = 0, kDepthBehind = 1, kDepthFront = 2, kDepthFull = 3;
+constexpr int kDepthMixed = 0, kDepthBehind = 1, kDepthFront = 2, kDepthFull = 3, kDepthMixedClean = 4;
 __device__ __forceinline__ int brick_depth_class(const float lo[3], const float hi[3], const FrameParams &P,
                                                  float inv_s, const unsigned *__restrict__ pyr)
 {
@@ -113,13 +116,14 @@ __device__ __forceinline__ int brick_depth_class(const float lo[3], const float 
     if (zmin > fmaf(dmax, inv_s, P.trunc_vox) + 1e-4f * zmin + 1e-3f) return kDepthBehind;
     if (fminf(dmin, 3.0e37f) * inv_s - zmax > P.trunc_vox + 1e-4f * zmax + 1e-3f)
         return within && !(holes >> 31) ? kDepthFull : kDepthFront;
-    return kDepthMixed;
+    return within && !(holes >> 31) ? kDepthMixedClean : kDepthMixed;
 }
 
 // The box of voxels n * bi .. n * bi + n - 1 per axis (clipped to the volume):
 // 0 when the frame updates none of them; 1 when it may; 2 when it may and
 // every voxel lies in front of every depth of its pixels by more than mu; 3
-// when, besides, every voxel projects onto an accepted depth (all updated).
+// when, besides, every voxel projects onto an accepted depth (all updated);
+// 4 when it may, and every voxel projects onto an accepted depth.
 __device__ __forceinline__ int box_class(const VolDev &v, const VolFrame &f, const FrameParams &P, int n,
                                          const int bi[3], float z_far, const unsigned *__restrict__ pyr)
 {
@@ -134,11 +138,12 @@ __device__ __forceinline__ int box_class(const VolDev &v, const VolFrame &f, con
     if (!box_visible(lo, hi, P, v.inv_s, z_far)) return 0;
     if (!pyr) return 1;
     const int cls = brick_depth_class(lo, hi, P, v.inv_s, pyr);
-    return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : (cls == kDepthFull ? 3 : 1));
+    return cls == kDepthBehind ? 0 : (cls == kDepthFront ? 2 : (cls == kDepthFull ? 3 : (cls == kDepthMixedClean ? 4 : 1)));
 }
 
 // 0: not listed; 1: listed; 2: listed, in front of every depth by more than mu;
-// 3: listed, every voxel updated with f = 1
+// 3: listed, every voxel updated with f = 1; 4: listed, every voxel projects
+// onto an accepted depth
 __device__ __forceinline__ int brick_visible(const VolDev &v, const VolFrame &f,
                                              const FrameParams &P, int bx, int by, int bz, float z_far,
                                              const unsigned *__restrict__ pyr)
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(256) brick_list_kernel(const VolDev *__restric
             const unsigned bz = byz / (unsigned)vd.nb[1];
             const int cls = brick_visible(vd, vfs[v], P, (int)bx, (int)by, (int)bz, z_far, pyr);
             vis = cls != 0;
-            packed = bx | (by << 10) | (bz << 20) | (cls >= 2 ? kListFree : 0u) | (cls == 3 ? kListFull : 0u);
+            packed = bx | (by << 10) | (bz << 20) | (cls == 2 || cls == 3 ? kListFree : 0u) | (cls >= 3 ? kListFull : 0u);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
         unsigned pos = 0;
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(256) brick_list_super_kernel(const VolDev *__r
             if (bx < vd.nb[0] && by < vd.nb[1] && bz < vd.nb[2]) {
                 const int cls = brick_visible(vd, vfs[v], P, bx, by, bz, z_far, pyr);
                 vis = cls != 0;
-                packed = (unsigned)bx | ((unsigned)by << 10) | ((unsigned)bz << 20) | (cls >= 2 ? kListFree : 0u) | (cls == 3 ? kListFull : 0u);
+                packed = (unsigned)bx | ((unsigned)by << 10) | ((unsigned)bz << 20) | (cls == 2 || cls == 3 ? kListFree : 0u) | (cls >= 3 ? kListFull : 0u);
             }
         }
         const unsigned mask = __ballot_sync(0xffffffffu, vis);
@@ -504,6 +509,9 @@ struct VoxelUpdate {
     unsigned inside; // bit j: voxel j inside the volume (not padding)
 };
 
+// CLEAN (kListFull without kListFree): every voxel is known to project into
+// the image onto an accepted depth, so those tests are left out.
+template <bool CLEAN>
 __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &fr,
                                                const FrameParams &P, int bx, int by, int bz,
                                                const float *__restrict__ depth, VoxelUpdate &u, bool front)
@@ -540,7 +548,7 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         const float uf = fmaf(P.fx * X, iz, P.cx);
         const float vf = fmaf(P.fy * Y, iz, P.cy);
         const int ui = __float2int_rd(uf + 0.5f), vi = __float2int_rd(vf + 0.5f);
-        const bool ok = in && (Z > 0.f) && (unsigned)ui < (unsigned)P.width && (unsigned)vi < (unsigned)P.height;
+        const bool ok = CLEAN ? in : in && (Z > 0.f) && (unsigned)ui < (unsigned)P.width && (unsigned)vi < (unsigned)P.height;
         Xj[j] = X;
         Yj[j] = Y;
         Zj[j] = Z;
@@ -556,7 +564,7 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
         u.f[j] = 0.f;
         u.pix[j] = 0;
         const float D = Dj[j];
-        if (!okj[j] || !(D > 0.f) || D < P.z_min || D > P.z_max) continue;
+        if (!okj[j] || (!CLEAN && (!(D > 0.f) || D < P.z_min || D > P.z_max))) continue;
         if (front) {
             // the brick lies nearer than every depth of its pixels by more
             // than mu: sdf >= mu, so f = 1 and no colour, as computed below
@@ -577,9 +585,10 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     }
 }
 
-// A brick listed with kListFull: every voxel projects onto an accepted depth
-// nearer than it by more than mu, so each voxel inside the volume takes
-// f = 1 and no colour, as project_voxels would find voxel by voxel.
+// A brick listed with kListFull and kListFree: every voxel projects onto an
+// accepted depth nearer than it by more than mu, so each voxel inside the
+// volume takes f = 1 and no colour, as project_voxels would find voxel by
+// voxel.
 __device__ __forceinline__ void full_front_voxels(const VolDev &v, int bx, int by, int bz, VoxelUpdate &u)
 {
     const int t = threadIdx.x;
@@ -684,10 +693,12 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
         a16 = *reinterpret_cast<const uint4 *>(reinterpret_cast<const uint32_t *>(v.fw) + vox0);
     }
     VoxelUpdate u;
-    if (packed & kListFull)
+    if ((packed & kListFull) && (packed & kListFree))
         full_front_voxels(v, bx, by, bz, u);
+    else if (packed & kListFull)
+        project_voxels<true>(v, fr, P, bx, by, bz, depth, u, false);
     else
-        project_voxels(v, fr, P, bx, by, bz, depth, u, (packed & kListFree) != 0u);
+        project_voxels<false>(v, fr, P, bx, by, bz, depth, u, (packed & kListFree) != 0u);
     bool all_pos = true;  // every voxel this thread updated is stored > 0
     bool mchg = false;    // the update changed a voxel's "observed" or "F <= 0" bit
     bool pair_chg = false;  // ... of this thread or of its partner (same 8-voxel row)

@@ -191,9 +191,9 @@ __host__ __device__ inline long long pyr_level_off(int width, int height, int le
 
 // Work-list entry (table slot, packed brick coordinates bx | by << 10 | bz << 20):
 // bit 30 marks a brick in front of every accepted depth of its pixels by
-// more than mu, whose updated voxels all take f = 1 and no colour; bit 31
-// (with bit 30) one whose voxels all project into the image onto accepted
-// depths, so that every voxel inside the volume is updated with f = 1.
+// more than mu, whose updated voxels all take f = 1 and no colour; bit 31 one
+// whose voxels all project into the image onto accepted depths (with bit 30:
+// every voxel inside the volume is updated with f = 1).
 constexpr unsigned kListFree = 1u << 30;
 constexpr unsigned kListFull = 1u << 31;
 __host__ __device__ inline int packed_bz(unsigned packed) { return (int)((packed >> 20) & 1023u); }
