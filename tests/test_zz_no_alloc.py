@@ -67,6 +67,49 @@ def test_noalloc_integrate_matches_context_call_twice():
     m.close()
 
 
+def test_brick_classes_equal_the_per_voxel_path_at_full_size():
+    """The 512^3 room (64^3 bricks, the allocation-free path's capacity) over
+    five frames: the context path, whose work list classes bricks against the
+    frame's depth tiles (behind: not listed; in front: f = 1; updated whole;
+    projecting onto accepted depths only), gives bit for bit the volume of the
+    allocation-free path, which lists every brick in the frustum and decides
+    voxel by voxel."""
+    import torch
+    wl = synth.room_512(frames=5)
+    (vs,) = wl.volumes
+    lib = _abi.lib()
+    m = Mapper()
+    vid = m.add_volume(vs.h, vs.r, vs.s, "f32")
+    nb = [(r + 7) // 8 for r in vs.r]
+    nbricks = nb[0] * nb[1] * nb[2]
+    fw = torch.zeros(nbricks * 512 * 2, dtype=torch.float32, device="cuda")
+    rgba = torch.zeros(nbricks * 512 * 4, dtype=torch.uint8, device="cuda")
+    flags = torch.full((nbricks,), 6, dtype=torch.uint8, device="cuda")
+    desc = _abi.mv_volume_desc((C.c_int32 * 3)(*vs.h), (C.c_int32 * 3)(*vs.r), vs.s, _abi.MV_TSDF_F32)
+    view = _abi.mv_volume_view(desc, fw.data_ptr(), rgba.data_ptr(), flags.data_ptr())
+    K = intrinsics(wl.cam)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        dd, dc = torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda()
+        m.integrate(dd, dc, wl.cam, wl.poses[i])
+        T = np.ascontiguousarray(wl.poses[i], np.float64).reshape(16)
+        st = lib.mv_integrate_noalloc(C.byref(view), None, C.c_void_p(dd.data_ptr()),
+                                      C.c_void_p(dc.data_ptr()), C.byref(K),
+                                      T.ctypes.data_as(C.POINTER(C.c_double)), stream)
+        assert st == _abi.MV_OK
+    torch.cuda.synchronize()
+    F_ref, W_ref, col_ref = m.read_decoded(vid)
+    lin = bricks_to_linear(fw.cpu().numpy().reshape(nbricks, 512, 2), vs.r, nb)
+    col = bricks_to_linear(rgba.cpu().numpy().reshape(nbricks, 512, 4), vs.r, nb)
+    assert (W_ref > 0).mean() > 0.02
+    np.testing.assert_array_equal(lin[..., 0], F_ref)
+    np.testing.assert_array_equal(lin[..., 1], W_ref)
+    np.testing.assert_array_equal(col, col_ref)
+    np.testing.assert_array_equal(flags.cpu().numpy(), m.read_brick_flags(vid).reshape(-1))
+    m.close()
+
+
 def test_noalloc_rejects_volumes_beyond_its_fixed_capacity():
     import torch
     lib = _abi.lib()
