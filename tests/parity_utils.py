@@ -2,7 +2,7 @@
 oracle volumes from the CUDA path's state, and compare raycast maps under the
 tolerances stated below.
 
-Tolerances (derived from the arithmetic):
+Tolerances (derived from the arithmetic of the FP32 path against the FP64 oracle):
   * TSDF, float32 storage: |dF| <= 1e-4 (units of mu) per lockstep frame on
     voxels whose FP64 decisions are not within the oracle's margins;
   * TSDF, half / int16 storage: 1e-4 + half a storage quantum at the value;
