@@ -392,15 +392,20 @@ typedef struct {
 } mv_volume_view;
 
 /* Integrate one frame into a caller-owned volume, allocating nothing.  cfg
- * may be NULL for defaults.  Works on the current CUDA device.  The first
- * call on a device looks up the address of the library's fixed working array
- * on that device, so make that first call before any stream capture.  All
- * calls share that one array: calls whose work overlaps on the GPU (on
- * different streams, or from different threads) race and must be serialised
- * by the caller.  Returns MV_ERR_CAPACITY, without launching anything, for a
- * volume of more than MV_NOALLOC_MAX_BRICKS bricks; MV_ERR_ARG for a null or
- * misaligned pointer or an invalid size, format or frame.  Asynchronous on
- * `stream` otherwise. */
+ * may be NULL for defaults; the configurations it accepts are those
+ * mv_create accepts.  Works on the current CUDA device.  Each call whose
+ * stream is not being captured looks up the device address of the library's
+ * fixed working array in the current context (a device reset moves it); a
+ * call on a capturing stream reuses the address found by the device's last
+ * uncaptured call, so make one call on each device before any stream capture
+ * (and again after a device reset).  All calls share that one array: calls
+ * whose work overlaps on the GPU (on different streams, or from different
+ * threads) race and must be serialised by the caller.  Returns
+ * MV_ERR_CAPACITY, without launching anything, for a volume of more than
+ * MV_NOALLOC_MAX_BRICKS bricks; MV_ERR_ARG for a null or misaligned pointer
+ * or an invalid size, format, configuration or frame; MV_ERR_CUDA for a first
+ * call on a device made during a stream capture.  Asynchronous on `stream`
+ * otherwise. */
 mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_config *cfg, const float *depth,
                                const uint8_t *rgb, const mv_intrinsics *K, const double T_c2w[16],
                                void *stream);

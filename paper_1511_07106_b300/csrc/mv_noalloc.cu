@@ -19,6 +19,7 @@ cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, co
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
                              cudaStream_t, uint2 *, unsigned *, unsigned);
 int integrate_occupancy_grid(int num_sms);
+bool valid_config(const mv_config &c);
 }  // namespace mv
 
 using namespace mv;
@@ -35,29 +36,47 @@ static_assert(sizeof(VolDev) <= 256 && sizeof(VolFrame) <= 256, "scratch slots t
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Per-device address of g_noalloc_scratch.  In host code the symbol's name is
-// only a host-side stand-in, never a device address: a kernel must be given
-// the address that cudaGetSymbolAddress returns for the current device.
+// Per-device address of g_noalloc_scratch, SM count and integration grid.
+// In host code the symbol's name is only a host-side stand-in, never a device
+// address: a kernel must be given the address that cudaGetSymbolAddress
+// returns for the current device.  The address belongs to the module loaded
+// in the device's current context; a device reset (cudaDeviceReset) or a new
+// primary context loads the module again, possibly elsewhere.  So every call
+// whose stream is not being captured looks the address up again (cheap once
+// the module is loaded) and refreshes the cache; a call on a capturing
+// stream, where that lookup could be refused, uses the cached address of the
+// device's last uncaptured call.  The SM count and the grid depend only on
+// the device and are kept from the first call.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
 int g_grid[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 
-cudaError_t device_scratch(int dev, unsigned char **ptr, int *grid)
+cudaError_t device_scratch(int dev, cudaStream_t s, unsigned char **ptr, int *grid, int *sms)
 {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_sms[dev]) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_grid[dev] = integrate_occupancy_grid(n);
+        g_sms[dev] = n;
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        g_grid[dev] = integrate_occupancy_grid(sms);
         g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;  // no uncaptured call has looked it up yet
     }
     *ptr = g_scratch_ptr[dev];
     *grid = g_grid[dev];
+    *sms = g_sms[dev];
     return cudaSuccess;
 }
 
@@ -85,9 +104,7 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     } else {
         mv_config_default(&c);
     }
-    if (!(c.trunc_voxels > 0.f) || !(c.w_max >= 1.f) || c.color_w_max < 1 || c.color_w_max > 255 ||
-        !(c.z_min >= 0.f) || !(c.z_max > c.z_min))
-        return MV_ERR_ARG;
+    if (!valid_config(c)) return MV_ERR_ARG;
     const mv_volume_desc &d = vol->desc;
     if (d.fmt < MV_TSDF_F32 || d.fmt > MV_TSDF_I16 || !(d.voxel_size > 0.f) || !is_finite(d.voxel_size))
         return MV_ERR_ARG;
@@ -108,9 +125,10 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MV_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
     unsigned char *scratch = nullptr;
-    int grid = 0;
-    if (device_scratch(dev, &scratch, &grid) != cudaSuccess) return MV_ERR_CUDA;
+    int grid = 0, sms = 0;
+    if (device_scratch(dev, s, &scratch, &grid, &sms) != cudaSuccess) return MV_ERR_CUDA;
     uint2 *list = reinterpret_cast<uint2 *>(scratch);
     VolDev *vdev = reinterpret_cast<VolDev *>(scratch + kVolOff);
     VolFrame *vframe = reinterpret_cast<VolFrame *>(scratch + kFrameOff);
@@ -149,9 +167,6 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     P.ray_step = c.ray_step;
     P.n_bisect = c.n_bisect;
 
-    cudaStream_t s = (cudaStream_t)stream;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MV_ERR_CUDA;
     store_voldev_kernel<<<1, 32, 0, s>>>(v, vdev);
     if (cudaGetLastError() != cudaSuccess) return MV_ERR_CUDA;
     // the frame setup zeroes the list counter and the depth maximum, the values

@@ -186,6 +186,20 @@ struct mv_ctx {
     std::string err;
 };
 
+namespace mv {
+
+// Method parameters every entry point accepts (mv_create and
+// mv_integrate_noalloc alike).
+bool valid_config(const mv_config &c)
+{
+    return c.trunc_voxels > 0.f && std::isfinite(c.trunc_voxels) && c.w_max >= 1.f &&
+           c.w_max <= 1e30f && c.color_w_max >= 1 && c.color_w_max <= 255 && c.z_min >= 0.f &&
+           c.z_max > c.z_min && c.ray_step >= 1.0f / 64.0f && c.ray_step <= 1.f && c.n_bisect >= 0 &&
+           c.n_bisect <= 64;
+}
+
+}  // namespace mv
+
 namespace {
 
 mv_status fail(mv_ctx *c, mv_status st, const std::string &msg)
@@ -205,14 +219,6 @@ mv_status cuda_fail(mv_ctx *c, cudaError_t e, const char *what)
         cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
     } while (0)
-
-bool valid_config(const mv_config &c)
-{
-    return c.trunc_voxels > 0.f && std::isfinite(c.trunc_voxels) && c.w_max >= 1.f &&
-           c.w_max <= 1e30f && c.color_w_max >= 1 && c.color_w_max <= 255 && c.z_min >= 0.f &&
-           c.z_max > c.z_min && c.ray_step >= 1.0f / 64.0f && c.ray_step <= 1.f && c.n_bisect >= 0 &&
-           c.n_bisect <= 64;
-}
 
 FrameParams make_params(const mv_ctx *c, const mv_intrinsics *K, const double T[16])
 {

@@ -29,20 +29,31 @@ def bricks_to_linear(a, r, nb):
     return g[: r[2], : r[1], : r[0]]
 
 
-def test_noalloc_integrate_matches_context_call_twice():
+FMTS = {"f32": _abi.MV_TSDF_F32, "f16": _abi.MV_TSDF_F16, "i16": _abi.MV_TSDF_I16}
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_noalloc_integrate_matches_context_call_twice(fmt):
+    """Two frames in a row through mv_integrate_noalloc equal the context
+    path (mv_integrate_volume) in every storage format: decoded TSDF within
+    the parity tests' tolerance, weights, colour and brick flags exact."""
     import torch
+    from paper_1511_07106_b300.mapper import decode
     wl = synth.single_volume_128(frames=2, res=64)
     (vs,) = wl.volumes
     lib = _abi.lib()
     m = Mapper()
-    vid = m.add_volume(vs.h, vs.r, vs.s, "f32")
+    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
     nb = [(r + 7) // 8 for r in vs.r]
     nbricks = nb[0] * nb[1] * nb[2]
     # caller-owned storage of a new volume: zero TSDF/weight/colour, every brick unobserved
-    fw = torch.zeros(nbricks * 512 * 2, dtype=torch.float32, device="cuda")
+    if fmt == "f32":
+        fw = torch.zeros(nbricks * 512 * 2, dtype=torch.float32, device="cuda")
+    else:
+        fw = torch.zeros(nbricks * 512, dtype=torch.int32, device="cuda")
     rgba = torch.zeros(nbricks * 512 * 4, dtype=torch.uint8, device="cuda")
     flags = torch.full((nbricks,), 6, dtype=torch.uint8, device="cuda")
-    desc = _abi.mv_volume_desc((C.c_int32 * 3)(*vs.h), (C.c_int32 * 3)(*vs.r), vs.s, _abi.MV_TSDF_F32)
+    desc = _abi.mv_volume_desc((C.c_int32 * 3)(*vs.h), (C.c_int32 * 3)(*vs.r), vs.s, FMTS[fmt])
     view = _abi.mv_volume_view(desc, fw.data_ptr(), rgba.data_ptr(), flags.data_ptr())
     K = intrinsics(wl.cam)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -57,14 +68,46 @@ def test_noalloc_integrate_matches_context_call_twice():
         assert st == _abi.MV_OK
         torch.cuda.synchronize()
         F_ref, W_ref, col_ref = m.read_decoded(vid)
-        lin = bricks_to_linear(fw.cpu().numpy().reshape(nbricks, 512, 2), vs.r, nb)
+        if fmt == "f32":
+            raw = bricks_to_linear(fw.cpu().numpy().reshape(nbricks, 512, 2), vs.r, nb)
+        else:
+            raw = bricks_to_linear(fw.cpu().numpy().view(np.uint32).reshape(nbricks, 512), vs.r, nb)
+        F, W = decode(raw, FMTS[fmt])
         col = bricks_to_linear(rgba.cpu().numpy().reshape(nbricks, 512, 4), vs.r, nb)
         assert (W_ref > 0).mean() > 0.05
-        assert np.abs(lin[..., 0] - F_ref).max() <= F32_TOL
-        np.testing.assert_array_equal(lin[..., 1], W_ref)
+        assert np.abs(F - F_ref).max() <= F32_TOL
+        np.testing.assert_array_equal(W, W_ref)
         np.testing.assert_array_equal(col, col_ref)
         np.testing.assert_array_equal(flags.cpu().numpy(), m.read_brick_flags(vid).reshape(-1))
     m.close()
+
+
+def test_noalloc_rejects_the_configs_the_context_rejects():
+    """An infinite truncation or weight cap would spread inf / NaN into the
+    caller's volume: both entry points refuse such a configuration."""
+    import torch
+    lib = _abi.lib()
+    vol = torch.zeros(512 * 2, dtype=torch.float32, device="cuda")
+    col = torch.zeros(512 * 4, dtype=torch.uint8, device="cuda")
+    flags = torch.full((1,), 6, dtype=torch.uint8, device="cuda")
+    desc = _abi.mv_volume_desc((C.c_int32 * 3)(0, 0, 0), (C.c_int32 * 3)(8, 8, 8), 0.01, _abi.MV_TSDF_F32)
+    view = _abi.mv_volume_view(desc, vol.data_ptr(), col.data_ptr(), flags.data_ptr())
+    cam = synth.Camera(10.0, 10.0, 4.5, 3.5, 10, 8)
+    K = intrinsics(cam)
+    T = np.eye(4).reshape(16)
+    depth = torch.ones(80, dtype=torch.float32, device="cuda")
+    for field, value in (("trunc_voxels", float("inf")), ("w_max", float("inf")), ("w_max", 1e31)):
+        cfg = _abi.mv_config()
+        assert lib.mv_config_default(C.byref(cfg)) == _abi.MV_OK
+        setattr(cfg, field, value)
+        st = lib.mv_integrate_noalloc(C.byref(view), C.byref(cfg), C.c_void_p(depth.data_ptr()), None,
+                                      C.byref(K), T.ctypes.data_as(C.POINTER(C.c_double)),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == _abi.MV_ERR_ARG, (field, value)
+        h = C.c_void_p()
+        assert lib.mv_create(C.byref(cfg), 0, C.byref(h)) == _abi.MV_ERR_ARG, (field, value)
+    torch.cuda.synchronize()
+    assert torch.all(vol == 0)
 
 
 def test_brick_classes_equal_the_per_voxel_path_at_full_size():
