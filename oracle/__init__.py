@@ -81,6 +81,9 @@ def _load():
         _lib.orc_raycast_pixels.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
                                             dp, C.POINTER(_Cfg), i64p, C.c_int64, dp, dp, u8p, dp,
                                             i32p, u8p]
+        _lib.orc_raycast_footprint.argtypes = [C.POINTER(_Volume), C.c_int32, C.POINTER(_Intr), dp,
+                                               C.POINTER(_Cfg), i64p, C.c_int64, i64p]
+        _lib.orc_raycast_footprint.restype = C.c_int
         _lib.orc_sample.argtypes = [C.POINTER(_Volume), dp, i32p]
         _lib.orc_sample.restype = C.c_double
         _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
@@ -243,6 +246,30 @@ def raycast(vols, cam, T, cfg: Config = Config(), ids=None, pixels=None):
                                _ptr(T, C.c_double), C.byref(cc), _ptr(pix, C.c_int64),
                                C.c_int64(pix.size), *outs)
     return out
+
+
+def raycast_footprint(vols, cam, T, cfg: Config = Config(), pixels=None):
+    """The voxels a dense march of this view must read (Sec. Raycasting: every
+    sample of every ray until its zero crossing, in every volume): per volume
+    (distinct voxels whose TSDF and weight are read -- the 2x2x2 neighbourhoods
+    of the samples and bisection midpoints --, distinct voxels whose colour the
+    hits read).  With ``pixels`` (linear indices) only those rays count."""
+    lib = _load()
+    vols = list(vols)
+    n = len(vols)
+    arr = (_Volume * max(n, 1))()
+    for i, v in enumerate(vols):
+        arr[i] = v._c()
+    counts = np.zeros(2 * max(n, 1), np.int64)
+    T = _pose(T)
+    ci, cc = _intr(cam), cfg._c()
+    pix = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+    rc = lib.orc_raycast_footprint(arr, C.c_int32(n), C.byref(ci), _ptr(T, C.c_double), C.byref(cc),
+                                   None if pix is None else _ptr(pix, C.c_int64),
+                                   C.c_int64(0 if pix is None else pix.size), _ptr(counts, C.c_int64))
+    if rc != 0:
+        raise MemoryError("raycast_footprint: bitmap allocation failed")
+    return [(int(counts[2 * i]), int(counts[2 * i + 1])) for i in range(n)]
 
 
 def sample(vol: Volume, q):

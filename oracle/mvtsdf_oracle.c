@@ -45,6 +45,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -311,9 +312,23 @@ typedef struct {
     uint8_t flags;
 } orc_hit;
 
-/* march one ray through one volume */
-static orc_hit march_volume(const orc_volume *v, const double o[3], const double d[3],
-                            const orc_config *c)
+/* mark the 8 corners of a cell in a bitmap of the volume's voxels */
+static void mark_cell(const orc_volume *v, const int64_t cell[3], uint64_t *bits)
+{
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const size_t i = vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz);
+                __atomic_fetch_or(&bits[i >> 6], (uint64_t)1 << (i & 63), __ATOMIC_RELAXED);
+            }
+}
+
+/* march one ray through one volume.  touched / touched_rgb (bitmaps over
+ * the volume's voxels, may be NULL) receive the voxels whose (F, W) the
+ * march reads -- the corners of every sample's cell and of every bisection
+ * midpoint's cell -- and the voxels whose colour the hit reads. */
+static orc_hit march_volume_marking(const orc_volume *v, const double o[3], const double d[3],
+                                    const orc_config *c, uint64_t *touched, uint64_t *touched_rgb)
 {
     orc_hit out;
     memset(&out, 0, sizeof(out));
@@ -359,6 +374,7 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
         int64_t cell[3];
         double fr[3];
         cell_of(v, q, cell, fr);
+        if (touched) mark_cell(v, cell, touched);
         const int valid = cell_valid(v, cell);
         const double F = valid ? trilinear_in_cell(v, cell, fr, NULL) : 0.0;
         out.flags |= sample_flags(v, q, valid, F, c);
@@ -374,6 +390,7 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
                 int64_t cm[3];
                 double fm[3];
                 cell_of(v, qm, cm, fm);
+                if (touched) mark_cell(v, cm, touched);
                 const double g = trilinear_in_cell(v, cm, fm, NULL);
                 if (g > 0.0) a = m; else b = m;
             }
@@ -389,9 +406,11 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
             }
             out.hit = 1;
             out.tau = ts;
+            if (touched) mark_cell(v, cs, touched);
             out.cell_ok = cell_valid(v, cs);
             trilinear_in_cell(v, cs, fs, out.grad);
             if (v->rgba) {
+                if (touched_rgb) mark_cell(v, cs, touched_rgb);
                 for (int ch = 0; ch < 3; ++ch) {
                     double acc = 0.0;
                     for (int dz = 0; dz < 2; ++dz)
@@ -412,6 +431,12 @@ static orc_hit march_volume(const orc_volume *v, const double o[3], const double
         tau_prev = tau;
     }
     return out;
+}
+
+static orc_hit march_volume(const orc_volume *v, const double o[3], const double d[3],
+                            const orc_config *c)
+{
+    return march_volume_marking(v, o, d, c, NULL, NULL);
 }
 
 /* One pixel: march every volume, keep the nearest hit (exact ties to the
@@ -508,6 +533,53 @@ ORC_EXPORT void orc_raycast_pixels(const orc_volume *vols, const int32_t *ids, i
         raycast_pixel(vols, ids, nvol, K, R, t, c, pix[j] % K->width, pix[j] / K->width, hits,
                       depth, normal, rgba, vertex, hit_vol, flags);
     }
+}
+
+/* Memory footprint of a raycast (the bytes a dense march must read): every
+ * pixel (or the listed ones) is marched through every volume as orc_raycast
+ * does, and counts[2 v] receives the number of distinct voxels of volume v
+ * whose (F, W) the march reads (the 2x2x2 neighbourhoods of its samples and
+ * bisection midpoints), counts[2 v + 1] the number of distinct voxels whose
+ * colour the hits read.  Returns 0, or -1 when a bitmap cannot be allocated. */
+ORC_EXPORT int orc_raycast_footprint(const orc_volume *vols, int32_t nvol, const orc_intrinsics *K,
+                                     const double T[16], const orc_config *c, const int64_t *pix,
+                                     int64_t npix, int64_t *counts)
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+    uint64_t **bits = (uint64_t **)calloc((size_t)(nvol > 0 ? 2 * nvol : 1), sizeof(uint64_t *));
+    if (!bits) return -1;
+    int ok = 1;
+    for (int32_t vi = 0; vi < nvol && ok; ++vi) {
+        const size_t n = (size_t)vols[vi].r[0] * vols[vi].r[1] * vols[vi].r[2];
+        bits[2 * vi] = (uint64_t *)calloc((n + 63) / 64, sizeof(uint64_t));
+        bits[2 * vi + 1] = (uint64_t *)calloc((n + 63) / 64, sizeof(uint64_t));
+        ok = bits[2 * vi] && bits[2 * vi + 1];
+    }
+    if (ok) {
+        const int64_t total = pix ? npix : (int64_t)K->width * K->height;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t j = 0; j < total; ++j) {
+            const int64_t p = pix ? pix[j] : j;
+            const double x = (double)(p % K->width), y = (double)(p / K->width);
+            const double dc[3] = { (x - K->cx) / K->fx, (y - K->cy) / K->fy, 1.0 };
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
+            for (int32_t vi = 0; vi < nvol; ++vi)
+                march_volume_marking(&vols[vi], t, d, c, bits[2 * vi], bits[2 * vi + 1]);
+        }
+        for (int32_t vi = 0; vi < nvol; ++vi) {
+            const size_t n = (size_t)vols[vi].r[0] * vols[vi].r[1] * vols[vi].r[2];
+            for (int k = 0; k < 2; ++k) {
+                int64_t cnt = 0;
+                for (size_t w = 0; w < (n + 63) / 64; ++w) cnt += __builtin_popcountll(bits[2 * vi + k][w]);
+                counts[2 * vi + k] = cnt;
+            }
+        }
+    }
+    for (int32_t vi = 0; vi < 2 * nvol; ++vi) free(bits[vi]);
+    free(bits);
+    return ok ? 0 : -1;
 }
 
 /* Trilinear value and validity at one point q (this volume's voxel

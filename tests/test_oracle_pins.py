@@ -222,6 +222,49 @@ def test_raycast_plane_is_exact(oracle_lib, seed):
     np.testing.assert_allclose(out["vertex"][inside], hit_pt[inside], atol=1e-9)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_raycast_hit_colour_is_the_affine_colour_at_the_hit(oracle_lib, seed):
+    """Hit colour (trilinear RGB of the hit cell, rounded half up): with a
+    linear signed distance (exact hit, as above) and a colour that is affine
+    in the voxel index -- which trilinear interpolation reproduces exactly --
+    each channel must equal the affine colour at the analytic ray--plane hit,
+    rounded half up.  Distinct signed gradients per channel catch a wrong
+    corner weight, a swapped axis or channel, a floor instead of rounding and
+    a colour taken from another cell than the hit's."""
+    rng = np.random.default_rng(10 + seed)
+    vol = oracle.Volume(h=(-30, -30, -30), r=(60, 60, 60), s=0.02)
+    mu = 4 * vol.s
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    dd = float(rng.uniform(-0.1, 0.1))
+    fill(vol, lambda p: dd - p @ n, mu)
+    # colour_ch(i) = c0_ch + g_ch . i over local voxel indices i = (x, y, z), inside [0, 255]
+    c0 = np.array([10.0, 20.0, 200.0])
+    g = np.array([[2.0, 1.0, 0.0], [0.0, 2.0, 1.0], [-1.0, 0.0, -2.0]])  # rows: channel; cols: x, y, z
+    z, y, x = np.meshgrid(*(np.arange(r) for r in vol.r[::-1]), indexing="ij")
+    idx = np.stack([x, y, z], -1).astype(np.float64)
+    col = c0 + idx @ g.T
+    assert col.min() >= 0 and col.max() <= 255
+    vol.rgba[..., :3] = col.astype(np.uint8)
+    vol.rgba[..., 3] = 1
+    eye = -0.9 * n + rng.normal(scale=0.05, size=3)
+    T = synth.look_at(eye, eye + n + rng.normal(scale=0.1, size=3))
+    out = oracle.raycast([vol], CAM_S, T, oracle.Config(trunc_vox=4.0))
+    o, d = rays(CAM_S, T)
+    tau = (dd - o @ n) / (d @ n)
+    hit_pt = o + tau[..., None] * d
+    inside = np.all((hit_pt > (np.array(vol.h) + 1) * vol.s) &
+                    (hit_pt < (np.array(vol.h) + np.array(vol.r) - 2) * vol.s), -1)
+    q = hit_pt / vol.s - np.array(vol.h)          # local voxel coordinates of the hit
+    want = c0 + q @ g.T                           # exact affine colour there
+    frac = want - np.floor(want)
+    safe = inside & np.all(np.abs(frac - 0.5) > 1e-6, -1)
+    assert safe.sum() > 0.5 * safe.size
+    got = out["rgba"][..., :3].astype(np.float64)
+    np.testing.assert_array_equal(got[safe], np.floor(want[safe] + 0.5))
+    assert np.all(out["rgba"][..., 3][inside] == 255)
+
+
 def test_raycast_sphere_within_interpolation_bound(oracle_lib):
     """Sphere of radius rho: trilinear interpolation of its distance function
     errs by at most s^2 / (4 rho) near the surface, which bounds the hit
@@ -333,6 +376,73 @@ def test_march_invalid_sample_breaks_the_pair(oracle_lib):
     vol2 = row_volume([1, 1, 1, 1, -1, -1, -1, -1])
     out2 = oracle.raycast([vol2], axis_cam(), x_ray_pose(0.05, 0.05), oracle.Config(step_vox=1.0))
     assert abs(out2["depth"][0, 0] - (0.5 + 0.35)) < 1e-12
+
+
+def test_footprint_of_an_axis_ray(oracle_lib):
+    """Voxels a dense march reads, counted by hand on a row: samples at every
+    voxel plane x = 0 .. n-1 (step 1 voxel), each reading its cell's 2x2x2
+    corners (the last plane's cell clamps to n-2).  No surface: all n x 2 x 2
+    voxels.  A root at x = 3.5: cells 0..4 are sampled (corners x = 0..5), the
+    bisection stays in cell 3, and the hit reads the colour of cell 3."""
+    vol = row_volume([1.0] * 10)
+    (fp,) = oracle.raycast_footprint([vol], axis_cam(), x_ray_pose(0.05, 0.05), oracle.Config(step_vox=1.0))
+    assert fp == (4 * 10, 0)
+    vol2 = row_volume([1, 1, 1, 1, -1, -1, -1, -1, -1, -1])
+    (fp2,) = oracle.raycast_footprint([vol2], axis_cam(), x_ray_pose(0.05, 0.05), oracle.Config(step_vox=1.0))
+    assert fp2 == (4 * 6, 8)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_footprint_matches_brute_force_sample_cells(oracle_lib, seed):
+    """A volume with no surface (F > 0 wherever observed, random observation
+    pattern) has no hit, so every sample on the global grid inside the domain
+    is read: the footprint is the union of the 2x2x2 corner sets of all those
+    samples' cells, enumerated here ray by ray from the grid definition."""
+    rng = np.random.default_rng(seed)
+    vol = oracle.Volume(h=(-5, -4, 20), r=(9, 8, 7), s=0.05)
+    vol.F[:] = rng.uniform(0.1, 1.0, size=vol.F.shape)
+    vol.W[:] = (rng.uniform(size=vol.W.shape) < 0.7).astype(np.float64)
+    cam = synth.Camera(12.0, 12.0, 5.5, 4.5, 12, 10)
+    T = synth.look_at(rng.normal(scale=0.05, size=3), (0.0, 0.0, 1.2))
+    step = 0.7
+    (fp,) = oracle.raycast_footprint([vol], cam, T, oracle.Config(step_vox=step))
+    o, d = synth.pixel_rays(cam, T)
+    h, r, s = np.array(vol.h), np.array(vol.r), vol.s
+    seen = np.zeros(vol.F.shape, bool)
+    for y in range(cam.height):
+        for x in range(cam.width):
+            q0, dv = o / s, d[y, x] / s
+            lo, hi = 0.0, np.inf
+            for a in range(3):
+                t0, t1 = (h[a] - q0[a]) / dv[a], (h[a] + r[a] - 1 - q0[a]) / dv[a]
+                lo, hi = max(lo, min(t0, t1)), min(hi, max(t0, t1))
+            if lo > hi:
+                continue
+            delta = step * s / np.linalg.norm(d[y, x])
+            for k in range(int(np.ceil(lo / delta)), int(np.floor(hi / delta)) + 1):
+                q = q0 + k * delta * dv
+                c = np.clip(np.floor(q).astype(int) - h, 0, r - 2)
+                seen[c[2]:c[2] + 2, c[1]:c[1] + 2, c[0]:c[0] + 2] = True
+    assert seen.sum() > 50
+    assert fp == (int(seen.sum()), 0)
+
+
+def test_footprint_of_a_pixel_subset_is_not_larger(oracle_lib):
+    """Reading fewer rays reads no new voxels: the footprint of every other
+    pixel is at most that of all pixels, and the two halves together cover at
+    least the whole."""
+    vol = oracle.Volume(h=(-30, -30, -30), r=(60, 60, 60), s=0.02)
+    n = np.array([0.2, -0.1, 1.0])
+    n /= np.linalg.norm(n)
+    fill(vol, lambda p: 0.05 - p @ n, 4 * vol.s)
+    T = synth.look_at(-0.9 * n, n)
+    full = oracle.raycast_footprint([vol], CAM_S, T)[0]
+    npx = CAM_S.width * CAM_S.height
+    even = oracle.raycast_footprint([vol], CAM_S, T, pixels=np.arange(0, npx, 2))[0]
+    odd = oracle.raycast_footprint([vol], CAM_S, T, pixels=np.arange(1, npx, 2))[0]
+    assert full[0] > 0 and full[1] > 0
+    for a in range(2):
+        assert even[a] <= full[a] and odd[a] <= full[a] <= even[a] + odd[a]
 
 
 def test_merge_takes_nearest_and_breaks_ties_by_id(oracle_lib):
