@@ -220,6 +220,32 @@ mv_status mv_frame(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv
                    const double T_c2w[16], float *depth_out, float *normal, uint8_t *rgba,
                    float *vertex, int32_t *vol_id, void *stream);
 
+/* One frame of the paper's per-frame loop from and to host memory
+ * (Algorithm 1: upload the frame, integrate it into every resident volume,
+ * raycast them, download the maps).  depth (float32 h*w) and rgb (uint8
+ * h*w*3, or NULL for no colour update) are HOST buffers; depth_out (float32
+ * h*w), normal (float32 h*w*3), rgba (uint8 h*w*4), vertex (float32 h*w*3)
+ * and vol_id (int32 h*w) are HOST output buffers, each may be NULL (that map
+ * is not downloaded).  The maps are those of mv_frame.  Page-locked host
+ * buffers make the copies asynchronous; pageable ones also work, the driver
+ * then stages them.  The call only enqueues work and returns a ticket: the
+ * library keeps two device buffer sets (frame in, maps out) and three
+ * internal streams, one per stage (upload, kernels, download), so the upload
+ * of the next frame and the download of the previous one overlap the kernels
+ * of this one.  mv_frame_host_wait(ctx, ticket) blocks until that frame's
+ * maps are in its output buffers; until then every buffer of the frame must
+ * stay valid and unmodified.  Calls on one context still execute in call
+ * order.  The buffers are allocated on the first call and again when the
+ * image size changes (which first waits for the frames in flight). */
+mv_status mv_frame_host(mv_ctx *ctx, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                        const double T_c2w[16], float *depth_out, float *normal, uint8_t *rgba,
+                        float *vertex, int32_t *vol_id, uint64_t *ticket);
+
+/* Wait until the frame of `ticket` (from mv_frame_host) has been downloaded
+ * (and its input buffers are no longer read).  MV_ERR_ARG for a ticket not
+ * yet issued. */
+mv_status mv_frame_host_wait(mv_ctx *ctx, uint64_t ticket);
+
 /* Full-cover out-of-core frame (Sec. Volumetric Integration and
  * Sec. Raycasting, Algorithm 1: every volume is uploaded, integrated,
  * raycast and downloaded again in every frame).  Resident volumes are
@@ -571,6 +597,41 @@ mv_status mv_placer_list(mv_placer *placer, int32_t *ids, int32_t *cells, int32_
 
 /* Wait until all work of the context (all streams it used) has finished. */
 mv_status mv_synchronize(mv_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Merge of maps raycast on different GPUs (volumes partitioned across GPUs).
+ *
+ * The paper merges the hits of all volumes per pixel by the shortest ray
+ * distance (Sec. Raycasting, last paragraph), and the integration of
+ * different volumes is independent (Sec. Comparison to KinectFusion), so the
+ * volumes of one map can live on several GPUs: each raycasts its own
+ * volumes (mv_raycast / mv_frame), packs its per-pixel hits into 64-bit keys
+ * (mv_pack_hits), the keys are combined by an all-reduce MIN (e.g. NCCL),
+ * each GPU clears the pixels it did not win and takes depth and volume id
+ * from the winning key (mv_merge_hits), and an all-reduce SUM of normal,
+ * colour and vertex maps completes every GPU's copy.  The merged maps equal
+ * those of one GPU holding every volume, bit for bit.  Neither call needs a
+ * context; both run on the current device, asynchronously on `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* keys[p] = (bits of depth[p] << 32) | global id, where the global id of a
+ * local volume id v is id_map[v] (id_map_len entries; id_map NULL with
+ * id_map_len 0: the local id itself); INT64_MAX (no hit) where vol_id[p] < 0,
+ * depth is not a positive finite value, or the id has no global id.  A hit
+ * key is a non-negative int64 below INT64_MAX, so signed 64-bit MIN picks the
+ * nearest hit, equal distances going to the lower global id (the single-GPU
+ * tie rule).  depth: float32 [n] (ray distance tau = z-depth), vol_id: int32
+ * [n], id_map: int32, keys: int64 [n], all device. */
+mv_status mv_pack_hits(const float *depth, const int32_t *vol_id, const int32_t *id_map, int32_t id_map_len,
+                       int64_t n, int64_t *keys, void *stream);
+
+/* With best_keys the element-wise minimum of every GPU's keys and own_keys
+ * this GPU's: depth[p] and vol_id[p] are set from best_keys (0 and -1 where
+ * no GPU hit); normal[3 p..], rgba[p] (4 bytes, 4-byte aligned) and
+ * vertex[3 p..] are cleared where this GPU's key is not the winner.  Each
+ * output may be NULL.  All device arrays of n pixels. */
+mv_status mv_merge_hits(const int64_t *best_keys, const int64_t *own_keys, int64_t n, float *depth,
+                        int32_t *vol_id, float *normal, uint8_t *rgba, float *vertex, void *stream);
 
 #ifdef __cplusplus
 }

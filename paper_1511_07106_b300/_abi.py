@@ -114,6 +114,9 @@ _SIGNATURES = {
     "mv_integrate_volume": ([_P, C.c_int32, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_raycast": ([_P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_frame": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
+    "mv_frame_host": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, C.POINTER(C.c_uint64)],
+                      C.c_int),
+    "mv_frame_host_wait": ([_P, C.c_uint64], C.c_int),
     "mv_frame_streamed": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, C.c_int32, _P],
                           C.c_int),
     "mv_raycast_volume": ([_P, C.c_int32, C.c_int32, C.POINTER(mv_intrinsics), _D16, _P, _P, _P,
@@ -134,6 +137,8 @@ _SIGNATURES = {
     "mv_synchronize": ([_P], C.c_int),
     "mv_integrate_noalloc": ([C.POINTER(mv_volume_view), C.POINTER(mv_config), _P, _P,
                               C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
+    "mv_pack_hits": ([_P, _P, _P, C.c_int32, C.c_int64, _P, _P], C.c_int),
+    "mv_merge_hits": ([_P, _P, C.c_int64, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_get_config": ([_P, C.POINTER(mv_config)], C.c_int),
     "mv_reserve_host": ([_P, C.POINTER(mv_volume_desc), C.c_int32], C.c_int),
     "mv_depth_to_maps": ([_P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P], C.c_int),

@@ -171,6 +171,18 @@ struct mv_ctx {
         cudaEvent_t loaded[kMaxStreamSlots] = {}, done[kMaxStreamSlots] = {}, freed[kMaxStreamSlots] = {};
         bool freed_rec[kMaxStreamSlots] = {};
     } ss;
+    // mv_frame_host: two device buffer sets (frame in, maps out) and one
+    // stream per pipeline stage; ticket t uses set t % 2
+    struct HostPipe {
+        cudaStream_t up = nullptr, run = nullptr, down = nullptr;
+        int width = 0, height = 0;
+        float *depth[2] = {}, *dout[2] = {}, *normal[2] = {}, *vertex[2] = {};
+        uint8_t *rgb[2] = {}, *rgba[2] = {};
+        int32_t *vid[2] = {};
+        cudaEvent_t uploaded[2] = {}, computed[2] = {}, downloaded[2] = {};
+        bool used[2] = {false, false};
+        uint64_t next = 0;  // tickets issued
+    } hp;
     // raycast backward: per-slot gradient pointers and the poses of one call
     float **d_grad_ptrs = nullptr;
     double *d_poses = nullptr;
@@ -634,6 +646,70 @@ void free_slots(mv_ctx *c, cudaStream_t s)
 
 }  // namespace
 
+namespace {
+
+// Device buffers and events of the host pipeline (after a full synchronise).
+void free_host_pipe(mv_ctx *c)
+{
+    auto &hp = c->hp;
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(hp.depth[b]);
+        cudaFree(hp.rgb[b]);
+        cudaFree(hp.dout[b]);
+        cudaFree(hp.normal[b]);
+        cudaFree(hp.rgba[b]);
+        cudaFree(hp.vertex[b]);
+        cudaFree(hp.vid[b]);
+        hp.depth[b] = hp.dout[b] = hp.normal[b] = hp.vertex[b] = nullptr;
+        hp.rgb[b] = hp.rgba[b] = nullptr;
+        hp.vid[b] = nullptr;
+        hp.used[b] = false;
+    }
+    hp.width = hp.height = 0;
+}
+
+// Allocate the pipeline's streams, events and the two buffer sets for w x h
+// frames (once, and again when the image size changes).
+cudaError_t ensure_host_pipe(mv_ctx *c, int w, int h)
+{
+    auto &hp = c->hp;
+    cudaError_t e = cudaSuccess;
+    if (!hp.up) {
+        for (cudaStream_t *st : {&hp.up, &hp.run, &hp.down})
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+            for (cudaEvent_t *ev : {&hp.uploaded[b], &hp.computed[b], &hp.downloaded[b]})
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    if (hp.width == w && hp.height == h) return cudaSuccess;
+    // the buffers of earlier frames may still be in use
+    for (cudaStream_t st : {hp.up, hp.run, hp.down}) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+    }
+    free_host_pipe(c);
+    const size_t n = (size_t)w * (size_t)h;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMalloc((void **)&hp.depth[b], n * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.rgb[b], n * 3);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.dout[b], n * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.normal[b], n * 12);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.rgba[b], n * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.vertex[b], n * 12);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&hp.vid[b], n * 4);
+    }
+    if (e != cudaSuccess) {
+        free_host_pipe(c);
+        return e;
+    }
+    hp.width = w;
+    hp.height = h;
+    return cudaSuccess;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *mv_version(void) { return "mvtsdf 0.1.0 (sm_103a)"; }
@@ -723,6 +799,12 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
     if (c->d_poses) cudaFree(c->d_poses);
+    free_host_pipe(c);
+    for (cudaStream_t st : {c->hp.up, c->hp.run, c->hp.down})
+        if (st) cudaStreamDestroy(st);
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t ev : {c->hp.uploaded[b], c->hp.computed[b], c->hp.downloaded[b]})
+            if (ev) cudaEventDestroy(ev);
     for (auto &t : c->timed_pending) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
@@ -1208,6 +1290,55 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     for (int k : kinds) c->launches[k] += 1;
     if (two_level) c->launches[MV_KERNEL_BRICK_LIST] += 1;
     return end_call(c, s);
+}
+
+mv_status mv_frame_host(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,
+                        const double T[16], float *depth_out, float *normal, uint8_t *rgba, float *vertex,
+                        int32_t *vol_id, uint64_t *ticket)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!depth || !ticket || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    cudaSetDevice(c->device);
+    MV_CUDA(c, ensure_host_pipe(c, K->width, K->height));
+    auto &hp = c->hp;
+    const int b = (int)(hp.next & 1u);
+    const size_t n = (size_t)K->width * (size_t)K->height;
+    // upload: the set's inputs are free once the frame that used them last has run
+    if (hp.used[b]) MV_CUDA(c, cudaStreamWaitEvent(hp.up, hp.computed[b], 0));
+    MV_CUDA(c, cudaMemcpyAsync(hp.depth[b], depth, n * 4, cudaMemcpyHostToDevice, hp.up));
+    if (rgb) MV_CUDA(c, cudaMemcpyAsync(hp.rgb[b], rgb, n * 3, cudaMemcpyHostToDevice, hp.up));
+    MV_CUDA(c, cudaEventRecord(hp.uploaded[b], hp.up));
+    // run: after this frame's upload and the download of the set's last maps
+    MV_CUDA(c, cudaStreamWaitEvent(hp.run, hp.uploaded[b], 0));
+    if (hp.used[b]) MV_CUDA(c, cudaStreamWaitEvent(hp.run, hp.downloaded[b], 0));
+    mv_status st = mv_frame(c, hp.depth[b], rgb ? hp.rgb[b] : nullptr, K, T, hp.dout[b],
+                            normal ? hp.normal[b] : nullptr, rgba ? hp.rgba[b] : nullptr,
+                            vertex ? hp.vertex[b] : nullptr, hp.vid[b], hp.run);
+    if (st) return st;
+    MV_CUDA(c, cudaEventRecord(hp.computed[b], hp.run));
+    // download of the requested maps
+    MV_CUDA(c, cudaStreamWaitEvent(hp.down, hp.computed[b], 0));
+    if (depth_out) MV_CUDA(c, cudaMemcpyAsync(depth_out, hp.dout[b], n * 4, cudaMemcpyDeviceToHost, hp.down));
+    if (normal) MV_CUDA(c, cudaMemcpyAsync(normal, hp.normal[b], n * 12, cudaMemcpyDeviceToHost, hp.down));
+    if (rgba) MV_CUDA(c, cudaMemcpyAsync(rgba, hp.rgba[b], n * 4, cudaMemcpyDeviceToHost, hp.down));
+    if (vertex) MV_CUDA(c, cudaMemcpyAsync(vertex, hp.vertex[b], n * 12, cudaMemcpyDeviceToHost, hp.down));
+    if (vol_id) MV_CUDA(c, cudaMemcpyAsync(vol_id, hp.vid[b], n * 4, cudaMemcpyDeviceToHost, hp.down));
+    MV_CUDA(c, cudaEventRecord(hp.downloaded[b], hp.down));
+    hp.used[b] = true;
+    *ticket = hp.next++;
+    return MV_OK;
+}
+
+mv_status mv_frame_host_wait(mv_ctx *c, uint64_t ticket)
+{
+    if (!c) return MV_ERR_ARG;
+    auto &hp = c->hp;
+    if (ticket >= hp.next) return fail(c, MV_ERR_ARG, "no such frame");
+    cudaSetDevice(c->device);
+    // the set's download event is that of the latest frame on the set, which
+    // finishes after every earlier frame's download (one download stream)
+    MV_CUDA(c, cudaEventSynchronize(hp.downloaded[ticket & 1u]));
+    return MV_OK;
 }
 
 mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_intrinsics *K,

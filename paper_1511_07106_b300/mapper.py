@@ -230,6 +230,54 @@ class Mapper:
         del keep
         return out
 
+    def alloc_host_maps(self, cam, vertex=False, vol_id=False):
+        """Page-locked host maps for frame_host: depth, normal, rgba (and
+        optionally vertex, vol_id)."""
+        import torch
+        H, W = cam.height, cam.width
+        out = {"depth": torch.empty((H, W), dtype=torch.float32).pin_memory(),
+               "normal": torch.empty((H, W, 3), dtype=torch.float32).pin_memory(),
+               "rgba": torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()}
+        if vertex:
+            out["vertex"] = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+        if vol_id:
+            out["vol_id"] = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        return out
+
+    def frame_host(self, depth, rgb, cam, T, out) -> int:
+        """mv_frame_host: host depth (H, W) float32 and rgb (H, W, 3) uint8 (or
+        None) in, host maps (dict of CPU tensors or numpy arrays, from
+        alloc_host_maps) out.  Asynchronous; returns the ticket for
+        frame_host_wait.  Every buffer must stay alive until that wait."""
+        K = intrinsics(cam)
+        _, Tp = keep = _pose(T)
+        n = cam.width * cam.height
+
+        def hp(a, numel, name, dtype):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or a.numel() != numel or str(a.dtype) != dtype:
+                    raise ValueError(f"{name} must be a contiguous CPU {dtype} tensor of {numel} elements")
+                return C.c_void_p(a.data_ptr())
+            if not a.flags["C_CONTIGUOUS"] or a.size != numel or str(a.dtype) != dtype.split(".")[-1]:
+                raise ValueError(f"{name} must be a contiguous {dtype} array of {numel} elements")
+            return C.c_void_p(a.ctypes.data)
+
+        ticket = C.c_uint64()
+        self._check(self._lib.mv_frame_host(
+            self._h, hp(depth, n, "depth", "torch.float32"), hp(rgb, 3 * n, "rgb", "torch.uint8"), C.byref(K), Tp,
+            hp(out.get("depth"), n, "depth_out", "torch.float32"),
+            hp(out.get("normal"), 3 * n, "normal", "torch.float32"),
+            hp(out.get("rgba"), 4 * n, "rgba", "torch.uint8"),
+            hp(out.get("vertex"), 3 * n, "vertex", "torch.float32"),
+            hp(out.get("vol_id"), n, "vol_id", "torch.int32"), C.byref(ticket)))
+        del keep
+        return int(ticket.value)
+
+    def frame_host_wait(self, ticket: int):
+        self._check(self._lib.mv_frame_host_wait(self._h, C.c_uint64(int(ticket))))
+
     def frame_streamed(self, depth, rgb, cam, T, out=None, n_slots=2, stream=None) -> dict:
         """Integrate the frame into every volume and raycast the same view,
         streaming the swapped-out volumes through n_slots device slots."""
