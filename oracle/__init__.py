@@ -89,6 +89,8 @@ def _load():
         _lib.orc_raycast_grad.argtypes = [C.POINTER(_Volume), i32p, C.c_int32, C.POINTER(_Intr),
                                           dp, C.POINTER(_Cfg), dp, dp, dp, dp, dp, dp,
                                           C.POINTER(C.POINTER(C.c_double)), u8p]
+        _lib.orc_raycast_grad_pixels.argtypes = (_lib.orc_raycast_grad.argtypes[:6] + [i64p, C.c_int64] +
+                                                 _lib.orc_raycast_grad.argtypes[6:])
         _lib.orc_endpoint_cells.argtypes = [fp, C.POINTER(_Intr), dp, C.c_double, C.c_double, C.c_double,
                                             i64p, u8p]
         _lib.orc_extract_points.argtypes = [C.POINTER(_Volume), dp, u8p, i64p, C.c_int64]
@@ -283,13 +285,14 @@ def sample(vol: Volume, q):
 
 
 def raycast_grad(vols, cam, T, grad_depth=None, grad_rgb=None, cfg: Config = Config(), ids=None,
-                 want_tsdf=True):
+                 want_tsdf=True, pixels=None):
     """Gradients of the raycast (left se(3) pose perturbation xi = (rho, phi)
     in the world frame, and the TSDF voxel values).  grad_depth (H, W) and
     grad_rgb (H, W, 3; colour in [0, 1]) are the upstream gradients (None =
     0).  Returns dict: depth, grad_pose (6,), jac_tau (H, W, 6), jac_rgb
     (H, W, 3, 6), grad_F (list of arrays like each volume's F, or None),
-    excluded (H, W) GX_* bits."""
+    excluded (H, W) GX_* bits.  With ``pixels`` (linear indices y*W + x,
+    ascending) only those pixels are computed and summed; the rest stay 0."""
     lib = _load()
     vols = list(vols)
     n = len(vols)
@@ -309,11 +312,17 @@ def raycast_grad(vols, cam, T, grad_depth=None, grad_rgb=None, cfg: Config = Con
             ptrs[i] = g.ctypes.data_as(C.POINTER(C.c_double))
     T = _pose(T)
     ci, cc = _intr(cam), cfg._c()
-    lib.orc_raycast_grad(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
-                         C.byref(cc), _ptr(out["depth"], C.c_double), _ptr(gd, C.c_double),
-                         _ptr(gc, C.c_double), _ptr(out["grad_pose"], C.c_double),
-                         _ptr(out["jac_tau"], C.c_double), _ptr(out["jac_rgb"], C.c_double),
-                         ptrs if gF is not None else None, _ptr(out["excluded"], C.c_uint8))
+    outs = (_ptr(out["depth"], C.c_double), _ptr(gd, C.c_double), _ptr(gc, C.c_double),
+            _ptr(out["grad_pose"], C.c_double), _ptr(out["jac_tau"], C.c_double),
+            _ptr(out["jac_rgb"], C.c_double), ptrs if gF is not None else None,
+            _ptr(out["excluded"], C.c_uint8))
+    if pixels is None:
+        lib.orc_raycast_grad(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
+                             C.byref(cc), *outs)
+    else:
+        pix = np.ascontiguousarray(pixels, np.int64)
+        lib.orc_raycast_grad_pixels(arr, _ptr(ids, C.c_int32), C.c_int32(n), C.byref(ci), _ptr(T, C.c_double),
+                                    C.byref(cc), _ptr(pix, C.c_int64), C.c_int64(pix.size), *outs)
     out["grad_F"] = gF
     return out
 

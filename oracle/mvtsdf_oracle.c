@@ -612,6 +612,123 @@ ORC_EXPORT double orc_sample(const orc_volume *v, const double q[3], int32_t *va
 /* ------------------------------------------------------------------------ */
 enum { ORC_GX_NOHIT = 1, ORC_GX_CELL = 2, ORC_GX_FACE = 4, ORC_GX_GRAZE = 8 };
 
+/* Gradients of one pixel's hit (the body of orc_raycast_grad). */
+static void grad_pixel(const orc_volume *vols, const int32_t *ids, int32_t nvol, const orc_intrinsics *K,
+                       const double R[9], const double t[3], const orc_config *c, int64_t x, int64_t y,
+                       double *depth, const double *grad_depth, const double *grad_rgb, double *grad_pose,
+                       double *jac_tau, double *jac_rgb, double **grad_F, uint8_t *excluded)
+{
+    const int64_t W = K->width;
+    const size_t p = (size_t)y * (size_t)W + (size_t)x;
+    if (jac_tau) for (int k = 0; k < 6; ++k) jac_tau[6 * p + k] = 0.0;
+    if (jac_rgb) for (int k = 0; k < 18; ++k) jac_rgb[18 * p + k] = 0.0;
+    const double dc[3] = { ((double)x - K->cx) / K->fx, ((double)y - K->cy) / K->fy, 1.0 };
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
+    orc_hit best;
+    memset(&best, 0, sizeof(best));
+    int32_t best_v = -1;
+    for (int32_t vi = 0; vi < nvol; ++vi) {
+        orc_hit hv = march_volume(&vols[vi], t, d, c);
+        if (!hv.hit) continue;
+        if (best_v < 0 || hv.tau < best.tau || (hv.tau == best.tau && ids[vi] < ids[best_v])) {
+            best = hv;
+            best_v = vi;
+        }
+    }
+    uint8_t ex = 0;
+    if (depth) depth[p] = best_v >= 0 ? best.tau : 0.0;
+    if (best_v < 0) {
+        if (excluded) excluded[p] = ORC_GX_NOHIT;
+        return;
+    }
+    const orc_volume *v = &vols[best_v];
+    const double s = v->s, tau = best.tau;
+    double q[3], xs[3];
+    for (int a = 0; a < 3; ++a) {
+        q[a] = t[a] / s + tau * (d[a] / s);
+        xs[a] = t[a] + tau * d[a];
+    }
+    int64_t cell[3];
+    double fr[3];
+    cell_of(v, q, cell, fr);
+    if (!cell_valid(v, cell)) ex |= ORC_GX_CELL;
+    for (int a = 0; a < 3; ++a)
+        if (fr[a] < c->eps_q || fr[a] > 1.0 - c->eps_q) ex |= ORC_GX_FACE;
+    /* corner values, weights and weight gradients (per metre) */
+    double wj[8], gw[8][3], Fj[8], cj[8][3];
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const double wx = dx ? fr[0] : 1.0 - fr[0];
+        const double wy = dy ? fr[1] : 1.0 - fr[1];
+        const double wz = dz ? fr[2] : 1.0 - fr[2];
+        wj[k] = wx * wy * wz;
+        gw[k][0] = (dx ? 1.0 : -1.0) * wy * wz / s;
+        gw[k][1] = wx * (dy ? 1.0 : -1.0) * wz / s;
+        gw[k][2] = wx * wy * (dz ? 1.0 : -1.0) / s;
+        const size_t vi = vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz);
+        Fj[k] = v->F[vi];
+        for (int ch = 0; ch < 3; ++ch) cj[k][ch] = v->rgba ? v->rgba[4 * vi + ch] / 255.0 : 0.0;
+        for (int a = 0; a < 3; ++a) g[a] += Fj[k] * gw[k][a];
+    }
+    const double gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(fabs(gd) > 1e-3 * gn * dn)) ex |= ORC_GX_GRAZE;
+    if (excluded) excluded[p] = ex;
+    if (ex) return;
+    /* dtau/dxi */
+    double jt[6];
+    const double xg[3] = { xs[1] * g[2] - xs[2] * g[1], xs[2] * g[0] - xs[0] * g[2],
+                           xs[0] * g[1] - xs[1] * g[0] };
+    for (int a = 0; a < 3; ++a) {
+        jt[a] = -g[a] / gd;
+        jt[3 + a] = -xg[a] / gd;
+    }
+    /* d(x*)/dxi = [I | -[x*]_x] + d jt^T */
+    double dxdxi[3][6];
+    const double mX[3][3] = { {0.0, xs[2], -xs[1]}, {-xs[2], 0.0, xs[0]}, {xs[1], -xs[0], 0.0} };
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 6; ++b)
+            dxdxi[a][b] = (b < 3 ? (a == b ? 1.0 : 0.0) : mX[a][b - 3]) + d[a] * jt[b];
+    /* colour Jacobian J_C (3x3, per metre) and dC/dxi */
+    double JC[3][3] = {{0.0}};
+    for (int k = 0; k < 8; ++k)
+        for (int ch = 0; ch < 3; ++ch)
+            for (int a = 0; a < 3; ++a) JC[ch][a] += cj[k][ch] * gw[k][a];
+    double jc[3][6];
+    for (int ch = 0; ch < 3; ++ch)
+        for (int b = 0; b < 6; ++b) {
+            jc[ch][b] = 0.0;
+            for (int a = 0; a < 3; ++a) jc[ch][b] += JC[ch][a] * dxdxi[a][b];
+        }
+    if (jac_tau) for (int b = 0; b < 6; ++b) jac_tau[6 * p + b] = jt[b];
+    if (jac_rgb)
+        for (int ch = 0; ch < 3; ++ch)
+            for (int b = 0; b < 6; ++b) jac_rgb[18 * p + 6 * ch + b] = jc[ch][b];
+    const double gdep = grad_depth ? grad_depth[p] : 0.0;
+    double gc[3] = {0.0, 0.0, 0.0};
+    if (grad_rgb) for (int ch = 0; ch < 3; ++ch) gc[ch] = grad_rgb[3 * p + ch];
+    if (grad_pose)
+        for (int b = 0; b < 6; ++b) {
+            double acc = gdep * jt[b];
+            for (int ch = 0; ch < 3; ++ch) acc += gc[ch] * jc[ch][b];
+            grad_pose[b] += acc;
+        }
+    if (grad_F && grad_F[best_v]) {
+        /* dtau/dF_j = -w_j / gd; dC/dF_j = J_C d dtau/dF_j */
+        double jcd = 0.0;
+        for (int ch = 0; ch < 3; ++ch)
+            jcd += gc[ch] * (JC[ch][0] * d[0] + JC[ch][1] * d[1] + JC[ch][2] * d[2]);
+        const double coef = -(gdep + jcd) / gd;
+        for (int k = 0; k < 8; ++k) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+            grad_F[best_v][vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz)] += coef * wj[k];
+        }
+    }
+}
+
 ORC_EXPORT void orc_raycast_grad(const orc_volume *vols, const int32_t *ids, int32_t nvol,
                                  const orc_intrinsics *K, const double T[16], const orc_config *c,
                                  double *depth, const double *grad_depth, const double *grad_rgb,
@@ -622,118 +739,27 @@ ORC_EXPORT void orc_raycast_grad(const orc_volume *vols, const int32_t *ids, int
     pose_split(T, R, t);
     const int64_t W = K->width, H = K->height;
     if (grad_pose) for (int k = 0; k < 6; ++k) grad_pose[k] = 0.0;
-    for (int64_t y = 0; y < H; ++y) {
-        for (int64_t x = 0; x < W; ++x) {
-            const size_t p = (size_t)y * (size_t)W + (size_t)x;
-            if (jac_tau) for (int k = 0; k < 6; ++k) jac_tau[6 * p + k] = 0.0;
-            if (jac_rgb) for (int k = 0; k < 18; ++k) jac_rgb[18 * p + k] = 0.0;
-            const double dc[3] = { ((double)x - K->cx) / K->fx, ((double)y - K->cy) / K->fy, 1.0 };
-            double d[3];
-            for (int a = 0; a < 3; ++a) d[a] = R[3 * a + 0] * dc[0] + R[3 * a + 1] * dc[1] + R[3 * a + 2] * dc[2];
-            orc_hit best;
-            memset(&best, 0, sizeof(best));
-            int32_t best_v = -1;
-            for (int32_t vi = 0; vi < nvol; ++vi) {
-                orc_hit hv = march_volume(&vols[vi], t, d, c);
-                if (!hv.hit) continue;
-                if (best_v < 0 || hv.tau < best.tau || (hv.tau == best.tau && ids[vi] < ids[best_v])) {
-                    best = hv;
-                    best_v = vi;
-                }
-            }
-            uint8_t ex = 0;
-            if (depth) depth[p] = best_v >= 0 ? best.tau : 0.0;
-            if (best_v < 0) {
-                if (excluded) excluded[p] = ORC_GX_NOHIT;
-                continue;
-            }
-            const orc_volume *v = &vols[best_v];
-            const double s = v->s, tau = best.tau;
-            double q[3], xs[3];
-            for (int a = 0; a < 3; ++a) {
-                q[a] = t[a] / s + tau * (d[a] / s);
-                xs[a] = t[a] + tau * d[a];
-            }
-            int64_t cell[3];
-            double fr[3];
-            cell_of(v, q, cell, fr);
-            if (!cell_valid(v, cell)) ex |= ORC_GX_CELL;
-            for (int a = 0; a < 3; ++a)
-                if (fr[a] < c->eps_q || fr[a] > 1.0 - c->eps_q) ex |= ORC_GX_FACE;
-            /* corner values, weights and weight gradients (per metre) */
-            double wj[8], gw[8][3], Fj[8], cj[8][3];
-            double g[3] = {0.0, 0.0, 0.0};
-            for (int k = 0; k < 8; ++k) {
-                const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-                const double wx = dx ? fr[0] : 1.0 - fr[0];
-                const double wy = dy ? fr[1] : 1.0 - fr[1];
-                const double wz = dz ? fr[2] : 1.0 - fr[2];
-                wj[k] = wx * wy * wz;
-                gw[k][0] = (dx ? 1.0 : -1.0) * wy * wz / s;
-                gw[k][1] = wx * (dy ? 1.0 : -1.0) * wz / s;
-                gw[k][2] = wx * wy * (dz ? 1.0 : -1.0) / s;
-                const size_t vi = vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz);
-                Fj[k] = v->F[vi];
-                for (int ch = 0; ch < 3; ++ch) cj[k][ch] = v->rgba ? v->rgba[4 * vi + ch] / 255.0 : 0.0;
-                for (int a = 0; a < 3; ++a) g[a] += Fj[k] * gw[k][a];
-            }
-            const double gd = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
-            const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (!(fabs(gd) > 1e-3 * gn * dn)) ex |= ORC_GX_GRAZE;
-            if (excluded) excluded[p] = ex;
-            if (ex) continue;
-            /* dtau/dxi */
-            double jt[6];
-            const double xg[3] = { xs[1] * g[2] - xs[2] * g[1], xs[2] * g[0] - xs[0] * g[2],
-                                   xs[0] * g[1] - xs[1] * g[0] };
-            for (int a = 0; a < 3; ++a) {
-                jt[a] = -g[a] / gd;
-                jt[3 + a] = -xg[a] / gd;
-            }
-            /* d(x*)/dxi = [I | -[x*]_x] + d jt^T */
-            double dxdxi[3][6];
-            const double mX[3][3] = { {0.0, xs[2], -xs[1]}, {-xs[2], 0.0, xs[0]}, {xs[1], -xs[0], 0.0} };
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 6; ++b)
-                    dxdxi[a][b] = (b < 3 ? (a == b ? 1.0 : 0.0) : mX[a][b - 3]) + d[a] * jt[b];
-            /* colour Jacobian J_C (3x3, per metre) and dC/dxi */
-            double JC[3][3] = {{0.0}};
-            for (int k = 0; k < 8; ++k)
-                for (int ch = 0; ch < 3; ++ch)
-                    for (int a = 0; a < 3; ++a) JC[ch][a] += cj[k][ch] * gw[k][a];
-            double jc[3][6];
-            for (int ch = 0; ch < 3; ++ch)
-                for (int b = 0; b < 6; ++b) {
-                    jc[ch][b] = 0.0;
-                    for (int a = 0; a < 3; ++a) jc[ch][b] += JC[ch][a] * dxdxi[a][b];
-                }
-            if (jac_tau) for (int b = 0; b < 6; ++b) jac_tau[6 * p + b] = jt[b];
-            if (jac_rgb)
-                for (int ch = 0; ch < 3; ++ch)
-                    for (int b = 0; b < 6; ++b) jac_rgb[18 * p + 6 * ch + b] = jc[ch][b];
-            const double gdep = grad_depth ? grad_depth[p] : 0.0;
-            double gc[3] = {0.0, 0.0, 0.0};
-            if (grad_rgb) for (int ch = 0; ch < 3; ++ch) gc[ch] = grad_rgb[3 * p + ch];
-            if (grad_pose)
-                for (int b = 0; b < 6; ++b) {
-                    double acc = gdep * jt[b];
-                    for (int ch = 0; ch < 3; ++ch) acc += gc[ch] * jc[ch][b];
-                    grad_pose[b] += acc;
-                }
-            if (grad_F && grad_F[best_v]) {
-                /* dtau/dF_j = -w_j / gd; dC/dF_j = J_C d dtau/dF_j */
-                double jcd = 0.0;
-                for (int ch = 0; ch < 3; ++ch)
-                    jcd += gc[ch] * (JC[ch][0] * d[0] + JC[ch][1] * d[1] + JC[ch][2] * d[2]);
-                const double coef = -(gdep + jcd) / gd;
-                for (int k = 0; k < 8; ++k) {
-                    const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-                    grad_F[best_v][vox_index(v, cell[0] + dx, cell[1] + dy, cell[2] + dz)] += coef * wj[k];
-                }
-            }
-        }
-    }
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x)
+            grad_pixel(vols, ids, nvol, K, R, t, c, x, y, depth, grad_depth, grad_rgb, grad_pose, jac_tau,
+                       jac_rgb, grad_F, excluded);
+}
+
+/* The same for a list of pixels (linear indices y * width + x, in order);
+ * per-pixel outputs are full-size maps of which only the listed pixels are
+ * written, and grad_pose / grad_F sum over the listed pixels only. */
+ORC_EXPORT void orc_raycast_grad_pixels(const orc_volume *vols, const int32_t *ids, int32_t nvol,
+                                        const orc_intrinsics *K, const double T[16], const orc_config *c,
+                                        const int64_t *pix, int64_t npix, double *depth,
+                                        const double *grad_depth, const double *grad_rgb, double *grad_pose,
+                                        double *jac_tau, double *jac_rgb, double **grad_F, uint8_t *excluded)
+{
+    double R[9], t[3];
+    pose_split(T, R, t);
+    if (grad_pose) for (int k = 0; k < 6; ++k) grad_pose[k] = 0.0;
+    for (int64_t j = 0; j < npix; ++j)
+        grad_pixel(vols, ids, nvol, K, R, t, c, pix[j] % K->width, pix[j] / K->width, depth, grad_depth,
+                   grad_rgb, grad_pose, jac_tau, jac_rgb, grad_F, excluded);
 }
 
 /* ------------------------------------------------------------------------

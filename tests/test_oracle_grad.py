@@ -197,3 +197,24 @@ def test_colour_tsdf_gradient_matches_central_differences():
                 assert abs(fd - g[z, yy, xx]) <= 1e-4 * abs(g[z, yy, xx]) + 1e-7
                 checked += 1
     assert checked >= 12
+
+
+def test_pixel_subset_gradients_equal_the_full_image_restricted():
+    """The pixel-list form computes exactly the listed pixels of the full
+    image's per-pixel outputs, and its sums run over those pixels only."""
+    vol, T = sphere_volume_with_colour(seed=4)
+    rng = np.random.default_rng(5)
+    gd = rng.normal(size=(CAM.height, CAM.width))
+    gc = rng.normal(size=(CAM.height, CAM.width, 3))
+    pix = np.arange(0, CAM.width * CAM.height, 5)
+    sel = np.zeros((CAM.height, CAM.width), bool)
+    sel.reshape(-1)[pix] = True
+    full = oracle.raycast_grad([vol], CAM, T, grad_depth=np.where(sel, gd, 0.0),
+                               grad_rgb=np.where(sel[..., None], gc, 0.0))
+    sub = oracle.raycast_grad([vol], CAM, T, grad_depth=gd, grad_rgb=gc, pixels=pix)
+    for k in ("depth", "jac_tau", "jac_rgb", "excluded"):
+        np.testing.assert_array_equal(sub[k][sel], full[k][sel])
+        assert not np.any(sub[k][~sel])
+    assert (sub["depth"][sel] > 0).mean() > 0.3
+    np.testing.assert_allclose(sub["grad_pose"], full["grad_pose"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(sub["grad_F"][0], full["grad_F"][0], rtol=1e-12, atol=1e-15)
