@@ -208,6 +208,17 @@ mv_status mv_raycast(mv_ctx *ctx, const mv_intrinsics *K, const double T_c2w[16]
                      float *depth, float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id,
                      void *stream);
 
+/* The raycast of mv_raycast for n_views views of the same resident volumes
+ * in one kernel launch (the views of a batch of camera poses, e.g. for pose
+ * refinement).  T_c2w: host, n_views x 16 doubles (1 <= n_views <= 65535).
+ * Each output (device, may be NULL) holds n_views maps one after the other,
+ * in the layout of mv_raycast: depth and vol_id n x h x w, normal and vertex
+ * n x h x w x 3, rgba n x h x w x 4.  View k's maps equal those of
+ * mv_raycast at pose k, bit for bit.  Asynchronous on `stream`. */
+mv_status mv_raycast_batch(mv_ctx *ctx, const mv_intrinsics *K, const double *T_c2w, int32_t n_views,
+                           float *depth, float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id,
+                           void *stream);
+
 /* One frame of the paper's per-frame loop: integrate the frame into every
  * resident volume, then raycast every resident volume at the same pose, as
  * one CUDA graph launch (6 kernels; 7 with the two-level work list).  Same semantics and outputs as
@@ -330,8 +341,9 @@ typedef struct {
  * (the forward's 8-bit rounding is passed straight through).  Pixels with no
  * hit, an unobserved corner, grazing incidence or a hit within 1e-3 voxel of
  * a cell face contribute nothing.  T_c2w: host, n_poses x 16 doubles.
- * Asynchronous on `stream`; float atomics make the summation order, and so
- * the last bits of the result, vary between runs. */
+ * Asynchronous on `stream`.  grad_pose is summed in a fixed order (the same
+ * bits on every run); the TSDF gradients are summed by float atomics, whose
+ * order, and so the last bits of the result, vary between runs. */
 mv_status mv_raycast_backward(mv_ctx *ctx, const mv_intrinsics *K, const double *T_c2w,
                               int32_t n_poses, const float *depth, const int32_t *vol_id,
                               const float *grad_depth, const float *grad_rgb, float *grad_pose,

@@ -113,6 +113,7 @@ _SIGNATURES = {
     "mv_integrate": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_integrate_volume": ([_P, C.c_int32, _P, _P, C.POINTER(mv_intrinsics), _D16, _P], C.c_int),
     "mv_raycast": ([_P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
+    "mv_raycast_batch": ([_P, C.POINTER(mv_intrinsics), _D16, C.c_int32, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_frame": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, _P], C.c_int),
     "mv_frame_host": ([_P, _P, _P, C.POINTER(mv_intrinsics), _D16, _P, _P, _P, _P, _P, C.POINTER(C.c_uint64)],
                       C.c_int),

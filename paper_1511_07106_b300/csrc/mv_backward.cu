@@ -12,24 +12,12 @@
 // from the forward's depth and volume id (one thread per pixel and pose).
 // Pixels without a hit, with an unobserved corner, at grazing incidence
 // (|g.d| <= 1e-3 |g||d|) or within 1e-3 voxel of a cell face are skipped.
+// The pose gradient is summed per CTA and then per pose in a fixed order, so
+// it is the same on every run; the TSDF gradients are float atomics.
 #include "mv_internal.cuh"
 
 namespace mv {
 
-struct BackwardArgs {
-    const VolDev *vols;
-    int nvol;
-    float *const *grad_tsdf;  // per table slot: dense float32 [z][y][x], or null
-    const double *poses;      // n x 16 row-major camera-to-world
-    int n_poses;
-    float fx, fy, cx, cy;
-    int width, height;
-    const float *depth;       // n x h x w (forward tau*)
-    const int *vol_id;        // n x h x w
-    const float *grad_depth;  // n x h x w or null
-    const float *grad_rgb;    // n x h x w x 3 or null
-    float *grad_pose;         // n x 6 (accumulated)
-};
 
 __device__ __forceinline__ int slot_of(const VolDev *vols, int nvol, int id)
 {
@@ -185,20 +173,64 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
             }
         }
     }
-    // pose gradient: warp sums, then one atomic per warp and component
+    // pose gradient: warp sums, then the CTA's sum of each component written
+    // to its own slot (reduced per pose in a fixed order by pose_sum_kernel;
+    // one atomic per warp on the same six addresses serialised in L2)
+    __shared__ float s_part[4][6];
+    const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         float s = jp[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(A.grad_pose + 6 * p + k, s);
+        if ((threadIdx.x & 31) == 0) s_part[warp][k] = s;
     }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const size_t per_pose = (size_t)gridDim.x * gridDim.y;
+        A.partial[((size_t)p * per_pose + cta) * 6 + k] = ((s_part[0][k] + s_part[1][k]) + s_part[2][k]) + s_part[3][k];
+    }
+}
+
+// grad_pose[6 p + k] = sum over the CTAs of pose p of their partial sums, in a
+// fixed order (one CTA of 256 threads per pose; the same bits on every run)
+__global__ void __launch_bounds__(256) pose_sum_kernel(const float *__restrict__ partial, int per_pose,
+                                                       float *__restrict__ grad_pose)
+{
+    __shared__ float s_acc[6][256];
+    const int p = blockIdx.x;
+    const float *src = partial + (size_t)p * per_pose * 6;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = threadIdx.x; c < per_pose; c += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += src[(size_t)c * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_acc[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s_acc[k][threadIdx.x] += s_acc[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) grad_pose[6 * p + threadIdx.x] = s_acc[threadIdx.x][0];
+}
+
+// CTAs per pose of the backward kernel (sizes the partial-sum buffer).
+size_t backward_ctas_per_pose(int width, int height)
+{
+    return (size_t)((width + 15) / 16) * (size_t)((height + 7) / 8);
 }
 
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s)
 {
     dim3 grid((A.width + 15) / 16, (A.height + 7) / 8, A.n_poses);
     raycast_backward_kernel<<<grid, 128, 0, s>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pose_sum_kernel<<<A.n_poses, 256, 0, s>>>(A.partial, (int)(grid.x * grid.y), A.grad_pose);
     return cudaGetLastError();
 }
 

@@ -272,6 +272,23 @@ inline cudaError_t graph_node(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode
     return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &p);
 }
 
+// Arguments of the raycast backward kernel (mv_backward.cu).
+struct BackwardArgs {
+    const VolDev *vols;
+    int nvol;
+    float *const *grad_tsdf;  // per table slot: dense float32 [z][y][x], or null
+    const double *poses;      // n x 16 row-major camera-to-world
+    int n_poses;
+    float fx, fy, cx, cy;
+    int width, height;
+    const float *depth;       // n x h x w (forward tau*)
+    const int *vol_id;        // n x h x w
+    const float *grad_depth;  // n x h x w or null
+    const float *grad_rgb;    // n x h x w x 3 or null
+    float *grad_pose;         // n x 6 (written by the reduction)
+    float *partial;           // n x (CTAs per pose) x 6 per-CTA sums of the pose gradient
+};
+
 // element offset of voxel (x, y, z) in brick-major order
 __device__ __forceinline__ long long vox_offset(const VolDev &v, int x, int y, int z)
 {

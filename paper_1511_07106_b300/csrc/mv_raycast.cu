@@ -727,11 +727,9 @@ struct Tile {
 };
 
 template <int TILE>
-__global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restrict__ vols,
-                                                         const VolFrame *__restrict__ vfs, int nvol,
-                                                         FrameParams P, RayOut out, int merge,
-                                                         Stats *__restrict__ stats,
-                                                         const VisList *__restrict__ vl)
+__device__ __forceinline__ void raycast_tile(const VolDev *__restrict__ vols, const VolFrame *__restrict__ vfs,
+                                             int nvol, const FrameParams &P, const RayOut &out, int merge,
+                                             Stats *__restrict__ stats, const VisList *__restrict__ vl)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int tx, ty;
@@ -778,6 +776,42 @@ __global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restric
     add_counts(stats, active ? 1u : 0u, rc.samples, rc.skips, rc.hits);
 }
 
+template <int TILE>
+__global__ void __launch_bounds__(128, 6) raycast_kernel(const VolDev *__restrict__ vols,
+                                                         const VolFrame *__restrict__ vfs, int nvol,
+                                                         FrameParams P, RayOut out, int merge,
+                                                         Stats *__restrict__ stats,
+                                                         const VisList *__restrict__ vl)
+{
+    raycast_tile<TILE>(vols, vfs, nvol, P, out, merge, stats, vl);
+}
+
+// Several views in one launch (blockIdx.z = view): the view's parameters are
+// staged in shared memory, its camera constants are vfs + z * nvol, its view
+// list vl + z, and its maps start z * width * height pixels into each output.
+template <int TILE>
+__global__ void __launch_bounds__(128, 6) raycast_batch_kernel(const VolDev *__restrict__ vols,
+                                                               const VolFrame *__restrict__ vfs, int nvol,
+                                                               const FrameParams *__restrict__ Pb, RayOut out,
+                                                               Stats *__restrict__ stats,
+                                                               const VisList *__restrict__ vl)
+{
+    __shared__ FrameParams s_P;
+    static_assert(sizeof(FrameParams) % 4 == 0 && sizeof(FrameParams) / 4 <= 128, "FrameParams staging");
+    const int z = blockIdx.z;
+    if (threadIdx.x < sizeof(FrameParams) / 4)
+        reinterpret_cast<int *>(&s_P)[threadIdx.x] = reinterpret_cast<const int *>(Pb + z)[threadIdx.x];
+    __syncthreads();
+    const size_t px = (size_t)s_P.width * (size_t)s_P.height * (size_t)z;
+    RayOut o = out;
+    if (o.depth) o.depth += px;
+    if (o.normal) o.normal += 3 * px;
+    if (o.rgba) o.rgba += px;
+    if (o.vertex) o.vertex += 3 * px;
+    if (o.vol_id) o.vol_id += px;
+    raycast_tile<TILE>(vols, vfs + (size_t)z * nvol, nvol, s_P, o, 0, stats, vl ? vl + z : nullptr);
+}
+
 static const void *raycast_fn(int tile)
 {
     switch (tile) {
@@ -820,6 +854,23 @@ cudaError_t launch_raycast(const VolDev *vols, const VolFrame *vfs, int nvol, co
     case 2: raycast_kernel<2><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
     case 3: raycast_kernel<3><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
     default: raycast_kernel<0><<<grid, 128, 0, s>>>(vols, vfs, nvol, P, o, merge, stats, vis); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raycast_batch(const VolDev *vols, const VolFrame *vfs, int nvol, const FrameParams *Pb,
+                                 int n_views, int width, int height, float *depth, float *normal, uint8_t *rgba,
+                                 float *vertex, int *vol_id, Stats *stats, int tile, cudaStream_t s,
+                                 const VisList *vis)
+{
+    RayOut o{depth, normal, reinterpret_cast<uint32_t *>(rgba), vertex, vol_id};
+    dim3 grid = raycast_grid(tile, width, height);
+    grid.z = (unsigned)n_views;
+    switch (tile) {
+    case 1: raycast_batch_kernel<1><<<grid, 128, 0, s>>>(vols, vfs, nvol, Pb, o, stats, vis); break;
+    case 2: raycast_batch_kernel<2><<<grid, 128, 0, s>>>(vols, vfs, nvol, Pb, o, stats, vis); break;
+    case 3: raycast_batch_kernel<3><<<grid, 128, 0, s>>>(vols, vfs, nvol, Pb, o, stats, vis); break;
+    default: raycast_batch_kernel<0><<<grid, 128, 0, s>>>(vols, vfs, nvol, Pb, o, stats, vis); break;
     }
     return cudaGetLastError();
 }

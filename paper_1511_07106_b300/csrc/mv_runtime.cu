@@ -41,23 +41,13 @@ cudaError_t launch_cell_masks(const VolDev *, const uint2 *, const unsigned *, u
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
                            float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t,
                            const VisList *);
+cudaError_t launch_raycast_batch(const VolDev *, const VolFrame *, int, const FrameParams *, int, int, int,
+                                 float *, float *, uint8_t *, float *, int *, Stats *, int, cudaStream_t,
+                                 const VisList *);
 int integrate_occupancy_grid(int num_sms);
 int integrate_max_ctas_per_sm();
-struct BackwardArgs {
-    const VolDev *vols;
-    int nvol;
-    float *const *grad_tsdf;
-    const double *poses;
-    int n_poses;
-    float fx, fy, cx, cy;
-    int width, height;
-    const float *depth;
-    const int *vol_id;
-    const float *grad_depth;
-    const float *grad_rgb;
-    float *grad_pose;
-};
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
+size_t backward_ctas_per_pose(int width, int height);
 cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long long *, unsigned long long,
                            unsigned long long *, int, cudaStream_t);
 cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float, const double *, float *, float *,
@@ -75,8 +65,8 @@ cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[6], cu
                             uint2 *, unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
                             uint2 *, unsigned, unsigned *);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
-                          const VolDev *, int, VolFrame *, const FrameParams &, float *, float *,
-                          uint8_t *, float *, int *, Stats *, int, VisList *);
+                          const VolDev *, int, VolFrame *, const FrameParams &, float *, float *, uint8_t *,
+                          float *, int *, Stats *, int, VisList *);
 }  // namespace mv
 
 using namespace mv;
@@ -183,10 +173,19 @@ struct mv_ctx {
         bool used[2] = {false, false};
         uint64_t next = 0;  // tickets issued
     } hp;
+    // mv_raycast_batch: per view its parameters, camera constants of every
+    // table slot and view list (capacity in views)
+    FrameParams *d_pb = nullptr;
+    VolFrame *d_vfb = nullptr;
+    VisList *d_visb = nullptr;
+    int batch_cap = 0;
+    std::vector<FrameParams> h_pb;
     // raycast backward: per-slot gradient pointers and the poses of one call
     float **d_grad_ptrs = nullptr;
     double *d_poses = nullptr;
     int poses_cap = 0;
+    float *d_bw_partial = nullptr;  // per-CTA partial sums of the pose gradient
+    size_t bw_partial_cap = 0;      // floats
     // per-kernel launch counts and optional event timing
     bool timing = false;
     struct Timed { int kind; cudaEvent_t a, b; };
@@ -799,7 +798,11 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
     if (c->d_poses) cudaFree(c->d_poses);
+    if (c->d_bw_partial) cudaFree(c->d_bw_partial);
     free_host_pipe(c);
+    if (c->d_pb) cudaFree(c->d_pb);
+    if (c->d_vfb) cudaFree(c->d_vfb);
+    if (c->d_visb) cudaFree(c->d_visb);
     for (cudaStream_t st : {c->hp.up, c->hp.run, c->hp.down})
         if (st) cudaStreamDestroy(st);
     for (int b = 0; b < 2; ++b)
@@ -1225,6 +1228,49 @@ mv_status mv_raycast(mv_ctx *c, const mv_intrinsics *K, const double T[16], floa
                      float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id, void *stream)
 {
     return raycast_impl(c, -1, 1, K, T, depth, normal, rgba, vertex, vol_id, stream);
+}
+
+mv_status mv_raycast_batch(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_views, float *depth,
+                           float *normal, uint8_t *rgba, float *vertex, int32_t *vol_id, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!T || n_views < 1 || n_views > 65535) return fail(c, MV_ERR_ARG, "bad view count");
+    for (int k = 0; k < n_views; ++k)
+        if (!valid_frame(K, T + 16 * (size_t)k)) return fail(c, MV_ERR_ARG, "bad view arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mv_status st = begin_call(c, s);
+    if (st) return st;
+    if (n_views > c->batch_cap) {
+        // earlier calls may still read the old buffers
+        MV_CUDA(c, cudaStreamSynchronize(s));
+        cudaFree(c->d_pb);
+        cudaFree(c->d_vfb);
+        cudaFree(c->d_visb);
+        c->d_pb = nullptr;
+        c->d_vfb = nullptr;
+        c->d_visb = nullptr;
+        c->batch_cap = 0;
+        MV_CUDA(c, cudaMalloc((void **)&c->d_pb, sizeof(FrameParams) * n_views));
+        MV_CUDA(c, cudaMalloc((void **)&c->d_vfb, sizeof(VolFrame) * (size_t)kMaxVolumes * n_views));
+        MV_CUDA(c, cudaMalloc((void **)&c->d_visb, sizeof(VisList) * n_views));
+        c->batch_cap = n_views;
+    }
+    const int nvol = (int)c->table.size();
+    c->h_pb.resize(n_views);
+    for (int k = 0; k < n_views; ++k) c->h_pb[k] = make_params(c, K, T + 16 * (size_t)k);
+    // the host vector is copied before cudaMemcpyAsync returns (pageable source)
+    MV_CUDA(c, cudaMemcpyAsync(c->d_pb, c->h_pb.data(), sizeof(FrameParams) * n_views, cudaMemcpyHostToDevice, s));
+    if (nvol > 0)
+        for (int k = 0; k < n_views; ++k)
+            MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
+                return launch_frame_setup(c->d_table, nvol, c->h_pb[k], c->d_vfb + (size_t)k * nvol, nullptr, s,
+                                          c->d_visb + k); }));
+    MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
+        return launch_raycast_batch(c->d_table, c->d_vfb, nvol, c->d_pb, n_views, K->width, K->height, depth,
+                                    normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, s,
+                                    nvol > 0 ? c->d_visb : nullptr); }));
+    return end_call(c, s);
 }
 
 mv_status mv_raycast_volume(mv_ctx *c, int32_t id, int32_t first, const mv_intrinsics *K,
@@ -1680,6 +1726,15 @@ mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T
     A.grad_depth = grad_depth;
     A.grad_rgb = grad_rgb;
     A.grad_pose = grad_pose;
+    const size_t need = backward_ctas_per_pose(K->width, K->height) * 6 * (size_t)n_poses;
+    if (need > c->bw_partial_cap) {
+        if (c->d_bw_partial) MV_CUDA(c, cudaFreeAsync(c->d_bw_partial, s));
+        c->d_bw_partial = nullptr;
+        c->bw_partial_cap = 0;
+        MV_CUDA(c, cudaMallocAsync((void **)&c->d_bw_partial, sizeof(float) * need, s));
+        c->bw_partial_cap = need;
+    }
+    A.partial = c->d_bw_partial;
     if (A.nvol > 0)
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BACKWARD, s, [&] { return launch_raycast_backward(A, s); }));
     return end_call(c, s);

@@ -217,6 +217,28 @@ class Mapper:
         del keep
         return out
 
+    def raycast_batch(self, cam, poses, out=None, stream=None) -> dict:
+        """Raycast n views (poses: (n, 4, 4) host) in one launch
+        (mv_raycast_batch); out: maps with a leading view axis, e.g. depth
+        (n, H, W) -- each may be missing; default depth, rgba and vol_id."""
+        import torch
+        P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+        n = P.shape[0]
+        if out is None:
+            dev = torch.device("cuda", self.device)
+            H, W = cam.height, cam.width
+            out = dict(depth=torch.empty((n, H, W), dtype=torch.float32, device=dev),
+                       rgba=torch.empty((n, H, W, 4), dtype=torch.uint8, device=dev),
+                       vol_id=torch.empty((n, H, W), dtype=torch.int32, device=dev))
+        K = intrinsics(cam)
+        px = n * cam.width * cam.height
+        self._check(self._lib.mv_raycast_batch(
+            self._h, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)), n,
+            _dptr(out.get("depth"), torch.float32, px, "depth"), _dptr(out.get("normal"), torch.float32, 3 * px, "normal"),
+            _dptr(out.get("rgba"), torch.uint8, 4 * px, "rgba"), _dptr(out.get("vertex"), torch.float32, 3 * px, "vertex"),
+            _dptr(out.get("vol_id"), torch.int32, px, "vol_id"), _stream(stream)))
+        return out
+
     def frame(self, depth, rgb, cam, T, out=None, stream=None) -> dict:
         """Integrate the frame and raycast the same view, as one CUDA graph."""
         import torch

@@ -82,25 +82,31 @@ def per_pixel_pose_jacobians(m, cam, T, maps, pix, channel=None):
 
 
 def check_pixel_jacobians(g, o, what):
-    """Per pixel: |g - o| <= 1e-3 |o| (6-vectors; FP32 gradient arithmetic at
-    the FP32-refined root against the FP64 exact root, on pixels whose hit is
-    away from cell faces and not grazing)."""
+    """Per pixel: |g - o| <= 1e-3 |o| + 1e-4 median |o| (6-vectors; FP32
+    gradient arithmetic at the FP32-refined root against the FP64 exact root,
+    on pixels whose hit is away from cell faces and not grazing; the second
+    term covers pixels whose Jacobian nearly cancels, e.g. a colour gradient
+    summed from eight corner colours)."""
     err = np.linalg.norm(g - o, axis=-1)
-    lim = 1e-3 * np.linalg.norm(o, axis=-1) + 1e-6
+    on = np.linalg.norm(o, axis=-1)
+    lim = 1e-3 * on + 1e-4 * np.median(on) + 1e-9
     bad = err > lim
     assert not bad.any(), (f"{what}: {bad.sum()} of {len(err)} pixels off; worst relative "
                            f"{(err / np.maximum(np.linalg.norm(o, axis=-1), 1e-30)).max():.3g}")
 
 
-def check_voxel_gradients(gts, ids, o_gF, what, rel=1e-3):
-    """Per voxel: |g - o| <= rel |o| + 1e-5 max |o| over all volumes."""
+def check_voxel_gradients(gts, ids, o_gF, what, rel=1e-3, floor=1e-5):
+    """Per voxel: |g - o| <= rel |o| + floor max |o| over all volumes.  The
+    floor covers the FP32 hit position's error in the small trilinear weights
+    of far corners: about r 2^-24 voxel for coordinates up to r voxels (1e-5
+    of the largest gradient at 64^3, 1e-4 at 256^3)."""
     top = max(np.abs(a).max() for a in o_gF)
     assert top > 0, f"{what}: no TSDF gradient"
     nz = 0
     for k, i in enumerate(ids):
         g = gts[i].cpu().numpy().astype(np.float64)
         o = o_gF[k]
-        bad = np.abs(g - o) > rel * np.abs(o) + 1e-5 * top
+        bad = np.abs(g - o) > rel * np.abs(o) + floor * top
         assert not bad.any(), (f"{what}: volume {i}: {bad.sum()} voxels off, e.g. "
                                f"{[(tuple(int(v) for v in q), g[tuple(q)], o[tuple(q)]) for q in np.argwhere(bad)[:3]]}")
         # every voxel that receives a gradient on one side receives it on the other
@@ -220,8 +226,81 @@ def test_adam_pose_refinement_reduces_pose_error():
         return t, r
 
     t0, r0 = err(T_init)
-    T_fin, losses = diff.refine_poses(m, wl.cam, np.stack(T_init), ref_d, ref_c, steps=50, lr=2e-3)
+    T_fin, losses = diff.refine_poses(m, wl.cam, np.stack(T_init), ref_d, ref_c, steps=50)
     t1, r1 = err(T_fin)
     assert losses[-1] < 0.5 * losses[0]
     assert t1 < 0.5 * t0 and r1 < 0.5 * r0, (t0, t1, r0, r1)
+    m.close()
+
+
+def test_full_size_tiles_gradients_sampled():
+    """The differentiable-raycast workload at full size: 8 x 256^3 tiles at
+    2 mm, 640x480, two poses perturbed by N(0, 2 cm) / N(0, 1 deg).  On a
+    sample of pixels (every 13th): per-pixel pose Jacobians of depth and
+    colour and per-voxel TSDF gradients against the FP64 oracle, and the
+    pose gradient against FP32 central differences."""
+    import torch
+    wl = synth.room_tiles(frames=30)
+    m, ids = prefilled(wl, 30)
+    random_colours(m, ids, 13)
+    ovs = [oracle_volume_from_gpu(m, i, v) for i, v in zip(ids, wl.volumes)]
+    cam = wl.cam
+    H, W = cam.height, cam.width
+    pix = np.arange(0, H * W, 13)
+    sel = np.zeros((H, W), bool)
+    sel.reshape(-1)[pix] = True
+    T_init = synth.perturb_poses([wl.poses[8], wl.poses[22]], seed=6)
+    rng = np.random.default_rng(21)
+    maps = m.alloc_maps(cam)
+    for T in T_init:
+        g0 = oracle.raycast_grad(ovs, cam, T, ids=ids, want_tsdf=False, pixels=pix)
+        o, d = synth.pixel_rays(cam, T)
+        dn = d / np.linalg.norm(d, axis=-1, keepdims=True)
+        raw = oracle.raycast(ovs, cam, T, ids=ids, pixels=pix)
+        safe = sel & (g0["excluded"] == 0) & (raw["vol"] >= 0)
+        safe &= np.abs(np.sum(raw["normal"] * dn, -1)) > 0.05
+        vol_of = {i: v for i, v in zip(ids, ovs)}
+        for y, x in zip(*np.nonzero(safe)):
+            v = vol_of[raw["vol"][y, x]]
+            q = (o + g0["depth"][y, x] * d[y, x]) / v.s - np.array(v.h)
+            fr = q - np.floor(q)
+            safe[y, x] = np.all((fr > 0.02) & (fr < 0.98))
+        assert safe.sum() > 0.3 * sel.sum()
+        m.raycast(cam, T, out=maps)
+        cand = np.argwhere(safe)
+        pp = [tuple(p) for p in cand[rng.choice(len(cand), size=96, replace=False)]]
+        g = per_pixel_pose_jacobians(m, cam, T, maps, pp)
+        check_pixel_jacobians(g, np.stack([g0["jac_tau"][p] for p in pp]), "dtau/dxi")
+        for ch in range(3):
+            g = per_pixel_pose_jacobians(m, cam, T, maps, pp, channel=ch)
+            check_pixel_jacobians(g, np.stack([g0["jac_rgb"][p][ch] for p in pp]), f"dC{ch}/dxi")
+        # FP32 central differences of sum_p w_p depth_p on the GPU forward;
+        # pixels whose hit jumps to another surface under a perturbation of
+        # 1e-4 (a silhouette nearer than the step) are left out of the sum
+        h = 1e-4
+        w = np.where(safe, rng.uniform(0.5, 1.5, size=safe.shape), 0.0)
+        pm = []
+        for k in range(6):
+            e = np.zeros(6)
+            e[k] = h
+            dp = gpu_maps(m.raycast(cam, oracle.se3_exp(e) @ T))["depth"].astype(np.float64)
+            dm = gpu_maps(m.raycast(cam, oracle.se3_exp(-e) @ T))["depth"].astype(np.float64)
+            pm.append((dp, dm))
+            w = np.where((dp > 0) & (dm > 0) & (np.abs(dp - dm) < 2e-3), w, 0.0)
+        assert (w > 0).sum() > 0.9 * safe.sum()
+        fd = np.array([np.sum(w * (dp - dm)) / (2 * h) for dp, dm in pm])
+        m.raycast(cam, T, out=maps)
+        # TSDF gradients of the depth path, per voxel, over all 8 volumes
+        ob = oracle.raycast_grad(ovs, cam, T, grad_depth=w, ids=ids, pixels=np.flatnonzero(w > 0))
+        gp = torch.zeros((1, 6), dtype=torch.float32, device="cuda")
+        gts = {i: torch.zeros(tuple(v.r[::-1]), dtype=torch.float32, device="cuda")
+               for i, v in zip(ids, wl.volumes)}
+        m.raycast_backward(cam, T[None], maps["depth"][None].contiguous(), maps["vol_id"][None].contiguous(),
+                           dev(w.astype(np.float32))[None].contiguous(), None, gp, gts)
+        nz = check_voxel_gradients(gts, ids, ob["grad_F"], "depth path", floor=1e-4)
+        assert nz > 10000
+        an = gp.cpu().numpy()[0].astype(np.float64)
+        assert np.linalg.norm(an - ob["grad_pose"]) <= 1e-3 * np.linalg.norm(ob["grad_pose"])
+        assert np.linalg.norm(an - fd) <= 5e-2 * np.linalg.norm(fd), (an, fd)
+        del gts
     m.close()

@@ -322,14 +322,15 @@ def test_errors_leave_context_usable():
     m.close()
 
 
-def test_full_size_512_sampled_parity():
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_full_size_512_sampled_parity(fmt):
     """The 512^3 / 640x480 room workload in the benchmark's launch
-    configuration: lockstep parity of frame 4 on 2 M sampled voxels and the
-    raycast on every 11th pixel."""
+    configuration, in each storage format: lockstep parity of frame 4 on 2 M
+    sampled voxels and the raycast on every 11th pixel."""
     wl = synth.room_512(frames=5)
     (vs,) = wl.volumes
     m = Mapper()
-    vid = m.add_volume(vs.h, vs.r, vs.s)
+    vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
     for i in range(4):
         d, c = wl.frame(i)
         m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
@@ -345,7 +346,7 @@ def test_full_size_512_sampled_parity():
     sel = np.zeros(before.F.shape, bool)
     sel.reshape(-1)[idx] = True
     fl = np.where(sel, flags, 255)  # unsampled voxels are excluded via the flag
-    check_lockstep(before, F, W, rgba, fl)
+    check_lockstep(before, F, W, rgba, fl, fmt=fmt)
     after = oracle_volume_from_gpu(m, vid, vs)
     T = wl.poses[4]
     pix = np.arange(0, wl.cam.width * wl.cam.height, 11)
@@ -468,6 +469,92 @@ def test_uneven_volumes_batched_equals_per_volume_and_oracle(levels):
     compare_raycast(g, o, wl.cam, T, pitch, require_hits=0.05)
     a.close()
     b.close()
+
+
+def read_observed_crop(m, vid, spec, margin=2):
+    """A volume's state cropped to the box of its observed voxels widened by
+    `margin` voxels (clipped to the volume), as an oracle volume with the
+    lattice offset moved to the box (voxel positions unchanged), plus the box
+    (lo, hi) per axis x, y, z; None if nothing is observed."""
+    F, W, rgba = m.read_decoded(vid)
+    obs = W > 0
+    if not obs.any():
+        return None
+    lo, hi = [], []
+    for ax in (2, 1, 0):  # x, y, z = array axes 2, 1, 0
+        other = tuple(a for a in range(3) if a != ax)
+        idx = np.flatnonzero(obs.any(axis=other))
+        lo.append(max(0, int(idx[0]) - margin))
+        hi.append(min(obs.shape[ax], int(idx[-1]) + 1 + margin))
+    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    v = oracle.Volume(tuple(int(spec.h[a] + lo[a]) for a in range(3)), tuple(hi[a] - lo[a] for a in range(3)),
+                      float(spec.s), F[sl].copy(), W[sl].copy(), rgba[sl].copy())
+    return v, (lo, hi)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_full_size_uneven_volumes_sampled_parity(fmt):
+    """The 64 uneven volumes at full size (edges 128-768, pitches 1-8 mm, 7.3 G
+    voxels) at 640x480, through the batched frame graph in each storage
+    format: lockstep parity of frame 5 on up to 2 M sampled voxels of every
+    observed volume, and the merged raycast of that frame on every 7th
+    pixel.  The oracle sees each observed volume cropped to its observed box
+    widened by 2 voxels: samples outside lie in cells with an unobserved
+    corner (invalid, so they cannot form a bracket) and the voxels there are
+    all unobserved, so the crop changes no hit; volumes with nothing
+    observed cannot hold a hit and are left out."""
+    wl = synth.uneven_volumes(frames=6)
+    m = Mapper()
+    ids = [m.add_volume(v.h, v.r, v.s, fmt) for v in wl.volumes]
+    k = 5
+    for i in range(k):
+        d, c = wl.frame(i)
+        m.frame(dev(d), dev(c), wl.cam, wl.poses[i])
+    m.synchronize()
+    # volumes with an observed brick after frame k (from the brick flags)
+    d, c = wl.frame(k)
+    T = wl.poses[k]
+    before = {}
+    for vid, v in zip(ids, wl.volumes):
+        fl = m.read_brick_flags(vid)
+        if not np.all(fl & 2):
+            before[vid] = m.read_decoded(vid)
+    maps = gpu_maps(m.frame(dev(d), dev(c), wl.cam, T))
+    rng = np.random.default_rng(7)
+    crops, checked = [], 0
+    for vid, v in zip(ids, wl.volumes):
+        got = read_observed_crop(m, vid, v)
+        if got is None:
+            continue
+        after, (lo, hi) = got
+        crops.append((vid, after))
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        if vid in before:
+            F0, W0, c0 = (a[sl] for a in before.pop(vid))
+        else:  # first observed in frame k
+            F0, W0 = np.zeros(after.F.shape), np.zeros(after.W.shape)
+            c0 = np.zeros(after.rgba.shape, np.uint8)
+        prior = oracle.Volume(after.h, after.r, after.s, F0.copy(), W0.copy(), c0.copy())
+        seen = np.flatnonzero(after.W.reshape(-1) > 0)
+        n = min(1_000_000, seen.size)
+        idx = np.unique(np.concatenate([rng.choice(seen, n, replace=False),
+                                        rng.integers(0, prior.F.size, n)]))
+        _, flags = oracle.integrate_voxels(prior, idx, d, c, wl.cam, T, ocfg(m.config))
+        sel = np.zeros(prior.F.shape, bool)
+        sel.reshape(-1)[idx] = True
+        check_lockstep(prior, after.F, after.W, after.rgba, np.where(sel, flags, 255), fmt=fmt)
+        checked += int(sel.sum())
+    assert len(crops) >= 2 and checked > 1_000_000
+    pix = np.arange(0, wl.cam.width * wl.cam.height, 2)
+    o = oracle.raycast([v for _, v in crops], wl.cam, T, ocfg(m.config), ids=[i for i, _ in crops], pixels=pix)
+    mask = np.zeros((wl.cam.height, wl.cam.width), bool)
+    mask.reshape(-1)[pix] = True
+    pitch = min(v.s for _, v in crops)
+    # the observed volumes cover a small part of this early view (about 1.4 %
+    # of the pixels hit): every 2nd pixel gives a few thousand hits
+    res = compare_raycast(maps, o, wl.cam, T, pitch, mask=mask, require_hits=0.01)
+    assert res["hits"] > 1000
+    m.close()
 
 
 def test_two_level_list_at_scale_equals_one_level():
@@ -605,3 +692,37 @@ def test_reserved_pinned_buffers_roundtrip():
             np.testing.assert_array_equal(a, b)
     m.reserve_host(vs.r, "f32", 0)
     m.close()
+
+
+def test_raycast_batch_equals_single_views():
+    """mv_raycast_batch (every view in one launch) gives each view the maps of
+    mv_raycast at that pose, bit for bit, on uneven volumes (view lists,
+    merge across volumes) and on an empty context."""
+    import torch
+    wl = synth.uneven_volumes(n_volumes=12, frames=6, edges=(16, 24, 40), pitch_mm=(15.0, 40.0),
+                              half_extent=1.6, height_m=2.2, width=160, height=120)
+    m = Mapper()
+    for v in wl.volumes:
+        m.add_volume(v.h, v.r, v.s)
+    for i in range(4):
+        d, c = wl.frame(i)
+        m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+    poses = np.stack([wl.poses[i] for i in (0, 2, 3, 5, 1)])
+    n, H, W = len(poses), wl.cam.height, wl.cam.width
+    out = dict(depth=torch.empty((n, H, W), dtype=torch.float32, device="cuda"),
+               normal=torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda"),
+               rgba=torch.empty((n, H, W, 4), dtype=torch.uint8, device="cuda"),
+               vertex=torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda"),
+               vol_id=torch.empty((n, H, W), dtype=torch.int32, device="cuda"))
+    m.raycast_batch(wl.cam, poses, out=out)
+    got = gpu_maps(out)
+    for k in range(n):
+        ref = gpu_maps(m.raycast(wl.cam, poses[k]))
+        for key in ("depth", "normal", "rgba", "vertex", "vol_id"):
+            np.testing.assert_array_equal(got[key][k], ref[key], err_msg=f"view {k} {key}")
+    assert (got["depth"] > 0).mean() > 0.05
+    m.close()
+    e = Mapper()
+    emp = e.raycast_batch(wl.cam, poses[:2])
+    assert np.all(host(emp["depth"]) == 0) and np.all(host(emp["vol_id"]) == -1)
+    e.close()
