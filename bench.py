@@ -44,6 +44,14 @@ WORKLOAD = "room 512^3 single volume, 640x480 depth+RGB, integrate + raycast per
 N_FRAMES_MAX = 300
 
 
+def CONFIG_OF(world):
+    """The workload named in every line of this benchmark (both arms)."""
+    return {"workload": WORKLOAD, "volume": "512^3 F32 TSDF + F32 weight + RGBA8, 5.86 mm",
+            "image": "640x480", "trunc_voxels": 4, "w_max": 128,
+            "l2": "inputs larger than L2 (1.61 GB volume per rank)",
+            "parallelism": f"independent mapping job per GPU x{world}"}
+
+
 def _render(i):
     wl = synth.room_512(frames=N_FRAMES_MAX)
     return wl.frame(i)
@@ -238,7 +246,21 @@ def integrate_bytes_per_voxel(fmt):
     return {"f32": 16, "f16": 8, "i16": 8}[fmt]
 
 
-def kernel_summary(res, fmt, cam, steps):
+RAY_OUT_BYTES = 36  # per pixel: depth 4 + normal 12 + rgba 4 + vertex 12 + volume id 4
+
+
+def raycast_bytes(cam, footprint, fmt):
+    """Algorithmic bytes of one raycast launch: its outputs, plus -- when the
+    oracle's count of the view's footprint is given (distinct voxels whose
+    TSDF/weight a dense march reads, distinct voxels whose colour the hits
+    read) -- those voxel bytes."""
+    b = RAY_OUT_BYTES * cam.width * cam.height
+    if footprint is not None:
+        b += footprint[0] * integrate_bytes_per_voxel(fmt) // 2 + footprint[1] * 4
+    return b
+
+
+def kernel_summary(res, fmt, cam, steps, footprint=None):
     """Per-kernel average launch time and algorithmic bytes per launch."""
     tm = res["timings"]
     H, W = cam.height, cam.width
@@ -260,8 +282,9 @@ def kernel_summary(res, fmt, cam, steps):
             e["algorithmic_bytes"] = b_int
             e["achieved_gbs"] = b_int / (avg_ms * 1e-3) / 1e9
         if name == "raycast":
-            b_ray = 36 * H * W  # outputs: depth 4 + normal 12 + rgba 4 + vertex 12 + id 4
+            b_ray = raycast_bytes(cam, footprint, fmt)
             e["algorithmic_bytes"] = b_ray
+            e["output_bytes"] = RAY_OUT_BYTES * H * W
             e["achieved_gbs"] = b_ray / (avg_ms * 1e-3) / 1e9
         out[name] = e
     tot = sum(v["avg_ms"] * v["launches"] for v in out.values())
@@ -270,46 +293,139 @@ def kernel_summary(res, fmt, cam, steps):
     return out
 
 
-def cpu_baseline_sample(wl, frames, m, vid, first):
-    """The FP64 oracle as it stands on a bounded sample of one step: frame
-    `first` integrated into 8 evenly spread z-slabs of 8 voxels (1/8 of the
-    volume, starting from the GPU's state) and the raycast of every 8th
-    pixel.  Returns (updated voxels/s, seconds, sample description, cores)."""
+def oracle_run(wl, frames, timed, footprint_at=(), one_core_at=None):
+    """The FP64 oracle as it stands on whole frames of the room workload, from
+    its own state: a volume that starts empty integrates frames 0, 1, ... in
+    order, every voxel of the 512^3 volume each frame.  Each frame in `timed`
+    is timed whole: its integration plus the raycast of every pixel at its
+    pose (std time.perf_counter around the two oracle calls).  The frame
+    `one_core_at` is timed the same way on one thread.  At each frame of
+    `footprint_at` the oracle also counts the voxels a dense march of that
+    view reads (the raycast's compulsory bytes).  Returns a dict; `volume` is
+    the oracle's state after the last frame processed."""
+    import oracle
+    oracle.build()
+    (vs,) = wl.volumes
+    vol = oracle.Volume(vs.h, vs.r, vs.s)
+    cfg = oracle.Config()
+    timed = set(timed)
+    last = max([*timed, *footprint_at, -1 if one_core_at is None else one_core_at])
+    cores = oracle.threads()
+    upd, secs, one, fps = 0, 0.0, None, []
+    for i in range(last + 1):
+        d, c = frames[i]
+        T = wl.poses[i % N_FRAMES_MAX]
+        if i == one_core_at:
+            oracle.set_threads(1)
+        t0 = time.perf_counter()
+        cnt, _ = oracle.integrate(vol, d, c, wl.cam, T, cfg)
+        if i in timed or i == one_core_at:
+            oracle.raycast([vol], wl.cam, T, cfg)
+            dt = time.perf_counter() - t0
+            if i == one_core_at:
+                one = (int(cnt[0]), dt)
+                oracle.set_threads(cores)
+            else:
+                upd += int(cnt[0])
+                secs += dt
+        if i in footprint_at:
+            fps.append(oracle.raycast_footprint([vol], wl.cam, T, cfg)[0])
+    return {"updated": upd, "seconds": secs, "frames": len(timed), "cores": cores, "one_core": one,
+            "footprints": fps, "volume": vol, "last_frame": last}
+
+
+ORACLE_SAMPLE = ("whole frames of the same workload: each frame integrated into every voxel of the "
+                 "512^3 volume and raycast at every pixel of 640x480, from the oracle's own state "
+                 "(frames integrated in order from an empty volume); FP64 C oracle, OpenMP")
+
+
+def accuracy_vs_oracle(torch, Mapper, Config, wl, frames, k, dev_depth, dev_rgb, own):
+    """Error of each storage format against the FP64 oracle at frame k of the
+    room workload (k = the oracle's last frame):
+      lockstep: the oracle applies frame k to the format's own GPU state after
+        frame k - 1; |dF| over the voxels that frame updated, excluding voxels
+        whose FP64 decisions lie within the oracle's margins (counted);
+      raycast: the oracle raycasts the format's GPU state after frame k at
+        pose k; |d tau| along the ray in voxels over pixels hit on both sides
+        and not flagged, plus hit/miss agreement;
+      drift: the format's GPU state after frames 0..k against the oracle's own
+        independent FP64 state (`own`), and the raycasts of the two states.
+    """
     import oracle
     (vs,) = wl.volumes
-    F, W, rgba = m.read_decoded(vid)
-    d, c = frames[first]
-    T = wl.poses[first % N_FRAMES_MAX]
+    cam = wl.cam
     cfg = oracle.Config()
-    upd = 0
-    t0 = time.perf_counter()
-    nz = vs.r[2]
-    for k in range(8):
-        z0 = k * (nz // 8)
-        sl = slice(z0, z0 + 8)
-        sub = oracle.Volume((vs.h[0], vs.h[1], vs.h[2] + z0), (vs.r[0], vs.r[1], 8), vs.s,
-                            F[sl].copy(), W[sl].copy(), rgba[sl].copy())
-        cnt, _ = oracle.integrate(sub, d, c, wl.cam, T, cfg)
-        upd += int(cnt[0])
-    t_int = time.perf_counter() - t0
-    full = oracle.Volume(vs.h, vs.r, vs.s, F, W, rgba)
-    pix = np.arange(0, wl.cam.width * wl.cam.height, 8)
-    t0 = time.perf_counter()
-    oracle.raycast([full], wl.cam, T, cfg, ids=[vid], pixels=pix)
-    t_ray = time.perf_counter() - t0
-    cores = oracle.threads()
-    sample = ("one step: frame integrated into 8 z-slabs x 8 voxels (1/8 of the 512^3 volume) + "
-              "raycast of every 8th pixel (1/8 of 640x480); FP64 C oracle, OpenMP")
-    return upd / (t_int + t_ray), t_int + t_ray, sample, cores
+    T = wl.poses[k % N_FRAMES_MAX]
+    d_k, c_k = frames[k]
+    xs = (np.arange(cam.width) - cam.cx) / cam.fx
+    ys = (np.arange(cam.height) - cam.cy) / cam.fy
+    dn = np.sqrt(xs[None, :] ** 2 + ys[:, None] ** 2 + 1.0)
+    own_maps = oracle.raycast([own], cam, T, cfg)
+
+    def q(a, p):
+        return float(np.percentile(a, p)) if a.size else None
+
+    def depth_err(g, o):
+        hard = (o["flags"] & (oracle.RF_SIGN | oracle.RF_CELL | oracle.RF_RANGE | oracle.RF_TIE)) != 0
+        gh, oh = g > 0, o["depth"] > 0
+        both = gh & oh & ~hard
+        e = np.abs(g.astype(np.float64) - o["depth"]) * dn / vs.s
+        return {"pixels_compared": int((~hard).sum()), "hit_agreement": float((gh == oh)[~hard].mean()),
+                "max_vox": float(e[both].max()) if both.any() else None, "p99_vox": q(e[both], 99),
+                "p50_vox": q(e[both], 50)}
+
+    out = {"frame": k, "tolerance_tsdf_f32": 1e-4, "tolerance_depth_vox": 0.1}
+    for fmt in ("f32", "f16", "i16"):
+        m = Mapper(Config())
+        vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
+        for i in range(k):
+            m.integrate(dev_depth[i], dev_rgb[i], cam, wl.poses[i % N_FRAMES_MAX])
+        F0, W0, c0 = m.read_decoded(vid)
+        W_prev = W0.copy()  # the oracle updates `before` (which shares F0, W0) in place
+        before = oracle.Volume(vs.h, vs.r, vs.s, F0, W0, c0)
+        del c0
+        _, flags = oracle.integrate(before, d_k, c_k, cam, T, cfg, want_flags=True)
+        m.integrate(dev_depth[k], dev_rgb[k], cam, T)
+        F1, W1, c1 = m.read_decoded(vid)
+        upd = W1 != W_prev
+        dec = (flags & (oracle.IF_Z | oracle.IF_PIX | oracle.IF_GATE)) != 0
+        ok = upd & ~dec
+        dF = np.abs(F1 - before.F)[ok]
+        weights_equal = bool(np.array_equal(W1[ok], before.W[ok]))
+        del before, F0, W0, W_prev
+        lock = {"voxels": int(ok.sum()), "flagged_fraction": float((upd & dec).sum() / max(upd.sum(), 1)),
+                "max": float(dF.max()) if dF.size else None, "p99": q(dF, 99), "p50": q(dF, 50),
+                "weights_equal": weights_equal}
+        del dF
+        g = m.raycast(cam, T)
+        gd = g["depth"].cpu().numpy()
+        after = oracle.Volume(vs.h, vs.r, vs.s, F1, W1, c1)
+        o = oracle.raycast([after], cam, T, cfg)
+        ray = depth_err(gd, o)
+        del after, o
+        both = (W1 > 0) & (own.W > 0)
+        dd = np.abs(F1 - own.F)[both]
+        drift = {"voxels_observed_both": int(both.sum()),
+                 "observed_agreement": float(((W1 > 0) == (own.W > 0)).mean()),
+                 "weight_agreement": float((W1 == own.W)[both].mean()),
+                 "tsdf_p50": q(dd, 50), "tsdf_p99": q(dd, 99), "tsdf_max": float(dd.max()) if dd.size else None,
+                 "raycast": depth_err(gd, own_maps)}
+        del dd, both, F1, W1, c1
+        out[fmt] = {"lockstep_tsdf": lock, "raycast_depth": ray, "drift_vs_independent_oracle": drift}
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    return out
 
 
 def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
-    """Same metric through the public API with host buffers: every step copies
-    its frame from pinned host memory, integrates and raycasts it (mv_frame),
-    and reads depth / normal / colour back to pinned host memory, where the
-    host reads them.  Steps are pipelined over three streams with two buffer
-    sets: the upload of step i+1 and the read-back of step i-1 overlap the
-    kernels of step i."""
+    """Same metric through the library's host-buffer call (mv_frame_host):
+    every step hands the library its depth + RGB frame in pinned host memory
+    and receives depth / normal / colour maps in pinned host memory; the
+    uploads, the frame's kernels and the downloads run on the library's own
+    streams, pipelined over its two device buffer sets, and the host reads
+    each step's maps after waiting for its ticket (one frame late, so that
+    the next frame is already queued)."""
     (vs,) = wl.volumes
     cam = wl.cam
     m = Mapper(Config())
@@ -317,56 +433,36 @@ def e2e_run(torch, Mapper, Config, wl, frames, steps, warmup):
     H, W = cam.height, cam.width
     hd = [torch.from_numpy(f[0]).pin_memory() for f in frames]
     hc = [torch.from_numpy(f[1]).pin_memory() for f in frames]
-    dd = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(2)]
-    dc = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    maps = [m.alloc_maps(cam, vertex=False) for _ in range(2)]
-    out = [(torch.empty((H, W), dtype=torch.float32).pin_memory(),
-            torch.empty((H, W, 3), dtype=torch.float32).pin_memory(),
-            torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()) for _ in range(2)]
-    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    ev = lambda: torch.cuda.Event()  # noqa: E731
-    loaded, used, ran, read = ([ev() for _ in range(2)] for _ in range(4))
-    seen = [False, False]
+    out = [m.alloc_host_maps(cam) for _ in range(3)]
     checksum = 0.0
+    pending = []
 
     def step(i):
         nonlocal checksum
-        b = i % 2
-        if seen[b]:
-            read[b].synchronize()        # the host has step i-2's result
-            checksum += float(out[b][0][0, 0])
-        with torch.cuda.stream(s_in):
-            if seen[b]:
-                s_in.wait_event(used[b])  # step i-2 is done with this input buffer
-            dd[b].copy_(hd[i], non_blocking=True)
-            dc[b].copy_(hc[i], non_blocking=True)
-            loaded[b].record(s_in)
-        s_run.wait_event(loaded[b])
-        if seen[b]:
-            s_run.wait_event(read[b])     # the maps of step i-2 were read back
-        m.frame(dd[b], dc[b], cam, wl.poses[i % N_FRAMES_MAX], out=maps[b], stream=s_run)
-        used[b].record(s_run)
-        ran[b].record(s_run)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ran[b])
-            out[b][0].copy_(maps[b]["depth"], non_blocking=True)
-            out[b][1].copy_(maps[b]["normal"], non_blocking=True)
-            out[b][2].copy_(maps[b]["rgba"], non_blocking=True)
-            read[b].record(s_out)
-        seen[b] = True
+        pending.append((m.frame_host(hd[i], hc[i], cam, wl.poses[i % N_FRAMES_MAX], out[i % 3]), i))
+        if len(pending) > 1:
+            t, j = pending.pop(0)
+            m.frame_host_wait(t)
+            checksum += float(out[j % 3]["depth"][H // 2, W // 2])
+
+    def drain():
+        nonlocal checksum
+        while pending:
+            t, j = pending.pop(0)
+            m.frame_host_wait(t)
+            checksum += float(out[j % 3]["depth"][H // 2, W // 2])
 
     for i in range(warmup):
         step(i)
-    torch.cuda.synchronize()
+    drain()
+    m.synchronize()
     m.stats(reset=True)
     barrier(torch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(steps):
         step(warmup + k)
-    for b in range(2):
-        read[b].synchronize()
-    torch.cuda.synchronize()
+    drain()
     dt = time.perf_counter() - t0
     barrier(torch)
     st = m.stats()
@@ -442,7 +538,10 @@ def bench_uneven(torch, Mapper, Config, frames, steps, warmup):
 def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
     """Differentiable raycast: 8 x 256^3 tiles (2 mm) prefilled from the given
     frames; 16 poses perturbed by N(0, 2 cm) / N(0, 1 deg); forward +
-    backward throughput and 50 Adam steps of pose refinement."""
+    backward through the autograd Function (all views in one raycast launch
+    and one backward launch, the tangent-space solve on the GPU), and 50 Adam
+    steps of pose refinement (each step one forward, the loss, one backward
+    and the update: refine_ms_per_step)."""
     from paper_1511_07106_b300 import diff
     wl = synth.room_tiles(frames=N_FRAMES_MAX)
     cam = wl.cam
@@ -484,8 +583,13 @@ def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
         return t, r
 
     curve = []
-    T_fin, losses = diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=adam_steps, lr=2e-3,
+    diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=2)  # first-call set-up outside the timing
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T_fin, losses = diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=adam_steps,
                                       callback=lambda it, Ts, l: curve.append(err(Ts)) if it % 10 == 9 else None)
+    torch.cuda.synchronize()
+    refine_ms_per_step = (time.perf_counter() - t0) * 1e3 / adam_steps
     m.close()
     rays = n_poses * cam.width * cam.height
     return {"workload": wl.name, "poses": n_poses, "prefill_frames": len(frames),
@@ -493,7 +597,8 @@ def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
             "backward_kernel_ms": tm["backward"][1] / max(tm["backward"][2], 1),
             "raycast_kernel_ms": tm["raycast"][1] / max(tm["raycast"][2], 1),
             "pose_error_m_deg_initial": err(T_init), "pose_error_m_deg_final": err(T_fin),
-            "pose_error_every_10_steps": curve, "loss_initial": losses[0], "loss_final": losses[-1]}
+            "pose_error_every_10_steps": curve, "loss_initial": losses[0], "loss_final": losses[-1],
+            "refine_ms_per_step": refine_ms_per_step}
 
 
 def bench_swap(torch, Mapper, Config, frames, steps):
@@ -729,46 +834,25 @@ def bench_track(torch, Mapper, Config, frames, n_map=20, n_track=10, iterations=
 
 
 def main_reference(args, rank):
-    """Reference arm: the FP64 CPU oracle, as it stands, on bounded samples."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on the same workload
+    and steps -- whole frames (integration into every voxel of the 512^3
+    volume + the raycast of every pixel) from its own state, the same
+    measurement as the native arm's cpu_baseline.  Under torchrun only rank 0
+    runs it."""
     if rank != 0:
         return
     wl = synth.room_512(frames=N_FRAMES_MAX)
     n = args.warmup + args.steps
     frames = make_frames(n, min(16, os.cpu_count() or 1))
-    import oracle
-    oracle.build()
-    (vs,) = wl.volumes
-    vol = oracle.Volume(vs.h, vs.r, vs.s)
-    cfg = oracle.Config()
-    nz = vs.r[2]
-    # each step integrates its frame into one 8-voxel z-slab (1/64 of the
-    # volume, cycling through the volume) and raycasts every 64th pixel
-    upd_total, t_total = 0, 0.0
-    for k in range(n):
-        d, c = frames[k]
-        T = wl.poses[k % N_FRAMES_MAX]
-        z0 = ((k * 7) % 64) * (nz // 64)
-        sl = slice(z0, z0 + 8)
-        sub = oracle.Volume((vs.h[0], vs.h[1], vs.h[2] + z0), (vs.r[0], vs.r[1], 8), vs.s,
-                            vol.F[sl], vol.W[sl], vol.rgba[sl])
-        t0 = time.perf_counter()
-        cnt, _ = oracle.integrate(sub, d, c, wl.cam, T, cfg)
-        vol.F[sl], vol.W[sl], vol.rgba[sl] = sub.F, sub.W, sub.rgba
-        oracle.raycast([vol], wl.cam, T, cfg, pixels=np.arange(k % 64, wl.cam.width * wl.cam.height, 64))
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            upd_total += int(cnt[0])
-            t_total += dt
-    value = upd_total / t_total if t_total > 0 else 0.0
-    cores = oracle.threads()
-    sample = ("per step: the frame integrated into one 8-voxel z-slab (1/64 of the 512^3 volume) and "
-              "every 64th pixel raycast; FP64 C oracle, OpenMP")
+    orc = oracle_run(wl, frames, timed=range(args.warmup, n))
+    value = orc["updated"] / orc["seconds"] if orc["seconds"] > 0 else 0.0
+    sample = f"{orc['frames']} {ORACLE_SAMPLE}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_total / max(args.steps, 1), "higher_is_better": True,
+            "ms_per_step": 1e3 * orc["seconds"] / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "config": CONFIG_OF(args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc["cores"], "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -787,6 +871,8 @@ def main():
                     help="fixed raycast tile and integration CTAs per SM (e.g. 0,8) instead of autotuning")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the uneven-volume, differentiable and swap measurements")
+    ap.add_argument("--extras", default="uneven,diff,swap,streamed,placement,resolution,tracking",
+                    help="comma-separated subset of the extra measurements to run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -801,9 +887,12 @@ def main():
     procs = max(1, min(16, (os.cpu_count() or 2) // max(world, 1)))
     frames = make_frames(n, procs)  # before any CUDA call
     extra_steps = 20
-    if not args.no_extra:
+    extras = set() if args.no_extra else set(args.extras.split(","))
+    if "uneven" in extras:
         uneven_frames = _gen(_render_uneven, range(args.warmup + extra_steps), procs)
+    if "diff" in extras:
         tile_frames = _gen(_render_tiles, range(100), procs)
+    if "placement" in extras:
         placement_frames = _gen(_render_placement, range(PLACEMENT_FRAMES), procs)
 
     import torch
@@ -828,8 +917,23 @@ def main():
                         dev_depth, dev_rgb, clocks=clocks, tuning=args.tuning)
     ms_max = allreduce_max(torch, res["ms"])
     value = weak_scaling_value(torch, res["stats"]["updated"], res["ms"])
-    kern = kernel_summary(res, "f32", cam, args.steps)
     peak, peak_kind = measured_peaks()
+    # kernels of the graph timed region (frame_graph counts graph launches, not kernels)
+    launches = sum(v[0] for k, v in res["graph_timings"].items() if k != "frame_graph")
+    m = res["mapper"]
+
+    # the FP64 oracle on the host cores (rank 0 of a 1-GPU run): whole frames
+    # timed, and the footprint of the raycast's views in the per-kernel pass
+    orc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        first_k = args.warmup + args.steps  # the per-kernel (eager) pass raycasts these frames
+        fp_at = sorted({first_k + (j * args.steps) // 4 for j in range(4)})
+        orc = oracle_run(wl, frames, timed=range(args.warmup, args.warmup + 3), footprint_at=fp_at,
+                         one_core_at=args.warmup + 3)
+    footprint = None
+    if orc and orc["footprints"]:
+        footprint = tuple(float(np.mean([f[a] for f in orc["footprints"]])) for a in range(2))
+    kern = kernel_summary(res, "f32", cam, args.steps, footprint)
     dom = max(kern, key=lambda k: kern[k]["avg_ms"] * kern[k]["launches"])
     dk = kern[dom]
     tr = traffic_record(dom)
@@ -838,22 +942,31 @@ def main():
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s"}
+    if dom == "raycast":
+        roofline["algorithmic_bytes"] = dk["algorithmic_bytes"]
+        roofline["output_bytes"] = dk["output_bytes"]
+        roofline["footprint_voxels"] = footprint  # (TSDF+weight voxels, colour voxels), oracle-counted
+        roofline["traffic_frac"] = (tr["dram_bytes_per_launch"] / (dk["avg_ms"] * 1e-3) / 1e9 / peak
+                                    if tr else None)
     ik = kern.get("integrate", {})
     tri = traffic_record("integrate")
     integrate_roofline = {"bound": "hbm", "achieved": ik.get("achieved_gbs"), "peak": peak,
                           "unit": "GB/s", "frac": (ik.get("achieved_gbs") or 0.0) / peak,
                           "traffic": tri["dram_bytes_per_launch"] if tri else None}
-    # kernels of the graph timed region (frame_graph counts graph launches, not kernels)
-    launches = sum(v[0] for k, v in res["graph_timings"].items() if k != "frame_graph")
-    m = res["mapper"]
+    # integrate + raycast of one frame, time-weighted: summed bytes over summed kernel time
+    rk = kern.get("raycast", {})
+    trr = traffic_record("raycast")
+    t_pair = (ik.get("avg_ms", 0.0) + rk.get("avg_ms", 0.0)) * 1e-3
+    frame_hbm = {"kernels": ["integrate", "raycast"], "seconds": t_pair, "peak": peak, "unit": "GB/s",
+                 "algorithmic_frac": ((ik.get("algorithmic_bytes", 0) + rk.get("algorithmic_bytes", 0))
+                                      / t_pair / 1e9 / peak) if t_pair else None,
+                 "dram_frac": ((tri["dram_bytes_per_launch"] + trr["dram_bytes_per_launch"]) / t_pair / 1e9 / peak)
+                 if (t_pair and tri and trr) else None}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "volume": "512^3 F32 TSDF + F32 weight + RGBA8, 5.86 mm",
-                       "image": "640x480", "frames": n, "trunc_voxels": 4, "w_max": 128,
-                       "l2": "inputs larger than L2 (1.61 GB volume per rank)",
-                       "parallelism": f"independent mapping job per GPU x{world}"},
+            "config": CONFIG_OF(world),
             "raycast_mrays_per_s": world * cam.width * cam.height * args.steps / (ms_max * 1e-3) / 1e6,
             "swept_voxel_updates_per_s": world * int(np.prod(vs.r)) * args.steps / (ms_max * 1e-3),
             "updated_voxels_per_frame": res["stats"]["updated"] / args.steps,
@@ -865,8 +978,18 @@ def main():
             "raycast_skips_per_ray": res["stats"]["ray_skips"] / max(res["stats"]["rays"], 1),
             "raycast_hit_fraction": res["stats"]["ray_hits"] / max(res["stats"]["rays"], 1),
             "kernels": kern, "roofline": roofline, "integrate_roofline": integrate_roofline,
+            "frame_hbm": frame_hbm,
             "tuning": {k: res["tuning"][k] for k in ("raycast_tile", "integrate_ctas_per_sm")},
             "gpu_launches": launches, "clocks": res["clocks"]}
+    if orc:
+        v1 = orc["one_core"]
+        line["cpu_baseline"] = {"value": orc["updated"] / orc["seconds"], "unit": UNIT, "cores": orc["cores"],
+                                "kind": "oracle", "sample": f"{orc['frames']} {ORACLE_SAMPLE}",
+                                "seconds": orc["seconds"], "ms_per_frame": 1e3 * orc["seconds"] / orc["frames"],
+                                "one_core_value": v1[0] / v1[1], "one_core_ms_per_frame": 1e3 * v1[1]}
+        line["accuracy"] = accuracy_vs_oracle(torch, Mapper, Config, wl, frames, orc["last_frame"],
+                                              dev_depth, dev_rgb, orc["volume"])
+        orc = None
 
     if not args.no_variants:
         variants = {}
@@ -889,25 +1012,23 @@ def main():
         line["e2e"] = {"value": allreduce_sum(torch, upd) / dt_max, "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        v, secs, sample, cores = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
-        oracle.set_threads(1)
-        v1, secs1, _, _ = cpu_baseline_sample(wl, frames, m, res["vid"], args.warmup)
-        oracle.set_threads(cores)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample, "seconds": secs, "one_core_value": v1,
-                                "one_core_seconds": secs1}
-    if not args.no_extra:
+    if extras:
         m.close()
         torch.cuda.empty_cache()
-        line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup)
-        line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
-        line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
-        line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
-        line["placement"] = bench_placement(torch, Mapper, Config, placement_frames)
-        line["resolution"] = bench_resolution(torch, Mapper, Config, frames)
-        line["tracking"] = bench_track(torch, Mapper, Config, frames)
+        if "uneven" in extras:
+            line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup)
+        if "diff" in extras:
+            line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
+        if "swap" in extras:
+            line["swap"] = bench_swap(torch, Mapper, Config, frames[:10], 50)
+        if "streamed" in extras:
+            line["streamed"] = bench_streamed(torch, Mapper, Config, frames)
+        if "placement" in extras:
+            line["placement"] = bench_placement(torch, Mapper, Config, placement_frames)
+        if "resolution" in extras:
+            line["resolution"] = bench_resolution(torch, Mapper, Config, frames)
+        if "tracking" in extras:
+            line["tracking"] = bench_track(torch, Mapper, Config, frames)
         m = None
 
     if m is not None:
