@@ -493,9 +493,60 @@ def _gen(fn, idx, procs):
         return list(ex.map(fn, idx))
 
 
-def bench_uneven(torch, Mapper, Config, frames, steps, warmup):
+def observed_box(m, vid, r, margin=2):
+    """Voxel box (lo, n) over the volume's observed bricks (no EMPTY flag),
+    widened by `margin` voxels and clipped to the volume; None if none."""
+    fl = m.read_brick_flags(vid)
+    obs = (fl & 2) == 0
+    if not obs.any():
+        return None
+    lo, n = [], []
+    for a, ax in enumerate((2, 1, 0)):
+        idx = np.flatnonzero(obs.any(axis=tuple(b for b in range(3) if b != ax)))
+        lo_a = max(0, int(idx[0]) * 8 - margin)
+        lo.append(lo_a)
+        n.append(min(int(r[a]), (int(idx[-1]) + 1) * 8 + margin) - lo_a)
+    return lo, n
+
+
+def uneven_raycast_accuracy(m, ids, wl, maps, T, stride=8):
+    """Raycast depth error of a frame of the uneven volumes against the FP64
+    oracle, which raycasts the same state: each observed volume read over
+    the box of its observed bricks widened by 2 voxels (outside it every
+    sample is invalid, so the box holds every hit); every `stride`-th pixel."""
+    import oracle
+    cam = wl.cam
+    vols, vids = [], []
+    for vid, v in zip(ids, wl.volumes):
+        box = observed_box(m, vid, v.r)
+        if box is None:
+            continue
+        lo, n = box
+        F, W, col = m.read_box_decoded(vid, lo, n)
+        vols.append(oracle.Volume(tuple(int(v.h[a] + lo[a]) for a in range(3)), tuple(n), float(v.s), F, W, col))
+        vids.append(vid)
+    pix = np.arange(0, cam.width * cam.height, stride)
+    o = oracle.raycast(vols, cam, T, oracle.Config(), ids=vids, pixels=pix)
+    g = maps["depth"].cpu().numpy().reshape(-1)[pix].astype(np.float64)
+    gid = maps["vol_id"].cpu().numpy().reshape(-1)[pix]
+    od, fl = o["depth"].reshape(-1)[pix], o["flags"].reshape(-1)[pix]
+    hard = (fl & (oracle.RF_SIGN | oracle.RF_CELL | oracle.RF_RANGE | oracle.RF_TIE)) != 0
+    xs, ys = (pix % cam.width - cam.cx) / cam.fx, (pix // cam.width - cam.cy) / cam.fy
+    dn = np.sqrt(xs ** 2 + ys ** 2 + 1.0)
+    pitch = {vid: v.s for vid, v in zip(ids, wl.volumes)}
+    both = (g > 0) & (od > 0) & ~hard
+    err = np.array([abs(g[i] - od[i]) * dn[i] / pitch[int(gid[i])] for i in np.flatnonzero(both)])
+    return {"pixels_compared": int((~hard).sum()), "hits": int(both.sum()),
+            "hit_agreement": float(((g > 0) == (od > 0))[~hard].mean()),
+            "max_vox": float(err.max()) if err.size else None,
+            "p99_vox": float(np.percentile(err, 99)) if err.size else None,
+            "volumes_read": len(vols)}
+
+
+def bench_uneven(torch, Mapper, Config, frames, steps, warmup, with_oracle=False):
     """64 volumes of uneven size and pitch (about 7.3 G voxels): one batched
-    graph per frame vs the paper's per-volume loop, and storage formats."""
+    graph per frame vs the paper's per-volume loop, and storage formats; with
+    the oracle, the raycast depth error of each format's last frame."""
     wl = synth.uneven_volumes(frames=N_FRAMES_MAX)
     cam = wl.cam
     dd = torch.from_numpy(np.stack([f[0] for f in frames])).cuda()
@@ -528,6 +579,9 @@ def bench_uneven(torch, Mapper, Config, frames, steps, warmup):
         out[key] = {"ms_per_step": ms / steps, "voxel_updates_per_s": st["updated"] / (ms * 1e-3),
                     "mrays_per_s": cam.width * cam.height * steps / (ms * 1e-3) / 1e6,
                     "updated_voxels_per_frame": st["updated"] / steps}
+        if with_oracle and mode == "batched":
+            out[key]["raycast_vs_oracle"] = uneven_raycast_accuracy(m, ids, wl, maps,
+                                                                    wl.poses[warmup + steps - 1])
         m.close()
         del m
         torch.cuda.empty_cache()
@@ -1016,7 +1070,8 @@ def main():
         m.close()
         torch.cuda.empty_cache()
         if "uneven" in extras:
-            line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup)
+            line["uneven_volumes"] = bench_uneven(torch, Mapper, Config, uneven_frames, extra_steps, args.warmup,
+                                                  with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
         if "diff" in extras:
             line["differentiable"] = bench_diff(torch, Mapper, Config, tile_frames)
         if "swap" in extras:

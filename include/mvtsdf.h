@@ -369,6 +369,16 @@ mv_status mv_swap_in(mv_ctx *ctx, int32_t id, void *stream);
  * and swapped-out volumes. */
 mv_status mv_read_volume(mv_ctx *ctx, int32_t id, void *host_fw, uint8_t *host_rgba);
 
+/* Synchronous copy of a box of a volume's voxels to host memory: voxels
+ * lo[a] .. lo[a] + n[a] - 1 along each axis a = x, y, z (0 <= lo[a],
+ * n[a] >= 1, lo[a] + n[a] <= h_r[a]), in the layout of mv_read_volume over the
+ * box (index ((z * n[1]) + y) * n[0] + x).  host_rgba may be NULL.  A
+ * resident volume's box is gathered on the GPU, a swapped-out one's from its
+ * host copy.  For reading the observed part of a large volume without
+ * copying all of it.  MV_ERR_ARG for a box outside the volume. */
+mv_status mv_read_box(mv_ctx *ctx, int32_t id, const int32_t lo[3], const int32_t n[3], void *host_fw,
+                      uint8_t *host_rgba);
+
 /* Synchronous overwrite of a volume's state from host memory in the layout of
  * mv_read_volume (host_rgba NULL keeps the colour).  Used to prefill volumes
  * and to restore checkpoints. */

@@ -130,6 +130,7 @@ _SIGNATURES = {
     "mv_swap_out": ([_P, C.c_int32, _P], C.c_int),
     "mv_swap_in": ([_P, C.c_int32, _P], C.c_int),
     "mv_read_volume": ([_P, C.c_int32, _P, _P], C.c_int),
+    "mv_read_box": ([_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _P, _P], C.c_int),
     "mv_write_volume": ([_P, C.c_int32, _P, _P], C.c_int),
     "mv_read_brick_flags": ([_P, C.c_int32, _P, C.c_uint64], C.c_int),
     "mv_get_stats": ([_P, C.POINTER(mv_stats), C.c_int32], C.c_int),

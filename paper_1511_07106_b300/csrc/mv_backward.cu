@@ -44,17 +44,18 @@ __device__ __forceinline__ void corner_fw(const VolDev &v, long long off, float 
 
 // Per-pixel gradient terms; returns false for skipped pixels.
 template <int FMT>
-__device__ bool pixel_grad(const VolDev &v, const double *T, float tau, const float d[3],
+__device__ bool pixel_grad(const VolDev &v, const float *Tf, const float *cam, float tau, const float d[3],
                            float gdep, const float gc[3], float jpose[6], long long corner_off[8],
                            long long lin[8], float &coef, float w[8])
 {
-    // hit point in this volume's voxel coordinates, from the camera position in FP64
+    // hit point in this volume's voxel coordinates, from the camera position
+    // (formed in double on the host: B300's FP64 rate is a small fraction of
+    // its FP32 rate, so the kernel does no FP64 arithmetic)
     float q[3], xs[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double cam = T[4 * a + 3] / (double)v.s - (double)v.h[a];
-        q[a] = (float)cam + tau * d[a] * v.inv_s;
-        xs[a] = (float)T[4 * a + 3] + tau * d[a];
+        q[a] = __ldg(cam + a) + tau * d[a] * v.inv_s;
+        xs[a] = __ldg(Tf + 9 + a) + tau * d[a];
     }
     int cell[3];
     float fr[3];
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
     const int p = blockIdx.z;
     const int px = blockIdx.x * 16 + (threadIdx.x & 15);
     const int py = blockIdx.y * 8 + (threadIdx.x >> 4);
-    const double *T = A.poses + 16 * p;
+    const float *Tf = A.pose_f + 12 * p;
     float jp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (px < A.width && py < A.height) {
         const size_t pix = ((size_t)p * A.height + py) * A.width + px;
@@ -143,11 +144,12 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
         const int slot = (tau > 0.f && id >= 0) ? slot_of(A.vols, A.nvol, id) : -1;
         if (slot >= 0) {
             const VolDev &v = A.vols[slot];
+            const float *cam = A.cam_f + 3 * ((size_t)p * A.nvol + slot);
             const float dc0 = ((float)px - A.cx) / A.fx, dc1 = ((float)py - A.cy) / A.fy;
             float d[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                d[a] = (float)T[4 * a] * dc0 + (float)T[4 * a + 1] * dc1 + (float)T[4 * a + 2];
+                d[a] = __ldg(Tf + 3 * a) * dc0 + __ldg(Tf + 3 * a + 1) * dc1 + __ldg(Tf + 3 * a + 2);
             const float gdep = A.grad_depth ? A.grad_depth[pix] : 0.f;
             float gc[3] = {0.f, 0.f, 0.f};
             if (A.grad_rgb) {
@@ -159,9 +161,9 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
             float w[8], coef = 0.f;
             bool ok;
             switch (v.fmt) {
-            case MV_TSDF_F32: ok = pixel_grad<MV_TSDF_F32>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
-            case MV_TSDF_F16: ok = pixel_grad<MV_TSDF_F16>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
-            default: ok = pixel_grad<MV_TSDF_I16>(v, T, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            case MV_TSDF_F32: ok = pixel_grad<MV_TSDF_F32>(v, Tf, cam, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            case MV_TSDF_F16: ok = pixel_grad<MV_TSDF_F16>(v, Tf, cam, tau, d, gdep, gc, jp, off, lin, coef, w); break;
+            default: ok = pixel_grad<MV_TSDF_I16>(v, Tf, cam, tau, d, gdep, gc, jp, off, lin, coef, w); break;
             }
             if (!ok) {
 #pragma unroll

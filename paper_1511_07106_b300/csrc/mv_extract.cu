@@ -146,4 +146,39 @@ cudaError_t launch_extract(const VolDev &v, float *xyz, uint8_t *rgb, unsigned l
     return cudaGetLastError();
 }
 
+// A box of a volume's voxels in linear order (x fastest), gathered from the
+// brick-major storage: voxels lo .. lo + n - 1 per axis.
+template <typename T>
+__global__ void __launch_bounds__(256) gather_box_kernel(const T *__restrict__ src, int nb0, int nb1, int lo0,
+                                                         int lo1, int lo2, int n0, int n1, long long total,
+                                                         T *__restrict__ dst)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % n0) + lo0;
+        const int y = (int)((i / n0) % n1) + lo1;
+        const int z = (int)(i / ((long long)n0 * n1)) + lo2;
+        const long long b = ((long long)(z >> 3) * nb1 + (y >> 3)) * nb0 + (x >> 3);
+        dst[i] = src[b * kBrickVox + (((z & 7) << 6) | ((y & 7) << 3) | (x & 7))];
+    }
+}
+
+cudaError_t launch_gather_box(const void *src, int elem_bytes, const int nb[3], const int lo[3], const int n[3],
+                              void *dst, int num_sms, cudaStream_t s)
+{
+    const long long total = (long long)n[0] * n[1] * n[2];
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+    if (blocks < 1) blocks = 1;
+    if (elem_bytes == 8)
+        gather_box_kernel<unsigned long long><<<(unsigned)blocks, 256, 0, s>>>(
+            static_cast<const unsigned long long *>(src), nb[0], nb[1], lo[0], lo[1], lo[2], n[0], n[1], total,
+            static_cast<unsigned long long *>(dst));
+    else
+        gather_box_kernel<unsigned><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const unsigned *>(src), nb[0], nb[1],
+                                                                    lo[0], lo[1], lo[2], n[0], n[1], total,
+                                                                    static_cast<unsigned *>(dst));
+    return cudaGetLastError();
+}
+
 }  // namespace mv

@@ -102,6 +102,7 @@ struct FrameParams {
     double R[9];       // camera-to-world rotation, row-major
     double t[3];       // camera centre, metres
     float Rf[9];
+    float tf[3];       // camera centre, metres, rounded to float (no FP64 in the kernels' per-pixel work)
     float fx, fy, cx, cy;
     int width, height;
     float z_min, z_max;
@@ -277,7 +278,9 @@ struct BackwardArgs {
     const VolDev *vols;
     int nvol;
     float *const *grad_tsdf;  // per table slot: dense float32 [z][y][x], or null
-    const double *poses;      // n x 16 row-major camera-to-world
+    const float *pose_f;      // per pose: R (9, row-major) and t (3) of the camera-to-world pose, float32
+    const float *cam_f;       // per pose and table slot: camera position in the volume's voxel coordinates
+                              // (t / s - h_t, computed in double, rounded once)
     int n_poses;
     float fx, fy, cx, cy;
     int width, height;

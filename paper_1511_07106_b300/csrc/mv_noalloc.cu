@@ -157,6 +157,7 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
             P.Rf[3 * a + b] = (float)T[4 * a + b];
         }
         P.t[a] = T[4 * a + 3];
+        P.tf[a] = (float)T[4 * a + 3];
     }
     P.fx = K->fx; P.fy = K->fy; P.cx = K->cx; P.cy = K->cy;
     P.width = K->width; P.height = K->height;

@@ -665,7 +665,7 @@ __device__ __forceinline__ void trace_pixel(const VolDev *__restrict__ vols,
     if (out.vertex) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            out.vertex[3 * p + a] = hit ? (float)P.t[a] + best.tau * d[a] : 0.f;
+            out.vertex[3 * p + a] = hit ? P.tf[a] + best.tau * d[a] : 0.f;
     }
 }
 

@@ -48,6 +48,8 @@ int integrate_occupancy_grid(int num_sms);
 int integrate_max_ctas_per_sm();
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
 size_t backward_ctas_per_pose(int width, int height);
+cudaError_t launch_gather_box(const void *src, int elem_bytes, const int nb[3], const int lo[3], const int n[3],
+                              void *dst, int num_sms, cudaStream_t s);
 cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long long *, unsigned long long,
                            unsigned long long *, int, cudaStream_t);
 cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float, const double *, float *, float *,
@@ -180,10 +182,21 @@ struct mv_ctx {
     VisList *d_visb = nullptr;
     int batch_cap = 0;
     std::vector<FrameParams> h_pb;
+    // pinned staging for the small per-call uploads (poses, view parameters,
+    // gradient pointers): a copy from pageable memory would first wait for
+    // the stream's earlier work; slot k is reused once its copy has run
+    struct Stage {
+        void *h = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+        bool recorded = false;
+    } stage[4];
+    int stage_next = 0;
     // raycast backward: per-slot gradient pointers and the poses of one call
     float **d_grad_ptrs = nullptr;
-    double *d_poses = nullptr;
-    int poses_cap = 0;
+    float *d_poses = nullptr;  // per pose R, t (float) and per pose and slot the camera in voxels
+    size_t poses_cap = 0;      // floats
+    std::vector<float> h_pose_f;
     float *d_bw_partial = nullptr;  // per-CTA partial sums of the pose gradient
     size_t bw_partial_cap = 0;      // floats
     // per-kernel launch counts and optional event timing
@@ -240,6 +253,7 @@ FrameParams make_params(const mv_ctx *c, const mv_intrinsics *K, const double T[
             P.Rf[3 * a + b] = (float)T[4 * a + b];
         }
         P.t[a] = T[4 * a + 3];
+        P.tf[a] = (float)T[4 * a + 3];
     }
     P.fx = K->fx; P.fy = K->fy; P.cx = K->cx; P.cy = K->cy;
     P.width = K->width; P.height = K->height;
@@ -799,6 +813,10 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
     if (c->d_poses) cudaFree(c->d_poses);
     if (c->d_bw_partial) cudaFree(c->d_bw_partial);
+    for (auto &st : c->stage) {
+        if (st.h) cudaFreeHost(st.h);
+        if (st.ev) cudaEventDestroy(st.ev);
+    }
     free_host_pipe(c);
     if (c->d_pb) cudaFree(c->d_pb);
     if (c->d_vfb) cudaFree(c->d_vfb);
@@ -1108,6 +1126,29 @@ mv_status mv_list_volumes(mv_ctx *c, int32_t *ids, int32_t cap, int32_t *count)
 
 // The depth-tile pyramid buffer, grown to the frame size (before any graph
 // or launch of the call uses it).
+// Copy `bytes` of host data to device memory on stream s through the
+// context's pinned staging ring (the source may be reused on return).
+static mv_status upload_small(mv_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    auto &st = c->stage[c->stage_next];
+    c->stage_next = (c->stage_next + 1) % 4;
+    if (!st.ev) MV_CUDA(c, cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming));
+    if (st.recorded) MV_CUDA(c, cudaEventSynchronize(st.ev));  // its previous copy has run
+    if (bytes > st.cap) {
+        if (st.h) MV_CUDA(c, cudaFreeHost(st.h));
+        st.h = nullptr;
+        st.cap = 0;
+        const size_t cap = bytes < 65536 ? 65536 : bytes;
+        MV_CUDA(c, cudaMallocHost(&st.h, cap));
+        st.cap = cap;
+    }
+    std::memcpy(st.h, src, bytes);
+    MV_CUDA(c, cudaMemcpyAsync(dst, st.h, bytes, cudaMemcpyHostToDevice, s));
+    MV_CUDA(c, cudaEventRecord(st.ev, s));
+    st.recorded = true;
+    return MV_OK;
+}
+
 static mv_status ensure_pyramid(mv_ctx *c, const mv_intrinsics *K)
 {
     // the largest-depth pyramid, then the smallest-depth one
@@ -1259,8 +1300,8 @@ mv_status mv_raycast_batch(mv_ctx *c, const mv_intrinsics *K, const double *T, i
     const int nvol = (int)c->table.size();
     c->h_pb.resize(n_views);
     for (int k = 0; k < n_views; ++k) c->h_pb[k] = make_params(c, K, T + 16 * (size_t)k);
-    // the host vector is copied before cudaMemcpyAsync returns (pageable source)
-    MV_CUDA(c, cudaMemcpyAsync(c->d_pb, c->h_pb.data(), sizeof(FrameParams) * n_views, cudaMemcpyHostToDevice, s));
+    st = upload_small(c, c->d_pb, c->h_pb.data(), sizeof(FrameParams) * n_views, s);
+    if (st) return st;
     if (nvol > 0)
         for (int k = 0; k < n_views; ++k)
             MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
@@ -1696,28 +1737,49 @@ mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
     if (st) return st;
-    if (n_poses > c->poses_cap) {
+    // per pose its rotation and translation in float, and per pose and table
+    // slot the camera position in that volume's voxel coordinates (in double,
+    // rounded once): the kernel then needs no FP64 arithmetic
+    const size_t nslot = c->table.size();
+    const size_t nf = 12 * (size_t)n_poses + 3 * (size_t)n_poses * nslot;
+    if (nf > c->poses_cap) {
         if (c->d_poses) MV_CUDA(c, cudaFreeAsync(c->d_poses, s));
         c->d_poses = nullptr;
         c->poses_cap = 0;
-        MV_CUDA(c, cudaMallocAsync((void **)&c->d_poses, sizeof(double) * 16 * n_poses, s));
-        c->poses_cap = n_poses;
+        MV_CUDA(c, cudaMallocAsync((void **)&c->d_poses, sizeof(float) * nf, s));
+        c->poses_cap = nf;
     }
-    MV_CUDA(c, cudaMemcpyAsync(c->d_poses, T, sizeof(double) * 16 * n_poses, cudaMemcpyHostToDevice, s));
+    c->h_pose_f.resize(nf);
+    for (int i = 0; i < n_poses; ++i) {
+        const double *Ti = T + 16 * (size_t)i;
+        float *pf = c->h_pose_f.data() + 12 * (size_t)i;
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) pf[3 * a + b] = (float)Ti[4 * a + b];
+            pf[9 + a] = (float)Ti[4 * a + 3];
+        }
+        float *cf = c->h_pose_f.data() + 12 * (size_t)n_poses + 3 * (size_t)i * nslot;
+        for (size_t k = 0; k < nslot; ++k)
+            for (int a = 0; a < 3; ++a)
+                cf[3 * k + a] = (float)(Ti[4 * a + 3] / (double)c->table[k].s - (double)c->table[k].h[a]);
+    }
+    st = upload_small(c, c->d_poses, c->h_pose_f.data(), sizeof(float) * nf, s);
+    if (st) return st;
     std::vector<float *> ptrs(c->table.size() > 0 ? c->table.size() : 1, nullptr);
     for (int i = 0; i < n_targets; ++i) {
         const int slot = table_slot(c, targets[i].id);
         if (slot >= 0) ptrs[slot] = targets[i].grad_tsdf;
     }
-    if (!c->table.empty())
-        MV_CUDA(c, cudaMemcpyAsync(c->d_grad_ptrs, ptrs.data(), sizeof(float *) * c->table.size(),
-                                   cudaMemcpyHostToDevice, s));
+    if (!c->table.empty()) {
+        st = upload_small(c, c->d_grad_ptrs, ptrs.data(), sizeof(float *) * c->table.size(), s);
+        if (st) return st;
+    }
     MV_CUDA(c, cudaMemsetAsync(grad_pose, 0, sizeof(float) * 6 * n_poses, s));
     BackwardArgs A;
     A.vols = c->d_table;
     A.nvol = (int)c->table.size();
     A.grad_tsdf = c->d_grad_ptrs;
-    A.poses = c->d_poses;
+    A.pose_f = c->d_poses;
+    A.cam_f = c->d_poses + 12 * (size_t)n_poses;
     A.n_poses = n_poses;
     A.fx = K->fx; A.fy = K->fy; A.cx = K->cx; A.cy = K->cy;
     A.width = K->width; A.height = K->height;
@@ -1851,6 +1913,55 @@ mv_status mv_read_volume(mv_ctx *c, int32_t id, void *host_fw, uint8_t *host_rgb
     else
         bricks_to_linear(*v, (const uint32_t *)src_fw, (uint32_t *)host_fw);
     if (host_rgba) bricks_to_linear(*v, (const uint32_t *)src_col, (uint32_t *)host_rgba);
+    return MV_OK;
+}
+
+mv_status mv_read_box(mv_ctx *c, int32_t id, const int32_t lo[3], const int32_t n[3], void *host_fw,
+                      uint8_t *host_rgba)
+{
+    if (!c || !host_fw || !lo || !n) return fail(c, MV_ERR_ARG, "null argument");
+    Volume *v;
+    mv_status st = find_volume(c, id, &v);
+    if (st) return st;
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < 0 || n[a] < 1 || (long long)lo[a] + n[a] > v->desc.h_r[a])
+            return fail(c, MV_ERR_ARG, "box outside the volume");
+    cudaSetDevice(c->device);
+    st = wait_all(c);
+    if (st) return st;
+    if (v->ready_pending) MV_CUDA(c, cudaEventSynchronize(v->ready));
+    const size_t total = (size_t)n[0] * n[1] * n[2];
+    const int eb = v->desc.fmt == MV_TSDF_F32 ? 8 : 4;
+    if (v->resident) {
+        // gathered on the GPU into a temporary buffer, then one copy per array
+        cudaStream_t s = c->swap_stream;
+        void *tmp = nullptr;
+        MV_CUDA(c, cudaMallocAsync(&tmp, total * 8, s));
+        cudaError_t e = launch_gather_box(v->d_fw, eb, v->nb, lo, n, tmp, c->num_sms, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_fw, tmp, total * eb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && host_rgba) e = launch_gather_box(v->d_rgba, 4, v->nb, lo, n, tmp, c->num_sms, s);
+        if (e == cudaSuccess && host_rgba) e = cudaMemcpyAsync(host_rgba, tmp, total * 4, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(tmp, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        MV_CUDA(c, e);
+        return MV_OK;
+    }
+    // swapped out: from the pinned host copy
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x) {
+                const int gx = lo[0] + x, gy = lo[1] + y, gz = lo[2] + z;
+                const size_t off = (size_t)((((long long)(gz >> 3) * v->nb[1] + (gy >> 3)) * v->nb[0] + (gx >> 3)) *
+                                                kBrickVox +
+                                            (((gz & 7) << 6) | ((gy & 7) << 3) | (gx & 7)));
+                const size_t i = ((size_t)z * n[1] + y) * n[0] + x;
+                if (eb == 8)
+                    static_cast<uint64_t *>(host_fw)[i] = static_cast<const uint64_t *>(v->h_fw)[off];
+                else
+                    static_cast<uint32_t *>(host_fw)[i] = static_cast<const uint32_t *>(v->h_fw)[off];
+                if (host_rgba)
+                    reinterpret_cast<uint32_t *>(host_rgba)[i] = static_cast<const uint32_t *>(v->h_rgba)[off];
+            }
     return MV_OK;
 }
 

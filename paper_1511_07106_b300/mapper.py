@@ -455,6 +455,28 @@ class Mapper:
                                              None if col is None else col.ctypes.data_as(C.c_void_p)))
         return raw, col
 
+    def read_box(self, vid, lo, n, rgba=True):
+        """Synchronous read of the voxel box lo .. lo + n - 1 (x, y, z) ->
+        (raw storage [z, y, x, ...], rgba [z, y, x, 4] or None)."""
+        q = self.query(vid)
+        nx, ny, nz = (int(a) for a in n)
+        if q["fmt"] == _abi.MV_TSDF_F32:
+            raw = np.empty((nz, ny, nx, 2), np.float32)
+        else:
+            raw = np.empty((nz, ny, nx), np.uint32)
+        col = np.empty((nz, ny, nx, 4), np.uint8) if rgba else None
+        lo3 = (C.c_int32 * 3)(*(int(a) for a in lo))
+        n3 = (C.c_int32 * 3)(nx, ny, nz)
+        self._check(self._lib.mv_read_box(self._h, int(vid), lo3, n3, raw.ctypes.data_as(C.c_void_p),
+                                          None if col is None else col.ctypes.data_as(C.c_void_p)))
+        return raw, col
+
+    def read_box_decoded(self, vid, lo, n):
+        """read_box -> (F, W, rgba) with F, W as float64 [z, y, x]."""
+        raw, col = self.read_box(vid, lo, n)
+        F, W = decode(raw, self.query(vid)["fmt"])
+        return F, W, col
+
     def read_decoded(self, vid):
         """Synchronous read -> (F, W, rgba) with F, W as float64 [z, y, x]."""
         raw, col = self.read_volume(vid)

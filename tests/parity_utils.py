@@ -128,3 +128,50 @@ def check_brick_flags(m, vid, spec, min_free_recall=0.0):
     recall = free[b_all_pos].mean() if b_all_pos.any() else 1.0
     assert recall >= min_free_recall, f"only {recall:.2%} of free bricks flagged"
     return float(recall)
+
+
+def observed_box(m, vid, spec, margin=2):
+    """Voxel box (lo, n) per axis x, y, z covering the volume's observed bricks
+    (brick flags without the EMPTY bit) widened by `margin` voxels and clipped
+    to the volume, or None when nothing is observed."""
+    fl = m.read_brick_flags(vid)  # [nbz, nby, nbx]
+    obs = (fl & 2) == 0
+    if not obs.any():
+        return None
+    lo, n = [], []
+    for a, ax in enumerate((2, 1, 0)):  # x, y, z = array axes 2, 1, 0
+        other = tuple(b for b in range(3) if b != ax)
+        idx = np.flatnonzero(obs.any(axis=other))
+        l = max(0, int(idx[0]) * 8 - margin)
+        h = min(int(spec.r[a]), (int(idx[-1]) + 1) * 8 + margin)
+        lo.append(l)
+        n.append(h - l)
+    return lo, n
+
+
+def frustum_box(spec, cam, T, z_far, margin=2):
+    """Voxel box (lo, n) of the volume covering the part of the camera's
+    viewing pyramid up to depth z_far (metres), widened by `margin` voxels and
+    clipped to the volume, or None when they do not meet."""
+    T = np.asarray(T, np.float64)
+    corners = [T[:3, 3]]
+    for x in (-0.5, cam.width - 0.5):
+        for y in (-0.5, cam.height - 0.5):
+            dc = np.array([(x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0])
+            corners.append(T[:3, 3] + z_far * (T[:3, :3] @ dc))
+    q = np.array(corners) / spec.s - np.array(spec.h)
+    lo = np.maximum(np.floor(q.min(0)) - margin, 0).astype(int)
+    hi = np.minimum(np.ceil(q.max(0)) + margin + 1, np.array(spec.r)).astype(int)
+    if np.any(hi <= lo):
+        return None
+    return list(lo), list(hi - lo)
+
+
+def union_box(a, b):
+    if a is None:
+        return b
+    if b is None:
+        return a
+    lo = [min(x, y) for x, y in zip(a[0], b[0])]
+    hi = [max(x + u, y + w) for x, u, y, w in zip(a[0], a[1], b[0], b[1])]
+    return lo, [h - l for l, h in zip(lo, hi)]

@@ -471,38 +471,20 @@ def test_uneven_volumes_batched_equals_per_volume_and_oracle(levels):
     b.close()
 
 
-def read_observed_crop(m, vid, spec, margin=2):
-    """A volume's state cropped to the box of its observed voxels widened by
-    `margin` voxels (clipped to the volume), as an oracle volume with the
-    lattice offset moved to the box (voxel positions unchanged), plus the box
-    (lo, hi) per axis x, y, z; None if nothing is observed."""
-    F, W, rgba = m.read_decoded(vid)
-    obs = W > 0
-    if not obs.any():
-        return None
-    lo, hi = [], []
-    for ax in (2, 1, 0):  # x, y, z = array axes 2, 1, 0
-        other = tuple(a for a in range(3) if a != ax)
-        idx = np.flatnonzero(obs.any(axis=other))
-        lo.append(max(0, int(idx[0]) - margin))
-        hi.append(min(obs.shape[ax], int(idx[-1]) + 1 + margin))
-    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
-    v = oracle.Volume(tuple(int(spec.h[a] + lo[a]) for a in range(3)), tuple(hi[a] - lo[a] for a in range(3)),
-                      float(spec.s), F[sl].copy(), W[sl].copy(), rgba[sl].copy())
-    return v, (lo, hi)
-
-
 @pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
 def test_full_size_uneven_volumes_sampled_parity(fmt):
     """The 64 uneven volumes at full size (edges 128-768, pitches 1-8 mm, 7.3 G
     voxels) at 640x480, through the batched frame graph in each storage
     format: lockstep parity of frame 5 on up to 2 M sampled voxels of every
-    observed volume, and the merged raycast of that frame on every 7th
-    pixel.  The oracle sees each observed volume cropped to its observed box
-    widened by 2 voxels: samples outside lie in cells with an unobserved
-    corner (invalid, so they cannot form a bracket) and the voxels there are
-    all unobserved, so the crop changes no hit; volumes with nothing
-    observed cannot hold a hit and are left out."""
+    observed volume, and the merged raycast of that frame on every 2nd
+    pixel.  Each volume is read (mv_read_box) over the box of its observed
+    bricks joined with the part of the view frustum that frame 5 can update
+    (depths up to its largest depth + mu), widened by 2 voxels: outside it no
+    voxel is observed, so samples there lie in cells with an unobserved
+    corner (invalid: they cannot bracket) and the oracle, given the box as a
+    volume, finds the same hits; volumes with nothing observed cannot hold a
+    hit and are left out."""
+    from parity_utils import frustum_box, observed_box, union_box
     wl = synth.uneven_volumes(frames=6)
     m = Mapper()
     ids = [m.add_volume(v.h, v.r, v.s, fmt) for v in wl.volumes]
@@ -511,34 +493,35 @@ def test_full_size_uneven_volumes_sampled_parity(fmt):
         d, c = wl.frame(i)
         m.frame(dev(d), dev(c), wl.cam, wl.poses[i])
     m.synchronize()
-    # volumes with an observed brick after frame k (from the brick flags)
     d, c = wl.frame(k)
     T = wl.poses[k]
-    before = {}
+    z_far = float(d.max()) + 0.05  # mu is 4 voxels of at most 8 mm
+    boxes, before = {}, {}
     for vid, v in zip(ids, wl.volumes):
-        fl = m.read_brick_flags(vid)
-        if not np.all(fl & 2):
-            before[vid] = m.read_decoded(vid)
+        box = union_box(observed_box(m, vid, v), frustum_box(v, wl.cam, T, z_far))
+        if box is not None:
+            boxes[vid] = box
+            before[vid] = m.read_box_decoded(vid, *box)
     maps = gpu_maps(m.frame(dev(d), dev(c), wl.cam, T))
     rng = np.random.default_rng(7)
     crops, checked = [], 0
     for vid, v in zip(ids, wl.volumes):
-        got = read_observed_crop(m, vid, v)
-        if got is None:
+        if vid not in boxes:
+            assert observed_box(m, vid, v) is None  # frame k observed nothing outside the frustum box
             continue
-        after, (lo, hi) = got
+        lo, n = boxes[vid]
+        F1, W1, c1 = m.read_box_decoded(vid, lo, n)
+        if not (W1 > 0).any():
+            continue
+        h = tuple(int(v.h[a] + lo[a]) for a in range(3))
+        after = oracle.Volume(h, tuple(n), float(v.s), F1, W1, c1)
         crops.append((vid, after))
-        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
-        if vid in before:
-            F0, W0, c0 = (a[sl] for a in before.pop(vid))
-        else:  # first observed in frame k
-            F0, W0 = np.zeros(after.F.shape), np.zeros(after.W.shape)
-            c0 = np.zeros(after.rgba.shape, np.uint8)
-        prior = oracle.Volume(after.h, after.r, after.s, F0.copy(), W0.copy(), c0.copy())
+        F0, W0, c0 = before[vid]
+        prior = oracle.Volume(h, tuple(n), float(v.s), F0.copy(), W0.copy(), c0.copy())
         seen = np.flatnonzero(after.W.reshape(-1) > 0)
-        n = min(1_000_000, seen.size)
-        idx = np.unique(np.concatenate([rng.choice(seen, n, replace=False),
-                                        rng.integers(0, prior.F.size, n)]))
+        nsm = min(1_000_000, seen.size)
+        idx = np.unique(np.concatenate([rng.choice(seen, nsm, replace=False),
+                                        rng.integers(0, prior.F.size, nsm)]))
         _, flags = oracle.integrate_voxels(prior, idx, d, c, wl.cam, T, ocfg(m.config))
         sel = np.zeros(prior.F.shape, bool)
         sel.reshape(-1)[idx] = True
@@ -555,6 +538,32 @@ def test_full_size_uneven_volumes_sampled_parity(fmt):
     res = compare_raycast(maps, o, wl.cam, T, pitch, mask=mask, require_hits=0.01)
     assert res["hits"] > 1000
     m.close()
+
+
+def test_read_box_equals_the_whole_volume_cropped():
+    """mv_read_box returns the box of mv_read_volume, resident or swapped out."""
+    wl = synth.single_volume_128(frames=3, res=40)
+    (vs,) = wl.volumes
+    for fmt in ("f32", "i16"):
+        m = Mapper()
+        vid = m.add_volume(vs.h, vs.r, vs.s, fmt)
+        for i in range(wl.n_frames):
+            d, c = wl.frame(i)
+            m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
+        raw, col = m.read_volume(vid)
+        for lo, n in (((0, 0, 0), tuple(vs.r)), ((3, 9, 17), (20, 5, 11)), ((39, 0, 7), (1, 40, 1))):
+            sl = (slice(lo[2], lo[2] + n[2]), slice(lo[1], lo[1] + n[1]), slice(lo[0], lo[0] + n[0]))
+            for swapped in (False, True):
+                if swapped:
+                    m.swap_out(vid)
+                r2, c2 = m.read_box(vid, lo, n)
+                np.testing.assert_array_equal(r2, raw[sl])
+                np.testing.assert_array_equal(c2, col[sl])
+                if swapped:
+                    m.swap_in(vid)
+        with pytest.raises(MVError):
+            m.read_box(vid, (0, 0, 0), (41, 1, 1))
+        m.close()
 
 
 def test_two_level_list_at_scale_equals_one_level():
