@@ -50,12 +50,27 @@ def pose_from_twist(xi: torch.Tensor, T0: torch.Tensor) -> torch.Tensor:
 
 def tangent_cotangent(T: torch.Tensor, g_xi: torch.Tensor) -> torch.Tensor:
     """dL/dT whose Frobenius pairing with the tangent directions G_k T gives
-    g_xi[k] exactly (the dual basis of {G_k T} in their span)."""
-    G = _generators(T.dtype, T.device)
-    B = torch.einsum("kij,njl->nkil", G, T).reshape(T.shape[0], 6, 16)  # rows: vec(G_k T)
-    gram = B @ B.transpose(1, 2)                                        # (n, 6, 6)
-    coeff = torch.linalg.solve(gram, g_xi.unsqueeze(-1)).squeeze(-1)    # (n, 6)
-    return (coeff.unsqueeze(-1) * B).sum(1).reshape(-1, 4, 4)
+    g_xi[k] exactly, taken in their span: sum_k c_k G_k T with the Gram
+    system of the directions solved in closed form.  For T = [R | t] with R
+    orthonormal the Gram matrix is [[I, C], [C^T, (2 + |t|^2) I - t t^T]]
+    with C e_j = e_j x t, whose Schur complement is 2 I; so c_phi =
+    (g_phi - t x g_rho) / 2, c_rho = g_rho - c_phi x t, and
+    dL/dT = [[c_phi]_x R, g_rho; 0, 0]."""
+    R, t = T[:, :3, :3], T[:, :3, 3]
+    g_rho, g_phi = g_xi[:, :3], g_xi[:, 3:]
+    c = 0.5 * (g_phi - torch.cross(t, g_rho, dim=1))
+    out = torch.zeros_like(T)
+    out[:, :3, :3] = hat_so3(c) @ R
+    out[:, :3, 3] = g_rho
+    return out
+
+
+def hat_so3(w: torch.Tensor) -> torch.Tensor:
+    """(n, 3) -> (n, 3, 3) cross-product matrices [w]_x."""
+    z = torch.zeros_like(w[:, 0])
+    return torch.stack([torch.stack([z, -w[:, 2], w[:, 1]], -1),
+                        torch.stack([w[:, 2], z, -w[:, 0]], -1),
+                        torch.stack([-w[:, 1], w[:, 0], z], -1)], -2)
 
 
 class RaycastFn(torch.autograd.Function):
@@ -94,9 +109,9 @@ class RaycastFn(torch.autograd.Function):
         gts = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ctx.tsdf_shapes]
         mapper.raycast_backward(cam, ctx.poses, depth, vid, gd, gc, grad_xi,
                                 dict(zip(ctx.tsdf_ids, gts)))
-        # the tangent-space solve on the GPU, next to grad_xi
-        gT = tangent_cotangent(T.detach().to(dev, torch.float64), grad_xi.to(torch.float64))
-        return (gT.to(T.device, T.dtype), None, None, None, *gts)
+        # dL/dT on the pose's own device (a closed form: no linear solve)
+        gT = tangent_cotangent(T.detach().to(torch.float64), grad_xi.to(T.device, torch.float64))
+        return (gT.to(T.dtype), None, None, None, *gts)
 
 
 def render(mapper: Mapper, cam, T: torch.Tensor, tsdf=None):

@@ -43,3 +43,18 @@ def test_tangent_cotangent_pairs_with_generators():
     for n in range(2):
         for k in range(6):
             assert abs(float((gT[n] * (G[k] @ T[n])).sum()) - float(g[n, k])) < 1e-12
+
+
+def test_tangent_cotangent_closed_form_equals_the_gram_solve():
+    """The closed form (Schur complement 2 I) equals solving the 6 x 6 Gram
+    system of the tangent directions G_k T, for poses far from the origin."""
+    torch.manual_seed(2)
+    n = 6
+    T = diff.pose_from_twist(torch.randn(n, 6, dtype=torch.float64) * 0.8, torch.eye(4, dtype=torch.float64))
+    T[:, :3, 3] += torch.randn(n, 3, dtype=torch.float64) * 3.0
+    g = torch.randn(n, 6, dtype=torch.float64)
+    G = diff._generators(torch.float64)
+    B = torch.einsum("kij,njl->nkil", G, T).reshape(n, 6, 16)
+    coeff = torch.linalg.solve(B @ B.transpose(1, 2), g.unsqueeze(-1)).squeeze(-1)
+    ref = (coeff.unsqueeze(-1) * B).sum(1).reshape(-1, 4, 4)
+    np.testing.assert_allclose(diff.tangent_cotangent(T, g).numpy(), ref.numpy(), rtol=0, atol=1e-12)
