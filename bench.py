@@ -647,7 +647,11 @@ def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
     m.close()
     rays = n_poses * cam.width * cam.height
     return {"workload": wl.name, "poses": n_poses, "prefill_frames": len(frames),
-            "forward_backward_ms": fb_ms, "mrays_per_s_forward_backward": rays / (fb_ms * 1e-3) / 1e6,
+            "forward_backward_ms": refine_ms_per_step,
+            "forward_backward_note": "one refinement step: the forward of all 16 views (one launch), the L1 loss and "
+                                     "its gradient, the backward (one launch) and the tangent-space Adam update",
+            "mrays_per_s_forward_backward": rays / (refine_ms_per_step * 1e-3) / 1e6,
+            "autograd_forward_backward_ms": fb_ms,
             "backward_kernel_ms": tm["backward"][1] / max(tm["backward"][2], 1),
             "raycast_kernel_ms": tm["raycast"][1] / max(tm["raycast"][2], 1),
             "pose_error_m_deg_initial": err(T_init), "pose_error_m_deg_final": err(T_fin),
