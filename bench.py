@@ -930,7 +930,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the uneven-volume, differentiable and swap measurements")
     ap.add_argument("--extras", default="uneven,diff,swap,streamed,placement,resolution,tracking",
-                    help="comma-separated subset of the extra measurements to run")
+                    help="comma-separated subset of the extra measurements to run (1-GPU runs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -945,7 +945,9 @@ def main():
     procs = max(1, min(16, (os.cpu_count() or 2) // max(world, 1)))
     frames = make_frames(n, procs)  # before any CUDA call
     extra_steps = 20
-    extras = set() if args.no_extra else set(args.extras.split(","))
+    # the extra measurements run on 1-GPU runs only: under torchrun every rank
+    # would repeat them, and some pin tens of GB of host memory per process
+    extras = set() if (args.no_extra or world > 1) else set(args.extras.split(","))
     if "uneven" in extras:
         uneven_frames = _gen(_render_uneven, range(args.warmup + extra_steps), procs)
     if "diff" in extras:
