@@ -134,6 +134,41 @@ def test_smallest_volume_and_invalid_depth():
     m.close()
 
 
+def test_axis_aligned_rays():
+    """Degenerate ray directions: poses whose rotations are exact axis
+    permutations (some entries -0.0) and an integral principal point, so the
+    centre row, column and pixel of every view have rays with exactly zero
+    direction components (the march's domain clip and the step-over DDA take
+    their zero-direction branches), some of them lying in lattice planes.
+    Lockstep integration and the raycast against the oracle."""
+    res = 64
+    s = float(np.float32(1.5 / res))
+    scene = synth.Scene(planes=np.array([[0.0, 0.0, 1.0, 0.0]]),
+                        spheres=np.array([[0.1, -0.05, 0.35, 0.3], [-0.3, 0.25, 0.2, 0.2]]),
+                        boxes=np.array([[0.2, 0.2, 0.0, 0.5, 0.45, 0.4]]))
+    cam = synth.Camera(100.0, 100.0, 40.0, 30.0, 81, 61)
+    views = [((0.0, 0.0, 1.6), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0)),
+             ((-1.3, 0.0, 0.3), (0.0, 0.0, 0.3), (0.0, 0.0, 1.0)),
+             ((0.0, 1.3, 0.25), (0.0, 0.0, 0.25), (0.0, 0.0, 1.0)),
+             ((0.9, 0.0, 0.3), (0.0, 0.0, 0.3), (0.0, 0.0, 1.0))]
+    poses = [synth.look_at(*views[i % 4]) for i in range(8)]
+    for T in poses:
+        assert set(np.unique(np.abs(T[:3, :3]))) == {0.0, 1.0}
+    wl = synth.Workload("axis-aligned views of a 64^3 volume", cam, scene, poses,
+                        [synth.VolumeSpec((-res // 2, -res // 2, -4), (res, res, res), s)], seed=9)
+    m, vid, worst, flagged = run_lockstep(wl)
+    assert worst <= 1e-4 and flagged < 0.01
+    (vs,) = wl.volumes
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    for T in poses[:4]:
+        g = gpu_maps(m.raycast(cam, T))
+        o = oracle.raycast([ov], cam, T, ocfg(m.config), ids=[vid])
+        compare_raycast(g, o, cam, T, s, require_hits=0.3)
+        # the centre pixel's ray runs exactly along an axis
+        assert g["depth"][30, 40] > 0 and o["depth"][30, 40] > 0
+    m.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
