@@ -169,6 +169,34 @@ def test_axis_aligned_rays():
     m.close()
 
 
+@pytest.mark.parametrize("cfg", [
+    Config(trunc_voxels=2.0, w_max=3, color_w_max=2),
+    Config(z_min=0.9, z_max=1.7, ray_step=0.5),
+    Config(trunc_voxels=7.5, w_max=65535, n_bisect=12),
+], ids=["narrow-band-low-caps", "depth-range-half-step", "wide-band-high-cap"])
+def test_nondefault_config_lockstep_and_raycast(cfg):
+    """Configurations other than the default: a narrow truncation band with
+    weight and colour caps reached within the frames (the capped running
+    average), a depth range that gates measurements and clips the march with
+    half-voxel samples, and a wide band with the largest weight cap."""
+    wl = synth.single_volume_128(frames=8, res=64)
+    m, vid, worst, flagged = run_lockstep(wl, cfg=cfg)
+    assert worst <= 1e-4 and flagged < 0.01
+    (vs,) = wl.volumes
+    F, W, _ = m.read_decoded(vid)
+    assert W.max() <= cfg.w_max
+    if cfg.w_max < wl.n_frames:
+        assert W.max() == cfg.w_max  # the cap was reached
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    for T in (wl.poses[2], wl.poses[7]):
+        g = gpu_maps(m.raycast(wl.cam, T))
+        o = oracle.raycast([ov], wl.cam, T, ocfg(cfg), ids=[vid])
+        compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.1)
+        hit = g["depth"] > 0
+        assert np.all((g["depth"][hit] >= cfg.z_min) & (g["depth"][hit] <= cfg.z_max))
+    m.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
