@@ -14,12 +14,15 @@ pytestmark = pytest.mark.gpu
 KEYS = ("depth", "normal", "rgba", "vertex", "vol_id")
 
 
-@pytest.mark.parametrize("n_slots", [1, 3])
-def test_streamed_frames_equal_resident_frames(n_slots):
+@pytest.mark.parametrize("n_slots,fmt", [(1, "f32"), (3, "f32"), (2, "f16"), (2, "i16"), (2, "mixed")])
+def test_streamed_frames_equal_resident_frames(n_slots, fmt):
+    """Every storage format, and the three mixed in one frame (slots are
+    sized in bytes, so one slot holds volumes of any format in turn)."""
     wl = synth.room_tiles(res=48, pitch=0.01, split=2, frames=6, width=160, height=120)
+    fmts = [("f32", "f16", "i16")[k % 3] if fmt == "mixed" else fmt for k in range(len(wl.volumes))]
     a, b = Mapper(), Mapper()
-    ida = [a.add_volume(v.h, v.r, v.s) for v in wl.volumes]
-    idb = [b.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    ida = [a.add_volume(v.h, v.r, v.s, f) for v, f in zip(wl.volumes, fmts)]
+    idb = [b.add_volume(v.h, v.r, v.s, f) for v, f in zip(wl.volumes, fmts)]
     streamed = [idb[k] for k in (1, 2, 4, 6, 7)]  # more volumes than slots
     for vid in streamed:
         b.swap_out(vid)
