@@ -44,12 +44,15 @@ def test_histogram_bit_exact():
     m.close()
 
 
-def test_placement_follows_oracle_policy_and_volumes_match_standalone():
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_placement_follows_oracle_policy_and_volumes_match_standalone(fmt):
+    """In each storage format: placed volumes are created, evicted to host
+    memory and restored in that format."""
     pw = small_room()
     wl = pw.wl
     m = Mapper()
     hyst = 1.2
-    p = Placer(m, pw.cell_voxels, pw.volume_voxels, pw.voxel_size, pw.max_volumes, hysteresis=hyst)
+    p = Placer(m, pw.cell_voxels, pw.volume_voxels, pw.voxel_size, pw.max_volumes, hysteresis=hyst, fmt=fmt)
     cell_m = pw.cell_voxels * float(np.float32(pw.voxel_size))
     st = oracle.PlacementState()
     frames = list(range(0, wl.n_frames, 2))
@@ -78,7 +81,9 @@ def test_placement_follows_oracle_policy_and_volumes_match_standalone():
     for vid, fr in resident_at.items():
         solo = Mapper()
         cell = spec[vid]
-        sid = solo.add_volume(tuple(k * pw.cell_voxels for k in cell), (pw.volume_voxels,) * 3, pw.voxel_size)
+        sid = solo.add_volume(tuple(k * pw.cell_voxels for k in cell), (pw.volume_voxels,) * 3, pw.voxel_size,
+                              fmt)
+        assert m.query(vid)["fmt"] == solo.query(sid)["fmt"]
         for i in fr:
             d, c = wl.frame(i)
             solo.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
