@@ -57,6 +57,12 @@ def _render(i):
     return wl.frame(i)
 
 
+def _first_frames(frames, n):
+    """The room's first n frames: those rendered for the run, and the rest
+    rendered here (short runs render fewer than some measurements need)."""
+    return list(frames[:n]) + [_render(i) for i in range(len(frames), n)]
+
+
 def make_frames(n, procs):
     idx = [i % N_FRAMES_MAX for i in range(n)]
     uniq = sorted(set(idx))
@@ -710,6 +716,7 @@ def bench_streamed(torch, Mapper, Config, frames, n_frames=6):
     wl = synth.tiled(synth.room_512(frames=N_FRAMES_MAX, res=1022), split=2)
     vols = wl.volumes[:4]
     cam = wl.cam
+    frames = _first_frames(frames, n_frames + 1)
     dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_frames + 1]])).cuda()
     dc = torch.from_numpy(np.stack([f[1] for f in frames[:n_frames + 1]])).cuda()
     out = {"workload": "4 x 512^3 tiles at 2.93 mm (lower half of the 3 m room), all swapped out, "
@@ -817,6 +824,7 @@ def bench_resolution(torch, Mapper, Config, frames, n_frames=30):
     volume."""
     out = {"workload": f"3 m room, {n_frames} frames at 640x480: one 512^3 volume (5.86 mm) vs "
                        "8 tiles of 512^3 (2.93 mm)", "paper_vertex_gain_8_volumes": 4.75}
+    frames = _first_frames(frames, n_frames)
     dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_frames]])).cuda()
     dc = torch.from_numpy(np.stack([f[1] for f in frames[:n_frames]])).cuda()
     for name, wl in (("single_512", synth.room_512(frames=N_FRAMES_MAX)),
@@ -856,6 +864,7 @@ def bench_track(torch, Mapper, Config, frames, n_map=20, n_track=10, iterations=
     previous true pose, from that pose."""
     wl = synth.room_512(frames=N_FRAMES_MAX)
     (vs,) = wl.volumes
+    frames = _first_frames(frames, n_map + n_track)
     m = Mapper(Config())
     vid = m.add_volume(vs.h, vs.r, vs.s)
     dd = torch.from_numpy(np.stack([f[0] for f in frames[:n_map + n_track]])).cuda()

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "mv_icp.cuh"
 #include "mv_internal.cuh"
 #include "mv_pinned.h"
 
@@ -57,6 +58,10 @@ cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float
 cudaError_t launch_icp_system(const float *, const float *, const mv_intrinsics &, const double *, const float *,
                               const float *, const double *, float, float, double *, int, cudaStream_t);
 int icp_grid(int num_sms);
+cudaError_t launch_icp_step(const float *vertex, const float *normal, const mv_intrinsics &K, double *T_dev,
+                            double *sys_dev, int *state_dev, const float *mvertex, const float *mnormal,
+                            const double *T_model, float dist, float cos_min, double *partials, int grid,
+                            cudaStream_t s);
 cudaError_t launch_stream_gather(const VolDev &, const VolFrame *, const FrameParams &, const void *, const void *,
                                  unsigned long long *, int, cudaStream_t);
 cudaError_t launch_stream_scatter(const VolDev &, const uint2 *, const unsigned *, void *, void *,
@@ -146,6 +151,7 @@ struct mv_ctx {
     float *d_trk_v = nullptr, *d_trk_n = nullptr;
     size_t trk_px = 0;
     double *d_trk_part = nullptr;
+    double *d_trk_loop = nullptr;  // mv_track's device loop: pose (16), system (44), then 2 ints of state
     // full-cover streaming (mv_frame_streamed): device staging slots that the
     // swapped-out volumes pass through, one copy stream per direction
     struct Slots {
@@ -497,86 +503,6 @@ void free_host(mv_ctx *c, Volume *v)
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// tracking helpers (host, FP64)
-// ---------------------------------------------------------------------------
-namespace {
-
-// T <- exp(x^) T for the twist x = (rho, phi): rotation by Rodrigues,
-// translation V rho.
-void apply_twist(const double x[6], double T[16])
-{
-    const double p0 = x[3], p1 = x[4], p2 = x[5];
-    const double th2 = p0 * p0 + p1 * p1 + p2 * p2, th = std::sqrt(th2);
-    double A, B, Cc;
-    if (th < 1e-9) {
-        A = 1.0 - th2 / 6.0;
-        B = 0.5 - th2 / 24.0;
-        Cc = 1.0 / 6.0 - th2 / 120.0;
-    } else {
-        A = std::sin(th) / th;
-        B = (1.0 - std::cos(th)) / th2;
-        Cc = (th - std::sin(th)) / (th2 * th);
-    }
-    const double P[9] = {0, -p2, p1, p2, 0, -p0, -p1, p0, 0};
-    double P2[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += P[3 * i + k] * P[3 * k + j];
-            P2[3 * i + j] = acc;
-        }
-    double R[9], V[9];
-    for (int i = 0; i < 9; ++i) {
-        const double I = (i % 4 == 0) ? 1.0 : 0.0;
-        R[i] = I + A * P[i] + B * P2[i];
-        V[i] = I + B * P[i] + Cc * P2[i];
-    }
-    double t[3];
-    for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * x[0] + V[3 * i + 1] * x[1] + V[3 * i + 2] * x[2];
-    double out[16] = {0};
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 4; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * T[4 * k + j];
-            out[4 * i + j] = acc + (j == 3 ? t[i] : 0.0);
-        }
-    }
-    out[15] = 1.0;
-    for (int i = 0; i < 16; ++i) T[i] = out[i];
-}
-
-// Solve the symmetric positive definite 6x6 system A x = b (Cholesky);
-// false when a pivot is not positive.
-bool solve6(const double A[36], const double b[6], double x[6])
-{
-    double L[36] = {0};
-    for (int i = 0; i < 6; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double acc = A[6 * i + j];
-            for (int k = 0; k < j; ++k) acc -= L[6 * i + k] * L[6 * j + k];
-            if (i == j) {
-                if (!(acc > 0.0)) return false;
-                L[6 * i + i] = std::sqrt(acc);
-            } else {
-                L[6 * i + j] = acc / L[6 * j + j];
-            }
-        }
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-        double acc = b[i];
-        for (int k = 0; k < i; ++k) acc -= L[6 * i + k] * y[k];
-        y[i] = acc / L[6 * i + i];
-    }
-    for (int i = 5; i >= 0; --i) {
-        double acc = y[i];
-        for (int k = i + 1; k < 6; ++k) acc -= L[6 * k + i] * x[k];
-        x[i] = acc / L[6 * i + i];
-    }
-    return true;
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------
 // full-cover streaming
@@ -808,6 +734,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->d_trk_v) cudaFree(c->d_trk_v);
     if (c->d_trk_n) cudaFree(c->d_trk_n);
     if (c->d_trk_part) cudaFree(c->d_trk_part);
+    if (c->d_trk_loop) cudaFree(c->d_trk_loop);
     if (c->d_grad_ptrs) cudaFree(c->d_grad_ptrs);
     if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
@@ -879,11 +806,14 @@ static mv_status track_scratch(mv_ctx *c, const mv_intrinsics *K, cudaStream_t s
     }
     if (!c->d_trk_part)
         MV_CUDA(c, cudaMalloc((void **)&c->d_trk_part, sizeof(double) * kIcpTerms * icp_grid(c->num_sms)));
+    if (!c->d_trk_loop) MV_CUDA(c, cudaMalloc((void **)&c->d_trk_loop, sizeof(double) * 61));
     return MV_OK;
 }
 
 // One ICP linearisation on device maps; the partials are added on the host
 // in CTA order (deterministic).
+static mv_status upload_small(mv_ctx *c, void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 static mv_status icp_linearise(mv_ctx *c, const float *v, const float *n, const mv_intrinsics *K,
                                const double T_est[16], const float *mv_, const float *mn, const double T_model[16],
                                const mv_icp_config *cfg, mv_icp_system *out, cudaStream_t s)
@@ -955,18 +885,30 @@ mv_status mv_track(mv_ctx *c, const float *depth, const mv_intrinsics *K, const 
     if (st) return st;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAPS, s, [&] {
         return launch_depth_maps(depth, *K, c->cfg.z_min, c->cfg.z_max, nullptr, c->d_trk_v, c->d_trk_n, s); }));
-    double T[16];
-    for (int i = 0; i < 16; ++i) T[i] = T_init[i];
-    mv_icp_system sys{};
-    for (int it = 0; it < cfg->iterations; ++it) {
-        st = icp_linearise(c, c->d_trk_v, c->d_trk_n, K, T, model_vertex, model_normal, T_model, cfg, &sys, s);
-        if (st) return st;
-        double x[6];
-        if (sys.inliers < 6 || !solve6(sys.A, sys.b, x)) break;
-        apply_twist(x, T);
+    // the Gauss-Newton loop on the device (no host round trip per step): the
+    // pose and the last system stay in device memory and are read back once
+    double *d_T = c->d_trk_loop, *d_sys = c->d_trk_loop + 16;
+    int *d_state = reinterpret_cast<int *>(c->d_trk_loop + 60);
+    st = upload_small(c, d_T, T_init, sizeof(double) * 16, s);
+    if (st) return st;
+    MV_CUDA(c, cudaMemsetAsync(d_sys, 0, sizeof(double) * 44 + sizeof(int) * 2, s));
+    const int grid = icp_grid(c->num_sms);
+    for (int it = 0; it < cfg->iterations; ++it)
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_ICP, s, [&] {
+            return launch_icp_step(c->d_trk_v, c->d_trk_n, *K, d_T, d_sys, d_state, model_vertex, model_normal,
+                                   T_model, cfg->dist, cfg->cos_min, c->d_trk_part, grid, s); }));
+    double back[60];
+    MV_CUDA(c, cudaMemcpyAsync(back, c->d_trk_loop, sizeof(back), cudaMemcpyDeviceToHost, s));
+    MV_CUDA(c, cudaStreamSynchronize(s));
+    for (int i = 0; i < 16; ++i) T_out[i] = back[i];
+    if (last) {
+        mv_icp_system sys{};
+        for (int i = 0; i < 36; ++i) sys.A[i] = back[16 + i];
+        for (int i = 0; i < 6; ++i) sys.b[i] = back[52 + i];
+        sys.error = back[58];
+        sys.inliers = (int64_t)std::llround(back[59]);
+        *last = sys;
     }
-    for (int i = 0; i < 16; ++i) T_out[i] = T[i];
-    if (last) *last = sys;
     return MV_OK;
 }
 

@@ -10,8 +10,14 @@
 // by the current estimate, projected into the model's camera, associated with
 // the model vertex / normal at the nearest pixel (rejected beyond a distance
 // or normal-angle threshold), and contributes J^T J, J^T r, r^2 and a count
-// (29 values) to a per-CTA partial in FP64; the host adds the partials in a
-// fixed order and solves the 6x6 system.
+// (29 values) to a per-CTA partial (lanes and warps in FP32, the CTA's 8
+// warp sums and everything after in FP64).  mv_icp_linearize adds the
+// partials on the host in a fixed order; mv_track keeps the whole Gauss-Newton
+// loop on the device: the pose lives in device memory, and the last CTA of
+// each linearisation adds the partials in a fixed order, solves the 6x6
+// system and updates the pose, so the iterations run back to back with no
+// host round trip.
+#include "mv_icp.cuh"
 #include "mv_internal.cuh"
 
 namespace mv {
@@ -103,8 +109,32 @@ struct IcpArgs {
     double *partials;      // gridDim.x x kIcpTerms
 };
 
-__global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A)
+// Device state of mv_track's Gauss-Newton loop.
+struct IcpLoop {
+    double *T;      // current estimate, camera to world (row-major 4x4)
+    double *sys;    // the last linearisation: A (36), b (6), r^2, count
+    int *state;     // [0] stopped (too few inliers or a failed solve), [1] CTAs done
+};
+
+// LOOP: the estimate is read from L.T, nothing runs once the loop stopped,
+// and the last CTA to finish completes the Gauss-Newton step.
+template <bool LOOP>
+__global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
 {
+    if (LOOP) {
+        if (*(volatile int *)L.state) return;  // written by an earlier launch
+        __shared__ float s_est[12];
+        if (threadIdx.x < 12) {
+            const int a = threadIdx.x < 9 ? threadIdx.x / 3 : threadIdx.x - 9;
+            const int b = threadIdx.x < 9 ? threadIdx.x % 3 : 3;
+            s_est[threadIdx.x] = (float)L.T[4 * a + b];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A.est.r[k] = s_est[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A.est.t[k] = s_est[9 + k];
+    }
     float acc[kIcpTerms];
 #pragma unroll
     for (int k = 0; k < kIcpTerms; ++k) acc[k] = 0.f;
@@ -148,15 +178,18 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A)
         acc[27] += r * r;
         acc[28] += 1.f;
     }
-    // CTA sum in FP64: warps by shuffles, then across the 8 warps in shared memory
+    // CTA sum: each warp by a pairwise tree of FP32 shuffles (5 roundings on
+    // top of the lanes' own sums; B300 runs FP64 at a small fraction of its
+    // FP32 rate, and an FP64 tree here took about half the kernel's time),
+    // then the 8 warp sums in FP64 in shared memory
     __shared__ double s_part[8][kIcpTerms];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kIcpTerms; ++k) {
-        double x = (double)acc[k];
+        float x = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) s_part[wid][k] = x;
+        if (lane == 0) s_part[wid][k] = (double)x;
     }
     __syncthreads();
     if (threadIdx.x < kIcpTerms) {
@@ -164,14 +197,60 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_part[w][threadIdx.x];
         A.partials[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = x;
     }
+    if (!LOOP) return;
+    // the last CTA to finish adds the partials (8 threads per term, each a
+    // fixed stride of CTAs, then the 8 in order: a fixed order), solves and
+    // updates the estimate
+    __shared__ bool s_last;
+    __shared__ double s_sum[kIcpTerms][8];
+    __shared__ double s_tot[kIcpTerms];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&L.state[1], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < 8 * kIcpTerms) {
+        const int k = threadIdx.x >> 3, j = threadIdx.x & 7;
+        double x = 0.0;
+        for (int g = j; g < (int)gridDim.x; g += 8) x += __ldcg(A.partials + (size_t)g * kIcpTerms + k);
+        s_sum[k][j] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kIcpTerms) {
+        double x = 0.0;
+        for (int j = 0; j < 8; ++j) x += s_sum[threadIdx.x][j];
+        s_tot[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double sum[kIcpTerms];
+    for (int k = 0; k < kIcpTerms; ++k) sum[k] = s_tot[k];
+    double Am[36], b[6], x[6];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) Am[6 * i + j] = Am[6 * j + i] = sum[k];
+    for (int i = 0; i < 6; ++i) b[i] = sum[21 + i];
+    for (int i = 0; i < 36; ++i) L.sys[i] = Am[i];
+    for (int i = 0; i < 6; ++i) L.sys[36 + i] = b[i];
+    L.sys[42] = sum[27];
+    L.sys[43] = sum[28];
+    L.state[1] = 0;  // for the next linearisation, which starts after this kernel
+    if (__double2ll_rn(sum[28]) < 6 || !solve6(Am, b, x)) {
+        L.state[0] = 1;
+        return;
+    }
+    double T[16];
+    for (int i = 0; i < 16; ++i) T[i] = L.T[i];
+    apply_twist(x, T);
+    for (int i = 0; i < 16; ++i) L.T[i] = T[i];
 }
 
 int icp_grid(int num_sms) { return num_sms * 2; }
 
-cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv_intrinsics &K,
-                              const double *T_est, const float *mvertex, const float *mnormal,
-                              const double *T_model, float dist, float cos_min, double *partials, int grid,
-                              cudaStream_t s)
+static IcpArgs icp_args(const float *vertex, const float *normal, const mv_intrinsics &K, const double *T_est,
+                        const float *mvertex, const float *mnormal, const double *T_model, float dist,
+                        float cos_min, double *partials)
 {
     IcpArgs A;
     A.vertex = vertex;
@@ -180,10 +259,10 @@ cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv
     A.H = K.height;
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) {
-            A.est.r[3 * a + b] = (float)T_est[4 * a + b];
+            A.est.r[3 * a + b] = T_est ? (float)T_est[4 * a + b] : 0.f;
             A.model_inv.r[3 * a + b] = (float)T_model[4 * b + a];  // R^T
         }
-        A.est.t[a] = (float)T_est[4 * a + 3];
+        A.est.t[a] = T_est ? (float)T_est[4 * a + 3] : 0.f;
     }
     for (int a = 0; a < 3; ++a) {  // -R^T t in FP64, then rounded
         double x = 0.0;
@@ -199,7 +278,28 @@ cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv
     A.dist2 = dist * dist;
     A.cos_min = cos_min;
     A.partials = partials;
-    icp_system_kernel<<<grid, 256, 0, s>>>(A);
+    return A;
+}
+
+cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv_intrinsics &K,
+                              const double *T_est, const float *mvertex, const float *mnormal,
+                              const double *T_model, float dist, float cos_min, double *partials, int grid,
+                              cudaStream_t s)
+{
+    const IcpArgs A = icp_args(vertex, normal, K, T_est, mvertex, mnormal, T_model, dist, cos_min, partials);
+    icp_system_kernel<false><<<grid, 256, 0, s>>>(A, IcpLoop{nullptr, nullptr, nullptr});
+    return cudaGetLastError();
+}
+
+// One Gauss-Newton step of mv_track on the device (estimate in T_dev; loop
+// state: 16 doubles of pose, 44 of system, 2 ints).
+cudaError_t launch_icp_step(const float *vertex, const float *normal, const mv_intrinsics &K, double *T_dev,
+                            double *sys_dev, int *state_dev, const float *mvertex, const float *mnormal,
+                            const double *T_model, float dist, float cos_min, double *partials, int grid,
+                            cudaStream_t s)
+{
+    const IcpArgs A = icp_args(vertex, normal, K, nullptr, mvertex, mnormal, T_model, dist, cos_min, partials);
+    icp_system_kernel<true><<<grid, 256, 0, s>>>(A, IcpLoop{T_dev, sys_dev, state_dev});
     return cudaGetLastError();
 }
 

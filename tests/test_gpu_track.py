@@ -82,3 +82,34 @@ def test_track_matches_oracle_and_ground_truth():
         assert np.degrees(np.arccos(np.clip((np.trace(Re) - 1) / 2, -1, 1))) < 0.2
         assert last["count"] > 5000
     m.close()
+
+
+def test_track_stops_without_inliers_and_iterates_on_the_device():
+    """The Gauss-Newton loop runs on the device: with model maps that hold no
+    surface the first linearisation has no inliers, the loop stops there and
+    the estimate is returned unchanged (bit for bit); with zero iterations
+    the estimate is returned as given.  A tracked frame launches one
+    linearisation kernel per iteration and nothing else."""
+    wl = room(4)
+    m = Mapper()
+    d, _ = wl.frame(2)
+    empty = np.zeros((wl.cam.height, wl.cam.width, 3), np.float32)
+    T0 = wl.poses[1].copy()
+    T0[:3, 3] += (0.0123, -0.0045, 0.0067)
+    Tg, last = m.track(dev(d), wl.cam, dev(empty), dev(empty), wl.poses[1], T0, iterations=10, dist=DIST,
+                       cos_min=COS)
+    np.testing.assert_array_equal(Tg, T0)
+    assert last["count"] == 0 and last["error"] == 0.0
+    Tz, lz = m.track(dev(d), wl.cam, dev(empty), dev(empty), wl.poses[1], T0, iterations=0, dist=DIST,
+                     cos_min=COS)
+    np.testing.assert_array_equal(Tz, T0)
+    assert lz["count"] == 0
+    mv, mn = model_maps(wl, 1)
+    m.timings(reset=True)
+    Tg, last = m.track(dev(d), wl.cam, dev(mv), dev(mn), wl.poses[1], wl.poses[1], iterations=7, dist=DIST,
+                       cos_min=COS)
+    t = m.timings()
+    assert t["icp"][0] == 7 and t["depth_maps"][0] == 1
+    To, _ = oracle.track(d, wl.cam, mv, mn, wl.poses[1], wl.poses[1], 7, DIST, COS)
+    assert np.abs(Tg[:3, 3] - To[:3, 3]).max() < 2e-5
+    m.close()
