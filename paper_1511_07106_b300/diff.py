@@ -137,6 +137,32 @@ def l1_loss(depth, colour, ref_depth, ref_colour, colour_weight=0.1):
     return ld + colour_weight * lc
 
 
+def l1_loss_grad(depth, colour, ref_depth, ref_colour, colour_weight=0.1):
+    """l1_loss and its gradients with respect to depth and colour in closed
+    form (what autograd returns: the derivative of |x| is sign(x), 0 at 0):
+    (loss as a 0-d tensor, dL/ddepth, dL/dcolour)."""
+    valid = (depth > 0) & (ref_depth > 0)
+    w = valid / valid.sum().clamp(min=1)
+    dd = depth - ref_depth
+    dc = colour - ref_colour
+    loss = (torch.abs(dd) * w).sum() + colour_weight * (torch.abs(dc).sum(-1) * w).sum()
+    return loss, torch.sign(dd) * w, (colour_weight * torch.sign(dc)) * w[..., None]
+
+
+def so3_exp(phi: np.ndarray) -> np.ndarray:
+    """(n, 3) rotation vectors -> (n, 3, 3) rotations (Rodrigues; below 1e-4
+    rad the coefficients from their Maclaurin series)."""
+    th2 = np.sum(phi * phi, axis=1)[:, None, None]
+    small = th2 < 1e-8
+    th = np.sqrt(np.where(small, 1.0, th2))
+    a = np.where(small, 1.0 - th2 / 6.0, np.sin(th) / th)
+    b = np.where(small, 0.5 - th2 / 24.0, (1.0 - np.cos(th)) / np.where(small, 1.0, th2))
+    K = np.zeros((phi.shape[0], 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -phi[:, 2], phi[:, 1], -phi[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = phi[:, 2], -phi[:, 1], phi[:, 0]
+    return np.eye(3)[None] + a * K + b * (K @ K)
+
+
 def centred_gradient(t: torch.Tensor, g_xi: torch.Tensor) -> torch.Tensor:
     """Gradient in camera-centred coordinates (translation rho_c of the camera
     centre, rotation phi_c about it: R' = exp(phi_c) R, t' = t + rho_c) from
@@ -161,50 +187,48 @@ def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, l
     (g_rho, g_phi - t x g_rho): a rotation step then no longer moves the camera
     centre, which the left perturbation's rotation about the world origin does
     (by phi x t), coupling the two blocks for cameras far from the origin.
-    Adam's moments live on the GPU; lr: (metres, radians) per step for
-    translation and rotation, or one number for both, decayed by a cosine
-    from lr to lr * lr_final over the steps (lr_final = 1: constant, which
-    did best on the 8 x 256^3 workload, as did centred steps).  Returns
-    (T_final (n, 4, 4) float64 numpy, losses)."""
+    The loss's gradients come in closed form (l1_loss_grad); each step reads
+    the n x 6 pose gradient back once, and Adam and the pose update run on
+    the host (the poses are host data of mv_raycast_batch anyway).  lr:
+    (metres, radians) per step for translation and rotation, or one number
+    for both, decayed by a cosine from lr to lr * lr_final over the steps
+    (lr_final = 1: constant, which did best on the 8 x 256^3 workload, as did
+    centred steps).  Returns (T_final (n, 4, 4) float64 numpy, losses)."""
     import math
     dev = torch.device("cuda", mapper.device)
-    T = torch.as_tensor(np.asarray(T_init), dtype=torch.float64).clone()
+    T = np.array(T_init, dtype=np.float64)
     n = T.shape[0]
     lr_t, lr_r = (lr, lr) if np.isscalar(lr) else lr
-    rate = torch.tensor([lr_t] * 3 + [lr_r] * 3, dtype=torch.float64, device=dev)
-    m1 = torch.zeros((n, 6), dtype=torch.float64, device=dev)
-    m2 = torch.zeros_like(m1)
+    rate = np.array([lr_t] * 3 + [lr_r] * 3, dtype=np.float64)
+    m1 = np.zeros((n, 6))
+    m2 = np.zeros((n, 6))
     b1, b2, eps = 0.9, 0.999, 1e-12
     H, W = cam.height, cam.width
     out = dict(depth=torch.empty((n, H, W), dtype=torch.float32, device=dev),
                rgba=torch.empty((n, H, W, 4), dtype=torch.uint8, device=dev),
                vol_id=torch.empty((n, H, W), dtype=torch.int32, device=dev))
     grad_xi = torch.empty((n, 6), dtype=torch.float32, device=dev)
-    G = _generators(torch.float64)
     losses = []
     for it in range(steps):
-        mapper.raycast_batch(cam, T.numpy(), out=out)
-        depth = out["depth"].clone().requires_grad_(True)
-        colour = (out["rgba"][..., :3].float() / 255.0).requires_grad_(True)
-        loss = l1_loss(depth, colour, ref_depth, ref_colour, colour_weight)
-        gd, gc = torch.autograd.grad(loss, (depth, colour))
-        mapper.raycast_backward(cam, T.numpy(), out["depth"], out["vol_id"], gd.contiguous(), gc.contiguous(),
-                                grad_xi, {})
-        g = grad_xi.to(torch.float64)
+        mapper.raycast_batch(cam, T, out=out)
+        colour = out["rgba"][..., :3].float() / 255.0
+        loss, gd, gc = l1_loss_grad(out["depth"], colour, ref_depth, ref_colour, colour_weight)
+        mapper.raycast_backward(cam, T, out["depth"], out["vol_id"], gd, gc, grad_xi, {})
+        # the step's one read-back: the pose gradient, for Adam on the host
+        g = grad_xi.cpu().numpy().astype(np.float64)
         if centred:
-            g = centred_gradient(T[:, :3, 3].to(dev), g)
-        m1.mul_(b1).add_(g, alpha=1 - b1)
-        m2.mul_(b2).addcmul_(g, g, value=1 - b2)
+            g = np.concatenate([g[:, :3], g[:, 3:] - np.cross(T[:, :3, 3], g[:, :3])], axis=1)
+        m1 = b1 * m1 + (1 - b1) * g
+        m2 = b2 * m2 + (1 - b2) * g * g
         scale = lr_final + (1 - lr_final) * 0.5 * (1 + math.cos(math.pi * it / max(steps - 1, 1)))
-        delta = (-(rate * scale) * (m1 / (1 - b1 ** (it + 1))) / ((m2 / (1 - b2 ** (it + 1))).sqrt() + eps)).cpu()
+        delta = -(rate * scale) * (m1 / (1 - b1 ** (it + 1))) / (np.sqrt(m2 / (1 - b2 ** (it + 1))) + eps)
+        T = T.copy()
         if centred:
-            Rs = torch.matrix_exp(torch.einsum("nk,kij->nij", delta[:, 3:], G[3:, :3, :3]))
-            T = T.clone()
-            T[:, :3, :3] = Rs @ T[:, :3, :3]
+            T[:, :3, :3] = so3_exp(delta[:, 3:]) @ T[:, :3, :3]
             T[:, :3, 3] = T[:, :3, 3] + delta[:, :3]
         else:
-            T = torch.matrix_exp(hat(delta)) @ T
-        losses.append(float(loss.detach()))
+            T = torch.matrix_exp(hat(torch.from_numpy(delta))).numpy() @ T
+        losses.append(float(loss))
         if callback:
-            callback(it, T.numpy().copy(), losses[-1])
-    return T.numpy(), losses
+            callback(it, T.copy(), losses[-1])
+    return T, losses

@@ -58,3 +58,35 @@ def test_tangent_cotangent_closed_form_equals_the_gram_solve():
     coeff = torch.linalg.solve(B @ B.transpose(1, 2), g.unsqueeze(-1)).squeeze(-1)
     ref = (coeff.unsqueeze(-1) * B).sum(1).reshape(-1, 4, 4)
     np.testing.assert_allclose(diff.tangent_cotangent(T, g).numpy(), ref.numpy(), rtol=0, atol=1e-12)
+
+
+def test_l1_loss_grad_equals_autograd():
+    """The closed-form gradient of the refinement loss equals autograd's,
+    including pixels invalid in either render and exact zeros of the
+    differences (where the derivative of |x| is taken as 0)."""
+    g = torch.Generator().manual_seed(3)
+    n, H, W = 2, 7, 9
+    depth = torch.rand((n, H, W), generator=g, dtype=torch.float32) + 0.5
+    ref = depth + 0.05 * torch.randn((n, H, W), generator=g)
+    depth[0, :2] = 0.0
+    ref[1, :, :3] = 0.0
+    ref[0, 5, 5] = depth[0, 5, 5]  # an exact zero of the difference
+    col = torch.rand((n, H, W, 3), generator=g)
+    rcol = torch.rand((n, H, W, 3), generator=g)
+    rcol[1, 2, 2] = col[1, 2, 2]
+    d = depth.clone().requires_grad_(True)
+    c = col.clone().requires_grad_(True)
+    loss = diff.l1_loss(d, c, ref, rcol, 0.1)
+    gd, gc = torch.autograd.grad(loss, (d, c))
+    loss2, gd2, gc2 = diff.l1_loss_grad(depth, col, ref, rcol, 0.1)
+    torch.testing.assert_close(loss2, loss.detach(), rtol=1e-6, atol=0)
+    torch.testing.assert_close(gd2, gd, rtol=0, atol=0)
+    torch.testing.assert_close(gc2, gc, rtol=0, atol=0)
+
+
+def test_so3_exp_equals_matrix_exponential():
+    rng = np.random.default_rng(4)
+    phi = np.concatenate([rng.normal(size=(5, 3)) * s for s in (1.0, 1e-3, 1e-5)] + [np.zeros((1, 3))])
+    got = diff.so3_exp(phi)
+    want = torch.matrix_exp(diff.hat_so3(torch.from_numpy(phi))).numpy()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
