@@ -20,7 +20,6 @@
 #include <string>
 #include <vector>
 
-#include "mv_icp.cuh"
 #include "mv_internal.cuh"
 #include "mv_pinned.h"
 

@@ -17,7 +17,6 @@
 // each linearisation adds the partials in a fixed order, solves the 6x6
 // system and updates the pose, so the iterations run back to back with no
 // host round trip.
-#include "mv_icp.cuh"
 #include "mv_internal.cuh"
 
 namespace mv {
@@ -116,6 +115,134 @@ struct IcpLoop {
     int *state;     // [0] stopped (too few inliers or a failed solve), [1] CTAs done
 };
 
+// 1 / sqrt(d) for d > 0: a float seed refined by two Newton steps
+// y <- y (3 - d y^2) / 2 in FP64 (the relative error e becomes about 1.5 e^2
+// per step: 2e-7, 1e-13, then below double rounding) -- a short dependent
+// chain where FP64 sqrt and division are long ones on B300.
+__device__ __forceinline__ double inv_sqrt(double d)
+{
+    if (d > 1e-30 && d < 1e30) {
+        double y = (double)rsqrtf((float)d);
+        y = y * (1.5 - 0.5 * d * y * y);
+        return y * (1.5 - 0.5 * d * y * y);
+    }
+    return 1.0 / sqrt(d);
+}
+
+// The coefficients of the twist's exponential at q = th^2 = |phi|^2:
+// sin(th)/th, (1 - cos th)/th^2, (th - sin th)/th^3.  For th < 0.1 rad (the
+// Gauss-Newton increments of tracking) from the Maclaurin series in th^2,
+// nested by the ratio of consecutive terms; the first omitted term
+// (th^10 / 11!, / 12!, / 13!) is below 3e-18 relative, so the series is exact
+// in double.  Every lane computes all three (no divergence).
+__device__ __forceinline__ void twist_coefs(double q, double &a, double &b, double &c)
+{
+    if (q < 1e-2) {
+        a = 1.0 - q * (1.0 / 6) * (1.0 - q * (1.0 / 20) * (1.0 - q * (1.0 / 42) * (1.0 - q * (1.0 / 72))));
+        b = 0.5 * (1.0 - q * (1.0 / 12) * (1.0 - q * (1.0 / 30) * (1.0 - q * (1.0 / 56) * (1.0 - q * (1.0 / 90)))));
+        c = (1.0 / 6) * (1.0 - q * (1.0 / 20) * (1.0 - q * (1.0 / 42) * (1.0 - q * (1.0 / 72) * (1.0 - q * (1.0 / 110)))));
+        return;
+    }
+    const double th = sqrt(q), sn = sin(th);
+    a = sn / th;
+    b = (1.0 - cos(th)) / q;
+    c = (th - sn) / (q * th);
+}
+
+// Warp 0 of the last CTA: the Gauss-Newton step from the 29 sums.  The
+// 6x6 system is reported as summed; A x = b is solved by a right-looking
+// Cholesky factorisation (per column one reciprocal square root, then the
+// column and the trailing triangle updated one entry per lane) and two
+// column-oriented triangular solves; then T <- exp(x^) T (Rodrigues, the
+// 3x3 products one entry per lane).  The loop stops (state[0]) when fewer
+// than 6 pixels associate or a pivot is not positive.
+__device__ __forceinline__ void icp_step_warp(const double *tot, const IcpLoop &L)
+{
+    __shared__ double sA[36], sy[6], sinv[6], sP[9], sR[9], sV[9], st[3], sT[16];
+    __shared__ int s_fail;
+    const int lane = threadIdx.x;
+    if (lane < 21) {  // upper-triangle sums, row-major -> both triangles
+        int i = 0, r = lane;
+        while (r >= 6 - i) { r -= 6 - i; ++i; }
+        sA[6 * i + i + r] = sA[6 * (i + r) + i] = tot[lane];
+    }
+    if (lane < 6) sy[lane] = tot[21 + lane];
+    if (lane == 0) s_fail = __double2ll_rn(tot[28]) < 6;
+    __syncwarp();
+    for (int e = lane; e < 36; e += 32) L.sys[e] = sA[e];
+    if (lane < 6) L.sys[36 + lane] = sy[lane];
+    if (lane == 0) {
+        L.sys[42] = tot[27];
+        L.sys[43] = tot[28];
+        L.state[1] = 0;  // for the next linearisation, which starts after this kernel
+    }
+    for (int j = 0; j < 6; ++j) {
+        __syncwarp();
+        if (s_fail) break;
+        if (lane == 0) {
+            const double d = sA[7 * j];
+            if (d > 0.0) sinv[j] = inv_sqrt(d);
+            else s_fail = 1;
+        }
+        __syncwarp();
+        if (s_fail) break;
+        if (lane > j && lane < 6) sA[6 * lane + j] *= sinv[j];  // L_ij
+        __syncwarp();
+        const int m = 5 - j;  // trailing lower triangle: rows and columns j+1 .. 5
+        if (lane < m * (m + 1) / 2) {
+            int i = 0, r = lane;
+            while (r > i) { r -= i + 1; ++i; }
+            const int row = j + 1 + i, col = j + 1 + r;
+            sA[6 * row + col] -= sA[6 * row + j] * sA[6 * col + j];
+        }
+    }
+    __syncwarp();
+    if (s_fail) {
+        if (lane == 0) L.state[0] = 1;
+        return;
+    }
+    for (int j = 0; j < 6; ++j) {  // L y = b
+        if (lane == 0) sy[j] *= sinv[j];
+        __syncwarp();
+        if (lane > j && lane < 6) sy[lane] -= sA[6 * lane + j] * sy[j];
+        __syncwarp();
+    }
+    for (int j = 5; j >= 0; --j) {  // L^T x = y
+        if (lane == 0) sy[j] *= sinv[j];
+        __syncwarp();
+        if (lane < j) sy[lane] -= sA[6 * j + lane] * sy[j];
+        __syncwarp();
+    }
+    // x = (rho, phi) = sy: T <- exp(x^) T
+    const double p0 = sy[3], p1 = sy[4], p2 = sy[5];
+    double ca, cb, cc;
+    twist_coefs(p0 * p0 + p1 * p1 + p2 * p2, ca, cb, cc);
+    if (lane < 9) {
+        const double P[9] = {0.0, -p2, p1, p2, 0.0, -p0, -p1, p0, 0.0};
+        sP[lane] = P[lane];
+    }
+    if (lane < 16) sT[lane] = L.T[lane];
+    __syncwarp();
+    if (lane < 9) {
+        const int i = lane / 3, k = lane % 3;
+        const double P2 = sP[3 * i] * sP[k] + sP[3 * i + 1] * sP[3 + k] + sP[3 * i + 2] * sP[6 + k];
+        const double I = i == k ? 1.0 : 0.0;
+        sR[lane] = I + ca * sP[lane] + cb * P2;
+        sV[lane] = I + cb * sP[lane] + cc * P2;
+    }
+    __syncwarp();
+    if (lane < 3) st[lane] = sV[3 * lane] * sy[0] + sV[3 * lane + 1] * sy[1] + sV[3 * lane + 2] * sy[2];
+    __syncwarp();
+    if (lane < 12) {
+        const int i = lane >> 2, c = lane & 3;
+        double acc = sR[3 * i] * sT[c] + sR[3 * i + 1] * sT[4 + c] + sR[3 * i + 2] * sT[8 + c];
+        if (c == 3) acc += st[i];
+        L.T[lane] = acc;
+    } else if (lane < 16) {
+        L.T[lane] = lane == 15 ? 1.0 : 0.0;
+    }
+}
+
 // LOOP: the estimate is read from L.T, nothing runs once the loop stopped,
 // and the last CTA to finish completes the Gauss-Newton step.
 template <bool LOOP>
@@ -211,9 +338,18 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x < 8 * kIcpTerms) {
-        const int k = threadIdx.x >> 3, j = threadIdx.x & 7;
+        const int k = threadIdx.x >> 3, j = threadIdx.x & 7, G = (int)gridDim.x;
+        const double *pk = A.partials + k;
         double x = 0.0;
-        for (int g = j; g < (int)gridDim.x; g += 8) x += __ldcg(A.partials + (size_t)g * kIcpTerms + k);
+        int g = j;
+        for (; g + 56 < G; g += 64) {  // 8 loads in flight, added in the same order
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pk + (size_t)(g + 8 * u) * kIcpTerms);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x += v[u];
+        }
+        for (; g < G; g += 8) x += __ldcg(pk + (size_t)g * kIcpTerms);
         s_sum[k][j] = x;
     }
     __syncthreads();
@@ -223,27 +359,8 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
         s_tot[threadIdx.x] = x;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double sum[kIcpTerms];
-    for (int k = 0; k < kIcpTerms; ++k) sum[k] = s_tot[k];
-    double Am[36], b[6], x[6];
-    int k = 0;
-    for (int i = 0; i < 6; ++i)
-        for (int j = i; j < 6; ++j, ++k) Am[6 * i + j] = Am[6 * j + i] = sum[k];
-    for (int i = 0; i < 6; ++i) b[i] = sum[21 + i];
-    for (int i = 0; i < 36; ++i) L.sys[i] = Am[i];
-    for (int i = 0; i < 6; ++i) L.sys[36 + i] = b[i];
-    L.sys[42] = sum[27];
-    L.sys[43] = sum[28];
-    L.state[1] = 0;  // for the next linearisation, which starts after this kernel
-    if (__double2ll_rn(sum[28]) < 6 || !solve6(Am, b, x)) {
-        L.state[0] = 1;
-        return;
-    }
-    double T[16];
-    for (int i = 0; i < 16; ++i) T[i] = L.T[i];
-    apply_twist(x, T);
-    for (int i = 0; i < 16; ++i) L.T[i] = T[i];
+    if (threadIdx.x >= 32) return;
+    icp_step_warp(s_tot, L);
 }
 
 int icp_grid(int num_sms) { return num_sms * 2; }
