@@ -13,9 +13,9 @@ pytestmark = pytest.mark.gpu
 EXACT = Config(n_bisect=30)  # the differentiable forward wants the exact root
 
 
-def prefilled(wl, frames, cfg=EXACT):
+def prefilled(wl, frames, cfg=EXACT, fmt="f32"):
     m = Mapper(cfg)
-    ids = [m.add_volume(v.h, v.r, v.s) for v in wl.volumes]
+    ids = [m.add_volume(v.h, v.r, v.s, fmt) for v in wl.volumes]
     for i in range(frames):
         d, c = wl.frame(i)
         m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
@@ -115,11 +115,13 @@ def check_voxel_gradients(gts, ids, o_gF, what, rel=1e-3, floor=1e-5):
     return nz
 
 
-def test_backward_pose_jacobians_match_oracle_per_pixel():
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_backward_pose_jacobians_match_oracle_per_pixel(fmt):
     """dtau/dxi and dC/dxi pixel by pixel (not summed over the image, where
-    errors of opposite sign could cancel) against the FP64 oracle."""
+    errors of opposite sign could cancel) against the FP64 oracle, in each
+    storage format (the oracle reads the same stored values, decoded)."""
     wl = synth.room_tiles(res=64, pitch=0.008, frames=12, width=160, height=120)
-    m, ids = prefilled(wl, 12)
+    m, ids = prefilled(wl, 12, fmt=fmt)
     random_colours(m, ids, 11)
     ovs = [oracle_volume_from_gpu(m, i, v) for i, v in zip(ids, wl.volumes)]
     T = wl.poses[5]
@@ -141,7 +143,8 @@ def test_backward_pose_jacobians_match_oracle_per_pixel():
     m.close()
 
 
-def test_backward_tsdf_gradients_match_oracle_per_voxel():
+@pytest.mark.parametrize("fmt", ["f32", "f16", "i16"])
+def test_backward_tsdf_gradients_match_oracle_per_voxel(fmt):
     """dL/dF voxel by voxel: (a) depth path, positive upstream weights on
     every safe pixel (the terms of one voxel share a sign, so a relative
     tolerance per voxel is meaningful); (b) colour path, random upstream on
@@ -150,7 +153,7 @@ def test_backward_tsdf_gradients_match_oracle_per_voxel():
     scale fails here even where the image-wide norm would agree."""
     import torch
     wl = synth.room_tiles(res=64, pitch=0.008, frames=12, width=160, height=120)
-    m, ids = prefilled(wl, 12)
+    m, ids = prefilled(wl, 12, fmt=fmt)
     random_colours(m, ids, 12)
     ovs = [oracle_volume_from_gpu(m, i, v) for i, v in zip(ids, wl.volumes)]
     T = wl.poses[5]
