@@ -1098,11 +1098,18 @@ __global__ void __launch_bounds__(kCellMaskCta) cell_masks_kernel(const VolDev *
             const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
             const int cz = packed_bz(it.y) - ((d >> 2) & 1);
             bool own = cx >= 0 && cy >= 0 && cz >= 0;
-            // not the owner when c + e changed for some e < d
-            for (int e = 0; own && e < d; ++e) {
-                const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), w = cz + (e >> 2);
-                if (x < v.nb[0] && y < v.nb[1] && w < v.nb[2])
-                    own = __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) != stamp_id;
+            // not the owner when c + e changed for some e < d (the stamps of
+            // all those bricks are loaded together, then tested)
+            if (own) {
+                unsigned st[7];
+#pragma unroll
+                for (int e = 0; e < 7; ++e) {
+                    const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), w = cz + (e >> 2);
+                    const bool in = e < d && x < v.nb[0] && y < v.nb[1] && w < v.nb[2];
+                    st[e] = in ? __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) : ~stamp_id;
+                }
+#pragma unroll
+                for (int e = 0; e < 7; ++e) own &= st[e] != stamp_id;
             }
             if (own) s_item[atomicAdd(&s_n, 1u)] = make_uint2(it.x, (unsigned)cx | ((unsigned)cy << 10) | ((unsigned)cz << 20));
         }
