@@ -766,16 +766,18 @@ def test_reserved_pinned_buffers_roundtrip():
     m.close()
 
 
-def test_raycast_batch_equals_single_views():
+@pytest.mark.parametrize("fmts", ["f32", "mixed"])
+def test_raycast_batch_equals_single_views(fmts):
     """mv_raycast_batch (every view in one launch) gives each view the maps of
     mv_raycast at that pose, bit for bit, on uneven volumes (view lists,
-    merge across volumes) and on an empty context."""
+    merge across volumes; F32 only, or the three storage formats mixed) and
+    on an empty context."""
     import torch
     wl = synth.uneven_volumes(n_volumes=12, frames=6, edges=(16, 24, 40), pitch_mm=(15.0, 40.0),
                               half_extent=1.6, height_m=2.2, width=160, height=120)
     m = Mapper()
-    for v in wl.volumes:
-        m.add_volume(v.h, v.r, v.s)
+    for k, v in enumerate(wl.volumes):
+        m.add_volume(v.h, v.r, v.s, "f32" if fmts == "f32" else ("f32", "f16", "i16")[k % 3])
     for i in range(4):
         d, c = wl.frame(i)
         m.integrate(dev(d), dev(c), wl.cam, wl.poses[i])
