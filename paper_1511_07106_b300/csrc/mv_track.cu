@@ -243,10 +243,16 @@ __device__ __forceinline__ void icp_step_warp(const double *tot, const IcpLoop &
     }
 }
 
+// One CTA of kIcpCta threads per SM: the partials the last CTA of a device
+// step adds are as few as the SMs, each term's added by kIcpSplit threads.
+constexpr int kIcpCta = 512;
+constexpr int kIcpSplit = 16;
+static_assert(kIcpSplit * kIcpTerms <= kIcpCta, "ICP partial split");
+
 // LOOP: the estimate is read from L.T, nothing runs once the loop stopped,
 // and the last CTA to finish completes the Gauss-Newton step.
 template <bool LOOP>
-__global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
+__global__ void __launch_bounds__(kIcpCta) icp_system_kernel(IcpArgs A, IcpLoop L)
 {
     if (LOOP) {
         if (*(volatile int *)L.state) return;  // written by an earlier launch
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
     // top of the lanes' own sums; B300 runs FP64 at a small fraction of its
     // FP32 rate, and an FP64 tree here took about half the kernel's time),
     // then the 8 warp sums in FP64 in shared memory
-    __shared__ double s_part[8][kIcpTerms];
+    __shared__ double s_part[kIcpCta / 32][kIcpTerms];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kIcpTerms; ++k) {
@@ -325,11 +331,11 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
         A.partials[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = x;
     }
     if (!LOOP) return;
-    // the last CTA to finish adds the partials (8 threads per term, each a
-    // fixed stride of CTAs, then the 8 in order: a fixed order), solves and
-    // updates the estimate
+    // the last CTA to finish adds the partials (kIcpSplit threads per term,
+    // each a fixed stride of CTAs, then those sums in order: a fixed order),
+    // solves and updates the estimate
     __shared__ bool s_last;
-    __shared__ double s_sum[kIcpTerms][8];
+    __shared__ double s_sum[kIcpTerms][kIcpSplit];
     __shared__ double s_tot[kIcpTerms];
     __threadfence();
     __syncthreads();
@@ -337,25 +343,25 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x < 8 * kIcpTerms) {
-        const int k = threadIdx.x >> 3, j = threadIdx.x & 7, G = (int)gridDim.x;
+    if (threadIdx.x < kIcpSplit * kIcpTerms) {
+        const int k = threadIdx.x / kIcpSplit, j = threadIdx.x % kIcpSplit, G = (int)gridDim.x;
         const double *pk = A.partials + k;
         double x = 0.0;
         int g = j;
-        for (; g + 56 < G; g += 64) {  // 8 loads in flight, added in the same order
+        for (; g + 7 * kIcpSplit < G; g += 8 * kIcpSplit) {  // 8 loads in flight, added in the same order
             double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pk + (size_t)(g + 8 * u) * kIcpTerms);
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pk + (size_t)(g + kIcpSplit * u) * kIcpTerms);
 #pragma unroll
             for (int u = 0; u < 8; ++u) x += v[u];
         }
-        for (; g < G; g += 8) x += __ldcg(pk + (size_t)g * kIcpTerms);
+        for (; g < G; g += kIcpSplit) x += __ldcg(pk + (size_t)g * kIcpTerms);
         s_sum[k][j] = x;
     }
     __syncthreads();
     if (threadIdx.x < kIcpTerms) {
         double x = 0.0;
-        for (int j = 0; j < 8; ++j) x += s_sum[threadIdx.x][j];
+        for (int j = 0; j < kIcpSplit; ++j) x += s_sum[threadIdx.x][j];
         s_tot[threadIdx.x] = x;
     }
     __syncthreads();
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(256) icp_system_kernel(IcpArgs A, IcpLoop L)
     icp_step_warp(s_tot, L);
 }
 
-int icp_grid(int num_sms) { return num_sms * 2; }
+int icp_grid(int num_sms) { return num_sms; }
 
 static IcpArgs icp_args(const float *vertex, const float *normal, const mv_intrinsics &K, const double *T_est,
                         const float *mvertex, const float *mnormal, const double *T_model, float dist,
@@ -404,7 +410,7 @@ cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv
                               cudaStream_t s)
 {
     const IcpArgs A = icp_args(vertex, normal, K, T_est, mvertex, mnormal, T_model, dist, cos_min, partials);
-    icp_system_kernel<false><<<grid, 256, 0, s>>>(A, IcpLoop{nullptr, nullptr, nullptr});
+    icp_system_kernel<false><<<grid, kIcpCta, 0, s>>>(A, IcpLoop{nullptr, nullptr, nullptr});
     return cudaGetLastError();
 }
 
@@ -416,7 +422,7 @@ cudaError_t launch_icp_step(const float *vertex, const float *normal, const mv_i
                             cudaStream_t s)
 {
     const IcpArgs A = icp_args(vertex, normal, K, nullptr, mvertex, mnormal, T_model, dist, cos_min, partials);
-    icp_system_kernel<true><<<grid, 256, 0, s>>>(A, IcpLoop{T_dev, sys_dev, state_dev});
+    icp_system_kernel<true><<<grid, kIcpCta, 0, s>>>(A, IcpLoop{T_dev, sys_dev, state_dev});
     return cudaGetLastError();
 }
 
