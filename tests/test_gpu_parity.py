@@ -197,6 +197,50 @@ def test_nondefault_config_lockstep_and_raycast(cfg):
     m.close()
 
 
+@pytest.mark.parametrize("size", [(1920, 1080), (2048, 96)], ids=["1920x1080", "2048x96"])
+def test_large_and_wide_images(size):
+    """Image sizes beyond the benchmark's: 1920x1080 and an extreme 2048x96
+    (a depth-tile pyramid three top-level tiles high).  Lockstep integration
+    against the oracle, the raycast against the oracle on every 13th pixel,
+    and the frame graph equal to separate calls, bit for bit."""
+    W, H = size
+    base = synth.single_volume_128(frames=4, res=64)
+    f = 0.8 * W if H > 200 else 0.25 * W  # the strip sees a band of the scene
+    # an integral principal point: with (W - 1) / 2 the voxel plane through the
+    # optical axis would project onto pixel-rounding ties (flagged, not compared)
+    cam = synth.Camera(f, f, W / 2.0, H / 2.0, W, H)
+    wl = synth.Workload(f"64^3 volume at {W}x{H}", cam, base.scene, base.poses, base.volumes, base.seed)
+    m, vid, worst, flagged = run_lockstep(wl)
+    assert worst <= 1e-4 and flagged < 0.01
+    (vs,) = wl.volumes
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    T = wl.poses[3]
+    g = gpu_maps(m.raycast(cam, T))
+    idx = np.arange(0, W * H, 13)
+    mask = np.zeros(W * H, bool)
+    mask[idx] = True
+    o = oracle.raycast([ov], cam, T, ocfg(m.config), ids=[vid], pixels=idx)
+    compare_raycast(g, o, cam, T, vs.s, mask=mask.reshape(H, W), require_hits=0.05)
+    # the same frames through the frame graph on a second mapper
+    b = Mapper()
+    bid = b.add_volume(vs.h, vs.r, vs.s)
+    maps = b.alloc_maps(cam)
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        b.frame(dev(d), dev(c), cam, wl.poses[i], out=maps)
+    fb = gpu_maps(maps)
+    fa = gpu_maps(m.raycast(cam, wl.poses[-1]))
+    for k in ("depth", "normal", "rgba", "vol_id"):
+        np.testing.assert_array_equal(fa[k], fb[k])
+    Fa, Wa, Ca = m.read_decoded(vid)
+    Fb, Wb, Cb = b.read_decoded(bid)
+    np.testing.assert_array_equal(Fa, Fb)
+    np.testing.assert_array_equal(Wa, Wb)
+    np.testing.assert_array_equal(Ca, Cb)
+    m.close()
+    b.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
