@@ -521,13 +521,16 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     const int gx = bx * kBrick + lx0, gy = by * kBrick + ly, gz = bz * kBrick + lz;
     // voxel position relative to the camera, in voxel units: exact lattice
     // difference minus the camera's sub-voxel fraction
-    const float rx = (float)(v.h[0] + gx - fr.cam_int[0]) - fr.cam_frac[0];
+    const int ix = v.h[0] + gx - fr.cam_int[0];
     const float ry = (float)(v.h[1] + gy - fr.cam_int[1]) - fr.cam_frac[1];
     const float rz = (float)(v.h[2] + gz - fr.cam_int[2]) - fr.cam_frac[2];
-    // camera coordinates p_c = R^T (p_w - t)
-    const float X0 = P.Rf[0] * rx + P.Rf[3] * ry + P.Rf[6] * rz;
-    const float Y0 = P.Rf[1] * rx + P.Rf[4] * ry + P.Rf[7] * rz;
-    const float Z0 = P.Rf[2] * rx + P.Rf[5] * ry + P.Rf[8] * rz;
+    // camera coordinates p_c = R^T (p_w - t), every voxel from its own exact
+    // lattice offset by the same expression: a voxel gets the same value in
+    // every volume of its pitch, whichever group of 4 holds it (the tiling
+    // invariance; a per-group increment X0 + j R would round differently)
+    const float KX = fmaf(P.Rf[3], ry, P.Rf[6] * rz);
+    const float KY = fmaf(P.Rf[4], ry, P.Rf[7] * rz);
+    const float KZ = fmaf(P.Rf[5], ry, P.Rf[8] * rz);
     const float mu = P.trunc_vox, inv_mu = 1.0f / P.trunc_vox;
     const bool row_in = gy < v.r[1] && gz < v.r[2];
     u.upd = u.band = u.inside = 0u;
@@ -539,9 +542,10 @@ __device__ __forceinline__ void project_voxels(const VolDev &v, const VolFrame &
     bool okj[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float X = X0 + (float)j * P.Rf[0];
-        const float Y = Y0 + (float)j * P.Rf[1];
-        const float Z = Z0 + (float)j * P.Rf[2];
+        const float rxj = (float)(ix + j) - fr.cam_frac[0];
+        const float X = fmaf(P.Rf[0], rxj, KX);
+        const float Y = fmaf(P.Rf[1], rxj, KY);
+        const float Z = fmaf(P.Rf[2], rxj, KZ);
         const bool in = row_in && gx + j < v.r[0];
         if (in) u.inside |= 1u << j;
         const float iz = __fdividef(1.0f, Z);  // ~2 ulp; decisions near pixel edges are margins

@@ -241,6 +241,64 @@ def test_large_and_wide_images(size):
     b.close()
 
 
+@pytest.mark.parametrize("size,split,res", [((160, 120), 12, 122), ((16, 8), 16, 98)],
+                         ids=["1728-volumes-160x120", "4096-volumes-16x8"])
+def test_many_volumes_equal_one_volume(size, split, res):
+    """1728 or 4096 volumes (tiles of one volume, two-voxel overlap): more
+    than the 256 the frame set-up ranks nearest first (the unranked view
+    list); at 16x8 with 16x8-pixel CTA tiles one CTA sees every volume in
+    view, hundreds of them holding surface, more than the 256 candidates its
+    shared-memory list holds (the CTA falls back to the view list).  Voxels
+    and maps equal the single volume's bit for bit (tiling invariance, Sec.
+    Comparison to KinectFusion)."""
+    W, H = size
+    base = synth.single_volume_128(frames=4, res=res)
+    cam = synth.Camera(W / 2.0, W / 2.0, W / 2.0, H / 2.0, W, H)
+    wl = synth.Workload(f"{res}^3 volume at {W}x{H}", cam, base.scene, base.poses, base.volumes, base.seed)
+    tl = synth.tiled(wl, split)
+    assert len(tl.volumes) == split ** 3
+    (vs,) = wl.volumes
+    single, tiles = Mapper(), Mapper()
+    tiles.set_tuning(0, 8)  # 16x8-pixel CTA tiles
+    sid = single.add_volume(vs.h, vs.r, vs.s)
+    tids = [tiles.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        single.integrate(dev(d), dev(c), cam, wl.poses[i])
+        tiles.integrate(dev(d), dev(c), cam, wl.poses[i])
+    Fs, Ws, Cs = single.read_decoded(sid)
+    assert (Ws > 0).mean() > 0.01
+    for t, tid in zip(tl.volumes, tids):
+        F, Wt, col = tiles.read_decoded(tid)
+        o = [t.h[a] - vs.h[a] for a in range(3)]
+        sl = (slice(o[2], o[2] + t.r[2]), slice(o[1], o[1] + t.r[1]), slice(o[0], o[0] + t.r[0]))
+        np.testing.assert_array_equal(F, Fs[sl])
+        np.testing.assert_array_equal(Wt, Ws[sl])
+        np.testing.assert_array_equal(col, Cs[sl])
+    for T in (wl.poses[1], wl.poses[3]):
+        a = gpu_maps(single.raycast(cam, T))
+        b = gpu_maps(tiles.raycast(cam, T))
+        assert (a["depth"] > 0).mean() > 0.3
+        for k in ("depth", "normal", "rgba"):
+            np.testing.assert_array_equal(a[k], b[k])
+    single.close()
+    tiles.close()
+
+
+def test_volume_capacity():
+    """4096 volumes fit a context; one more is refused with a status, and a
+    removal frees a slot again."""
+    m = Mapper()
+    ids = [m.add_volume((3 * k, 0, 0), (2, 2, 2), 0.01) for k in range(4096)]
+    with pytest.raises(MVError) as e:
+        m.add_volume((0, 5, 0), (2, 2, 2), 0.01)
+    assert "CAPACITY" in str(e.value) or "volumes" in str(e.value)
+    m.remove_volume(ids[100])
+    m.add_volume((0, 5, 0), (2, 2, 2), 0.01)
+    assert len(m.volumes()) == 4096
+    m.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
