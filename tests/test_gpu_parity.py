@@ -299,6 +299,38 @@ def test_volume_capacity():
     m.close()
 
 
+def test_far_from_the_origin():
+    """The single-volume workload moved by (40000, -30000, 20000) voxels
+    (about 0.9, 0.7 and 0.5 km) with its camera and scene: voxel positions
+    are exact lattice differences from the camera's lattice point plus its
+    sub-voxel fraction (the camera split in FP64), so lockstep integration and
+    the raycast match the oracle, which works with the world coordinates in
+    FP64, as they do at the origin."""
+    base = synth.single_volume_128(frames=6, res=64)
+    (vs,) = base.volumes
+    N = np.array([40000, -30000, 20000])
+    off = N * vs.s
+    sc = base.scene
+    scene = synth.Scene(planes=np.array([[*p[:3], p[3] + np.dot(p[:3], off)] for p in sc.planes]),
+                        spheres=np.array([[*(p[:3] + off), p[3]] for p in sc.spheres]),
+                        boxes=np.array([[*(b[:3] + off), *(b[3:] + off)] for b in sc.boxes]))
+    poses = []
+    for T in base.poses:
+        T = T.copy()
+        T[:3, 3] += off
+        poses.append(T)
+    far = synth.VolumeSpec(tuple(int(a) for a in np.array(vs.h) + N), vs.r, vs.s)
+    wl = synth.Workload("64^3 volume 1 km from the origin", base.cam, scene, poses, [far], base.seed)
+    m, vid, worst, flagged = run_lockstep(wl)
+    assert worst <= 1e-4 and flagged < 0.01
+    ov = oracle_volume_from_gpu(m, vid, far)
+    for T in (poses[2], poses[5]):
+        g = gpu_maps(m.raycast(wl.cam, T))
+        o = oracle.raycast([ov], wl.cam, T, ocfg(m.config), ids=[vid])
+        compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.3)
+    m.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
