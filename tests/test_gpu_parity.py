@@ -331,6 +331,52 @@ def test_far_from_the_origin():
     m.close()
 
 
+@pytest.mark.parametrize("size", [(1, 1), (1, 37), (53, 1), (3, 2)], ids=["1x1", "1x37", "53x1", "3x2"])
+def test_tiny_images(size):
+    """Images of one pixel, one column, one row and 3x2 (a depth-tile pyramid
+    of a single partial tile, raycast tiles mostly outside the image):
+    lockstep integration, the raycast against the oracle, and the frame graph
+    equal to separate calls."""
+    W, H = size
+    base = synth.single_volume_128(frames=6, res=32)
+    cam = synth.Camera(60.0, 60.0, (W - 1) / 2.0 + 0.25, (H - 1) / 2.0 - 0.125, W, H)
+    wl = synth.Workload(f"32^3 volume at {W}x{H}", cam, base.scene, base.poses, base.volumes, base.seed)
+    m, vid, worst, flagged = run_lockstep(wl)
+    assert worst <= 1e-4
+    assert m.read_decoded(vid)[1].max() > 0  # something was integrated
+    (vs,) = wl.volumes
+    # the raycast of a volume built from 160x120 frames, at the tiny image
+    full = synth.Workload("32^3 volume", synth.Camera(100.0, 100.0, 80.0, 60.0, 160, 120), base.scene,
+                          base.poses, base.volumes, base.seed)
+    r = Mapper()
+    rid = r.add_volume(vs.h, vs.r, vs.s)
+    for i in range(full.n_frames):
+        d, c = full.frame(i)
+        r.integrate(dev(d), dev(c), full.cam, full.poses[i])
+    ov = oracle_volume_from_gpu(r, rid, vs)
+    hits = 0
+    for T in wl.poses:
+        g = gpu_maps(r.raycast(cam, T))
+        o = oracle.raycast([ov], cam, T, ocfg(r.config), ids=[rid])
+        compare_raycast(g, o, cam, T, vs.s, require_hits=0.0)
+        hits += int((g["depth"] > 0).sum())
+    assert hits > 0
+    r.close()
+    b = Mapper()
+    bid = b.add_volume(vs.h, vs.r, vs.s)
+    maps = b.alloc_maps(cam)
+    for i in range(wl.n_frames):
+        d, c = wl.frame(i)
+        b.frame(dev(d), dev(c), cam, wl.poses[i], out=maps)
+    fa = gpu_maps(m.raycast(cam, wl.poses[-1]))
+    fb = gpu_maps(maps)
+    for k in ("depth", "normal", "rgba", "vol_id"):
+        np.testing.assert_array_equal(fa[k], fb[k])
+    np.testing.assert_array_equal(m.read_decoded(vid)[0], b.read_decoded(bid)[0])
+    m.close()
+    b.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
