@@ -241,9 +241,10 @@ def test_large_and_wide_images(size):
     b.close()
 
 
-@pytest.mark.parametrize("size,split,res", [((160, 120), 12, 122), ((16, 8), 16, 98)],
-                         ids=["1728-volumes-160x120", "4096-volumes-16x8"])
-def test_many_volumes_equal_one_volume(size, split, res):
+@pytest.mark.parametrize("size,split,res,fmt", [((160, 120), 12, 122, "f32"), ((16, 8), 16, 98, "f32"),
+                                                ((160, 120), 12, 122, "f16"), ((160, 120), 12, 122, "i16")],
+                         ids=["1728-volumes-160x120", "4096-volumes-16x8", "1728-volumes-f16", "1728-volumes-i16"])
+def test_many_volumes_equal_one_volume(size, split, res, fmt):
     """1728 or 4096 volumes (tiles of one volume, two-voxel overlap): more
     than the 256 the frame set-up ranks nearest first (the unranked view
     list); at 16x8 with 16x8-pixel CTA tiles one CTA sees every volume in
@@ -260,8 +261,8 @@ def test_many_volumes_equal_one_volume(size, split, res):
     (vs,) = wl.volumes
     single, tiles = Mapper(), Mapper()
     tiles.set_tuning(0, 8)  # 16x8-pixel CTA tiles
-    sid = single.add_volume(vs.h, vs.r, vs.s)
-    tids = [tiles.add_volume(t.h, t.r, t.s) for t in tl.volumes]
+    sid = single.add_volume(vs.h, vs.r, vs.s, fmt)
+    tids = [tiles.add_volume(t.h, t.r, t.s, fmt) for t in tl.volumes]
     for i in range(wl.n_frames):
         d, c = wl.frame(i)
         single.integrate(dev(d), dev(c), cam, wl.poses[i])
