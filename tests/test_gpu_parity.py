@@ -378,6 +378,47 @@ def test_tiny_images(size):
     b.close()
 
 
+class _CorruptedFrames:
+    """A workload whose depth frames have a tenth of their pixels replaced by
+    invalid or extreme values."""
+
+    def __init__(self, wl, z_min, z_max, seed=7):
+        self.wl, self.cam, self.poses, self.volumes = wl, wl.cam, wl.poses, wl.volumes
+        self.n_frames = wl.n_frames
+        self.bad = np.array([0.0, -1.0, np.nan, np.inf, -np.inf, 1e30, z_min * 0.999, min(z_max * 1.001, 1e30)],
+                            np.float32)
+        self.seed = seed
+
+    def frame(self, i):
+        d, c = self.wl.frame(i)
+        rng = np.random.default_rng(self.seed + i)
+        sel = rng.random(d.shape) < 0.1
+        d = d.copy()
+        d[sel] = rng.choice(self.bad, size=int(sel.sum()))
+        return d, c
+
+
+@pytest.mark.parametrize("zr", [(0.0, float("inf")), (0.5, 3.0)], ids=["default-range", "range-0.5-3"])
+def test_invalid_and_extreme_depths(zr):
+    """A tenth of every frame's pixels set to 0, -1, NaN, +-inf, 1e30 and
+    values just outside [z_min, z_max]: a depth counts when it is > 0 and
+    inside the range (so +inf and 1e30 count when z_max is infinite, as free
+    space along their rays); lockstep integration and the raycast against
+    the oracle."""
+    cfg = Config(z_min=zr[0], z_max=zr[1])
+    base = synth.single_volume_128(frames=5, res=48)
+    wl = _CorruptedFrames(base, max(zr[0], 1e-3), zr[1])
+    m, vid, worst, flagged = run_lockstep(wl, cfg=cfg)
+    assert worst <= 1e-4 and flagged < 0.01
+    (vs,) = wl.volumes
+    ov = oracle_volume_from_gpu(m, vid, vs)
+    for T in (wl.poses[1], wl.poses[4]):
+        g = gpu_maps(m.raycast(wl.cam, T))
+        o = oracle.raycast([ov], wl.cam, T, ocfg(cfg), ids=[vid])
+        compare_raycast(g, o, wl.cam, T, vs.s, require_hits=0.2)
+    m.close()
+
+
 def test_empty_context_raycast_is_all_miss():
     cam = synth.Camera(20.0, 20.0, 9.5, 7.5, 20, 15)
     m = Mapper()
