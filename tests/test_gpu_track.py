@@ -29,6 +29,9 @@ def test_depth_maps_match_oracle():
     m = Mapper()
     d, _ = wl.frame(2)
     d[::17, ::5] = 0.0
+    d[3::23, 1::7] = np.nan  # invalid depths of other kinds: no vertex, no normal
+    d[5::29, 2::3] = -1.0
+    d[7::31, 4::11] = -np.inf
     for T in (None, wl.poses[2]):
         gv, gn = (t.cpu().numpy().astype(np.float64) for t in m.depth_to_maps(dev(d), wl.cam, T))
         ov, on = oracle.depth_maps(d, wl.cam, T)
