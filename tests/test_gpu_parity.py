@@ -526,6 +526,54 @@ def test_plane_filled_volume_raycast_is_exact():
     m.close()
 
 
+def test_sphere_filled_volume_outside_and_inside():
+    """A sphere's signed distance written into the volume (radius 0.4 m,
+    1.6 cm voxels).  From outside: the hit within the trilinear error bound
+    of the analytic ray--sphere intersection (3 s^2 / (8 rho) over the incidence
+    cosine, plus the refinement)
+    and equal to the oracle's raycast of the same volume.  From inside: every
+    ray's first valid sample is <= 0 and it leaves through a -/+ crossing, so
+    no pixel has a hit (Sec. Raycasting: only a +/- change of sign is a
+    surface), on the GPU and in the oracle."""
+    m = Mapper()
+    h, r, s = (-40, -40, -40), (80, 80, 80), 0.016
+    vid = m.add_volume(h, r, s)
+    c, rho, mu = np.array([0.02, -0.03, 0.01]), 0.4, 4 * s
+    z, y, x = np.meshgrid(*[np.arange(k) for k in r[::-1]], indexing="ij")
+    p = np.stack([(h[0] + x) * s, (h[1] + y) * s, (h[2] + z) * s], -1)
+    F = np.clip((np.linalg.norm(p - c, axis=-1) - rho) / mu, -1, 1)
+    m.write_decoded(vid, F, np.ones_like(F))
+    ov = oracle_volume_from_gpu(m, vid, synth.VolumeSpec(h, r, s))
+    cam = synth.Camera(40.0, 40.0, 31.5, 23.5, 64, 48)
+    # outside
+    eye = np.array([0.1, -0.55, 0.45])
+    T = synth.look_at(eye, c + np.array([0.03, 0.0, -0.02]))
+    g = gpu_maps(m.raycast(cam, T))
+    o_ray, d = synth.pixel_rays(cam, T)
+    oc = o_ray - c
+    a2, b2, c2 = np.sum(d * d, -1), 2 * (d @ oc), oc @ oc - rho * rho
+    disc = b2 * b2 - 4 * a2 * c2
+    tau = np.where(disc > 0, (-b2 - np.sqrt(np.maximum(disc, 0))) / (2 * a2), np.nan)
+    hit = np.isfinite(tau)
+    cosi = np.abs(np.sum((o_ray + np.nan_to_num(tau)[..., None] * d - c) / rho * d, -1)) / np.linalg.norm(d, axis=-1)
+    safe = hit & (cosi > 0.3)  # away from grazing rays
+    assert safe.mean() > 0.2 and np.all(g["depth"][safe] > 0)
+    # trilinear interpolation of the distance errs by at most 3 s^2 / (8 rho) (s^2 / 8 times
+    # the curvature 1 / rho on each axis), a depth error of that over the incidence cosine;
+    # plus the refinement (0.002 voxel)
+    err = np.abs(g["depth"] - np.nan_to_num(tau)) * np.linalg.norm(d, axis=-1) / s
+    bound = 3 * s / (8 * rho) / np.maximum(cosi, 1e-9) + 0.002
+    assert np.all(err[safe] <= bound[safe]), float((err - bound)[safe].max())
+    o = oracle.raycast([ov], cam, T, ocfg(m.config), ids=[vid])
+    compare_raycast(g, o, cam, T, s, require_hits=0.2)
+    # inside, near the centre
+    T = synth.look_at(c + np.array([0.05, 0.02, -0.03]), c + np.array([0.5, 0.3, 0.1]))
+    g = gpu_maps(m.raycast(cam, T))
+    o = oracle.raycast([ov], cam, T, ocfg(m.config), ids=[vid])
+    assert not (g["depth"] > 0).any() and not (o["depth"] > 0).any()
+    m.close()
+
+
 def test_swap_out_in_roundtrip():
     wl = synth.single_volume_128(frames=6, res=34)
     tl = synth.tiled(wl, 2)
