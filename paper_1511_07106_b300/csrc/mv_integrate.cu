@@ -645,6 +645,7 @@ __device__ __forceinline__ uint32_t blend_rgba(uint32_t old, const uint8_t *__re
 struct MaskOut {
     uint2 *list;
     unsigned *count;
+    unsigned stamp_id;
 };
 
 // A CTA collects the bricks whose voxel masks it changed in shared memory and
@@ -807,8 +808,9 @@ __device__ __forceinline__ void integrate_brick(const VolDev &v, const VolFrame 
     const int brick_any = __syncthreads_or(u.upd != 0u ? 1 : 0);
     const int brick_pos = __syncthreads_and(all_pos ? 1 : 0);
     if (track && cb.flag[parity]) {
-        // the brick is listed for the cell-mask refresh
+        // the brick is stamped and listed for the cell-mask refresh
         if (t == 0) {
+            v.stamp[b] = mo.stamp_id;
             if (cb.n == kChgBuf) flush_changed(cb, mo);
             cb.items[cb.n++] = item;
         }
@@ -1068,40 +1070,75 @@ __global__ void __launch_bounds__(256) cell_flags_kernel(const VolDev *__restric
 }
 
 // After an integration, for volumes with cell masks: the integration listed
-// the bricks whose voxel masks changed, and every cell brick c that reads one
-// of them (c = b - d, d in {0,1}^3) gets its cell masks and its flag
-// recomputed.  Each (changed brick, d) pair refreshes its cell brick with 8
-// threads (one per slice): a cell brick fed by several changed bricks is
-// refreshed by each of them with the same values, and its flag changes by an
-// atomic that tells exactly one of them (update_cell_flag), so no pair waits
-// on another.
+// the bricks whose voxel masks changed (and stamped them with stamp_id);
+// every cell brick c that reads one of them (c = b - d, d in {0,1}^3) gets its
+// cell masks and its flag recomputed, once: by the smallest d for which
+// c + d changed.  Each CTA first gives one thread to each of kCellMaskPairs
+// (changed brick, d) pairs and collects the cell bricks they own in shared
+// memory, then refreshes those with 8 threads each (one per slice), so that
+// pairs owned elsewhere hold no lanes during the refresh.
 constexpr int kCellMaskCta = 256;
+constexpr int kCellMaskPairs = 64;
 __global__ void __launch_bounds__(kCellMaskCta) cell_masks_kernel(const VolDev *__restrict__ vols,
                                                                 const uint2 *__restrict__ changed,
-                                                                const unsigned *__restrict__ counter)
+                                                                const unsigned *__restrict__ counter,
+                                                                unsigned stamp_id)
 {
-    const unsigned long long n = 64ull * (*counter);  // 8 offsets x 8 slices per changed brick
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    __shared__ uint2 s_item[kCellMaskPairs];  // (table slot, packed cell brick) owned by this CTA
+    __shared__ unsigned s_n;
+    const unsigned long long n = 8ull * (*counter);
     const int t = threadIdx.x, z = t & 7;
     const unsigned group = 0xFFu << (t & 24);  // the 8 slice threads of one cell brick
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + t; i < n; i += stride) {
-        const uint2 it = changed[i >> 6];
-        const int d = (int)((i >> 3) & 7);
-        const VolDev &v = vols[it.x];
-        const int cx = (int)(it.y & 1023u) - (d & 1);
-        const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
-        const int cz = packed_bz(it.y) - ((d >> 2) & 1);
-        if (cx < 0 || cy < 0 || cz < 0) continue;  // uniform over the 8 slice threads
-        const long long c = ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
-        const ulonglong2 mk = cell_mask_slice(v, cx, cy, cz, z);
-        v.cmask[c * 8 + z] = mk;
-        unsigned long long nz = mk.y;
-        nz |= __shfl_xor_sync(group, nz, 1);
-        nz |= __shfl_xor_sync(group, nz, 2);
-        nz |= __shfl_xor_sync(group, nz, 4);
-        int ch = z == 0 ? update_cell_flag(v, cx, cy, cz, nz == 0ull) : 0;
-        ch = __shfl_sync(group, ch, t & 24);
-        if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, z, 8);
+    for (unsigned long long base = (unsigned long long)blockIdx.x * kCellMaskPairs; base < n;
+         base += (unsigned long long)gridDim.x * kCellMaskPairs) {
+        if (t == 0) s_n = 0;
+        __syncthreads();
+        const unsigned long long i = base + t;
+        if (t < kCellMaskPairs && i < n) {
+            const uint2 it = changed[i >> 3];
+            const int d = (int)(i & 7);
+            const VolDev &v = vols[it.x];
+            const int cx = (int)(it.y & 1023u) - (d & 1);
+            const int cy = (int)((it.y >> 10) & 1023u) - ((d >> 1) & 1);
+            const int cz = packed_bz(it.y) - ((d >> 2) & 1);
+            bool own = cx >= 0 && cy >= 0 && cz >= 0;
+            // not the owner when c + e changed for some e < d (the stamps of
+            // all those bricks are loaded together, then tested)
+            if (own) {
+                unsigned st[7];
+#pragma unroll
+                for (int e = 0; e < 7; ++e) {
+                    const int x = cx + (e & 1), y = cy + ((e >> 1) & 1), w = cz + (e >> 2);
+                    const bool in = e < d && x < v.nb[0] && y < v.nb[1] && w < v.nb[2];
+                    st[e] = in ? __ldg(v.stamp + ((long long)w * v.nb[1] + y) * v.nb[0] + x) : ~stamp_id;
+                }
+#pragma unroll
+                for (int e = 0; e < 7; ++e) own &= st[e] != stamp_id;
+            }
+            if (own) s_item[atomicAdd(&s_n, 1u)] = make_uint2(it.x, (unsigned)cx | ((unsigned)cy << 10) | ((unsigned)cz << 20));
+        }
+        __syncthreads();
+        const unsigned m = s_n;
+        for (unsigned k = (unsigned)t >> 3; k < m; k += kCellMaskCta / 8) {
+            const uint2 it = s_item[k];
+            const VolDev &v = vols[it.x];
+            const int cx = (int)(it.y & 1023u), cy = (int)((it.y >> 10) & 1023u), cz = (int)(it.y >> 20);
+            const long long c = ((long long)cz * v.nb[1] + cy) * v.nb[0] + cx;
+            const ulonglong2 mk = cell_mask_slice(v, cx, cy, cz, z);
+            v.cmask[c * 8 + z] = mk;
+            // the cell brick can be stepped over when none of its cells has an
+            // observed corner with F <= 0 (OR of the 8 slices' N rows)
+            unsigned long long nz = mk.y;
+            nz |= __shfl_xor_sync(group, nz, 1);
+            nz |= __shfl_xor_sync(group, nz, 2);
+            nz |= __shfl_xor_sync(group, nz, 4);
+            int ch = z == 0 ? update_cell_flag(v, cx, cy, cz, nz == 0ull) : 0;
+            // a change of the super count to or from zero: the 8 slice threads
+            // share the neighbour updates
+            ch = __shfl_sync(group, ch, t & 24);
+            if (ch) super_occupancy_changed(v, cx / kSuper, cy / kSuper, cz / kSuper, ch > 0, z, 8);
+        }
+        __syncthreads();
     }
 }
 
@@ -1318,10 +1355,10 @@ cudaError_t launch_depth_max(const float *depth, const FrameParams &P, unsigned 
 cudaError_t launch_integrate(const VolDev *vols, const VolFrame *vfs, const uint2 *list,
                              const unsigned *counter, const FrameParams &P, const float *depth,
                              const uint8_t *rgb, Stats *stats, int grid, cudaStream_t s,
-                             uint2 *changed, unsigned *chg_count)
+                             uint2 *changed, unsigned *chg_count, unsigned stamp_id)
 {
     integrate_kernel<<<grid, 128, 0, s>>>(vols, vfs, list, counter, P, depth, rgb, stats,
-                                          MaskOut{changed, chg_count});
+                                          MaskOut{changed, chg_count, stamp_id});
     return cudaGetLastError();
 }
 
@@ -1378,9 +1415,9 @@ cudaError_t launch_cell_flags(const VolDev *vols, const uint2 *list, const unsig
 }
 
 cudaError_t launch_cell_masks(const VolDev *vols, const uint2 *changed, const unsigned *counter,
-                              int num_sms, cudaStream_t s)
+                              unsigned stamp_id, int num_sms, cudaStream_t s)
 {
-    cell_masks_kernel<<<num_sms * 8, kCellMaskCta, 0, s>>>(vols, changed, counter);
+    cell_masks_kernel<<<num_sms * 8, kCellMaskCta, 0, s>>>(vols, changed, counter, stamp_id);
     return cudaGetLastError();
 }
 
@@ -1401,7 +1438,7 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
                             cudaGraphNode_t dep, const VolDev *vols, int nvol, VolFrame *vf,
                             const FrameParams &P, long long total, long long total_sup, uint2 *slist,
                             uint2 *list, unsigned *counter, const float *depth, const uint8_t *rgb, Stats *stats,
-                            int grid_int, int num_sms, VisList *vis, uint2 *changed,
+                            int grid_int, int num_sms, VisList *vis, uint2 *changed, unsigned stamp_id,
                             unsigned *pyr)
 {
     NodeArgs<const VolDev *, int, FrameParams, VolFrame *, unsigned *, VisList *> a0(vols, nvol, P, vf, counter,
@@ -1433,11 +1470,11 @@ cudaError_t graph_integrate(cudaGraph_t g, cudaGraphExec_t exec, cudaGraphNode_t
     if (e != cudaSuccess) return e;
     NodeArgs<const VolDev *, const VolFrame *, const uint2 *, const unsigned *, FrameParams, const float *,
              const uint8_t *, Stats *, MaskOut>
-        a2(vols, vf, list, counter, P, depth, rgb, stats, MaskOut{changed, counter + 2});
+        a2(vols, vf, list, counter, P, depth, rgb, stats, MaskOut{changed, counter + 2, stamp_id});
     e = graph_node(g, exec, &nodes[4], slist ? nodes[3] : nodes[2],
                    a2.params((const void *)integrate_kernel, grid_int, 128));
     if (e != cudaSuccess) return e;
-    NodeArgs<const VolDev *, const uint2 *, const unsigned *> a3(vols, changed, counter + 2);
+    NodeArgs<const VolDev *, const uint2 *, const unsigned *, unsigned> a3(vols, changed, counter + 2, stamp_id);
     return graph_node(g, exec, &nodes[5], nodes[4], a3.params((const void *)cell_masks_kernel, num_sms * 8, kCellMaskCta));
 }
 

@@ -20,7 +20,10 @@
 //   cmask, 8 x (u64 V, u64 N) per brick: for the trilinear cell whose lower
 //          corner is voxel (x, y, z) of the brick, bit 8 y + x of V is set when
 //          all 8 corners are observed and of N when some corner is observed
-//          with F <= 0 (corners beyond the brick come from its neighbours).
+//          with F <= 0 (corners beyond the brick come from its neighbours);
+//   stamp, 1 x u32 per brick: the id of the last integration call whose work
+//          list held the brick (lets the cell-mask refresh visit each cell
+//          brick once).
 // The raycast decides most samples from one 16-byte cmask load: a cell with
 // N clear cannot end a bracket, and its V bit gives the march state.  With
 // masks, a cell brick carries kCellSkip exactly when none of its cells has N
@@ -73,6 +76,7 @@ struct VolDev {
     unsigned *sup;     // per super brick: counts of non-skippable cell bricks and neighbours (may be null)
     unsigned long long *vmask;  // per-voxel masks, 16 x u64 per brick (may be null)
     ulonglong2 *cmask;          // per-cell masks, 8 x (V, N) per brick (may be null)
+    unsigned *stamp;            // per brick: id of the last integration that listed it (may be null)
     int h[3];          // lattice offset h_t
     int r[3];          // voxels per axis h_r
     int nb[3];         // bricks per axis
@@ -145,9 +149,9 @@ inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
     return super_offset(nbricks) + 4 * (size_t)nsuper;
 }
 
-// Mask allocation of a volume: vmask (128 B per brick), then cmask (128 B per
-// brick).
-constexpr size_t kMaskBytesPerBrick = 256;
+// Mask allocation of a volume: vmask (128 B per brick), cmask (128 B per
+// brick), then the listing stamps (4 B per brick).
+constexpr size_t kMaskBytesPerBrick = 260;
 inline size_t mask_alloc_bytes(long long nbricks) { return (size_t)nbricks * kMaskBytesPerBrick; }
 
 // Per-frame pyramids of the largest and of the smallest accepted depth over

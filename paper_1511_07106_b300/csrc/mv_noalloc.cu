@@ -17,7 +17,7 @@ cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const Frame
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
-                             cudaStream_t, uint2 *, unsigned *);
+                             cudaStream_t, uint2 *, unsigned *, unsigned);
 int integrate_occupancy_grid(int num_sms);
 bool valid_config(const mv_config &c);
 }  // namespace mv
@@ -178,7 +178,7 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
                           nullptr, 0) !=
         cudaSuccess)
         return MV_ERR_CUDA;
-    if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s, nullptr, nullptr) != cudaSuccess)
+    if (launch_integrate(vdev, vframe, list, counter, P, depth, rgb, nullptr, grid, s, nullptr, nullptr, 0u) != cudaSuccess)
         return MV_ERR_CUDA;
     return MV_OK;
 }

@@ -33,11 +33,11 @@ cudaError_t launch_brick_list(const VolDev *, int, const VolFrame *, const Frame
 cudaError_t launch_depth_max(const float *, const FrameParams &, unsigned *, int, cudaStream_t, unsigned *);
 cudaError_t launch_integrate(const VolDev *, const VolFrame *, const uint2 *, const unsigned *,
                              const FrameParams &, const float *, const uint8_t *, Stats *, int,
-                             cudaStream_t, uint2 *, unsigned *);
+                             cudaStream_t, uint2 *, unsigned *, unsigned);
 cudaError_t launch_brick_flags(const VolDev &, int, cudaStream_t);
 cudaError_t launch_mask_rebuild(const VolDev &, int, cudaStream_t);
 cudaError_t launch_cell_flags(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
-cudaError_t launch_cell_masks(const VolDev *, const uint2 *, const unsigned *, int, cudaStream_t);
+cudaError_t launch_cell_masks(const VolDev *, const uint2 *, const unsigned *, unsigned, int, cudaStream_t);
 cudaError_t launch_raycast(const VolDev *, const VolFrame *, int, const FrameParams &, float *,
                            float *, uint8_t *, float *, int *, int, Stats *, int, cudaStream_t,
                            const VisList *);
@@ -69,7 +69,7 @@ constexpr int kIcpTerms = 29;
 cudaError_t graph_integrate(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t[6], cudaGraphNode_t,
                             const VolDev *, int, VolFrame *, const FrameParams &, long long, long long, uint2 *,
                             uint2 *, unsigned *, const float *, const uint8_t *, Stats *, int, int, VisList *,
-                            uint2 *, unsigned *);
+                            uint2 *, unsigned, unsigned *);
 cudaError_t graph_raycast(cudaGraph_t, cudaGraphExec_t, cudaGraphNode_t *, cudaGraphNode_t,
                           const VolDev *, int, VolFrame *, const FrameParams &, float *, float *, uint8_t *,
                           float *, int *, Stats *, int, VisList *);
@@ -111,6 +111,7 @@ struct mv_ctx {
     int ctas_per_sm = 0;
     std::map<int, Volume *> vols;
     int next_id = 0;
+    unsigned integrations = 0;  // id of the last integration call (brick listing stamps)
     cudaStream_t swap_stream = nullptr;
     cudaEvent_t last_event = nullptr;
     bool last_recorded = false;
@@ -296,6 +297,9 @@ VolDev make_voldev(const Volume &v)
     d.vmask = v.d_mask ? reinterpret_cast<unsigned long long *>(v.d_mask) : nullptr;
     d.cmask = v.d_mask ? reinterpret_cast<ulonglong2 *>(reinterpret_cast<uint8_t *>(v.d_mask) +
                                                          (size_t)v.nbricks * 128)
+                       : nullptr;
+    d.stamp = v.d_mask ? reinterpret_cast<unsigned *>(reinterpret_cast<uint8_t *>(v.d_mask) +
+                                                      (size_t)v.nbricks * 256)
                        : nullptr;
     for (int a = 0; a < 3; ++a) d.nsb[a] = v.nsb[a];
     for (int a = 0; a < 3; ++a) {
@@ -1131,6 +1135,7 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     const bool two_level = vis && two_level_list(c);
     st = ensure_pyramid(c, K);
     if (st) return st;
+    const unsigned stamp = ++c->integrations;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_SETUP, s, [&] {
         return launch_frame_setup(tab, nvol, P, vf, c->d_counter, s, vis); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAX, s, [&] {
@@ -1145,9 +1150,9 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
     uint2 *changed = c->d_list + c->list_cap;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
         return launch_integrate(tab, vf, c->d_list, c->d_counter, P, depth, rgb, c->d_stats,
-                                c->grid_integrate, s, changed, c->d_counter + 2); }));
+                                c->grid_integrate, s, changed, c->d_counter + 2, stamp); }));
     MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
-        return launch_cell_masks(tab, changed, c->d_counter + 2, c->num_sms, s); }));
+        return launch_cell_masks(tab, changed, c->d_counter + 2, stamp, c->num_sms, s); }));
     return end_call(c, s);
 }
 
@@ -1295,7 +1300,7 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
     MV_CUDA(c, graph_integrate(fg.g, upd, fg.nodes, nullptr, c->d_table, nvol, c->d_vf, P, total, c->total_sup,
                                two_level ? c->d_slist : nullptr, c->d_list, c->d_counter, depth, rgb,
                                c->d_stats, c->grid_integrate,
-                               c->num_sms, c->d_vis, c->d_list + c->list_cap, c->d_pyr));
+                               c->num_sms, c->d_vis, c->d_list + c->list_cap, ++c->integrations, c->d_pyr));
     MV_CUDA(c, graph_raycast(fg.g, upd, &fg.nodes[6], fg.nodes[5], c->d_table, nvol, c->d_vf, P,
                              depth_out, normal, rgba, vertex, vol_id, c->d_stats, c->ray_tile, c->d_vis));
     if (rebuild) {
@@ -1446,7 +1451,7 @@ mv_status mv_frame_streamed(mv_ctx *c, const float *depth, const uint8_t *rgb, c
                                      c->d_pyr, nullptr, 0); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_INTEGRATE, s, [&] {
             return launch_integrate(dv, vf, list, cnt, P, depth, rgb, c->d_stats, c->grid_integrate, s,
-                                    nullptr, nullptr); }));
+                                    nullptr, nullptr, 0u); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_CELL_FLAGS, s, [&] {
             return launch_cell_flags(dv, list, cnt, c->num_sms, s); }));
         MV_CUDA(c, counted_launch(c, MV_KERNEL_RAYCAST, s, [&] {
@@ -1572,6 +1577,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
         sv.sup = nullptr;
         sv.vmask = nullptr;
         sv.cmask = nullptr;
+        sv.stamp = nullptr;
         sv.brick_base = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(stab, &sv, sizeof(VolDev), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sv is a stack value
@@ -1595,7 +1601,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
                 if (e == cudaSuccess) e = cudaEventRecord(a, s);
                 if (e == cudaSuccess)
                     e = launch_integrate(stab, svf, slist, scount, P, depth, rgb, nullptr,
-                                         c->num_sms * ctas, s, nullptr, nullptr);
+                                         c->num_sms * ctas, s, nullptr, nullptr, 0u);
                 if (e == cudaSuccess) e = cudaEventRecord(b, s);
                 if (e == cudaSuccess && rep > 0) t[nt++] = time_ms(s, a, b);
             }
