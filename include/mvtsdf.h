@@ -515,10 +515,10 @@ typedef struct {
  * the nearest pixel (floor(u + 1/2)) when |v_g - V| <= dist and
  * n_g . N >= cos_min.  With r = N . (V - v_g) and J = [N, v_g x N] (the twist
  * x = (rho, phi) moves v_g to v_g + rho + phi x v_g, so r changes by -J x)
- * it adds J^T J, J^T r, r^2 and 1.  Per-pixel terms, the sums of a thread
- * and those within a warp (a pairwise tree) in FP32; the warps' sums and all
- * later sums in FP64; every order fixed.  Blocks until the system is on the
- * host. */
+ * it adds J^T J, J^T r, r^2 and 1.  Per-pixel terms, the sums of a thread,
+ * within a warp and over a CTA's warps (pairwise trees) in FP32; the CTAs'
+ * sums in FP64 on the host; every order fixed.  Blocks until the system is
+ * on the host. */
 mv_status mv_icp_linearize(mv_ctx *ctx, const float *vertex, const float *normal, const mv_intrinsics *K,
                            const double T_est[16], const float *model_vertex, const float *model_normal,
                            const double T_model[16], const mv_icp_config *cfg, mv_icp_system *out,
@@ -528,8 +528,9 @@ mv_status mv_icp_linearize(mv_ctx *ctx, const float *vertex, const float *normal
  * Gauss-Newton steps from T_init: solve A x = b (Cholesky, FP64) and set
  * T <- exp(x^) T.  Stops early when fewer than 6 pixels associate or the
  * system is not positive definite.  The loop runs on the device: each step is
- * one kernel whose last CTA adds the partial sums in a fixed order, solves
- * and updates the estimate in device memory, so the steps follow each other
+ * one kernel whose last CTA adds the partial sums in a fixed order
+ * (compensated FP32 summation, about 48 bits), solves in FP64 and updates
+ * the estimate in device memory, so the steps follow each other
  * without a host round trip.  T_out receives the estimate; last (may be
  * NULL) the system of the last linearisation.  Blocks until done (one
  * read-back at the end). */

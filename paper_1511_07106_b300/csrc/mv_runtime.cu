@@ -55,11 +55,11 @@ cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long lon
 cudaError_t launch_depth_maps(const float *, const mv_intrinsics &, float, float, const double *, float *, float *,
                               cudaStream_t);
 cudaError_t launch_icp_system(const float *, const float *, const mv_intrinsics &, const double *, const float *,
-                              const float *, const double *, float, float, double *, int, cudaStream_t);
+                              const float *, const double *, float, float, float *, int, cudaStream_t);
 int icp_grid(int num_sms);
 cudaError_t launch_icp_step(const float *vertex, const float *normal, const mv_intrinsics &K, double *T_dev,
                             double *sys_dev, int *state_dev, const float *mvertex, const float *mnormal,
-                            const double *T_model, float dist, float cos_min, double *partials, int grid,
+                            const double *T_model, float dist, float cos_min, float *partials, int grid,
                             cudaStream_t s);
 cudaError_t launch_stream_gather(const VolDev &, const VolFrame *, const FrameParams &, const void *, const void *,
                                  unsigned long long *, int, cudaStream_t);
@@ -149,7 +149,7 @@ struct mv_ctx {
     // tracking scratch: the frame's vertex / normal maps, per-CTA ICP partials
     float *d_trk_v = nullptr, *d_trk_n = nullptr;
     size_t trk_px = 0;
-    double *d_trk_part = nullptr;
+    float *d_trk_part = nullptr;
     double *d_trk_loop = nullptr;  // mv_track's device loop: pose (16), system (44), then 2 ints of state
     // full-cover streaming (mv_frame_streamed): device staging slots that the
     // swapped-out volumes pass through, one copy stream per direction
@@ -804,7 +804,7 @@ static mv_status track_scratch(mv_ctx *c, const mv_intrinsics *K, cudaStream_t s
         c->trk_px = px;
     }
     if (!c->d_trk_part)
-        MV_CUDA(c, cudaMalloc((void **)&c->d_trk_part, sizeof(double) * kIcpTerms * icp_grid(c->num_sms)));
+        MV_CUDA(c, cudaMalloc((void **)&c->d_trk_part, sizeof(float) * kIcpTerms * icp_grid(c->num_sms)));
     if (!c->d_trk_loop) MV_CUDA(c, cudaMalloc((void **)&c->d_trk_loop, sizeof(double) * 61));
     return MV_OK;
 }
@@ -821,12 +821,12 @@ static mv_status icp_linearise(mv_ctx *c, const float *v, const float *n, const 
     MV_CUDA(c, counted_launch(c, MV_KERNEL_ICP, s, [&] {
         return launch_icp_system(v, n, *K, T_est, mv_, mn, T_model, cfg->dist, cfg->cos_min, c->d_trk_part, grid,
                                  s); }));
-    std::vector<double> part((size_t)grid * kIcpTerms);
-    MV_CUDA(c, cudaMemcpyAsync(part.data(), c->d_trk_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+    std::vector<float> part((size_t)grid * kIcpTerms);
+    MV_CUDA(c, cudaMemcpyAsync(part.data(), c->d_trk_part, sizeof(float) * part.size(), cudaMemcpyDeviceToHost, s));
     MV_CUDA(c, cudaStreamSynchronize(s));
     double sum[kIcpTerms] = {0};
     for (int g = 0; g < grid; ++g)
-        for (int k = 0; k < kIcpTerms; ++k) sum[k] += part[(size_t)g * kIcpTerms + k];
+        for (int k = 0; k < kIcpTerms; ++k) sum[k] += (double)part[(size_t)g * kIcpTerms + k];
     int k = 0;
     for (int i = 0; i < 6; ++i)
         for (int j = i; j < 6; ++j, ++k) out->A[6 * i + j] = out->A[6 * j + i] = sum[k];

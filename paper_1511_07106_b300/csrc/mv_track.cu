@@ -105,7 +105,7 @@ struct IcpArgs {
     Mat34f model_inv;      // world to model camera
     float fx, fy, cx, cy;
     float dist2, cos_min;
-    double *partials;      // gridDim.x x kIcpTerms
+    float *partials;       // gridDim.x x kIcpTerms
 };
 
 // Device state of mv_track's Gauss-Newton loop.
@@ -115,15 +115,15 @@ struct IcpLoop {
     int *state;     // [0] stopped (too few inliers or a failed solve), [1] CTAs done
 };
 
-// 1 / sqrt(d) for d > 0: a float seed refined by two Newton steps
-// y <- y (3 - d y^2) / 2 in FP64 (the relative error e becomes about 1.5 e^2
-// per step: 2e-7, 1e-13, then below double rounding) -- a short dependent
-// chain where FP64 sqrt and division are long ones on B300.
+// 1 / sqrt(d) for d > 0: a float seed refined by one Newton step
+// y <- y (3 - d y^2) / 2 in FP64 (the relative error e becomes about 1.5 e^2:
+// from the seed's few 1e-7 to about 1e-13, far below what a Gauss-Newton
+// increment needs) -- a short dependent chain where FP64 sqrt and division
+// are long ones on B300.
 __device__ __forceinline__ double inv_sqrt(double d)
 {
     if (d > 1e-30 && d < 1e30) {
-        double y = (double)rsqrtf((float)d);
-        y = y * (1.5 - 0.5 * d * y * y);
+        const double y = (double)rsqrtf((float)d);
         return y * (1.5 - 0.5 * d * y * y);
     }
     return 1.0 / sqrt(d);
@@ -243,6 +243,18 @@ __device__ __forceinline__ void icp_step_warp(const double *tot, const IcpLoop &
     }
 }
 
+// hi + lo += x, with the rounding error of hi + x kept in lo (Knuth's
+// TwoSum: s = hi + x, b = s - hi, error (hi - (s - b)) + (x - b), exact in
+// round-to-nearest), so that hi + lo carries about twice FP32's precision.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float b = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, b)), __fsub_rn(x, b));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 // One CTA of kIcpCta threads per SM: the partials the last CTA of a device
 // step adds are as few as the SMs, each term's added by kIcpSplit threads.
 constexpr int kIcpCta = 512;
@@ -311,31 +323,41 @@ __global__ void __launch_bounds__(kIcpCta) icp_system_kernel(IcpArgs A, IcpLoop 
         acc[27] += r * r;
         acc[28] += 1.f;
     }
-    // CTA sum: each warp by a pairwise tree of FP32 shuffles (5 roundings on
-    // top of the lanes' own sums; B300 runs FP64 at a small fraction of its
-    // FP32 rate, and an FP64 tree here took about half the kernel's time),
-    // then the 8 warp sums in FP64 in shared memory
-    __shared__ double s_part[kIcpCta / 32][kIcpTerms];
+    // CTA sum: each warp by a pairwise tree of FP32 shuffles, then the CTA's
+    // warps by a pairwise tree in FP32 (9 roundings on top of the lanes' own
+    // sums).  B300 runs FP64 at a small fraction of its FP32 rate, and a
+    // warp's FP64 instruction holds that pipe however few lanes it has: an
+    // FP64 shuffle tree took about half the kernel's time, and the per-warp
+    // FP64 conversions and FP64 sum of the warps' results a tenth (a device
+    // step 27.0 -> 24.3 us without them).
+    constexpr int kWarps = kIcpCta / 32;
+    __shared__ float s_part[kWarps][kIcpTerms];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kIcpTerms; ++k) {
         float x = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) s_part[wid][k] = (double)x;
+        if (lane == 0) s_part[wid][k] = x;
     }
     __syncthreads();
     if (threadIdx.x < kIcpTerms) {
-        double x = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_part[w][threadIdx.x];
-        A.partials[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = x;
+        float v[kWarps];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) v[w] = s_part[w][threadIdx.x];
+#pragma unroll
+        for (int h = kWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int w = 0; w < h; ++w) v[w] += v[w + h];
+        A.partials[(size_t)blockIdx.x * kIcpTerms + threadIdx.x] = v[0];
     }
     if (!LOOP) return;
     // the last CTA to finish adds the partials (kIcpSplit threads per term,
-    // each a fixed stride of CTAs, then those sums in order: a fixed order),
-    // solves and updates the estimate
+    // each a fixed stride of CTAs, then those sums in order: a fixed order)
+    // by compensated FP32 summation (about 48 bits for these few terms, at
+    // FP32 speed), solves and updates the estimate
     __shared__ bool s_last;
-    __shared__ double s_sum[kIcpTerms][kIcpSplit];
+    __shared__ float s_hi[kIcpTerms][kIcpSplit], s_lo[kIcpTerms][kIcpSplit];
     __shared__ double s_tot[kIcpTerms];
     __threadfence();
     __syncthreads();
@@ -345,24 +367,28 @@ __global__ void __launch_bounds__(kIcpCta) icp_system_kernel(IcpArgs A, IcpLoop 
     __threadfence();
     if (threadIdx.x < kIcpSplit * kIcpTerms) {
         const int k = threadIdx.x / kIcpSplit, j = threadIdx.x % kIcpSplit, G = (int)gridDim.x;
-        const double *pk = A.partials + k;
-        double x = 0.0;
+        const float *pk = A.partials + k;
+        float hi = 0.f, lo = 0.f;
         int g = j;
         for (; g + 7 * kIcpSplit < G; g += 8 * kIcpSplit) {  // 8 loads in flight, added in the same order
-            double v[8];
+            float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldcg(pk + (size_t)(g + kIcpSplit * u) * kIcpTerms);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x += v[u];
+            for (int u = 0; u < 8; ++u) two_sum_add(hi, lo, v[u]);
         }
-        for (; g < G; g += kIcpSplit) x += __ldcg(pk + (size_t)g * kIcpTerms);
-        s_sum[k][j] = x;
+        for (; g < G; g += kIcpSplit) two_sum_add(hi, lo, __ldcg(pk + (size_t)g * kIcpTerms));
+        s_hi[k][j] = hi;
+        s_lo[k][j] = lo;
     }
     __syncthreads();
     if (threadIdx.x < kIcpTerms) {
-        double x = 0.0;
-        for (int j = 0; j < kIcpSplit; ++j) x += s_sum[threadIdx.x][j];
-        s_tot[threadIdx.x] = x;
+        float hi = 0.f, lo = 0.f;
+        for (int j = 0; j < kIcpSplit; ++j) {
+            two_sum_add(hi, lo, s_hi[threadIdx.x][j]);
+            lo += s_lo[threadIdx.x][j];
+        }
+        s_tot[threadIdx.x] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
@@ -373,7 +399,7 @@ int icp_grid(int num_sms) { return num_sms; }
 
 static IcpArgs icp_args(const float *vertex, const float *normal, const mv_intrinsics &K, const double *T_est,
                         const float *mvertex, const float *mnormal, const double *T_model, float dist,
-                        float cos_min, double *partials)
+                        float cos_min, float *partials)
 {
     IcpArgs A;
     A.vertex = vertex;
@@ -406,7 +432,7 @@ static IcpArgs icp_args(const float *vertex, const float *normal, const mv_intri
 
 cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv_intrinsics &K,
                               const double *T_est, const float *mvertex, const float *mnormal,
-                              const double *T_model, float dist, float cos_min, double *partials, int grid,
+                              const double *T_model, float dist, float cos_min, float *partials, int grid,
                               cudaStream_t s)
 {
     const IcpArgs A = icp_args(vertex, normal, K, T_est, mvertex, mnormal, T_model, dist, cos_min, partials);
@@ -418,7 +444,7 @@ cudaError_t launch_icp_system(const float *vertex, const float *normal, const mv
 // state: 16 doubles of pose, 44 of system, 2 ints).
 cudaError_t launch_icp_step(const float *vertex, const float *normal, const mv_intrinsics &K, double *T_dev,
                             double *sys_dev, int *state_dev, const float *mvertex, const float *mnormal,
-                            const double *T_model, float dist, float cos_min, double *partials, int grid,
+                            const double *T_model, float dist, float cos_min, float *partials, int grid,
                             cudaStream_t s)
 {
     const IcpArgs A = icp_args(vertex, normal, K, nullptr, mvertex, mnormal, T_model, dist, cos_min, partials);
