@@ -650,12 +650,23 @@ def bench_diff(torch, Mapper, Config, frames, n_poses=16, adam_steps=50):
                                       callback=lambda it, Ts, l: curve.append(err(Ts)) if it % 10 == 9 else None)
     torch.cuda.synchronize()
     refine_ms_per_step = (time.perf_counter() - t0) * 1e3 / adam_steps
+    # the same steps with the loss and its gradients as torch operations
+    # between mv_raycast_batch and mv_raycast_backward (the unfused path)
+    diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=2, fused=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    diff.refine_poses(m, cam, T_init, ref_d, ref_c, steps=adam_steps, fused=False)
+    torch.cuda.synchronize()
+    unfused_ms_per_step = (time.perf_counter() - t0) * 1e3 / adam_steps
     m.close()
     rays = n_poses * cam.width * cam.height
     return {"workload": wl.name, "poses": n_poses, "prefill_frames": len(frames),
             "forward_backward_ms": refine_ms_per_step,
-            "forward_backward_note": "one refinement step: the forward of all 16 views (one launch), the L1 loss and "
-                                     "its gradient, the backward (one launch) and the tangent-space Adam update",
+            "forward_backward_note": "one refinement step: the forward of all 16 views (one launch), the L1 loss, "
+                                     "its gradient and the backward in one call (mv_raycast_backward_l1: the "
+                                     "loss statistics, then the backward forming each pixel's gradient) and the "
+                                     "tangent-space Adam update",
+            "refine_unfused_ms_per_step": unfused_ms_per_step,
             "mrays_per_s_forward_backward": rays / (refine_ms_per_step * 1e-3) / 1e6,
             "autograd_forward_backward_ms": fb_ms,
             "backward_kernel_ms": tm["backward"][1] / max(tm["backward"][2], 1),

@@ -349,6 +349,30 @@ mv_status mv_raycast_backward(mv_ctx *ctx, const mv_intrinsics *K, const double 
                               const float *grad_depth, const float *grad_rgb, float *grad_pose,
                               const mv_grad_target *targets, int32_t n_targets, void *stream);
 
+/* The L1 loss of pose refinement and its pose gradient in one call (not in
+ * the paper; the loss the Python binding's refinement minimises).  For
+ * n_poses views raycast with mv_raycast_batch (depth, rgba and vol_id,
+ * device, n x h x w, and n x h x w x 4 bytes for rgba) against reference
+ * renders ref_depth (n x h x w) and ref_rgba (n x h x w x 4 bytes, A unused):
+ * with the pixels valid in both renders (depth > 0 in each) counted as
+ * n_valid, the loss is the mean over them of |depth - ref_depth| +
+ * colour_weight * sum over R, G, B of |c - ref_c|, colours c = byte / 255;
+ * its gradient at a pixel is w sign(depth - ref_depth) for depth and
+ * (colour_weight sign(c - ref_c)) w for colour, w = 1 / n_valid (1 / 1 when
+ * none is valid, so every gradient is then 0), 0 elsewhere.  grad_pose
+ * (device, n x 6, overwritten) receives that gradient carried through the
+ * raycast as mv_raycast_backward carries grad_depth and grad_rgb (the same
+ * per-pixel values in the same order: the same bits); loss (device, one
+ * float) receives the loss, its sums in a fixed order.  One kernel adds the
+ * statistics, then the backward kernel forms each pixel's gradient itself:
+ * no per-pixel gradient buffers.  Asynchronous on `stream`; calls of one
+ * context share its statistics scratch, so calls on different streams must
+ * not overlap. */
+mv_status mv_raycast_backward_l1(mv_ctx *ctx, const mv_intrinsics *K, const double *T_c2w,
+                                 int32_t n_poses, const float *depth, const uint8_t *rgba,
+                                 const int32_t *vol_id, const float *ref_depth, const uint8_t *ref_rgba,
+                                 float colour_weight, float *grad_pose, float *loss, void *stream);
+
 /* Move a volume to pinned host memory (the paper's download to the CPU, Algorithm 1)
  * on the library's swap stream, after the work already queued on `stream`;
  * its GPU memory is released once the copy has finished.  From this call on

@@ -127,6 +127,8 @@ _SIGNATURES = {
     "mv_get_tuning": ([_P, C.POINTER(mv_tuning)], C.c_int),
     "mv_raycast_backward": ([_P, C.POINTER(mv_intrinsics), _D16, C.c_int32, _P, _P, _P, _P, _P,
                              C.POINTER(mv_grad_target), C.c_int32, _P], C.c_int),
+    "mv_raycast_backward_l1": ([_P, C.POINTER(mv_intrinsics), _D16, C.c_int32, _P, _P, _P, _P, _P, C.c_float,
+                                _P, _P, _P], C.c_int),
     "mv_swap_out": ([_P, C.c_int32, _P], C.c_int),
     "mv_swap_in": ([_P, C.c_int32, _P], C.c_int),
     "mv_read_volume": ([_P, C.c_int32, _P, _P], C.c_int),

@@ -130,6 +130,159 @@ __device__ bool pixel_grad(const VolDev &v, const float *Tf, const float *cam, f
     return true;
 }
 
+// sign(x) as torch.sign gives it for finite x: -1, 0 or 1
+__device__ __forceinline__ float sign_of(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// The L1 loss of pose refinement: the mean over the n_valid pixels valid in
+// both renders (depth > 0 in each) of |depth - ref_depth| + colour_weight *
+// sum over RGB of |colour - ref_colour|, colour = 8-bit value / 255.  Its
+// gradient at a pixel: w = 1 / n_valid where valid (else 0),
+// dL/ddepth = sign(ddepth) w, dL/dcolour = (colour_weight sign(dcolour)) w,
+// the same operations in the same order as the closed form of the Python
+// binding (l1_loss_grad), and the colour signs taken from the 8-bit values,
+// so the two give the same bits.  The pixel's inputs (reference depth, both
+// colours, n_valid) are loaded with its depth and volume id.
+struct L1Pixel {
+    float rd;
+    uchar4 a, b;
+    unsigned n_valid;
+};
+
+__device__ __forceinline__ void l1_pixel_grad(const BackwardArgs &A, const L1Pixel &q, float tau, float &gdep,
+                                              float gc[3])
+{
+    const float w = (tau > 0.f && q.rd > 0.f) ? __fdiv_rn(1.f, (float)max(q.n_valid, 1u)) : 0.f;
+    gdep = sign_of(tau - q.rd) * w;
+    const uchar4 a = q.a, b = q.b;
+    const float cw = A.colour_weight;
+    gc[0] = (cw * sign_of((float)a.x - (float)b.x)) * w;
+    gc[1] = (cw * sign_of((float)a.y - (float)b.y)) * w;
+    gc[2] = (cw * sign_of((float)a.z - (float)b.z)) * w;
+}
+
+// One pixel's share of the L1 statistics (colours packed R, G, B, A from the
+// low byte up).
+__device__ __forceinline__ void l1_accumulate(float d, float r, unsigned a, unsigned b, unsigned &cnt, float &ld,
+                                              unsigned long long &lc)
+{
+    if (!(d > 0.f && r > 0.f)) return;
+    ++cnt;
+    ld += fabsf(d - r);
+    lc += (unsigned)(abs((int)(a & 0xFFu) - (int)(b & 0xFFu)) + abs((int)((a >> 8) & 0xFFu) - (int)((b >> 8) & 0xFFu)) +
+                     abs((int)((a >> 16) & 0xFFu) - (int)((b >> 16) & 0xFFu)));
+}
+
+// Sum over a CTA of 256 threads in a fixed order (warp trees, then the 8
+// warps in order); the result is valid in thread 0.
+__device__ __forceinline__ void l1_cta_sum(unsigned &cnt, float &ld, unsigned long long &lc)
+{
+    __shared__ unsigned s_c[8];
+    __shared__ unsigned long long s_l[8];
+    __shared__ float s_d[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        ld += __shfl_down_sync(0xffffffffu, ld, o);
+        lc += __shfl_down_sync(0xffffffffu, lc, o);
+    }
+    __syncthreads();  // the slots may still be read by a previous sum
+    if (lane == 0) {
+        s_c[w] = cnt;
+        s_d[w] = ld;
+        s_l[w] = lc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cnt = 0;
+        ld = 0.f;
+        lc = 0;
+        for (int k = 0; k < 8; ++k) {
+            cnt += s_c[k];
+            ld += s_d[k];
+            lc += s_l[k];
+        }
+    }
+}
+
+// Statistics of the L1 loss over all n pixels of all views: the count of
+// pixels valid in both renders and the loss (see l1_pixel_grad; the colour
+// term as the exact integer sum of the 8-bit differences, divided by 255
+// once).  Four pixels per step with 16-byte loads where the arrays allow
+// them.  Per CTA a count, the colour sum and a float sum of the depth
+// differences, then the last CTA to finish adds them (its threads a fixed
+// stride of CTAs each, then the CTA sum: a fixed order), writes the count to
+// state[1] and the loss to *loss, and resets state[0] for the next call.
+__global__ void __launch_bounds__(256) l1_stats_kernel(const float *__restrict__ depth,
+                                                       const float *__restrict__ ref_depth,
+                                                       const uint8_t *__restrict__ rgba,
+                                                       const uint8_t *__restrict__ ref_rgba, long long n,
+                                                       float colour_weight, unsigned *state, float *loss)
+{
+    unsigned long long *col_part = reinterpret_cast<unsigned long long *>(state + 2);
+    unsigned *cnt_part = state + 2 + 2 * kL1Ctas;
+    float *dep_part = reinterpret_cast<float *>(state + 2 + 3 * kL1Ctas);
+    unsigned cnt = 0;
+    unsigned long long lc = 0;
+    float ld = 0.f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(depth) | reinterpret_cast<uintptr_t>(ref_depth) |
+                       reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(ref_rgba)) & 15u) == 0;
+    long long tail = 0;
+    if (vec) {
+        const long long n4 = n >> 2;
+        for (long long q = first; q < n4; q += stride) {
+            const float4 d = reinterpret_cast<const float4 *>(depth)[q];
+            const float4 r = reinterpret_cast<const float4 *>(ref_depth)[q];
+            const uint4 a = reinterpret_cast<const uint4 *>(rgba)[q];
+            const uint4 b = reinterpret_cast<const uint4 *>(ref_rgba)[q];
+            l1_accumulate(d.x, r.x, a.x, b.x, cnt, ld, lc);
+            l1_accumulate(d.y, r.y, a.y, b.y, cnt, ld, lc);
+            l1_accumulate(d.z, r.z, a.z, b.z, cnt, ld, lc);
+            l1_accumulate(d.w, r.w, a.w, b.w, cnt, ld, lc);
+        }
+        tail = n4 << 2;
+    }
+    const unsigned *rgba4 = reinterpret_cast<const unsigned *>(rgba);
+    const unsigned *ref4 = reinterpret_cast<const unsigned *>(ref_rgba);
+    for (long long i = tail + first; i < n; i += stride) l1_accumulate(depth[i], ref_depth[i], rgba4[i], ref4[i], cnt, ld, lc);
+    l1_cta_sum(cnt, ld, lc);
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        cnt_part[blockIdx.x] = cnt;
+        col_part[blockIdx.x] = lc;
+        dep_part[blockIdx.x] = ld;
+        __threadfence();
+        s_last = atomicAdd(state, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    cnt = 0;
+    lc = 0;
+    ld = 0.f;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+        cnt += __ldcg(cnt_part + k);
+        lc += __ldcg(col_part + k);
+        ld += __ldcg(dep_part + k);
+    }
+    l1_cta_sum(cnt, ld, lc);
+    if (threadIdx.x == 0) {
+        const float wgt = __fdiv_rn(1.f, (float)max(cnt, 1u));
+        state[1] = cnt;
+        *loss = ld * wgt + colour_weight * (((float)lc / 255.f) * wgt);
+        state[0] = 0u;
+    }
+}
+
+cudaError_t launch_l1_stats(const float *depth, const float *ref_depth, const uint8_t *rgba, const uint8_t *ref_rgba,
+                            long long n, float colour_weight, unsigned *scratch, float *loss, cudaStream_t s)
+{
+    l1_stats_kernel<<<kL1Ctas, 256, 0, s>>>(depth, ref_depth, rgba, ref_rgba, n, colour_weight, scratch, loss);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
 {
     const int p = blockIdx.z;
@@ -141,6 +294,13 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
         const size_t pix = ((size_t)p * A.height + py) * A.width + px;
         const float tau = A.depth[pix];
         const int id = A.vol_id[pix];
+        L1Pixel q1{0.f, make_uchar4(0, 0, 0, 0), make_uchar4(0, 0, 0, 0), 1u};
+        if (A.ref_depth) {
+            q1.rd = A.ref_depth[pix];
+            q1.a = reinterpret_cast<const uchar4 *>(A.rgba)[pix];
+            q1.b = reinterpret_cast<const uchar4 *>(A.ref_rgba)[pix];
+            q1.n_valid = __ldg(A.l1_count);
+        }
         const int slot = (tau > 0.f && id >= 0) ? slot_of(A.vols, A.nvol, id) : -1;
         if (slot >= 0) {
             const VolDev &v = A.vols[slot];
@@ -150,9 +310,11 @@ __global__ void __launch_bounds__(128) raycast_backward_kernel(BackwardArgs A)
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 d[a] = __ldg(Tf + 3 * a) * dc0 + __ldg(Tf + 3 * a + 1) * dc1 + __ldg(Tf + 3 * a + 2);
-            const float gdep = A.grad_depth ? A.grad_depth[pix] : 0.f;
+            float gdep = A.grad_depth ? A.grad_depth[pix] : 0.f;
             float gc[3] = {0.f, 0.f, 0.f};
-            if (A.grad_rgb) {
+            if (A.ref_depth) {
+                l1_pixel_grad(A, q1, tau, gdep, gc);
+            } else if (A.grad_rgb) {
                 gc[0] = A.grad_rgb[3 * pix];
                 gc[1] = A.grad_rgb[3 * pix + 1];
                 gc[2] = A.grad_rgb[3 * pix + 2];

@@ -290,7 +290,20 @@ struct BackwardArgs {
     const float *grad_rgb;    // n x h x w x 3 or null
     float *grad_pose;         // n x 6 (written by the reduction)
     float *partial;           // n x (CTAs per pose) x 6 per-CTA sums of the pose gradient
+    // L1 mode (ref_depth not null): grad_depth / grad_rgb are not read; each
+    // pixel's are those of the L1 loss of the render against the reference
+    const uint8_t *rgba;      // n x h x w x 4 (forward colour)
+    const float *ref_depth;   // n x h x w
+    const uint8_t *ref_rgba;  // n x h x w x 4
+    float colour_weight;
+    const unsigned *l1_count; // pixels valid in both renders (l1_stats_kernel)
 };
+
+// Scratch of the L1 statistics (32-bit words): [0] CTAs done, [1] pixels
+// valid in both renders, then per CTA its colour sum (64-bit), its count and
+// its depth sum (float).
+constexpr int kL1Ctas = 592;
+constexpr size_t kL1ScratchBytes = 4 * (2 + 4 * (size_t)kL1Ctas);
 
 // element offset of voxel (x, y, z) in brick-major order
 __device__ __forceinline__ long long vox_offset(const VolDev &v, int x, int y, int z)

@@ -48,6 +48,8 @@ int integrate_occupancy_grid(int num_sms);
 int integrate_max_ctas_per_sm();
 cudaError_t launch_raycast_backward(const BackwardArgs &A, cudaStream_t s);
 size_t backward_ctas_per_pose(int width, int height);
+cudaError_t launch_l1_stats(const float *, const float *, const uint8_t *, const uint8_t *, long long, float,
+                            unsigned *, float *, cudaStream_t);
 cudaError_t launch_gather_box(const void *src, int elem_bytes, const int nb[3], const int lo[3], const int n[3],
                               void *dst, int num_sms, cudaStream_t s);
 cudaError_t launch_extract(const VolDev &, float *, uint8_t *, unsigned long long *, unsigned long long,
@@ -204,6 +206,7 @@ struct mv_ctx {
     std::vector<float> h_pose_f;
     float *d_bw_partial = nullptr;  // per-CTA partial sums of the pose gradient
     size_t bw_partial_cap = 0;      // floats
+    unsigned *d_l1 = nullptr;       // L1 loss statistics (kL1ScratchBytes), zeroed once
     // per-kernel launch counts and optional event timing
     bool timing = false;
     struct Timed { int kind; cudaEvent_t a, b; };
@@ -739,6 +742,7 @@ mv_status mv_destroy(mv_ctx *c)
     if (c->fg.g) cudaGraphDestroy(c->fg.g);
     if (c->d_poses) cudaFree(c->d_poses);
     if (c->d_bw_partial) cudaFree(c->d_bw_partial);
+    if (c->d_l1) cudaFree(c->d_l1);
     for (auto &st : c->stage) {
         if (st.h) cudaFreeHost(st.h);
         if (st.ev) cudaEventDestroy(st.ev);
@@ -1656,10 +1660,19 @@ mv_status mv_get_tuning(mv_ctx *c, mv_tuning *t)
     return MV_OK;
 }
 
-mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,
-                              const float *depth, const int32_t *vol_id, const float *grad_depth,
-                              const float *grad_rgb, float *grad_pose, const mv_grad_target *targets,
-                              int32_t n_targets, void *stream)
+// The L1 loss of pose refinement formed on the device (mv_raycast_backward_l1).
+struct L1Loss {
+    const uint8_t *rgba;
+    const float *ref_depth;
+    const uint8_t *ref_rgba;
+    float colour_weight;
+    float *loss;
+};
+
+static mv_status raycast_backward_impl(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,
+                                       const float *depth, const int32_t *vol_id, const float *grad_depth,
+                                       const float *grad_rgb, float *grad_pose, const mv_grad_target *targets,
+                                       int32_t n_targets, void *stream, const L1Loss *l1)
 {
     if (!c) return MV_ERR_ARG;
     if (n_poses < 1 || n_poses > 65535 || !depth || !vol_id || !grad_pose || (n_targets > 0 && !targets) ||
@@ -1738,9 +1751,51 @@ mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T
         c->bw_partial_cap = need;
     }
     A.partial = c->d_bw_partial;
+    A.rgba = nullptr;
+    A.ref_depth = nullptr;
+    A.ref_rgba = nullptr;
+    A.colour_weight = 0.f;
+    A.l1_count = nullptr;
+    if (l1) {
+        if (!c->d_l1) {
+            MV_CUDA(c, cudaMallocAsync((void **)&c->d_l1, kL1ScratchBytes, s));
+            MV_CUDA(c, cudaMemsetAsync(c->d_l1, 0, kL1ScratchBytes, s));
+        }
+        const long long npx = (long long)n_poses * K->width * K->height;
+        MV_CUDA(c, counted_launch(c, MV_KERNEL_BACKWARD, s, [&] {
+            return launch_l1_stats(depth, l1->ref_depth, l1->rgba, l1->ref_rgba, npx, l1->colour_weight, c->d_l1,
+                                   l1->loss, s); }));
+        A.rgba = l1->rgba;
+        A.ref_depth = l1->ref_depth;
+        A.ref_rgba = l1->ref_rgba;
+        A.colour_weight = l1->colour_weight;
+        A.l1_count = c->d_l1 + 1;
+    }
     if (A.nvol > 0)
         MV_CUDA(c, counted_launch(c, MV_KERNEL_BACKWARD, s, [&] { return launch_raycast_backward(A, s); }));
     return end_call(c, s);
+}
+
+mv_status mv_raycast_backward(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,
+                              const float *depth, const int32_t *vol_id, const float *grad_depth,
+                              const float *grad_rgb, float *grad_pose, const mv_grad_target *targets,
+                              int32_t n_targets, void *stream)
+{
+    return raycast_backward_impl(c, K, T, n_poses, depth, vol_id, grad_depth, grad_rgb, grad_pose, targets,
+                                 n_targets, stream, nullptr);
+}
+
+mv_status mv_raycast_backward_l1(mv_ctx *c, const mv_intrinsics *K, const double *T, int32_t n_poses,
+                                 const float *depth, const uint8_t *rgba, const int32_t *vol_id,
+                                 const float *ref_depth, const uint8_t *ref_rgba, float colour_weight,
+                                 float *grad_pose, float *loss, void *stream)
+{
+    if (!c) return MV_ERR_ARG;
+    if (!rgba || !ref_depth || !ref_rgba || !loss || !std::isfinite(colour_weight))
+        return fail(c, MV_ERR_ARG, "bad L1 loss arguments");
+    const L1Loss l1{rgba, ref_depth, ref_rgba, colour_weight, loss};
+    return raycast_backward_impl(c, K, T, n_poses, depth, vol_id, nullptr, nullptr, grad_pose, nullptr, 0, stream,
+                                 &l1);
 }
 
 mv_status mv_swap_out(mv_ctx *c, int32_t id, void *stream)

@@ -174,7 +174,7 @@ def centred_gradient(t: torch.Tensor, g_xi: torch.Tensor) -> torch.Tensor:
 
 
 def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, lr=(3e-3, 1.5e-3),
-                 colour_weight=0.1, callback=None, lr_final=1.0, centred=True):
+                 colour_weight=0.1, callback=None, lr_final=1.0, centred=True, fused=True):
     """Pose refinement by Adam in the tangent space of each pose.  Every step
     renders the n views at the current poses (mv_raycast_batch), takes the
     loss l1_loss against the reference renders and, from the loss's gradients
@@ -193,7 +193,10 @@ def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, l
     (metres, radians) per step for translation and rotation, or one number
     for both, decayed by a cosine from lr to lr * lr_final over the steps
     (lr_final = 1: constant, which did best on the 8 x 256^3 workload, as did
-    centred steps).  Returns (T_final (n, 4, 4) float64 numpy, losses)."""
+    centred steps).  With `fused` the loss, its gradients and the backward
+    are one library call (mv_raycast_backward_l1: the same gradient bits,
+    without the per-pixel gradient tensors); otherwise l1_loss_grad and
+    mv_raycast_backward.  Returns (T_final (n, 4, 4) float64 numpy, losses)."""
     import math
     dev = torch.device("cuda", mapper.device)
     T = np.array(T_init, dtype=np.float64)
@@ -208,12 +211,24 @@ def refine_poses(mapper: Mapper, cam, T_init, ref_depth, ref_colour, steps=50, l
                rgba=torch.empty((n, H, W, 4), dtype=torch.uint8, device=dev),
                vol_id=torch.empty((n, H, W), dtype=torch.int32, device=dev))
     grad_xi = torch.empty((n, 6), dtype=torch.float32, device=dev)
+    if fused:
+        # the reference colour back to its bytes (c = byte / 255 exactly
+        # recovers them), so that equal colours compare equal on the device
+        ref_rgba = torch.zeros((n, H, W, 4), dtype=torch.uint8, device=dev)
+        ref_rgba[..., :3] = torch.round(ref_colour * 255.0).clamp(0, 255).to(torch.uint8)
+        ref_d = ref_depth.contiguous()
+        loss_t = torch.empty(1, dtype=torch.float32, device=dev)
     losses = []
     for it in range(steps):
         mapper.raycast_batch(cam, T, out=out)
-        colour = out["rgba"][..., :3].float() / 255.0
-        loss, gd, gc = l1_loss_grad(out["depth"], colour, ref_depth, ref_colour, colour_weight)
-        mapper.raycast_backward(cam, T, out["depth"], out["vol_id"], gd, gc, grad_xi, {})
+        if fused:
+            mapper.raycast_backward_l1(cam, T, out["depth"], out["rgba"], out["vol_id"], ref_d, ref_rgba,
+                                       colour_weight, grad_xi, loss_t)
+            loss = loss_t
+        else:
+            colour = out["rgba"][..., :3].float() / 255.0
+            loss, gd, gc = l1_loss_grad(out["depth"], colour, ref_depth, ref_colour, colour_weight)
+            mapper.raycast_backward(cam, T, out["depth"], out["vol_id"], gd, gc, grad_xi, {})
         # the step's one read-back: the pose gradient, for Adam on the host
         g = grad_xi.cpu().numpy().astype(np.float64)
         if centred:

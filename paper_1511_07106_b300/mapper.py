@@ -435,6 +435,27 @@ class Mapper:
             _dptr(grad_rgb, torch.float32, 3 * npx, "grad_rgb"),
             _dptr(grad_pose, torch.float32, 6 * n, "grad_pose"), arr, len(targets), _stream(stream)))
 
+    def raycast_backward_l1(self, cam, poses, depth, rgba, vol_id, ref_depth, ref_rgba, colour_weight,
+                            grad_pose, loss, stream=None):
+        """The L1 loss of pose refinement and its pose gradient in one call
+        (mv_raycast_backward_l1).  poses: (n, 4, 4) host float64; depth (n, H,
+        W) float32, rgba (n, H, W, 4) uint8 and vol_id (n, H, W) int32: the
+        forward's maps; ref_depth / ref_rgba: the reference renders, same
+        shapes; grad_pose (n, 6) float32 and loss (1,) float32: device
+        outputs."""
+        import torch
+        P = np.ascontiguousarray(np.asarray(poses, np.float64).reshape(-1, 16))
+        n = P.shape[0]
+        npx = n * cam.width * cam.height
+        K = intrinsics(cam)
+        self._check(self._lib.mv_raycast_backward_l1(
+            self._h, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)), n,
+            _dptr(depth, torch.float32, npx, "depth"), _dptr(rgba, torch.uint8, 4 * npx, "rgba"),
+            _dptr(vol_id, torch.int32, npx, "vol_id"), _dptr(ref_depth, torch.float32, npx, "ref_depth"),
+            _dptr(ref_rgba, torch.uint8, 4 * npx, "ref_rgba"), float(colour_weight),
+            _dptr(grad_pose, torch.float32, 6 * n, "grad_pose"), _dptr(loss, torch.float32, 1, "loss"),
+            _stream(stream)))
+
     # -- memory passing ---------------------------------------------------
     def swap_out(self, vid, stream=None):
         self._check(self._lib.mv_swap_out(self._h, int(vid), _stream(stream)))

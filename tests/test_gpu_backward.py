@@ -236,6 +236,47 @@ def test_adam_pose_refinement_reduces_pose_error():
     m.close()
 
 
+@pytest.mark.parametrize("fmt", ["f32", "i16"])
+def test_fused_l1_backward_equals_loss_grad_then_backward(fmt):
+    """mv_raycast_backward_l1 against the Python closed form (l1_loss_grad)
+    followed by mv_raycast_backward on the same renders: the same pose-gradient
+    bits and the loss to float rounding; the fused and unfused refinement then
+    take the same steps (the same poses, bit for bit); with no pixel valid in
+    both renders the gradient and the loss are 0."""
+    import torch
+    wl = synth.room_tiles(res=64, pitch=0.008, frames=40, width=160, height=120, seed=5)
+    m, ids = prefilled(wl, 40, fmt=fmt)
+    random_colours(m, ids, 3)
+    cam = wl.cam
+    T_true = np.stack([wl.poses[i] for i in (4, 14, 24, 34)])
+    T = np.stack(synth.perturb_poses(list(T_true), seed=6, sigma_t=0.02, sigma_r_deg=1.0))
+    n = T.shape[0]
+    ref = m.raycast_batch(cam, T_true)
+    ref_d, ref_rgba = ref["depth"], ref["rgba"]
+    ref_c = ref_rgba[..., :3].float() / 255.0
+    out = m.raycast_batch(cam, T)
+    colour = out["rgba"][..., :3].float() / 255.0
+    loss, gd, gc = diff.l1_loss_grad(out["depth"], colour, ref_d, ref_c, 0.1)
+    g1 = torch.zeros((n, 6), dtype=torch.float32, device="cuda")
+    m.raycast_backward(cam, T, out["depth"], out["vol_id"], gd.contiguous(), gc.contiguous(), g1, {})
+    g2 = torch.zeros_like(g1)
+    l2 = torch.zeros(1, dtype=torch.float32, device="cuda")
+    m.raycast_backward_l1(cam, T, out["depth"], out["rgba"], out["vol_id"], ref_d, ref_rgba, 0.1, g2, l2)
+    assert torch.count_nonzero(g1) == 6 * n
+    assert torch.equal(g1, g2)
+    assert abs(float(l2) - float(loss)) <= 1e-5 * abs(float(loss))
+
+    Ta, la = diff.refine_poses(m, cam, T, ref_d, ref_c, steps=3, fused=True)
+    Tb, lb = diff.refine_poses(m, cam, T, ref_d, ref_c, steps=3, fused=False)
+    np.testing.assert_array_equal(Ta, Tb)
+    np.testing.assert_allclose(la, lb, rtol=1e-5)
+
+    none = torch.zeros_like(ref_d)
+    m.raycast_backward_l1(cam, T, out["depth"], out["rgba"], out["vol_id"], none, ref_rgba, 0.1, g2, l2)
+    assert torch.count_nonzero(g2) == 0 and float(l2) == 0.0
+    m.close()
+
+
 def test_full_size_tiles_gradients_sampled():
     """The differentiable-raycast workload at full size: 8 x 256^3 tiles at
     2 mm, 640x480, two poses perturbed by N(0, 2 cm) / N(0, 1 deg).  On a
