@@ -365,7 +365,8 @@ mv_status mv_raycast_backward(mv_ctx *ctx, const mv_intrinsics *K, const double 
  * per-pixel values in the same order: the same bits); loss (device, one
  * float) receives the loss, its sums in a fixed order.  One kernel adds the
  * statistics, then the backward kernel forms each pixel's gradient itself:
- * no per-pixel gradient buffers.  Asynchronous on `stream`; calls of one
+ * no per-pixel gradient buffers.  Every buffer 4-byte aligned (else
+ * MV_ERR_ARG, nothing launched).  Asynchronous on `stream`; calls of one
  * context share its statistics scratch, so calls on different streams must
  * not overlap. */
 mv_status mv_raycast_backward_l1(mv_ctx *ctx, const mv_intrinsics *K, const double *T_c2w,

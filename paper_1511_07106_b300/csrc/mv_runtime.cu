@@ -1793,6 +1793,11 @@ mv_status mv_raycast_backward_l1(mv_ctx *c, const mv_intrinsics *K, const double
     if (!c) return MV_ERR_ARG;
     if (!rgba || !ref_depth || !ref_rgba || !loss || !std::isfinite(colour_weight))
         return fail(c, MV_ERR_ARG, "bad L1 loss arguments");
+    // the kernels read a pixel's colour as one 4-byte word and its depths as floats
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(ref_rgba) |
+         reinterpret_cast<uintptr_t>(depth) | reinterpret_cast<uintptr_t>(ref_depth) |
+         reinterpret_cast<uintptr_t>(loss)) & 3u)
+        return fail(c, MV_ERR_ARG, "L1 loss buffers must be 4-byte aligned");
     const L1Loss l1{rgba, ref_depth, ref_rgba, colour_weight, loss};
     return raycast_backward_impl(c, K, T, n_poses, depth, vol_id, nullptr, nullptr, grad_pose, nullptr, 0, stream,
                                  &l1);

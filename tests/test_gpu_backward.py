@@ -274,6 +274,20 @@ def test_fused_l1_backward_equals_loss_grad_then_backward(fmt):
     none = torch.zeros_like(ref_d)
     m.raycast_backward_l1(cam, T, out["depth"], out["rgba"], out["vol_id"], none, ref_rgba, 0.1, g2, l2)
     assert torch.count_nonzero(g2) == 0 and float(l2) == 0.0
+
+    # a colour buffer that does not start on a 4-byte boundary is refused on
+    # the host before any launch
+    import ctypes as C
+    from paper_1511_07106_b300 import _abi
+    from paper_1511_07106_b300.mapper import intrinsics
+    shifted = torch.zeros(ref_rgba.numel() + 4, dtype=torch.uint8, device="cuda")
+    P = np.ascontiguousarray(T.reshape(-1, 16))
+    K = intrinsics(cam)
+    st = m._lib.mv_raycast_backward_l1(
+        m._h, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)), n, C.c_void_p(out["depth"].data_ptr()),
+        C.c_void_p(shifted.data_ptr() + 1), C.c_void_p(out["vol_id"].data_ptr()), C.c_void_p(ref_d.data_ptr()),
+        C.c_void_p(ref_rgba.data_ptr()), 0.1, C.c_void_p(g2.data_ptr()), C.c_void_p(l2.data_ptr()), None)
+    assert st == _abi.MV_ERR_ARG
     m.close()
 
 
