@@ -31,6 +31,10 @@
  *   - Device buffers passed in are owned by the caller and must stay valid
  *     until the work queued on `stream` has finished.  Volume storage in GPU
  *     memory and in pinned host memory is owned by the library.
+ *   - Device buffers of floats, ints and 8-bit RGBA start on a 4-byte
+ *     boundary, 64-bit keys and edge ids on an 8-byte one (RGB frames,
+ *     3 bytes a pixel, may start anywhere); a call given another pointer
+ *     returns MV_ERR_ARG and queues nothing.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls that take a stream are asynchronous with respect to the
  *     host unless stated otherwise.

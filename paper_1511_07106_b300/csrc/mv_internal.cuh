@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
 #include <tuple>
 #include <utility>
 
@@ -144,6 +145,17 @@ inline size_t flag_count_offset(long long nbricks)
     return (cflag_offset(nbricks) + (size_t)nbricks + 7) & ~(size_t)7;
 }
 inline size_t super_offset(long long nbricks) { return flag_count_offset(nbricks) + 8; }
+
+// Device buffers that the kernels access as 4-byte words (floats, ints,
+// packed colours) must start on a 4-byte boundary, 8-byte keys on an 8-byte
+// one, or the access faults: the entry points refuse other pointers (null
+// passes, for the optional ones) before any launch.
+inline bool aligned_to(std::initializer_list<const void *> ps, uintptr_t a)
+{
+    for (const void *p : ps)
+        if (reinterpret_cast<uintptr_t>(p) & (a - 1)) return false;
+    return true;
+}
 inline size_t flag_alloc_bytes(long long nbricks, long long nsuper)
 {
     return super_offset(nbricks) + 4 * (size_t)nsuper;

@@ -76,6 +76,7 @@ extern "C" mv_status mv_pack_hits(const float *depth, const int32_t *vol_id, con
                                   int32_t id_map_len, int64_t n, int64_t *keys, void *stream)
 {
     if (!depth || !vol_id || !keys || n < 0 || id_map_len < 0 || (id_map_len > 0 && !id_map)) return MV_ERR_ARG;
+    if (!aligned_to({depth, vol_id, id_map}, 4) || !aligned_to({keys}, 8)) return MV_ERR_ARG;
     if (n == 0) return MV_OK;
     pack_hits_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
         depth, vol_id, id_map_len > 0 ? id_map : nullptr, id_map_len, n,
@@ -87,7 +88,7 @@ extern "C" mv_status mv_merge_hits(const int64_t *best_keys, const int64_t *own_
                                    int32_t *vol_id, float *normal, uint8_t *rgba, float *vertex, void *stream)
 {
     if (!best_keys || !own_keys || n < 0) return MV_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(rgba) & 3u) return MV_ERR_ARG;
+    if (!aligned_to({best_keys, own_keys}, 8) || !aligned_to({depth, vol_id, normal, rgba, vertex}, 4)) return MV_ERR_ARG;
     if (n == 0) return MV_OK;
     merge_hits_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const long long *>(best_keys), reinterpret_cast<const long long *>(own_keys),

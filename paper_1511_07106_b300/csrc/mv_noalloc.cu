@@ -98,6 +98,7 @@ extern "C" mv_status mv_integrate_noalloc(const mv_volume_view *vol, const mv_co
     if (!vol || !depth || !K || !T || !vol->fw || !vol->rgba || !vol->brick_flags) return MV_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(vol->fw) & 15u) || (reinterpret_cast<uintptr_t>(vol->rgba) & 15u))
         return MV_ERR_ARG;
+    if (!aligned_to({depth}, 4)) return MV_ERR_ARG;
     mv_config c;
     if (cfg) {
         c = *cfg;

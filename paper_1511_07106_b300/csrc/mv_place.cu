@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdint>
 #include <map>
 #include <string>
 #include <vector>
@@ -175,6 +176,7 @@ mv_status histogram(mv_placer *p, const float *depth, const mv_intrinsics *K, co
                     std::vector<Cell> &cells, std::vector<unsigned> &counts, cudaStream_t s)
 {
     if (!depth || !valid_view(K, T)) return pfail(p, MV_ERR_ARG, "bad frame arguments");
+    if (reinterpret_cast<uintptr_t>(depth) & 3u) return pfail(p, MV_ERR_ARG, "depth must be 4-byte aligned");
     cudaSetDevice(p->device);
     const long long npx = (long long)K->width * K->height;
     unsigned need = 1024;

@@ -772,6 +772,8 @@ mv_status mv_extract_points(mv_ctx *c, int32_t id, float *xyz, uint8_t *rgb, uin
                             uint64_t *n, void *stream)
 {
     if (!c || !n) return fail(c, MV_ERR_ARG, "null argument");
+    if (!aligned_to({xyz}, 4) || !aligned_to({edge}, 8))
+        return fail(c, MV_ERR_ARG, "xyz must be 4-byte and edge 8-byte aligned");
     Volume *v;
     mv_status st = find_volume(c, id, &v);
     if (st) return st;
@@ -852,6 +854,7 @@ mv_status mv_depth_to_maps(mv_ctx *c, const float *depth, const mv_intrinsics *K
     if (!c) return MV_ERR_ARG;
     if (!depth || !vertex || !normal || !valid_frame(K, T ? T : kIdentity))
         return fail(c, MV_ERR_ARG, "bad arguments");
+    if (!aligned_to({depth, vertex, normal}, 4)) return fail(c, MV_ERR_ARG, "maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     MV_CUDA(c, counted_launch(c, MV_KERNEL_DEPTH_MAPS, s, [&] {
@@ -867,6 +870,8 @@ mv_status mv_icp_linearize(mv_ctx *c, const float *vertex, const float *normal, 
     if (!vertex || !normal || !model_vertex || !model_normal || !out || !valid_frame(K, T_est) ||
         !valid_frame(K, T_model) || !valid_icp(cfg))
         return fail(c, MV_ERR_ARG, "bad arguments");
+    if (!aligned_to({vertex, normal, model_vertex, model_normal}, 4))
+        return fail(c, MV_ERR_ARG, "maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = track_scratch(c, K, s);
@@ -882,6 +887,7 @@ mv_status mv_track(mv_ctx *c, const float *depth, const mv_intrinsics *K, const 
     if (!depth || !model_vertex || !model_normal || !T_out || !valid_frame(K, T_model) ||
         !valid_frame(K, T_init) || !valid_icp(cfg))
         return fail(c, MV_ERR_ARG, "bad arguments");
+    if (!aligned_to({depth, model_vertex, model_normal}, 4)) return fail(c, MV_ERR_ARG, "maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = track_scratch(c, K, s);
@@ -1113,6 +1119,7 @@ static mv_status integrate_impl(mv_ctx *c, int32_t only_id, const float *depth, 
 {
     if (!c) return MV_ERR_ARG;
     if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    if (!aligned_to({depth}, 4)) return fail(c, MV_ERR_ARG, "depth must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (only_id >= 0) {
@@ -1182,6 +1189,8 @@ static mv_status raycast_impl(mv_ctx *c, int32_t only_id, int first, const mv_in
     const bool merge = only_id >= 0 && !first;
     if (only_id >= 0 && (!depth || !vol_id))
         return fail(c, MV_ERR_ARG, "per-volume raycast needs depth and vol_id (merge state)");
+    if (!aligned_to({depth, normal, rgba, vertex, vol_id}, 4))
+        return fail(c, MV_ERR_ARG, "maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (only_id >= 0) {
@@ -1223,6 +1232,8 @@ mv_status mv_raycast_batch(mv_ctx *c, const mv_intrinsics *K, const double *T, i
     if (!T || n_views < 1 || n_views > 65535) return fail(c, MV_ERR_ARG, "bad view count");
     for (int k = 0; k < n_views; ++k)
         if (!valid_frame(K, T + 16 * (size_t)k)) return fail(c, MV_ERR_ARG, "bad view arguments");
+    if (!aligned_to({depth, normal, rgba, vertex, vol_id}, 4))
+        return fail(c, MV_ERR_ARG, "maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
@@ -1273,6 +1284,8 @@ mv_status mv_frame(mv_ctx *c, const float *depth, const uint8_t *rgb, const mv_i
 {
     if (!c) return MV_ERR_ARG;
     if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    if (!aligned_to({depth, depth_out, normal, rgba, vertex, vol_id}, 4))
+        return fail(c, MV_ERR_ARG, "depth and maps must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
@@ -1493,6 +1506,7 @@ mv_status mv_autotune(mv_ctx *c, const float *depth, const uint8_t *rgb, const m
 {
     if (!c || !out) return MV_ERR_ARG;
     if (!depth || !valid_frame(K, T)) return fail(c, MV_ERR_ARG, "bad frame arguments");
+    if (!aligned_to({depth}, 4)) return fail(c, MV_ERR_ARG, "depth must be 4-byte aligned");
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     mv_status st = begin_call(c, s);
@@ -1678,6 +1692,10 @@ static mv_status raycast_backward_impl(mv_ctx *c, const mv_intrinsics *K, const 
     if (n_poses < 1 || n_poses > 65535 || !depth || !vol_id || !grad_pose || (n_targets > 0 && !targets) ||
         n_targets < 0)
         return fail(c, MV_ERR_ARG, "bad backward arguments");
+    if (!aligned_to({depth, vol_id, grad_depth, grad_rgb, grad_pose}, 4))
+        return fail(c, MV_ERR_ARG, "backward buffers must be 4-byte aligned");
+    for (int i = 0; i < n_targets; ++i)
+        if (!aligned_to({targets[i].grad_tsdf}, 4)) return fail(c, MV_ERR_ARG, "gradient buffers must be 4-byte aligned");
     for (int i = 0; i < n_poses; ++i)
         if (!valid_frame(K, T + 16 * i)) return fail(c, MV_ERR_ARG, "bad view arguments");
     for (int i = 0; i < n_targets; ++i) {

@@ -82,3 +82,18 @@ def test_create_without_device_reports_cuda_error(lib):
     h = C.c_void_p()
     assert lib.mv_create(None, 0, C.byref(h)) == _abi.MV_ERR_CUDA
     assert not h.value
+
+
+def test_merge_calls_refuse_misaligned_buffers_before_any_launch(lib):
+    """mv_pack_hits and mv_merge_hits check their buffers' alignment on the
+    host before anything else: addresses off a 4-byte (maps) or 8-byte (keys)
+    boundary come back as MV_ERR_ARG, never dereferenced."""
+    word, odd, half = C.c_void_p(0x1000), C.c_void_p(0x1001), C.c_void_p(0x1004)
+    keys = C.c_void_p(0x2000)
+    assert lib.mv_pack_hits(odd, word, None, 0, 16, keys, None) == _abi.MV_ERR_ARG
+    assert lib.mv_pack_hits(word, odd, None, 0, 16, keys, None) == _abi.MV_ERR_ARG
+    assert lib.mv_pack_hits(word, word, None, 0, 16, half, None) == _abi.MV_ERR_ARG
+    assert lib.mv_merge_hits(half, keys, 16, None, None, None, None, None, None) == _abi.MV_ERR_ARG
+    assert lib.mv_merge_hits(keys, half, 16, None, None, None, None, None, None) == _abi.MV_ERR_ARG
+    assert lib.mv_merge_hits(keys, keys, 16, None, None, odd, None, None, None) == _abi.MV_ERR_ARG
+    assert lib.mv_merge_hits(keys, keys, 16, None, None, None, C.c_void_p(0x1002), None, None) == _abi.MV_ERR_ARG

@@ -123,3 +123,33 @@ def test_8192_voxel_long_volume_equals_small_volume(axis):
     scene = synth.Scene(planes=np.array([[0.0, 0.0, 1.0, plane_z]]))
     poses = _poses(centre, 4, 31 + axis)
     _check_against_small(big, small, scene, cam, poses, min_pixels=40 if axis == 2 else 100)
+
+
+def test_misaligned_buffers_are_refused_before_any_launch():
+    """Device buffers the kernels access as 4-byte words must start on a
+    4-byte boundary: the entry points return MV_ERR_ARG for a depth frame or
+    a map one or two bytes off, launch nothing, and the context keeps
+    working."""
+    import ctypes as C
+    import torch
+    from paper_1511_07106_b300 import _abi
+    from paper_1511_07106_b300.mapper import intrinsics
+    cam = synth.Camera(40.0, 40.0, 15.5, 11.5, 32, 24)
+    m = Mapper()
+    m.add_volume((-8, -8, 20), (16, 16, 16), 0.02)
+    K = intrinsics(cam)
+    T = np.ascontiguousarray(np.eye(4).reshape(16))
+    Tp = T.ctypes.data_as(C.POINTER(C.c_double))
+    buf = torch.zeros(4 * cam.width * cam.height + 16, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    assert m._lib.mv_integrate(m._h, C.c_void_p(base + 1), None, C.byref(K), Tp, None) == _abi.MV_ERR_ARG
+    assert m._lib.mv_raycast(m._h, C.byref(K), Tp, None, None, C.c_void_p(base + 2), None, None,
+                             None) == _abi.MV_ERR_ARG
+    assert m._lib.mv_depth_to_maps(m._h, C.c_void_p(base + 2), C.byref(K), None, C.c_void_p(base),
+                                   C.c_void_p(base), None) == _abi.MV_ERR_ARG
+    depth = torch.full((cam.height, cam.width), 0.5, dtype=torch.float32, device="cuda")
+    rgb = torch.zeros((cam.height, cam.width, 3), dtype=torch.uint8, device="cuda")
+    m.integrate(depth, rgb, cam, np.eye(4))
+    maps = m.raycast(cam, np.eye(4))
+    assert maps["depth"].shape == (cam.height, cam.width)
+    m.close()
