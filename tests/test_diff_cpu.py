@@ -90,3 +90,18 @@ def test_so3_exp_equals_matrix_exponential():
     got = diff.so3_exp(phi)
     want = torch.matrix_exp(diff.hat_so3(torch.from_numpy(phi))).numpy()
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_float_colours_give_back_their_bytes_and_byte_order():
+    """The fused L1 path (mv_raycast_backward_l1) takes colours as the forward's
+    bytes while the closed form (l1_loss_grad) takes them as byte / 255 in
+    float32: every byte comes back from its float by round(c * 255), and the
+    sign of a float difference is the sign of the byte difference for all
+    65536 pairs, so both give each pixel the same colour gradient."""
+    import torch
+    b = torch.arange(256, dtype=torch.uint8)
+    c = b.float() / 255.0
+    assert torch.equal(torch.round(c * 255.0).to(torch.uint8), b)
+    a_f, b_f = c[:, None], c[None, :]
+    a_i, b_i = b.to(torch.int32)[:, None], b.to(torch.int32)[None, :]
+    assert torch.equal(torch.sign(a_f - b_f), torch.sign(a_i - b_i).float())
